@@ -1,0 +1,175 @@
+/*
+ * rd.h -- C ABI of the GB300 ridge-directed ring detector.
+ *
+ * The detector is the method of Afik, "Robust and highly performant ring
+ * detection algorithm for 3d particle tracking using 2d microscope imaging"
+ * (Sci. Rep. 5, 13584, 2015):
+ *   frame -> Gaussian smoothing -> 5x5 second-order Sobel Hessian
+ *   (Methods, "Algorithm implementation"; Detailed algorithm, step 1)
+ *   -> least principal curvature k- and its direction X- (Results,
+ *   "Directed ridge detection & votes collection")
+ *   -> directed-ridge mask: k- < tau and k- a local minimum along X-
+ *   (Detailed algorithm, step 2)
+ *   -> ridge-directed circle Hough voting, (x, y) +/- r X- for every r in
+ *   [r_min - 1, r_max + 1] (Results; Additional notes)
+ *   -> integer hotspot threshold, radius-dependent Gaussian smoothing with
+ *   sigma(r) = sig_a r + sig_b and 1/r normalisation (Results, "Local maxima
+ *   detection in a noisy parameter space"; Methods; Detailed algorithm,
+ *   step 4)
+ *   -> float threshold peak_frac * 2 pi and 3x3x3 local maxima with r in
+ *   [r_min, r_max] (Detailed algorithm, step 4; Additional notes)
+ *   -> annulus classification of ridge pixels and a circle fit per peak
+ *   (Results, "Ridge points classification & sub-pixel accuracy"; Detailed
+ *   algorithm, step 5).
+ *
+ * Every stage runs as hand-written sm_103a CUDA kernels on one GPU.  Pointers
+ * marked _dev are device pointers; all work is enqueued on the caller's
+ * stream (a cudaStream_t passed as void*, NULL = legacy default stream) and
+ * is asynchronous: outputs are valid once that stream has synchronised.
+ * Functions return rd_status codes; they never abort, throw or trap.
+ * A context is not thread-safe: one host thread (or external locking) per
+ * context.  Distinct contexts are independent.
+ */
+#ifndef RD_H
+#define RD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RD_ABI_VERSION 1
+
+/* Pixel type of the frames.  Integer frames are smoothed with exact integer
+ * arithmetic (quantised Gaussian taps), which makes the Hessian exact. */
+typedef enum { RD_U8 = 0, RD_U16 = 1 } rd_dtype;
+
+typedef enum {
+  RD_OK = 0,
+  RD_E_INVAL = 1,     /* bad argument: the call did nothing                      */
+  RD_E_NOMEM = 2,     /* device allocation failed at rd_create                   */
+  RD_E_CUDA = 3,      /* a CUDA runtime call failed; see rd_last_error           */
+  RD_E_OVERFLOW = 4,  /* a capacity was exceeded; counts are true, lists truncated */
+  RD_E_TIMEOUT = 5,   /* a bounded device wait gave up                           */
+  RD_E_BUSY = 6       /* the context is in use by an unfinished call             */
+} rd_status;
+
+/* Method parameters (the C struct holds floats; the detector widens them to
+ * double wherever it computes in double). */
+typedef struct rd_params {
+  float sigma;        /* Gaussian smoothing scale in px, (0, 4]; taps |i| <= ceil(4 sigma)
+                         (Results, scale selection)                              */
+  int   r_min, r_max; /* radius search range in px, 2 <= r_min <= r_max <= 250;
+                         votes cover r_min-1 .. r_max+1 (Additional notes)       */
+  float ridge_thresh; /* curvature threshold tau <= 0 on k- in intensity/px^2
+                         (Detailed algorithm, step 2)                            */
+  float peak_frac;    /* float threshold: a peak needs S > peak_frac * 2 pi, >= 0
+                         (Detailed algorithm, step 4)                            */
+  int   vote_thresh;  /* integer hotspot threshold: a voxel is a hotspot when its
+                         vote count exceeds this value, >= 0 (step 4)            */
+  float annulus_w;    /* annulus half-width in px, >= 0: ridge pixels with
+                         | |p - c| - r | <= annulus_w are fitted (step 5)       */
+  float sig_a, sig_b; /* level smoothing sigma(r) = sig_a r + sig_b, > 0 for all
+                         levels (Methods: 0.05, 0.25)                            */
+} rd_params;
+
+/* One detected ring.  (ix, iy, ir) is the integer peak of the smoothed,
+ * normalised circle parameter space; (cx, cy, r) the sub-pixel circle fitted
+ * to the ridge pixels of its annulus.  x is the column, y the row. */
+typedef struct rd_ring {
+  int   frame;        /* index of the frame in the rd_detect batch                */
+  float cx, cy, r;    /* fitted centre and radius (px)                            */
+  int   ix, iy, ir;   /* integer peak                                             */
+  float score;        /* S = smoothed votes / r at the peak (ideal ring ~ 2 pi)   */
+  int   n_fit;        /* ridge pixels in the annulus                              */
+  int   flags;        /* RD_RING_FIT_FAIL: fewer than 5 points or singular fit;
+                         (cx, cy, r) then equal (ix, iy, ir)                      */
+} rd_ring;
+
+#define RD_RING_FIT_FAIL 1
+
+/* Device-side status of the last rd_detect, read back by rd_get_stats. */
+typedef struct rd_stats {
+  int64_t ridge_pixels;     /* directed ridge pixels over the batch               */
+  int64_t votes;            /* votes inside the image over all levels             */
+  int64_t peaks;            /* integer peaks (true count, before any truncation)  */
+  int64_t exact_fallbacks;  /* decisions re-taken in double precision             */
+  int32_t overflow;         /* bit mask of RD_OVF_* capacities that overflowed    */
+  int32_t n_frames;
+} rd_stats;
+
+#define RD_OVF_RIDGE 1      /* ridge list of a frame full                         */
+#define RD_OVF_BINS  2      /* vote bin pool full                                 */
+#define RD_OVF_PEAKS 4      /* peak list of a frame full                          */
+#define RD_OVF_RINGS 8      /* caller's ring buffer too small                     */
+#define RD_OVF_SCORE 16     /* a smoothed vote sum exceeded 32 bits               */
+
+typedef struct rd_ctx rd_ctx;
+
+/* Create a detector.  Validates *params, builds the weight tables (Gaussian
+ * taps, per-level smoothing weights, per-level peak thresholds) and allocates
+ * every device workspace for frames up to max_H x max_W (12 <= size <= 65535)
+ * and batches up to max_batch frames.  *out receives the context, or NULL on
+ * failure.  Errors: RD_E_INVAL (bad params or sizes), RD_E_NOMEM, RD_E_CUDA. */
+rd_status rd_create(const rd_params* params, int max_H, int max_W, int max_batch, rd_ctx** out);
+
+/* Detect rings in n frames.
+ *   frames_dev : n frames of H x W pixels of type dtype, row-major, frame i at
+ *                frames_dev + i*H*W*sizeof(pixel); read only; caller-owned.
+ *   rings_dev  : caller-owned array of ring_cap rd_ring; frame i's rings are
+ *                rings_dev[offsets_dev[i] .. offsets_dev[i] + counts_dev[i]),
+ *                sorted by (ir, iy, ix).  Rings past ring_cap are dropped and
+ *                RD_OVF_RINGS is raised.
+ *   counts_dev, offsets_dev : caller-owned int[n]; true ring count per frame
+ *                and the exclusive prefix sum of the counts.
+ * Enqueues every kernel on stream and returns without waiting.  Errors:
+ * RD_E_INVAL (sizes above the rd_create maxima, bad dtype, NULL pointers;
+ * nothing is enqueued), RD_E_CUDA (a launch failed).  Capacity overflows are
+ * reported after the stream syncs, by rd_get_stats. */
+rd_status rd_detect(rd_ctx* ctx, const void* frames_dev, int n, int H, int W, int dtype,
+                    void* stream, rd_ring* rings_dev, int ring_cap,
+                    int* counts_dev, int* offsets_dev);
+
+/* Synchronise the stream of the last rd_detect on ctx and copy its device
+ * counters to *out.  Returns RD_E_OVERFLOW when any RD_OVF_* bit is set. */
+rd_status rd_get_stats(rd_ctx* ctx, rd_stats* out);
+
+rd_status rd_destroy(rd_ctx* ctx);
+
+/* Last error message of ctx (or of the last failed rd_create when ctx is
+ * NULL).  The string lives until the next call on the same context. */
+const char* rd_last_error(const rd_ctx* ctx);
+
+/* ---- host-only helpers (no GPU work): the exact weight tables -------------
+ * rd_gaussian_taps writes the integer Gaussian taps Q_i = floor(2^14 g_i + 1/2),
+ * |i| <= ceil(4 sigma), of the smoothing step and returns their count (or -1
+ * if cap is too small).  rd_level_weights writes the (2R+1)^2 integer level
+ * smoothing weights floor(2^16 exp(-(dx^2+dy^2) / (2 sigma(r)^2)) + 1/2),
+ * R = ceil(3 sigma(r)), row-major over (dy, dx), and returns their count (or
+ * -1).  rd_peak_threshold returns the smallest smoothed vote sum N that
+ * passes the float threshold at level r: N > ((peak_frac 2 pi) 2^16) r. */
+int     rd_gaussian_taps(float sigma, int32_t* taps, int cap);
+int     rd_level_weights(float sig_a, float sig_b, int r, int32_t* w, int cap);
+int64_t rd_peak_threshold(float peak_frac, int r);
+
+/* ---- diagnostics (test and profiling use) ---------------------------------
+ * rd_debug_ridges copies frame f's ridge pixels of the last rd_detect (after
+ * the stream syncs) to host arrays of capacity cap: xy[2i], xy[2i+1] = x, y;
+ * dir[2i], dir[2i+1] = X-, Y- (float, canonical sign); hess[3i..3i+2] = the
+ * exact integer Hessian (Hxx', Hyy', Hxy') = 64 S^2 (Lxx, Lyy, Lxy).  Any
+ * pointer may be NULL.  Returns the number of ridge pixels of frame f (which
+ * may exceed cap), or -1 on error.  Order: by stencil tile, row-major inside
+ * each tile.
+ * rd_debug_capture makes the next rd_detect write frame 0's raw accumulator
+ * (acc_dev, int32) and smoothed accumulator (sm_dev, uint32) for every voting
+ * level r_min-1 .. r_max+1 as [level][H][W] device arrays (either may be
+ * NULL; NULL for both turns capture off). */
+int       rd_debug_ridges(rd_ctx* ctx, int f, int32_t* xy, float* dir, int64_t* hess, int cap);
+rd_status rd_debug_capture(rd_ctx* ctx, int32_t* acc_dev, uint32_t* sm_dev);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RD_H */

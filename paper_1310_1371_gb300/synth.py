@@ -1,0 +1,167 @@
+"""Seeded synthetic microscope frames shaped like the paper's ring video.
+
+This module only draws random ring geometry and renders intensity images.
+It holds none of the detector's arithmetic, so both the GPU path and the
+CPU oracle can be fed from it without sharing any of the method.
+
+Workloads (sizes and distributions follow the paper's experiment: frames of
+out-of-focus tracer images with tens to hundreds of rings, overlapping and
+nested, the outermost ring thicker than the inner fringes; Results section,
+"Robustness assessment" and "Performance assessment"):
+
+* ``plain_small``  256x256 u8, 8 non-overlapping rings, r in [8, 30].
+* ``plain_full``   1024x1024 u16 (12-bit), 150 overlapping rings, r in
+  [10, 80], each with 2-3 inner fringes, Poisson shot + Gaussian read noise.
+* ``video``        1024x1024 u8 frames; 20-300 rings per frame drawn from a
+  pool of drifting tracks (centre step N(0, 1.5^2), radius step U[-0.3, 0.3]).
+* ``diff_frames``  512x512 f32 frames, 64 rings, r in [10, 50], sub-pixel
+  centres and radii, no rounding or clipping.
+* ``requests``     a Poisson arrival stream of frames of mixed sizes.
+
+Seeds: workload k uses ``numpy.random.default_rng(1000 + k)``; frame i of a
+multi-frame workload uses ``default_rng([1000 + k, i])``.
+"""
+from __future__ import annotations
+
+import dataclasses
+import numpy as np
+
+# Detector settings used with each workload (the method's parameters; the
+# values are the ones the workloads were specified with).
+PLAIN_SMALL_PARAMS = dict(sigma=2.0, r_min=5, r_max=40, ridge_thresh=-1.0,
+                          peak_frac=0.35, vote_thresh=3, annulus_w=2.0,
+                          sig_a=0.05, sig_b=0.25)
+PLAIN_FULL_PARAMS = dict(sigma=2.0, r_min=8, r_max=96, ridge_thresh=-2.0,
+                         peak_frac=0.35, vote_thresh=3, annulus_w=2.0,
+                         sig_a=0.05, sig_b=0.25)
+VIDEO_PARAMS = dict(PLAIN_SMALL_PARAMS)
+DIFF_PARAMS = dict(sigma=2.0, r_min=8, r_max=56, ridge_thresh=-1.0,
+                   peak_frac=0.35, vote_thresh=3, annulus_w=2.0,
+                   sig_a=0.05, sig_b=0.25)
+
+
+@dataclasses.dataclass
+class Frame:
+    image: np.ndarray          # [H, W], u8 / u16 / f32
+    rings: np.ndarray          # [n, 3] float64: cx, cy, R  (x = column, y = row)
+    params: dict
+
+
+def _render(H, W, rings, profile, background):
+    """Sum ring profiles (functions of rho - R) on a flat background."""
+    img = np.full((H, W), float(background))
+    for cx, cy, R in rings:
+        ext = R + 12.0
+        x0, x1 = max(0, int(np.floor(cx - ext))), min(W, int(np.ceil(cx + ext)) + 1)
+        y0, y1 = max(0, int(np.floor(cy - ext))), min(H, int(np.ceil(cy + ext)) + 1)
+        if x0 >= x1 or y0 >= y1:
+            continue
+        yy, xx = np.mgrid[y0:y1, x0:x1]
+        rho = np.hypot(xx - cx, yy - cy)
+        img[y0:y1, x0:x1] += profile(rho, R)
+    return img
+
+
+def _gauss_ring(amp, width):
+    return lambda rho, R: amp * np.exp(-0.5 * ((rho - R) / width) ** 2)
+
+
+def _fringed_ring(amp, width, n_fringes):
+    """Main Gaussian ring plus inner fringes: a non-negative cosine of period
+    4 px in radius, halving per fringe (fringe k peaks at R - 4k)."""
+    def prof(rho, R):
+        main = amp * np.exp(-0.5 * ((rho - R) / width) ** 2)
+        d = R - rho
+        k = np.floor((d + 2.0) / 4.0)
+        inside = (d > 2.0) & (d <= 4.0 * n_fringes + 1.0) & (k >= 1)
+        fr = amp * np.power(0.5, np.maximum(k, 1)) * np.maximum(0.0, np.cos(2 * np.pi * d / 4.0))
+        return main + np.where(inside, fr, 0.0)
+    return prof
+
+
+def _nonoverlap(rng, n, lo, hi, rlo, rhi, gap, tries=10000):
+    out = []
+    t = 0
+    while len(out) < n:
+        t += 1
+        if t > tries:
+            raise RuntimeError("could not place non-overlapping rings")
+        c = rng.uniform(lo, hi, size=2)
+        R = rng.uniform(rlo, rhi)
+        if all(np.hypot(c[0] - q[0], c[1] - q[1]) > R + q[2] + gap for q in out):
+            out.append((c[0], c[1], R))
+    return np.array(out, dtype=np.float64)
+
+
+def plain_small(seed: int = 1001, H: int = 256, W: int = 256, n_rings: int = 8) -> Frame:
+    """One 256x256 u8 frame: 8 non-overlapping rings, centres in a 40 px
+    inner margin, R ~ U[8, 30], cross-section sigma 1.5, amplitude 120 on a
+    background of 40, additive N(0, 8^2) noise, rounded and clipped."""
+    rng = np.random.default_rng(seed)
+    rings = _nonoverlap(rng, n_rings, 40.0, min(H, W) - 40.0, 8.0, 30.0, 6.0)
+    img = _render(H, W, rings, _gauss_ring(120.0, 1.5), 40.0)
+    img += rng.normal(0.0, 8.0, size=img.shape)
+    img = np.clip(np.rint(img), 0, 255).astype(np.uint8)
+    return Frame(img, rings, dict(PLAIN_SMALL_PARAMS))
+
+
+def plain_full(seed=1002, H: int = 1024, W: int = 1024, n_rings: int = 150) -> Frame:
+    """One 1024x1024 u16 frame with 12-bit values: 150 rings (overlaps
+    allowed), R ~ U[10, 80], main ring amplitude 600 (sigma 1.5) plus 2-3
+    inner fringes; background 400, Poisson shot noise and N(0, 10^2) read
+    noise, rounded and clipped to [0, 4095]."""
+    rng = np.random.default_rng(seed)
+    cx = rng.uniform(0.0, W, size=n_rings)
+    cy = rng.uniform(0.0, H, size=n_rings)
+    R = rng.uniform(10.0, 80.0, size=n_rings)
+    K = rng.integers(2, 4, size=n_rings)
+    rings = np.stack([cx, cy, R], axis=1)
+    img = np.full((H, W), 400.0)
+    for i in range(n_rings):
+        img += _render(H, W, rings[i:i + 1], _fringed_ring(600.0, 1.5, int(K[i])), 0.0)
+    img = rng.poisson(img).astype(np.float64) + rng.normal(0.0, 10.0, size=img.shape)
+    img = np.clip(np.rint(img), 0, 4095).astype(np.uint16)
+    return Frame(img, rings, dict(PLAIN_FULL_PARAMS))
+
+
+def plain_full_batch(n: int, seed0: int = 1002, **kw) -> list[Frame]:
+    """n independent full-size frames; frame i is seeded with [seed0, i]."""
+    return [plain_full(seed=[seed0, i], **kw) for i in range(n)]
+
+
+def video(n_frames: int, seed: int = 1003, H: int = 1024, W: int = 1024,
+          pool: int = 300, n_min: int = 20, n_max: int = 300) -> list[Frame]:
+    """A drifting-track video of u8 frames rendered like ``plain_small``.
+    Frame i shows the first n_i ~ U{n_min..n_max} tracks of the pool."""
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(40.0, np.array([W - 40.0, H - 40.0]), size=(pool, 2))
+    R = rng.uniform(8.0, 30.0, size=pool)
+    frames = []
+    for i in range(n_frames):
+        fr = np.random.default_rng([seed, i])
+        n = int(fr.integers(n_min, n_max + 1))
+        rings = np.concatenate([c[:n], R[:n, None]], axis=1)
+        img = _render(H, W, rings, _gauss_ring(120.0, 1.5), 40.0)
+        img += fr.normal(0.0, 8.0, size=img.shape)
+        img = np.clip(np.rint(img), 0, 255).astype(np.uint8)
+        frames.append(Frame(img, rings.copy(), dict(VIDEO_PARAMS)))
+        c = c + rng.normal(0.0, 1.5, size=c.shape)
+        c[:, 0] = np.clip(c[:, 0], 0.0, W - 1.0)
+        c[:, 1] = np.clip(c[:, 1], 0.0, H - 1.0)
+        R = np.clip(R + rng.uniform(-0.3, 0.3, size=R.shape), 8.0, 30.0)
+    return frames
+
+
+def diff_frames(n: int, seed: int = 1004, H: int = 512, W: int = 512, n_rings: int = 64) -> list[Frame]:
+    """f32 frames with sub-pixel centres and radii, no rounding or clipping."""
+    frames = []
+    for i in range(n):
+        rng = np.random.default_rng([seed, i])
+        cx = rng.uniform(40.0, W - 40.0, size=n_rings)
+        cy = rng.uniform(40.0, H - 40.0, size=n_rings)
+        R = rng.uniform(10.0, 50.0, size=n_rings)
+        rings = np.stack([cx, cy, R], axis=1)
+        img = _render(H, W, rings, _gauss_ring(120.0, 1.5), 40.0)
+        img += rng.normal(0.0, 8.0, size=img.shape)
+        frames.append(Frame(img.astype(np.float32), rings, dict(DIFF_PARAMS)))
+    return frames
