@@ -1,0 +1,290 @@
+#!/usr/bin/env python3
+"""Throughput of the ring detector on one or more GPUs (one process per GPU).
+
+Workload: batches of synthetic 1024x1024 uint16 microscope frames (12-bit,
+150 overlapping rings with inner fringes, Poisson + read noise), detector
+radius range 8-96 px, sigma 2.  One step = one rd_detect call over a batch of
+B distinct frames resident in HBM (B = 96: 192 MiB of input, larger than L2,
+so no flush is needed between steps).  Multi-GPU runs are independent
+replicas (each rank its own frames; no data exchange).
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "frames/s at 1024x1024 u16, r 8-96 (ridge-directed ring detection)"
+WORKLOAD = "plain_full: 1024x1024 u16 frames, 150 rings r 10-80 with fringes, search r 8-96, sigma 2"
+H = W = 1024
+KERNELS_PER_CALL = 11   # stencil, refine, bin count, 3 scan, bin fill, vote, sort, offsets, fit
+STAGES = ["stencil_ridge", "ridge_refine", "vote_bin", "vote_accumulate_peaks", "sort_fit"]
+
+
+def env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def _one_frame(seed):
+    from paper_1310_1371_gb300 import synth
+    return synth.plain_full(seed=seed).image
+
+
+def make_frames(n, rank):
+    """n distinct seeded frames (seeds [1002 + 1000 rank, i]), rendered in a
+    spawn-started process pool before any CUDA call."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    seeds = [[1002 + 1000 * rank, i] for i in range(n)]
+    workers = max(1, min(16, (os.cpu_count() or 2) - 1))
+    with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_one_frame, seeds))
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = os.path.join(tempfile.gettempdir(), f"rd_clocks_{os.getpid()}.csv")
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(gpu_index)], stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        out.update(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=reasons, samples=len(rows))
+        return out
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_rate(frames, params, budget_s):
+    """Frames/s and Mvotes/s of the FP64 oracle, single process, on as many
+    frames as fit in budget_s (at least one)."""
+    from oracle import ringdet as O
+    p = O.Params.make(**params)
+    t0 = time.perf_counter()
+    done, votes = 0, 0
+    for img in frames:
+        res = O.detect(img, p)
+        done += 1
+        votes += res.votes_in
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return done / dt, votes / dt / 1e6, done, dt
+
+
+def run_reference(args):
+    rank, _, world = env_rank()
+    if rank != 0:
+        return
+    from paper_1310_1371_gb300 import synth
+    frames = [f.image for f in synth.plain_full_batch(2)]
+    params = synth.PLAIN_FULL_PARAMS
+    from oracle import ringdet as O
+    p = O.Params.make(**params)
+    for _ in range(args.warmup):
+        O.detect(frames[0], p)
+    t0 = time.perf_counter()
+    votes = 0
+    for k in range(args.steps):
+        votes += O.detect(frames[k % len(frames)], p).votes_in
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "step": "one frame through the FP64 CPU oracle"},
+            "mvotes_per_s": votes / dt / 1e6,
+            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} frames of the workload, one per step"},
+            "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU
+def run_ours(args):
+    import torch
+    rank, local_rank, world = env_rank()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    from paper_1310_1371_gb300 import rd, synth
+
+    B = args.batch
+    params = synth.PLAIN_FULL_PARAMS
+    imgs = np.stack(make_frames(B, rank))
+    frames = torch.from_numpy(imgs).cuda()
+    det = rd.Detector(params, H, W, B)
+    stream = torch.cuda.current_stream()
+
+    # warm-up (also the parity smoke of this launch: overflow must not occur)
+    for _ in range(args.warmup):
+        det.detect_async(frames)
+    st0 = det.stats()
+    if st0.overflow:
+        raise RuntimeError(f"capacity overflow in the benchmark workload: {st0.overflow}")
+
+    # ---- device-resident throughput
+    det.set_timing(True)
+    stage_ms = np.zeros(len(STAGES))
+    sampler = ClockSampler(local_rank) if rank == 0 else None
+    time.sleep(0.3 if sampler else 0)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        det.detect_async(frames)
+        stage_ms += det.timing()          # waits for this step's last stage event
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    ms = ev0.elapsed_time(ev1)
+    stats = det.stats()
+    det.set_timing(False)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    value = B * args.steps * world / (ms / 1e3)
+    votes_per_step = stats.votes
+
+    # ---- end to end through rd_detect_host (pinned host frames, host rings)
+    pinned = torch.from_numpy(imgs).pin_memory()
+    host = pinned.numpy()
+    det.detect_host(host)
+    torch.cuda.synchronize()
+    e2e_steps = max(3, args.steps // 4)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(e2e_steps):
+        rings, counts, offs, stt = det.detect_host(host)
+        d2h = 8 * B + 40 * int(counts.sum())
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = B * e2e_steps * world / e2e_s
+
+    if rank == 0:
+        # ---- roofline of the dominant stage
+        per_launch = stage_ms / args.steps
+        dom = int(np.argmax(per_launch))
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        ridge_per_step = stats.ridge_pixels
+        # algorithmic bytes per launch of each stage ("Kernels and their rooflines")
+        alg_bytes = {
+            0: B * H * W * 2 + ridge_per_step * (4 + 24),                  # frames read, ridge records written
+            1: ridge_per_step * (24 + 16 + 8),                             # Hessians read, directions written
+            2: ridge_per_step * (4 + 16) * 2,                              # two passes over records
+            3: ridge_per_step * (4 + 16 + 8) + stats.peaks * 16,           # records read once, peaks written
+            4: stats.peaks * (16 + 40) + ridge_per_step * 4,               # peaks, rings, annulus records
+        }
+        achieved = alg_bytes[dom] / (per_launch[dom] / 1e3) / 1e9
+        traffic = None
+        tfile = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(tfile):
+            traffic = json.load(open(tfile)).get(STAGES[dom])
+        # ---- CPU baseline (oracle, bounded sample)
+        cpu_fps, cpu_mv, ndone, cpu_dt = oracle_rate(imgs[: max(1, args.cpu_frames)], params, args.cpu_budget)
+        line = {
+            "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "batch_frames": B, "frames_bytes": int(imgs.nbytes),
+                       "l2": "inputs (192 MiB) larger than L2; no flush", "parallelism": f"replicas x{world}"},
+            "mvotes_per_s": votes_per_step * args.steps * world / (ms / 1e3) / 1e6,
+            "votes_per_frame": votes_per_step / B, "ridge_pixels_per_frame": ridge_per_step / B,
+            "rings_per_frame": stats.peaks / B, "exact_fallbacks_per_frame": stats.exact_fallbacks / B,
+            "stage_ms_per_step": {s: round(float(v), 4) for s, v in zip(STAGES, per_launch)},
+            "roofline": {"kernel": STAGES[dom], "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": traffic,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
+            "cpu_baseline": {"value": cpu_fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{ndone} frames of the workload in {cpu_dt:.1f} s",
+                             "mvotes_per_s": cpu_mv},
+            "e2e": {"value": e2e_value, "unit": "frames/s", "h2d_bytes_per_step": int(imgs.nbytes),
+                    "d2h_bytes_per_step": int(d2h), "api": "rd_detect_host", "steps": e2e_steps},
+            "gpu_launches": KERNELS_PER_CALL * args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    det.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=96)
+    ap.add_argument("--cpu-frames", type=int, default=4)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

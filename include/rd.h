@@ -131,6 +131,17 @@ rd_status rd_detect(rd_ctx* ctx, const void* frames_dev, int n, int H, int W, in
                     void* stream, rd_ring* rings_dev, int ring_cap,
                     int* counts_dev, int* offsets_dev);
 
+/* rd_detect on HOST buffers: copies the n frames from frames_host (pinned
+ * memory makes the copy asynchronous) into the context's device staging
+ * buffer, runs rd_detect, copies counts, offsets and the rings back to the
+ * host arrays (ring_cap rings, n counts, n offsets) and waits for the stream.
+ * Returns like rd_get_stats (RD_E_OVERFLOW when a capacity overflowed; the
+ * rings that fit are valid).  Staging buffers are sized at rd_create:
+ * ring_cap may not exceed max_batch * 4096. */
+rd_status rd_detect_host(rd_ctx* ctx, const void* frames_host, int n, int H, int W, int dtype,
+                         void* stream, rd_ring* rings_host, int ring_cap,
+                         int* counts_host, int* offsets_host);
+
 /* Synchronise the stream of the last rd_detect on ctx and copy its device
  * counters to *out.  Returns RD_E_OVERFLOW when any RD_OVF_* bit is set. */
 rd_status rd_get_stats(rd_ctx* ctx, rd_stats* out);
@@ -152,6 +163,17 @@ const char* rd_last_error(const rd_ctx* ctx);
 int     rd_gaussian_taps(float sigma, int32_t* taps, int cap);
 int     rd_level_weights(float sig_a, float sig_b, int r, int32_t* w, int cap);
 int64_t rd_peak_threshold(float peak_frac, int r);
+
+/* ---- stage timing ----------------------------------------------------------
+ * rd_set_timing(ctx, 1) makes every following rd_detect record CUDA events on
+ * its stream around its stages; rd_get_timing waits for the last call and
+ * writes the stage durations in milliseconds to ms[0 .. RD_N_STAGES-1]:
+ * stencil + ridge mask, direction refinement, vote binning, voting + peak
+ * epilogue, sort + circle fit.  Returns the number of stages written, or -1
+ * (timing off, or no call yet). */
+#define RD_N_STAGES 5
+rd_status rd_set_timing(rd_ctx* ctx, int on);
+int       rd_get_timing(rd_ctx* ctx, float* ms, int cap);
 
 /* ---- diagnostics (test and profiling use) ---------------------------------
  * rd_debug_ridges copies frame f's ridge pixels of the last rd_detect (after

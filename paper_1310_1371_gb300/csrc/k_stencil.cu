@@ -1,0 +1,382 @@
+// k_stencil.cu -- K1: fused Gaussian smoothing, second-order Sobel Hessian,
+// principal curvature k- and direction X-, and the directed-ridge mask, in
+// one pass over the frame; K2: double-float refinement of X- per ridge pixel.
+//
+// Method: Methods ("Algorithm implementation": Gaussian convolution, then the
+// 5x5 second-order Sobel operator); Results ("Directed ridge detection &
+// votes collection": k- < 0 and a local minimum along X-); Detailed algorithm,
+// steps 1-2 (k- below a curvature threshold tau <= 0, X- computed for those
+// pixels, local-minimum test along X-, ridge coordinates recorded).
+#include "rd_internal.cuh"
+#include <climits>
+
+namespace rd {
+
+
+// reflect-101 index (valid outputs only ever need one reflection; far
+// indices, used only by discarded outputs of partial tiles, are clamped)
+__device__ __forceinline__ int reflect101(int i, int n) {
+  i = i < 0 ? -i : i;
+  i = i >= n ? 2 * (n - 1) - i : i;
+  return min(max(i, 0), n - 1);
+}
+
+constexpr float U32 = 5.9604645e-8f;  // 2^-24
+
+// FP32 k- with a bound on |k32 - k_def| (k_def: the double-precision value).
+// Inputs a, b, c carry <= 2u relative error (conversion and scaling).
+__device__ __forceinline__ void eig32_k(float a, float b, float c, float& k, float& ek, float& hdf, float& rad) {
+  float htr = (a + c) * 0.5f;
+  hdf = (a - c) * 0.5f;
+  rad = sqrtf(hdf * hdf + b * b);
+  k = htr - rad;
+  float M = fabsf(a) + fabsf(b) + fabsf(c);
+  ek = M * (16.0f * U32) + 1e-30f;
+}
+
+// Stable FP32 X- (no cancellation: the large component is |hdf| + rad) with a
+// bound eX on each component's distance to the exact direction (same sign).
+// exact_axis: the Hessian's off-diagonal is exactly 0, so X- is exactly an
+// axis in every precision and eX = 0.
+__device__ __forceinline__ bool eig32_dir(float b, float hdf, float rad, float M, bool exact_axis, float& X,
+                                          float& Y, float& eX) {
+  float w = fabsf(hdf) + rad;
+  float vx, vy;
+  if (hdf >= 0.0f) {
+    vx = b;
+    vy = -w;
+  } else {
+    vx = -w;
+    vy = b;
+  }
+  float nrm = sqrtf(vx * vx + vy * vy);
+  if (!(nrm > 0.0f)) return false;
+  X = vx / nrm;
+  Y = vy / nrm;
+  if (X < 0.0f || (X == 0.0f && Y < 0.0f)) {
+    X = -X;
+    Y = -Y;
+  }
+  eX = exact_axis ? 0.0f : (M * (16.0f * U32)) / nrm + 4.0f * U32;
+  return true;
+}
+
+// Exact (double-precision definition) ridge test of the pixel at Hessian
+// tile coordinates (hy, hx) = image (gy, gx).  Reads exact Hessians of the
+// pixel and of the bilinear corners from shared memory.
+__device__ bool ridge_exact(const long long* sHxx, const long long* sHyy, const long long* sHxy, int stride, int hy,
+                            int hx, int gx, int gy, int H, int W, double D, double tau) {
+  int c = hy * stride + hx;
+  Eig64 e = eigen64(sHxx[c], sHyy[c], sHxy[c], D);
+  if (!(e.k < tau) || e.degenerate) return false;
+  for (int s = 0; s < 2; ++s) {
+    double qx = s == 0 ? d_add((double)gx, e.X) : d_sub((double)gx, e.X);
+    double qy = s == 0 ? d_add((double)gy, e.Y) : d_sub((double)gy, e.Y);
+    if (qx < 0.0 || qx > (double)(W - 1) || qy < 0.0 || qy > (double)(H - 1)) return false;
+    double x0f = floor(qx), y0f = floor(qy);
+    double fx = d_sub(qx, x0f), fy = d_sub(qy, y0f);
+    int cx0 = (int)x0f, cy0 = (int)y0f;
+    int cx1 = min(cx0 + 1, W - 1), cy1 = min(cy0 + 1, H - 1);
+    if (fx == 0.0) cx1 = cx0;  // zero-weight corner: any finite value gives the same sum
+    if (fy == 0.0) cy1 = cy0;
+    int lx0 = hx + (cx0 - gx), lx1 = hx + (cx1 - gx), ly0 = hy + (cy0 - gy), ly1 = hy + (cy1 - gy);
+    int i00 = ly0 * stride + lx0, i01 = ly0 * stride + lx1, i10 = ly1 * stride + lx0, i11 = ly1 * stride + lx1;
+    double k00 = eigen64(sHxx[i00], sHyy[i00], sHxy[i00], D).k;
+    double k01 = eigen64(sHxx[i01], sHyy[i01], sHxy[i01], D).k;
+    double k10 = eigen64(sHxx[i10], sHyy[i10], sHxy[i10], D).k;
+    double k11 = eigen64(sHxx[i11], sHyy[i11], sHxy[i11], D).k;
+    double kt = bilinear64(fx, fy, k00, k01, k10, k11);
+    if (s == 0 ? !(e.k < kt) : !(e.k <= kt)) return false;
+  }
+  return true;
+}
+
+// 0 = certainly not a ridge, 1 = certainly a ridge, 2 = undecided in FP32
+__device__ __forceinline__ int ridge_fast(const float* sK, const float* sE, int stride, int hy, int hx, int gx, int gy,
+                                          int H, int W, float k, float ek, float tau, float X, float Y, float eX) {
+  int verdict = 1;
+  for (int s = 0; s < 2; ++s) {
+    float ox = s == 0 ? X : -X, oy = s == 0 ? Y : -Y;
+    float lowx = (float)(-gx), highx = (float)(W - 1 - gx);
+    float lowy = (float)(-gy), highy = (float)(H - 1 - gy);
+    if (ox < lowx - eX || ox > highx + eX || oy < lowy - eX || oy > highy + eX) return 0;
+    if (eX > 0.0f) {
+      if (ox <= lowx + eX || ox >= highx - eX || oy <= lowy + eX || oy >= highy - eX) return 2;
+      // a sample within eX of a cell edge may lie in the neighbouring cell
+      if (fabsf(ox - rintf(ox)) <= eX || fabsf(oy - rintf(oy)) <= eX) return 2;
+    }
+    float flx = floorf(ox), fly = floorf(oy);
+    float fx = ox - flx, fy = oy - fly;
+    int cx0 = gx + (int)flx, cy0 = gy + (int)fly;
+    int cx1 = fx == 0.0f ? cx0 : min(cx0 + 1, W - 1);
+    int cy1 = fy == 0.0f ? cy0 : min(cy0 + 1, H - 1);
+    int lx0 = hx + (cx0 - gx), lx1 = hx + (cx1 - gx), ly0 = hy + (cy0 - gy), ly1 = hy + (cy1 - gy);
+    int i00 = ly0 * stride + lx0, i01 = ly0 * stride + lx1, i10 = ly1 * stride + lx0, i11 = ly1 * stride + lx1;
+    float k00 = sK[i00], k01 = sK[i01], k10 = sK[i10], k11 = sK[i11];
+    float gxw = 1.0f - fx, gyw = 1.0f - fy;
+    float kt = gyw * (gxw * k00 + fx * k01) + fy * (gxw * k10 + fx * k11);
+    float kmax = fmaxf(fmaxf(k00, k01), fmaxf(k10, k11));
+    float kmin = fminf(fminf(k00, k01), fminf(k10, k11));
+    float ekc = fmaxf(fmaxf(sE[i00], sE[i01]), fmaxf(sE[i10], sE[i11]));
+    float kabs = fmaxf(fabsf(kmax), fabsf(kmin));
+    float m = ek + ekc + 2.0f * eX * (kmax - kmin) + 8.0f * U32 * kabs + 1e-30f;
+    float diff = kt - k;  // need k < kt (s = +) or k <= kt (s = -)
+    if (diff < -m) return 0;
+    if (!(diff > m)) verdict = 2;
+  }
+  return verdict;
+}
+
+template <typename Tin>
+__global__ void __launch_bounds__(ST_THREADS) k_stencil_ridge(StencilArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tid = threadIdx.x;
+  const int R = a.taps.R;
+  const int HALO = R + 3;
+  const int IW = ST_TW + 2 * HALO, IH = ST_TH + 2 * HALO;
+  const int PW = ST_TW + 6, LH = ST_TH + 6;
+  const int HW2 = ST_TW + 2, HH2 = ST_TH + 2;
+  const int H = a.H, W = a.W;
+
+  // shared memory carve-up (8-byte aligned pieces first)
+  unsigned long long* sL = reinterpret_cast<unsigned long long*>(smem);      // LH*PW
+  long long* sHxx = reinterpret_cast<long long*>(sL + LH * PW);             // HH2*HW2 each
+  long long* sHyy = sHxx + HH2 * HW2;
+  long long* sHxy = sHyy + HH2 * HW2;
+  uint32_t* sI = reinterpret_cast<uint32_t*>(sHxy + HH2 * HW2);             // IH*IW
+  uint32_t* sP = sI + IH * IW;                                              // IH*PW
+  float* sK = reinterpret_cast<float*>(sP + IH * PW);                       // HH2*HW2
+  float* sE = sK + HH2 * HW2;
+  int* sScan = reinterpret_cast<int*>(sE + HH2 * HW2);                      // 8 warps + 2
+  __shared__ int32_t q[2 * MAX_RG + 1];
+
+  if (tid < 2 * R + 1) q[tid] = a.taps.q[tid];
+
+  const int f = blockIdx.z;
+  const int x0 = blockIdx.x * ST_TW, y0 = blockIdx.y * ST_TH;
+  const Tin* img = reinterpret_cast<const Tin*>(a.frames) + (size_t)f * H * W;
+
+  // ---- A: input tile with reflect-101 halo
+  for (int i = tid; i < IH * IW; i += ST_THREADS) {
+    int iy = i / IW, ix = i - iy * IW;
+    int gy = reflect101(y0 - HALO + iy, H), gx = reflect101(x0 - HALO + ix, W);
+    sI[i] = (uint32_t)img[(size_t)gy * W + gx];
+  }
+  __syncthreads();
+
+  // ---- B: horizontal Gaussian, exact u32 (sum Q_i I < 2^31)
+  for (int i = tid; i < IH * PW; i += ST_THREADS) {
+    int iy = i / PW, px = i - iy * PW;
+    const uint32_t* row = sI + iy * IW + px;
+    uint32_t acc = (uint32_t)q[R] * row[R];
+    for (int j = 0; j < R; ++j) acc += (uint32_t)q[j] * (row[j] + row[2 * R - j]);
+    sP[i] = acc;
+  }
+  __syncthreads();
+
+  // ---- C: vertical Gaussian, exact u64: L' = sum_i sum_j Q_i Q_j I
+  for (int i = tid; i < LH * PW; i += ST_THREADS) {
+    int ly = i / PW, px = i - ly * PW;
+    const uint32_t* col = sP + ly * PW + px;
+    unsigned long long acc = (unsigned long long)(uint32_t)q[R] * col[R * PW];
+    for (int j = 0; j < R; ++j)
+      acc += (unsigned long long)(uint32_t)q[j] * (unsigned long long)(col[j * PW] + col[(2 * R - j) * PW]);
+    sL[i] = acc;
+  }
+  __syncthreads();
+
+  // ---- D: exact Hessian (5x5 second-order Sobel of L') and FP32 k- on the
+  //         tile plus a one-pixel ring
+  for (int i = tid; i < HH2 * HW2; i += ST_THREADS) {
+    int hy = i / HW2, hx = i - hy * HW2;
+    long long hxx = 0, hyy = 0, hxy = 0;
+    const long long s5[5] = {1, 4, 6, 4, 1}, d2[5] = {1, 0, -2, 0, 1}, d1[5] = {-1, -2, 0, 2, 1};
+#pragma unroll
+    for (int dy = 0; dy < 5; ++dy) {
+      const long long* row = reinterpret_cast<const long long*>(sL) + (hy + dy) * PW + hx;
+      long long l0 = row[0], l1 = row[1], l2 = row[2], l3 = row[3], l4 = row[4];
+      long long sx = l0 + 4 * (l1 + l3) + 6 * l2 + l4;
+      long long d2x = l0 - 2 * l2 + l4;
+      long long d1x = (l4 - l0) + 2 * (l3 - l1);
+      hxx += s5[dy] * d2x;
+      hyy += d2[dy] * sx;
+      hxy += d1[dy] * d1x;
+    }
+    sHxx[i] = hxx;
+    sHyy[i] = hyy;
+    sHxy[i] = hxy;
+    float fa = __ll2float_rn(hxx) * a.invD, fb = __ll2float_rn(hxy) * a.invD, fc = __ll2float_rn(hyy) * a.invD;
+    float k, ek, hdf, rad;
+    eig32_k(fa, fb, fc, k, ek, hdf, rad);
+    sK[i] = k;
+    sE[i] = ek;
+  }
+  __syncthreads();
+
+  // ---- E: directed-ridge test of the tile's pixels, 4 per thread
+  bool flag[4];
+  int nfb = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    int pi = tid + j * ST_THREADS;
+    int ty = pi / ST_TW, tx = pi - ty * ST_TW;
+    int gx = x0 + tx, gy = y0 + ty;
+    bool rid = false;
+    if (gx < W && gy < H) {
+      int hy = ty + 1, hx = tx + 1, c = hy * HW2 + hx;
+      long long hxx = sHxx[c], hyy = sHyy[c], hxy = sHxy[c];
+      bool degenerate = (hxy == 0 && hxx == hyy);
+      float k = sK[c], ek = sE[c];
+      float dk = k - a.tau;  // exact near the boundary (Sterbenz)
+      int verdict;
+      if (degenerate || dk >= ek) {
+        verdict = 0;
+      } else if (!(dk < -ek)) {
+        verdict = 2;
+      } else {
+        float fa = __ll2float_rn(hxx) * a.invD, fb = __ll2float_rn(hxy) * a.invD, fc = __ll2float_rn(hyy) * a.invD;
+        float k2, ek2, hdf, rad, X, Y, eX;
+        eig32_k(fa, fb, fc, k2, ek2, hdf, rad);
+        float M = fabsf(fa) + fabsf(fb) + fabsf(fc);
+        if (!eig32_dir(fb, hdf, rad, M, hxy == 0, X, Y, eX))
+          verdict = 2;
+        else
+          verdict = ridge_fast(sK, sE, HW2, hy, hx, gx, gy, H, W, k, ek, a.tau, X, Y, eX);
+      }
+      if (verdict == 2) {
+        ++nfb;
+        rid = ridge_exact(sHxx, sHyy, sHxy, HW2, hy, hx, gx, gy, H, W, a.D64, a.tau64);
+      } else {
+        rid = verdict == 1;
+      }
+    }
+    flag[j] = rid;
+  }
+  if (nfb) atomicAdd(&a.stats->fallbacks, (unsigned long long)nfb);
+
+  // ---- compaction in row-major order: 4 rounds of 256 pixels
+  const int lane = tid & 31, warp = tid >> 5;
+  int pos[4];
+  int base = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    unsigned bal = __ballot_sync(0xffffffffu, flag[j]);
+    if (lane == 0) sScan[warp] = __popc(bal);
+    __syncthreads();
+    int wpre = 0, tot = 0;
+    for (int w = 0; w < ST_THREADS / 32; ++w) {
+      int c = sScan[w];
+      wpre += (w < warp) ? c : 0;
+      tot += c;
+    }
+    pos[j] = base + wpre + __popc(bal & ((1u << lane) - 1u));
+    base += tot;
+    __syncthreads();
+  }
+  const int total = base;
+  const int tile = blockIdx.y * a.rl.n_stx + blockIdx.x;
+  const size_t tbase = (size_t)f * a.rl.n_stx * a.rl.n_sty + tile;
+  if (tid == 0) {
+    int start = total ? atomicAdd(&a.rl.count[f], total) : 0;
+    sScan[8] = start;
+    int keep = max(0, min(total, a.rl.cap - start));
+    if (keep < total) atomicOr(&a.stats->overflow, 1);
+    a.rl.tile_off[tbase] = total ? start : 0;
+    a.rl.tile_cnt[tbase] = keep;
+    if (total) atomicAdd(&a.stats->ridge, (unsigned long long)total);
+  }
+  __syncthreads();
+  const int start = sScan[8];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (!flag[j]) continue;
+    int o = start + pos[j];
+    if (o >= a.rl.cap) continue;
+    int pi = tid + j * ST_THREADS;
+    int ty = pi / ST_TW, tx = pi - ty * ST_TW;
+    int c = (ty + 1) * HW2 + (tx + 1);
+    size_t g = (size_t)f * a.rl.cap + o;
+    a.rl.xy[g] = (uint32_t)(x0 + tx) | ((uint32_t)(y0 + ty) << 16);
+    a.rl.hess[3 * g + 0] = sHxx[c];
+    a.rl.hess[3 * g + 1] = sHyy[c];
+    a.rl.hess[3 * g + 2] = sHxy[c];
+  }
+}
+
+// K2: X- of each ridge pixel as a double-float from its exact Hessian, and
+// the vote-rounding margins.  With P = Hxx' - Hyy', Bq = 2 Hxy',
+// R = sqrt(P^2 + Bq^2): X- is proportional to (Bq, -(P + R)) for P >= 0 and
+// to (-(|P| + R), Bq) otherwise; both components are computed without
+// cancellation, so the direction is accurate to ~2^-44.
+__global__ void __launch_bounds__(256) k_ridge_refine(RidgeList rl, int n_frames) {
+  const int gstride = gridDim.x * blockDim.x;
+  for (int f = 0; f < n_frames; ++f) {
+    int cnt = min(rl.count[f], rl.cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gstride) {
+      size_t g = (size_t)f * rl.cap + i;
+      long long A = rl.hess[3 * g + 0], C = rl.hess[3 * g + 1], B = rl.hess[3 * g + 2];
+      long long P = A - C, Bq = 2 * B;
+      dfl dP = df_from_ll(P), dB = df_from_ll(Bq);
+      dfl Rr = df_sqrt(df_add(df_mul(dP, dP), df_mul(dB, dB)));
+      dfl aP = P >= 0 ? dP : dfl{-dP.hi, -dP.lo};
+      dfl Wc = df_add(aP, Rr);
+      dfl vx, vy;
+      if (P >= 0) {
+        vx = dB;
+        vy = {-Wc.hi, -Wc.lo};
+      } else {
+        vx = {-Wc.hi, -Wc.lo};
+        vy = dB;
+      }
+      dfl nrm = df_sqrt(df_add(df_mul(vx, vx), df_mul(vy, vy)));
+      dfl X = df_div(vx, nrm), Y = df_div(vy, nrm);
+      if (X.hi < 0.0f || (X.hi == 0.0f && Y.hi < 0.0f)) {
+        X = {-X.hi, -X.lo};
+        Y = {-Y.hi, -Y.lo};
+      }
+      // bounds: double-float direction error <= 2^-40; the double-precision
+      // definition's own error <= 2^-48 * cond, cond = |H| / |v| (its
+      // eigenvector formula cancels when the eigenvalue gap is small)
+      float M = fabsf(__ll2float_rn(A)) + fabsf(__ll2float_rn(B)) + fabsf(__ll2float_rn(C));
+      float cond = 2.0f * M / fmaxf(nrm.hi, 1e-30f);
+      float eXr = 9.094947e-13f + 3.5527137e-15f * cond;  // 2^-40 + 2^-48 cond
+      float lo = fmaxf(fabsf(X.lo), fabsf(Y.lo));
+      float kfast = 1.25f * (lo + eXr + U32) + U32;
+      float kref = 1.25f * eXr + 2.842171e-14f;           // + 2^-45
+      rl.dir[g] = make_float4(X.hi, Y.hi, X.lo, Y.lo);
+      rl.kvote[g] = make_float2(kfast, kref);
+    }
+  }
+}
+
+template __global__ void k_stencil_ridge<uint8_t>(StencilArgs);
+template __global__ void k_stencil_ridge<uint16_t>(StencilArgs);
+
+size_t stencil_smem_bytes(int R) {
+  const int HALO = R + 3;
+  const int IW = ST_TW + 2 * HALO, IH = ST_TH + 2 * HALO;
+  const int PW = ST_TW + 6, LH = ST_TH + 6;
+  const int HW2 = ST_TW + 2, HH2 = ST_TH + 2;
+  return (size_t)LH * PW * 8 + (size_t)3 * HH2 * HW2 * 8 + (size_t)IH * IW * 4 + (size_t)IH * PW * 4 +
+         (size_t)2 * HH2 * HW2 * 4 + 16 * 4;
+}
+
+cudaError_t launch_stencil(const StencilArgs& a, int dtype, cudaStream_t st) {
+  dim3 grid((a.W + ST_TW - 1) / ST_TW, (a.H + ST_TH - 1) / ST_TH, a.n);
+  size_t sm = stencil_smem_bytes(a.taps.R);
+  if (dtype == 0) {
+    cudaFuncSetAttribute(k_stencil_ridge<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_stencil_ridge<uint8_t><<<grid, ST_THREADS, sm, st>>>(a);
+  } else {
+    cudaFuncSetAttribute(k_stencil_ridge<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_stencil_ridge<uint16_t><<<grid, ST_THREADS, sm, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refine(const RidgeList& rl, int n_frames, int n_sm, cudaStream_t st) {
+  k_ridge_refine<<<n_sm * 4, 256, 0, st>>>(rl, n_frames);
+  return cudaGetLastError();
+}
+
+}  // namespace rd

@@ -1,0 +1,336 @@
+// k_vote.cu -- K3: binning of ridge pixels into (frame, accumulator tile,
+// r-slab) bins; K4: ridge-directed voting into a shared-memory accumulator
+// and the fused epilogue (hotspot threshold, radius-dependent smoothing, 1/r
+// normalisation, float threshold and 3x3x3 local maxima).
+//
+// Method: Results ("each directed ridge pixel votes ... (x, y) +/- r X-";
+// "Local maxima detection in a noisy parameter space": smoothing of each
+// equi-radius level with a width proportional to r, 1/r normalisation,
+// nearest-neighbour comparison); Methods (sigma(r) = 0.05 r + 0.25); Detailed
+// algorithm step 4 (integer hotspot threshold, float threshold as a fraction
+// of 2 pi, 3x3x3 box); Additional notes (votes over [r_min - 1, r_max + 1],
+// peaks only inside [r_min, r_max]).
+//
+// The paper streams equi-radius levels through a three-level cyclic buffer.
+// Here each CTA owns one x-y tile and one slab of levels: it casts the votes
+// of one level into a shared-memory slab (tile plus the smoothing halo), maps
+// that level's hotspots into a three-level cyclic buffer of smoothed sums,
+// and peak-tests the middle level, so the 3-d accumulator never leaves the SM.
+#include "rd_internal.cuh"
+#include <climits>
+
+namespace rd {
+
+
+__device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// Visit the bins that one (ridge pixel, slab, sign) segment can reach: the
+// vote positions p + s r X for r in [lo-1, hi+1] lie on a segment; a bin's
+// tile collects votes within `halo` px of the tile, and a vote bin is within
+// 1/2 px of its real position (1 px margin).
+template <bool FILL>
+__global__ void __launch_bounds__(256) k_bin(BinArgs a) {
+  const int gstride = gridDim.x * blockDim.x;
+  for (int f = 0; f < a.n_frames; ++f) {
+    const int cnt = min(a.rl.count[f], a.rl.cap);
+    const long long total = (long long)cnt * a.n_slabs;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total; it += gstride) {
+      int i = (int)(it / a.n_slabs), s = (int)(it - (long long)i * a.n_slabs);
+      size_t g = (size_t)f * a.rl.cap + i;
+      uint32_t xy = a.rl.xy[g];
+      float4 d = a.rl.dir[g];
+      float px = (float)(xy & 0xffffu), py = (float)(xy >> 16);
+      int4 sl = a.slabs[s];
+      float r0 = (float)(sl.x - 1), r1 = (float)(sl.y + 1);
+      int h = sl.z;
+      for (int sg = 0; sg < 2; ++sg) {
+        float sgn = sg == 0 ? 1.0f : -1.0f;
+        float ax0 = px + sgn * r0 * d.x, ax1 = px + sgn * r1 * d.x;
+        float ay0 = py + sgn * r0 * d.y, ay1 = py + sgn * r1 * d.y;
+        int bx0 = (int)floorf(fminf(ax0, ax1)) - 1, bx1 = (int)ceilf(fmaxf(ax0, ax1)) + 1;
+        int by0 = (int)floorf(fminf(ay0, ay1)) - 1, by1 = (int)ceilf(fmaxf(ay0, ay1)) + 1;
+        bx0 = max(bx0, 0);
+        by0 = max(by0, 0);
+        bx1 = min(bx1, a.W - 1);
+        by1 = min(by1, a.H - 1);
+        if (bx0 > bx1 || by0 > by1) continue;
+        int tx0 = max(floordiv(bx0 - h, a.T), 0), tx1 = min(floordiv(bx1 + h, a.T), a.n_atx - 1);
+        int ty0 = max(floordiv(by0 - h, a.T), 0), ty1 = min(floordiv(by1 + h, a.T), a.n_aty - 1);
+        for (int ty = ty0; ty <= ty1; ++ty)
+          for (int tx = tx0; tx <= tx1; ++tx) {
+            long long b = (((long long)f * a.n_aty + ty) * a.n_atx + tx) * a.n_slabs + s;
+            if (!FILL) {
+              atomicAdd(&a.bin_cnt[b], 1);
+            } else {
+              long long pos = (long long)a.bin_off[b] + atomicAdd(&a.bin_fill[b], 1);
+              if (pos < a.pool_cap) a.pool[pos] = ((uint32_t)i << 1) | (uint32_t)sg;
+            }
+          }
+      }
+    }
+  }
+}
+
+// ---- exclusive scan of int counts (three phases, 1024 per block) ----------
+__global__ void k_scan_blocks(const int* in, int* out, int* block_sums, long long n) {
+  __shared__ int s[1024];
+  long long i = blockIdx.x * 1024LL + threadIdx.x;
+  int v = i < n ? in[i] : 0;
+  s[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    int t = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
+    __syncthreads();
+    s[threadIdx.x] += t;
+    __syncthreads();
+  }
+  if (i < n) out[i] = s[threadIdx.x] - v;
+  if (threadIdx.x == 1023) block_sums[blockIdx.x] = s[1023];
+}
+
+__global__ void k_scan_sums(int* block_sums, int nb, long long* total_out) {
+  __shared__ long long s[1024];
+  __shared__ long long carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nb; base += 1024) {
+    int i = base + threadIdx.x;
+    long long v = i < nb ? block_sums[i] : 0;
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      long long t = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
+      __syncthreads();
+      s[threadIdx.x] += t;
+      __syncthreads();
+    }
+    long long ex = s[threadIdx.x] - v + carry;
+    if (i < nb) block_sums[i] = (int)min(ex, (long long)INT_MAX);
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += s[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && total_out) *total_out = carry;
+}
+
+__global__ void k_scan_add(int* out, const int* block_sums, long long n) {
+  long long i = blockIdx.x * 1024LL + threadIdx.x;
+  if (i < n) out[i] = (int)min((long long)out[i] + block_sums[blockIdx.x], (long long)INT_MAX);
+}
+
+// ---- K4 ---------------------------------------------------------------------
+
+size_t vote_smem_bytes(int max_rw, int T, int max_qn) {
+  int rw2 = T + 2;
+  return (size_t)max_rw * max_rw * 4 + (size_t)3 * rw2 * rw2 * 4 + (size_t)max_qn * 8 + (size_t)rw2 * rw2 * 2 + 64;
+}
+
+__global__ void __launch_bounds__(VOTE_THREADS) k_vote(VoteArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int b = blockIdx.x;
+  const int cnt_raw = a.bin_cnt[b];
+  if (cnt_raw == 0) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int NW = VOTE_THREADS / 32;
+  int t = b;
+  const int s = t % a.n_slabs;
+  t /= a.n_slabs;
+  const int tx = t % a.n_atx;
+  t /= a.n_atx;
+  const int ty = t % a.n_aty;
+  const int f = t / a.n_aty;
+  const long long off = a.bin_off[b];
+  const int cnt = (int)max(0LL, min((long long)cnt_raw, a.pool_cap - off));
+  if (threadIdx.x == 0 && cnt < cnt_raw) atomicOr(&a.stats->overflow, 2);
+  const int4 sl = a.slabs[s];
+  const int lo = sl.x, hi = sl.y, h = sl.z;
+  const int T = a.T, RW = T + 2 * h, RW2 = T + 2;
+  const int ox = tx * T - h, oy = ty * T - h;  // image coords of the slab's (0, 0)
+  const int H = a.H, W = a.W;
+
+  uint32_t* sA = reinterpret_cast<uint32_t*>(smem);                    // RW*RW (max_rw^2)
+  uint32_t* sN = sA + a.max_rw * a.max_rw;                             // 3 * RW2*RW2
+  int32_t* sQ = reinterpret_cast<int32_t*>(sN + 3 * RW2 * RW2);        // max_qn
+  int32_t* sQo = sQ + a.max_qn;                                        // max_qn
+  uint16_t* sHot = reinterpret_cast<uint16_t*>(sQo + a.max_qn);        // RW2*RW2
+  __shared__ int s_nhot;
+  __shared__ unsigned long long s_votes, s_fb;
+  if (tid == 0) {
+    s_votes = 0;
+    s_fb = 0;
+  }
+
+  const size_t fbase = (size_t)f * a.rl.cap;
+  const int lv0 = a.r_min - 1;  // level index origin
+
+  for (int r = lo - 1; r <= hi + 1; ++r) {
+    const int li = r - lv0;
+    const int Rs = a.q_rad[li];
+    const int Wq = 2 * Rs + 1, nq = Wq * Wq;
+    for (int i = tid; i < RW * RW; i += VOTE_THREADS) sA[i] = 0;
+    for (int i = tid; i < nq; i += VOTE_THREADS) {
+      int dy = i / Wq, dx = i - dy * Wq;
+      sQ[i] = a.q_tab[a.q_off[li] + i];
+      sQo[i] = (dy - Rs) * RW + (dx - Rs);
+    }
+    if (tid == 0) s_nhot = 0;
+    __syncthreads();
+
+    // ---- cast this level's votes
+    const bool owned = (r >= lo && r <= hi) || (r == lo - 1 && lo == a.r_min) || (r == hi + 1 && hi == a.r_max);
+    unsigned nv = 0, nfb = 0;
+    const float rf = (float)r;
+    for (int e = tid; e < cnt; e += VOTE_THREADS) {
+      uint32_t ent = a.pool[off + e];
+      int i = (int)(ent >> 1);
+      bool neg = ent & 1u;
+      size_t g = fbase + i;
+      uint32_t xy = a.rl.xy[g];
+      float4 d = a.rl.dir[g];
+      float2 kv = a.rl.kvote[g];
+      int px = (int)(xy & 0xffffu), py = (int)(xy >> 16);
+      float sr = neg ? -rf : rf;
+      int vx = vote_offset(sr, rf, d.x, d.z, kv.x, kv.y);
+      int vy = vote_offset(sr, rf, d.y, d.w, kv.x, kv.y);
+      int bx, by;
+      if (vx == INT_MIN || vy == INT_MIN) {
+        ++nfb;
+        Eig64 e64 = eigen64(a.rl.hess[3 * g], a.rl.hess[3 * g + 1], a.rl.hess[3 * g + 2], a.D64);
+        double X = e64.X, Y = e64.Y;
+        if (X * (double)d.x + Y * (double)d.y < 0.0) {
+          X = -X;
+          Y = -Y;
+        }
+        bx = vote_bin64(px, (double)sr, X);
+        by = vote_bin64(py, (double)sr, Y);
+      } else {
+        bx = px + vx;
+        by = py + vy;
+      }
+      if (bx < 0 || bx >= W || by < 0 || by >= H) continue;
+      int lx = bx - ox, ly = by - oy;
+      if (lx < 0 || lx >= RW || ly < 0 || ly >= RW) continue;
+      atomicAdd(&sA[ly * RW + lx], 1u);
+      if (owned && lx >= h && lx < h + T && ly >= h && ly < h + T) ++nv;
+    }
+    if (nv) atomicAdd(&s_votes, (unsigned long long)nv);
+    if (nfb) atomicAdd(&s_fb, (unsigned long long)nfb);
+    __syncthreads();
+
+    // ---- hotspots of this level on the tile plus a one-voxel ring
+    uint32_t* slot = sN + (r % 3) * RW2 * RW2;
+    for (int v = tid; v < RW2 * RW2; v += VOTE_THREADS) {
+      int vy_ = v / RW2, vx_ = v - vy_ * RW2;
+      int gx = tx * T - 1 + vx_, gy = ty * T - 1 + vy_;
+      uint32_t av = 0;
+      if (gx >= 0 && gx < W && gy >= 0 && gy < H) av = sA[(vy_ + h - 1) * RW + (vx_ + h - 1)];
+      slot[v] = 0;
+      if ((long long)av > (long long)a.vote_thresh) {
+        int k = atomicAdd(&s_nhot, 1);
+        sHot[k] = (uint16_t)v;
+      }
+    }
+    __syncthreads();
+
+    // ---- radius-dependent smoothing at the hotspots (one warp per hotspot)
+    const int nhot = s_nhot;
+    for (int k = warp; k < nhot; k += NW) {
+      int v = sHot[k];
+      int vy_ = v / RW2, vx_ = v - vy_ * RW2;
+      int center = (vy_ + h - 1) * RW + (vx_ + h - 1);
+      unsigned long long acc = 0;
+      for (int q = lane; q < nq; q += 32) acc += (unsigned long long)(uint32_t)sQ[q] * sA[center + sQo[q]];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) {
+        if (acc > 0xffffffffULL) {
+          atomicOr(&a.stats->overflow, 16);
+          acc = 0xffffffffULL;
+        }
+        slot[v] = (uint32_t)acc;
+      }
+    }
+    __syncthreads();
+
+    if (a.dbg_acc && f == 0) {
+      for (int v = tid; v < T * T; v += VOTE_THREADS) {
+        int iy = v / T, ix = v - iy * T;
+        int gx = tx * T + ix, gy = ty * T + iy;
+        if (gx < W && gy < H) {
+          a.dbg_acc[((size_t)li * H + gy) * W + gx] = (int32_t)sA[(iy + h) * RW + (ix + h)];
+          if (a.dbg_sm) a.dbg_sm[((size_t)li * H + gy) * W + gx] = slot[(iy + 1) * RW2 + ix + 1];
+        }
+      }
+    }
+
+    // ---- peak test of level r - 1 (levels r - 2, r - 1, r are in the buffer)
+    const int rp = r - 1;
+    if (rp >= lo && rp <= hi) {
+      const uint32_t* Nlo = sN + ((rp + 2) % 3) * RW2 * RW2;  // level rp - 1
+      const uint32_t* Nmid = sN + (rp % 3) * RW2 * RW2;
+      const uint32_t* Nhi = slot;                             // level rp + 1
+      const unsigned long long thr = a.nthr[rp - lv0];
+      for (int v = tid; v < T * T; v += VOTE_THREADS) {
+        int iy = v / T, ix = v - iy * T;
+        int gx = tx * T + ix, gy = ty * T + iy;
+        if (gx >= W || gy >= H) continue;
+        int c = (iy + 1) * RW2 + ix + 1;
+        unsigned long long nv0 = Nmid[c];
+        if (nv0 < thr) continue;
+        bool ok = true;
+#pragma unroll
+        for (int dr = -1; dr <= 1; ++dr) {
+          const uint32_t* L = dr < 0 ? Nlo : (dr == 0 ? Nmid : Nhi);
+          unsigned long long lhs = nv0 * (unsigned long long)(rp + dr);
+#pragma unroll
+          for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+              if (dr == 0 && dy == 0 && dx == 0) continue;
+              unsigned long long rhs = (unsigned long long)L[c + dy * RW2 + dx] * (unsigned long long)rp;
+              bool precedes = dr < 0 || (dr == 0 && (dy < 0 || (dy == 0 && dx < 0)));
+              ok = ok && (precedes ? lhs > rhs : lhs >= rhs);
+            }
+        }
+        if (ok) {
+          int k = atomicAdd(&a.peak_count[f], 1);
+          if (k < a.peak_cap)
+            a.peaks[(size_t)f * a.peak_cap + k] = make_int4(gx, gy, rp, (int)nv0);
+          else
+            atomicOr(&a.stats->overflow, 4);
+          atomicAdd(&a.stats->peaks, 1ULL);
+        }
+      }
+    }
+    // the next level's first barrier orders these reads before the buffer
+    // slot is overwritten
+  }
+  __syncthreads();
+  if (tid == 0) {
+    if (s_votes) atomicAdd(&a.stats->votes, s_votes);
+    if (s_fb) atomicAdd(&a.stats->fallbacks, s_fb);
+  }
+}
+
+cudaError_t launch_bins(const BinArgs& a, int n_sm, cudaStream_t st, long long n_bins, int* block_sums,
+                        long long* total_dev) {
+  cudaError_t e;
+  k_bin<false><<<n_sm * 8, 256, 0, st>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  int nb = (int)((n_bins + 1023) / 1024);
+  k_scan_blocks<<<nb, 1024, 0, st>>>(a.bin_cnt, const_cast<int*>(a.bin_off), block_sums, n_bins);
+  k_scan_sums<<<1, 1024, 0, st>>>(block_sums, nb, total_dev);
+  k_scan_add<<<nb, 1024, 0, st>>>(const_cast<int*>(a.bin_off), block_sums, n_bins);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_bin<true><<<n_sm * 8, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vote(const VoteArgs& a, long long n_bins, cudaStream_t st) {
+  size_t sm = vote_smem_bytes(a.max_rw, a.T, a.max_qn);
+  cudaFuncSetAttribute(k_vote, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_vote<<<(unsigned)n_bins, VOTE_THREADS, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace rd

@@ -1,0 +1,510 @@
+// rd_api.cu -- host side of the C ABI declared in include/rd.h: parameter
+// validation, the exact weight tables, device workspaces and the launch
+// sequence of one rd_detect call.
+//
+// The tables follow the definition operation by operation (compile with
+// -ffp-contract=off so that no multiply-add is fused):
+//   Gaussian taps  Q_i = floor(2^14 g_i + 1/2), g_i = e_i / sum(e),
+//                  e_i = exp(-(i^2) / (2 sigma sigma)), |i| <= ceil(4 sigma)
+//   level weights  floor(2^16 exp(-(dy^2 + dx^2) / (2 s s)) + 1/2),
+//                  s = sig_a r + sig_b, |dx|, |dy| <= ceil(3 s)
+//   peak threshold S > peak_frac 2 pi  <=>  N > ((peak_frac 2 pi) 2^16) r
+#include "rd_internal.cuh"
+#include "../../include/rd.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+
+using namespace rd;
+
+static thread_local std::string g_create_error;
+
+struct rd_ctx {
+  rd_params p;
+  int max_H, max_W, max_batch;
+  int device, n_sm;
+  // tables
+  GaussTaps taps;
+  double D64;
+  float invD;
+  int n_levels, n_slabs, max_rw, max_qn;
+  std::vector<int4> h_slabs;
+  // device buffers
+  int4* slabs = nullptr;
+  int* q_off = nullptr;
+  int* q_rad = nullptr;
+  int32_t* q_tab = nullptr;
+  unsigned long long* nthr = nullptr;
+  RidgeList rl{};
+  int* bin_cnt = nullptr;
+  int* bin_off = nullptr;
+  int* bin_fill = nullptr;
+  int* block_sums = nullptr;
+  long long* bin_total = nullptr;
+  uint32_t* pool = nullptr;
+  long long pool_cap = 0, n_bins_max = 0;
+  int4* peaks = nullptr;
+  int* peak_count = nullptr;
+  int peak_cap = 4096;
+  DevStats* stats = nullptr;
+  // state of the last call
+  cudaStream_t last_stream = nullptr;
+  int last_n = 0, last_H = 0, last_W = 0;
+  int32_t* dbg_acc = nullptr;
+  uint32_t* dbg_sm = nullptr;
+  // staging for rd_detect_host
+  void* stage_frames = nullptr;
+  rd_ring* stage_rings = nullptr;
+  int* stage_counts = nullptr;
+  int* stage_offsets = nullptr;
+  // stage timing
+  bool timing = false, timed = false;
+  cudaEvent_t ev[RD_N_STAGES + 1] = {};
+  std::string err;
+};
+
+// ---------------------------------------------------------------- tables
+static int gaussian_radius(float sigma) { return (int)std::ceil(4.0 * (double)sigma); }
+
+static int gaussian_taps_impl(float sigma, int32_t* taps, int cap) {
+  const double s = (double)sigma;
+  const int R = gaussian_radius(sigma);
+  if (2 * R + 1 > cap) return -1;
+  const double den = 2.0 * s * s;
+  std::vector<double> e(2 * R + 1);
+  double tot = 0.0;
+  for (int k = 0; k <= 2 * R; ++k) {
+    double i = (double)(k - R);
+    e[k] = std::exp(-(i * i) / den);
+  }
+  for (int k = 0; k <= 2 * R; ++k) tot = tot + e[k];
+  for (int k = 0; k <= 2 * R; ++k) {
+    double g = e[k] / tot;
+    taps[k] = (int32_t)std::floor(g * (double)(1 << GAUSS_BITS) + 0.5);
+  }
+  return 2 * R + 1;
+}
+
+static double level_sigma(float sig_a, float sig_b, int r) { return (double)sig_a * (double)r + (double)sig_b; }
+static int level_radius(float sig_a, float sig_b, int r) { return (int)std::ceil(3.0 * level_sigma(sig_a, sig_b, r)); }
+
+static int level_weights_impl(float sig_a, float sig_b, int r, int32_t* w, int cap) {
+  const double sg = level_sigma(sig_a, sig_b, r);
+  const int Rs = (int)std::ceil(3.0 * sg);
+  const int Wq = 2 * Rs + 1;
+  if ((long long)Wq * Wq > cap) return -1;
+  const double den = 2.0 * sg * sg;
+  for (int dy = -Rs; dy <= Rs; ++dy)
+    for (int dx = -Rs; dx <= Rs; ++dx) {
+      double fy = (double)dy, fx = (double)dx;
+      double d2 = fy * fy + fx * fx;
+      w[(dy + Rs) * Wq + (dx + Rs)] = (int32_t)std::floor(std::exp(-d2 / den) * (double)(1 << SMOOTH_BITS) + 0.5);
+    }
+  return Wq * Wq;
+}
+
+static long long peak_threshold_impl(float peak_frac, int r) {
+  const double two_pi = 2.0 * M_PI;
+  double thr = (((double)peak_frac * two_pi) * (double)(1 << SMOOTH_BITS)) * (double)r;
+  return (long long)std::floor(thr) + 1;
+}
+
+extern "C" int rd_gaussian_taps(float sigma, int32_t* taps, int cap) {
+  if (!(sigma > 0.0f) || !taps) return -1;
+  return gaussian_taps_impl(sigma, taps, cap);
+}
+extern "C" int rd_level_weights(float sig_a, float sig_b, int r, int32_t* w, int cap) {
+  if (!w || r < 1 || !(level_sigma(sig_a, sig_b, r) > 0.0)) return -1;
+  return level_weights_impl(sig_a, sig_b, r, w, cap);
+}
+extern "C" int64_t rd_peak_threshold(float peak_frac, int r) { return peak_threshold_impl(peak_frac, r); }
+
+// ---------------------------------------------------------------- helpers
+static rd_status fail(rd_ctx* c, rd_status s, const std::string& m) {
+  if (c)
+    c->err = m;
+  else
+    g_create_error = m;
+  return s;
+}
+
+static void free_all(rd_ctx* c) {
+  void* ptrs[] = {c->slabs, c->q_off, c->q_rad, c->q_tab, c->nthr, c->rl.xy, c->rl.dir, c->rl.kvote, c->rl.hess,
+                  c->rl.count, c->rl.tile_off, c->rl.tile_cnt, c->bin_cnt, c->bin_off, c->bin_fill, c->block_sums,
+                  c->bin_total, c->pool, c->peaks, c->peak_count, c->stats, c->stage_frames, c->stage_rings,
+                  c->stage_counts, c->stage_offsets};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+template <typename T>
+static bool dalloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, sizeof(T) * (count ? count : 1)) == cudaSuccess;
+}
+
+static std::string validate(const rd_params* p) {
+  if (!p) return "params is NULL";
+  if (!(p->sigma > 0.0f && p->sigma <= 4.0f)) return "sigma must be in (0, 4]";
+  if (p->r_min < 2 || p->r_max < p->r_min || p->r_max > 250) return "need 2 <= r_min <= r_max <= 250";
+  if (!(p->ridge_thresh <= 0.0f)) return "ridge_thresh must be <= 0";
+  if (!(p->peak_frac >= 0.0f) || !std::isfinite(p->peak_frac)) return "peak_frac must be finite and >= 0";
+  if (p->vote_thresh < 0) return "vote_thresh must be >= 0";
+  if (!(p->annulus_w >= 0.0f) || p->annulus_w > 64.0f) return "annulus_w must be in [0, 64]";
+  if (!(p->sig_a >= 0.0f) || !std::isfinite(p->sig_a) || !std::isfinite(p->sig_b)) return "sig_a must be >= 0";
+  if (!(level_sigma(p->sig_a, p->sig_b, p->r_min - 1) > 0.0)) return "sigma(r) must be > 0 for every level";
+  if (level_radius(p->sig_a, p->sig_b, p->r_max + 1) > MAX_RS) return "level smoothing radius ceil(3 sigma(r)) above 40";
+  return "";
+}
+
+// ---------------------------------------------------------------- C ABI
+extern "C" rd_status rd_create(const rd_params* params, int max_H, int max_W, int max_batch, rd_ctx** out) {
+  if (!out) return fail(nullptr, RD_E_INVAL, "out is NULL");
+  *out = nullptr;
+  std::string v = validate(params);
+  if (!v.empty()) return fail(nullptr, RD_E_INVAL, v);
+  const int R = gaussian_radius(params->sigma);
+  if (max_H < R + 4 || max_W < R + 4 || max_H < 12 || max_W < 12 || max_H > 65535 || max_W > 65535)
+    return fail(nullptr, RD_E_INVAL, "frame size must be at least max(12, ceil(4 sigma) + 4) and at most 65535");
+  if (max_batch < 1 || max_batch > 65535) return fail(nullptr, RD_E_INVAL, "max_batch must be in [1, 65535]");
+
+  rd_ctx* c = new rd_ctx();
+  c->p = *params;
+  c->max_H = max_H;
+  c->max_W = max_W;
+  c->max_batch = max_batch;
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+    delete c;
+    return fail(nullptr, RD_E_CUDA, "no CUDA device");
+  }
+  // Gaussian taps and the Hessian scale D = 64 S^2
+  c->taps.R = R;
+  gaussian_taps_impl(params->sigma, c->taps.q, 2 * MAX_RG + 1);
+  long long S = 0;
+  for (int i = 0; i <= 2 * R; ++i) S += c->taps.q[i];
+  c->D64 = (double)(64LL * S * S);
+  c->invD = (float)(1.0 / c->D64);
+  // levels, weights, thresholds
+  const int lv0 = params->r_min - 1, lv1 = params->r_max + 1;
+  c->n_levels = lv1 - lv0 + 1;
+  std::vector<int> h_qoff(c->n_levels), h_qrad(c->n_levels);
+  std::vector<int32_t> h_qtab;
+  std::vector<unsigned long long> h_nthr(c->n_levels, 0);
+  c->max_qn = 1;
+  for (int li = 0; li < c->n_levels; ++li) {
+    int r = lv0 + li;
+    int Rs = level_radius(params->sig_a, params->sig_b, r);
+    int nq = (2 * Rs + 1) * (2 * Rs + 1);
+    h_qoff[li] = (int)h_qtab.size();
+    h_qrad[li] = Rs;
+    h_qtab.resize(h_qtab.size() + nq);
+    level_weights_impl(params->sig_a, params->sig_b, r, h_qtab.data() + h_qoff[li], nq);
+    h_nthr[li] = (unsigned long long)peak_threshold_impl(params->peak_frac, r);
+    c->max_qn = std::max(c->max_qn, nq);
+  }
+  // r-slabs of SLAB_LEVELS peak levels; halo = 1 + the largest R_s of the slab's voting levels
+  c->max_rw = 0;
+  for (int lo = params->r_min; lo <= params->r_max; lo += SLAB_LEVELS) {
+    int hi = std::min(lo + SLAB_LEVELS - 1, params->r_max);
+    int h = 0;
+    for (int r = lo - 1; r <= hi + 1; ++r) h = std::max(h, h_qrad[r - lv0]);
+    h += 1;
+    c->h_slabs.push_back(make_int4(lo, hi, h, 0));
+    c->max_rw = std::max(c->max_rw, ACC_T + 2 * h);
+  }
+  c->n_slabs = (int)c->h_slabs.size();
+  if (vote_smem_bytes(c->max_rw, ACC_T, c->max_qn) > 227 * 1024) {
+    delete c;
+    return fail(nullptr, RD_E_INVAL, "radius range needs more shared memory than one SM has");
+  }
+  // workspaces
+  const int n_stx = (max_W + ST_TW - 1) / ST_TW, n_sty = (max_H + ST_TH - 1) / ST_TH;
+  const int n_atx = (max_W + ACC_T - 1) / ACC_T, n_aty = (max_H + ACC_T - 1) / ACC_T;
+  c->rl.cap = std::max(4096, (int)std::min<long long>((long long)max_H * max_W / 4, 1LL << 24));
+  c->rl.n_stx = n_stx;
+  c->rl.n_sty = n_sty;
+  const size_t nrec = (size_t)c->rl.cap * max_batch;
+  c->n_bins_max = (long long)max_batch * n_atx * n_aty * c->n_slabs;
+  c->pool_cap = std::min<long long>((long long)max_batch * max_H * max_W * 2, (1LL << 31) - 1);
+  bool ok = dalloc(&c->slabs, c->n_slabs) && dalloc(&c->q_off, c->n_levels) && dalloc(&c->q_rad, c->n_levels) &&
+            dalloc(&c->q_tab, h_qtab.size()) && dalloc(&c->nthr, c->n_levels) && dalloc(&c->rl.xy, nrec) &&
+            dalloc(&c->rl.dir, nrec) && dalloc(&c->rl.kvote, nrec) && dalloc(&c->rl.hess, 3 * nrec) &&
+            dalloc(&c->rl.count, max_batch) && dalloc(&c->rl.tile_off, (size_t)max_batch * n_stx * n_sty) &&
+            dalloc(&c->rl.tile_cnt, (size_t)max_batch * n_stx * n_sty) && dalloc(&c->bin_cnt, c->n_bins_max) &&
+            dalloc(&c->bin_off, c->n_bins_max) && dalloc(&c->bin_fill, c->n_bins_max) &&
+            dalloc(&c->block_sums, (c->n_bins_max + 1023) / 1024 + 1) && dalloc(&c->bin_total, 1) &&
+            dalloc(&c->pool, c->pool_cap) && dalloc(&c->peaks, (size_t)max_batch * c->peak_cap) &&
+            dalloc(&c->peak_count, max_batch) && dalloc(&c->stats, 1) &&
+            dalloc((unsigned char**)&c->stage_frames, (size_t)max_batch * max_H * max_W * 2) &&
+            dalloc(&c->stage_rings, (size_t)max_batch * c->peak_cap) && dalloc(&c->stage_counts, max_batch) &&
+            dalloc(&c->stage_offsets, max_batch);
+  if (!ok) {
+    cudaGetLastError();
+    free_all(c);
+    delete c;
+    return fail(nullptr, RD_E_NOMEM, "device allocation failed");
+  }
+  cudaError_t e = cudaMemcpy(c->slabs, c->h_slabs.data(), sizeof(int4) * c->n_slabs, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->q_off, h_qoff.data(), sizeof(int) * c->n_levels, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->q_rad, h_qrad.data(), sizeof(int) * c->n_levels, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c->q_tab, h_qtab.data(), sizeof(int32_t) * h_qtab.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c->nthr, h_nthr.data(), sizeof(unsigned long long) * c->n_levels, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(c->stats, 0, sizeof(DevStats));
+  if (e != cudaSuccess) {
+    std::string m = std::string("table upload failed: ") + cudaGetErrorString(e);
+    free_all(c);
+    delete c;
+    return fail(nullptr, RD_E_CUDA, m);
+  }
+  *out = c;
+  return RD_OK;
+}
+
+extern "C" rd_status rd_detect(rd_ctx* c, const void* frames_dev, int n, int H, int W, int dtype, void* stream,
+                               rd_ring* rings_dev, int ring_cap, int* counts_dev, int* offsets_dev) {
+  if (!c) return RD_E_INVAL;
+  if (!frames_dev || !counts_dev || !offsets_dev || (ring_cap > 0 && !rings_dev) || ring_cap < 0)
+    return fail(c, RD_E_INVAL, "NULL buffer or negative ring_cap");
+  if (n < 1 || n > c->max_batch) return fail(c, RD_E_INVAL, "n must be in [1, max_batch]");
+  if (H > c->max_H || W > c->max_W || H < c->taps.R + 4 || W < c->taps.R + 4 || H < 12 || W < 12)
+    return fail(c, RD_E_INVAL, "frame size outside [max(12, ceil(4 sigma) + 4), rd_create maxima]");
+  if (dtype != RD_U8 && dtype != RD_U16) return fail(c, RD_E_INVAL, "dtype must be RD_U8 or RD_U16");
+  cudaStream_t st = (cudaStream_t)stream;
+  c->last_stream = st;
+  c->last_n = n;
+  c->last_H = H;
+  c->last_W = W;
+
+  const int n_stx = (W + ST_TW - 1) / ST_TW, n_sty = (H + ST_TH - 1) / ST_TH;
+  const int n_atx = (W + ACC_T - 1) / ACC_T, n_aty = (H + ACC_T - 1) / ACC_T;
+  const long long n_bins = (long long)n * n_atx * n_aty * c->n_slabs;
+  RidgeList rl = c->rl;
+  rl.n_stx = n_stx;
+  rl.n_sty = n_sty;
+
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t x) {
+    if (e == cudaSuccess) e = x;
+  };
+  chk(cudaMemsetAsync(rl.count, 0, sizeof(int) * n, st));
+  chk(cudaMemsetAsync(c->bin_cnt, 0, sizeof(int) * n_bins, st));
+  chk(cudaMemsetAsync(c->bin_fill, 0, sizeof(int) * n_bins, st));
+  chk(cudaMemsetAsync(c->peak_count, 0, sizeof(int) * n, st));
+  chk(cudaMemsetAsync(c->stats, 0, sizeof(DevStats), st));
+  if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("memset: ") + cudaGetErrorString(e));
+
+  auto mark = [&](int i) {
+    if (c->timing) chk(cudaEventRecord(c->ev[i], st));
+  };
+  c->timed = c->timing;
+  mark(0);
+  StencilArgs sa;
+  sa.frames = frames_dev;
+  sa.n = n;
+  sa.H = H;
+  sa.W = W;
+  sa.taps = c->taps;
+  sa.tau = c->p.ridge_thresh;
+  sa.tau64 = (double)c->p.ridge_thresh;
+  sa.D64 = c->D64;
+  sa.invD = c->invD;
+  sa.rl = rl;
+  sa.stats = c->stats;
+  chk(launch_stencil(sa, dtype, st));
+  mark(1);
+  chk(launch_refine(rl, n, c->n_sm, st));
+  mark(2);
+  if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("stencil: ") + cudaGetErrorString(e));
+
+  BinArgs ba;
+  ba.rl = rl;
+  ba.n_frames = n;
+  ba.H = H;
+  ba.W = W;
+  ba.n_atx = n_atx;
+  ba.n_aty = n_aty;
+  ba.n_slabs = c->n_slabs;
+  ba.T = ACC_T;
+  ba.slabs = c->slabs;
+  ba.bin_cnt = c->bin_cnt;
+  ba.bin_off = c->bin_off;
+  ba.bin_fill = c->bin_fill;
+  ba.pool = c->pool;
+  ba.pool_cap = c->pool_cap;
+  ba.stats = c->stats;
+  chk(launch_bins(ba, c->n_sm, st, n_bins, c->block_sums, c->bin_total));
+  mark(3);
+  if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("bins: ") + cudaGetErrorString(e));
+
+  VoteArgs va;
+  va.rl = rl;
+  va.n_frames = n;
+  va.H = H;
+  va.W = W;
+  va.n_atx = n_atx;
+  va.n_aty = n_aty;
+  va.n_slabs = c->n_slabs;
+  va.T = ACC_T;
+  va.slabs = c->slabs;
+  va.bin_cnt = c->bin_cnt;
+  va.bin_off = c->bin_off;
+  va.pool = c->pool;
+  va.pool_cap = c->pool_cap;
+  va.q_off = c->q_off;
+  va.q_rad = c->q_rad;
+  va.q_tab = c->q_tab;
+  va.nthr = c->nthr;
+  va.r_min = c->p.r_min;
+  va.r_max = c->p.r_max;
+  va.vote_thresh = c->p.vote_thresh;
+  va.peaks = c->peaks;
+  va.peak_cap = c->peak_cap;
+  va.peak_count = c->peak_count;
+  va.stats = c->stats;
+  va.D64 = c->D64;
+  va.dbg_acc = c->dbg_acc;
+  va.dbg_sm = c->dbg_sm;
+  va.max_rw = c->max_rw;
+  va.max_qn = c->max_qn;
+  chk(launch_vote(va, n_bins, st));
+  mark(4);
+  if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("vote: ") + cudaGetErrorString(e));
+
+  FitArgs fa;
+  fa.rl = rl;
+  fa.n_frames = n;
+  fa.H = H;
+  fa.W = W;
+  fa.peaks = c->peaks;
+  fa.peak_count = c->peak_count;
+  fa.peak_cap = c->peak_cap;
+  fa.offsets = offsets_dev;
+  fa.rings = rings_dev;
+  fa.ring_cap = ring_cap;
+  fa.w = c->p.annulus_w;
+  fa.w_int = (std::floor(c->p.annulus_w) == c->p.annulus_w) ? 1 : 0;
+  fa.stats = c->stats;
+  chk(launch_fit(fa, c->peaks, counts_dev, offsets_dev, st));
+  mark(5);
+  if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("fit: ") + cudaGetErrorString(e));
+  return RD_OK;
+}
+
+extern "C" rd_status rd_detect_host(rd_ctx* c, const void* frames_host, int n, int H, int W, int dtype, void* stream,
+                                    rd_ring* rings_host, int ring_cap, int* counts_host, int* offsets_host) {
+  if (!c) return RD_E_INVAL;
+  if (!frames_host || !counts_host || !offsets_host || (ring_cap > 0 && !rings_host) || ring_cap < 0)
+    return fail(c, RD_E_INVAL, "NULL buffer or negative ring_cap");
+  if (n < 1 || n > c->max_batch || H < 1 || W < 1 || H > c->max_H || W > c->max_W)
+    return fail(c, RD_E_INVAL, "batch or frame size above the rd_create maxima");
+  if (ring_cap > c->max_batch * c->peak_cap) return fail(c, RD_E_INVAL, "ring_cap above max_batch * 4096");
+  if (dtype != RD_U8 && dtype != RD_U16) return fail(c, RD_E_INVAL, "dtype must be RD_U8 or RD_U16");
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t bytes = (size_t)n * H * W * (dtype == RD_U8 ? 1 : 2);
+  cudaError_t e = cudaMemcpyAsync(c->stage_frames, frames_host, bytes, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("frames copy: ") + cudaGetErrorString(e));
+  rd_status s = rd_detect(c, c->stage_frames, n, H, W, dtype, stream, c->stage_rings, ring_cap, c->stage_counts,
+                          c->stage_offsets);
+  if (s != RD_OK) return s;
+  e = cudaMemcpyAsync(counts_host, c->stage_counts, sizeof(int) * n, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(offsets_host, c->stage_offsets, sizeof(int) * n, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && ring_cap > 0) {
+    long long used = (long long)offsets_host[n - 1] + counts_host[n - 1];
+    used = std::min<long long>(used, ring_cap);
+    if (used > 0)
+      e = cudaMemcpyAsync(rings_host, c->stage_rings, sizeof(rd_ring) * used, cudaMemcpyDeviceToHost, st);
+  }
+  if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("result copy: ") + cudaGetErrorString(e));
+  rd_stats stats;
+  return rd_get_stats(c, &stats);
+}
+
+extern "C" rd_status rd_get_stats(rd_ctx* c, rd_stats* out) {
+  if (!c || !out) return RD_E_INVAL;
+  cudaError_t e = cudaStreamSynchronize(c->last_stream);
+  DevStats d{};
+  if (e == cudaSuccess) e = cudaMemcpy(&d, c->stats, sizeof(DevStats), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("stats: ") + cudaGetErrorString(e));
+  out->ridge_pixels = (int64_t)d.ridge;
+  out->votes = (int64_t)d.votes;
+  out->peaks = (int64_t)d.peaks;
+  out->exact_fallbacks = (int64_t)d.fallbacks;
+  out->overflow = d.overflow;
+  out->n_frames = c->last_n;
+  return d.overflow ? RD_E_OVERFLOW : RD_OK;
+}
+
+extern "C" rd_status rd_set_timing(rd_ctx* c, int on) {
+  if (!c) return RD_E_INVAL;
+  if (on && !c->ev[0]) {
+    for (int i = 0; i <= RD_N_STAGES; ++i)
+      if (cudaEventCreate(&c->ev[i]) != cudaSuccess) return fail(c, RD_E_CUDA, "cudaEventCreate failed");
+  }
+  c->timing = on != 0;
+  return RD_OK;
+}
+
+extern "C" int rd_get_timing(rd_ctx* c, float* ms, int cap) {
+  if (!c || !ms || !c->timed || !c->ev[0]) return -1;
+  if (cudaEventSynchronize(c->ev[RD_N_STAGES]) != cudaSuccess) return -1;
+  int n = std::min(cap, RD_N_STAGES);
+  for (int i = 0; i < n; ++i)
+    if (cudaEventElapsedTime(&ms[i], c->ev[i], c->ev[i + 1]) != cudaSuccess) return -1;
+  return n;
+}
+
+extern "C" rd_status rd_destroy(rd_ctx* c) {
+  if (!c) return RD_E_INVAL;
+  cudaDeviceSynchronize();
+  for (int i = 0; i <= RD_N_STAGES; ++i)
+    if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  free_all(c);
+  delete c;
+  return RD_OK;
+}
+
+extern "C" const char* rd_last_error(const rd_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+extern "C" int rd_debug_ridges(rd_ctx* c, int f, int32_t* xy, float* dir, int64_t* hess, int cap) {
+  if (!c || f < 0 || f >= c->last_n || cap < 0) return -1;
+  if (cudaStreamSynchronize(c->last_stream) != cudaSuccess) return -1;
+  int cnt = 0;
+  if (cudaMemcpy(&cnt, c->rl.count + f, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+  int n = std::min(std::min(cnt, c->rl.cap), cap);
+  size_t base = (size_t)f * c->rl.cap;
+  if (n > 0) {
+    std::vector<uint32_t> hxy(n);
+    std::vector<float4> hdir(n);
+    if (cudaMemcpy(hxy.data(), c->rl.xy + base, 4 * n, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+    if (cudaMemcpy(hdir.data(), c->rl.dir + base, 16 * n, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+    for (int i = 0; i < n; ++i) {
+      if (xy) {
+        xy[2 * i] = (int32_t)(hxy[i] & 0xffffu);
+        xy[2 * i + 1] = (int32_t)(hxy[i] >> 16);
+      }
+      if (dir) {
+        dir[2 * i] = hdir[i].x;
+        dir[2 * i + 1] = hdir[i].y;
+      }
+    }
+    if (hess && cudaMemcpy(hess, c->rl.hess + 3 * base, 24 * (size_t)n, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return -1;
+  }
+  return cnt;
+}
+
+extern "C" rd_status rd_debug_capture(rd_ctx* c, int32_t* acc_dev, uint32_t* sm_dev) {
+  if (!c) return RD_E_INVAL;
+  c->dbg_acc = acc_dev;
+  c->dbg_sm = acc_dev ? sm_dev : nullptr;
+  return RD_OK;
+}

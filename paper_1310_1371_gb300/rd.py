@@ -1,0 +1,245 @@
+"""ctypes binding of librd.so (the C ABI in include/rd.h).
+
+The functions below carry the C names and only marshal arguments: every step
+of the detector runs in the library's CUDA kernels.  PyTorch is used for
+device memory and streams.  There is no CPU fallback: if the library is
+missing or has no GPU, the calls fail loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_float, c_int, c_int32, c_int64, c_uint32, c_void_p
+
+import numpy as np
+
+from . import _build
+
+RD_U8, RD_U16 = 0, 1
+RD_OK, RD_E_INVAL, RD_E_NOMEM, RD_E_CUDA, RD_E_OVERFLOW, RD_E_TIMEOUT, RD_E_BUSY = range(7)
+STATUS_NAMES = ["RD_OK", "RD_E_INVAL", "RD_E_NOMEM", "RD_E_CUDA", "RD_E_OVERFLOW", "RD_E_TIMEOUT", "RD_E_BUSY"]
+RD_RING_FIT_FAIL = 1
+PEAK_CAP = 4096   # per-frame peak capacity of a context
+
+
+class rd_params(ctypes.Structure):
+    _fields_ = [("sigma", c_float), ("r_min", c_int), ("r_max", c_int), ("ridge_thresh", c_float),
+                ("peak_frac", c_float), ("vote_thresh", c_int), ("annulus_w", c_float),
+                ("sig_a", c_float), ("sig_b", c_float)]
+
+
+class rd_ring(ctypes.Structure):
+    _fields_ = [("frame", c_int), ("cx", c_float), ("cy", c_float), ("r", c_float), ("ix", c_int),
+                ("iy", c_int), ("ir", c_int), ("score", c_float), ("n_fit", c_int), ("flags", c_int)]
+
+
+class rd_stats(ctypes.Structure):
+    _fields_ = [("ridge_pixels", c_int64), ("votes", c_int64), ("peaks", c_int64),
+                ("exact_fallbacks", c_int64), ("overflow", c_int32), ("n_frames", c_int32)]
+
+
+RING_NP = np.dtype([("frame", "<i4"), ("cx", "<f4"), ("cy", "<f4"), ("r", "<f4"), ("ix", "<i4"),
+                    ("iy", "<i4"), ("ir", "<i4"), ("score", "<f4"), ("n_fit", "<i4"), ("flags", "<i4")])
+assert RING_NP.itemsize == ctypes.sizeof(rd_ring) == 40
+
+_lib = None
+
+
+def load_library(build: bool = False) -> ctypes.CDLL:
+    """Load librd.so from the package (building it first when asked)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"librd.so not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P = POINTER
+    sig = {
+        "rd_create": (c_int, [P(rd_params), c_int, c_int, c_int, P(c_void_p)]),
+        "rd_detect": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_int,
+                              c_void_p, c_void_p]),
+        "rd_detect_host": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_int,
+                                   c_void_p, c_void_p]),
+        "rd_get_stats": (c_int, [c_void_p, P(rd_stats)]),
+        "rd_destroy": (c_int, [c_void_p]),
+        "rd_last_error": (ctypes.c_char_p, [c_void_p]),
+        "rd_gaussian_taps": (c_int, [c_float, P(c_int32), c_int]),
+        "rd_level_weights": (c_int, [c_float, c_float, c_int, P(c_int32), c_int]),
+        "rd_peak_threshold": (c_int64, [c_float, c_int]),
+        "rd_debug_ridges": (c_int, [c_void_p, c_int, P(c_int32), P(c_float), P(c_int64), c_int]),
+        "rd_debug_capture": (c_int, [c_void_p, c_void_p, c_void_p]),
+        "rd_set_timing": (c_int, [c_void_p, c_int]),
+        "rd_get_timing": (c_int, [c_void_p, P(c_float), c_int]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class RdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+def make_params(**kw) -> rd_params:
+    return rd_params(float(kw["sigma"]), int(kw["r_min"]), int(kw["r_max"]), float(kw["ridge_thresh"]),
+                     float(kw["peak_frac"]), int(kw["vote_thresh"]), float(kw.get("annulus_w", 2.0)),
+                     float(kw.get("sig_a", 0.05)), float(kw.get("sig_b", 0.25)))
+
+
+# ---- host-only helpers -----------------------------------------------------------
+def rd_gaussian_taps(sigma: float) -> np.ndarray:
+    lib = load_library()
+    buf = (c_int32 * 64)()
+    n = lib.rd_gaussian_taps(sigma, buf, 64)
+    if n < 0:
+        raise RdError(RD_E_INVAL, "rd_gaussian_taps")
+    return np.frombuffer(buf, dtype=np.int32, count=n).copy()
+
+
+def rd_level_weights(sig_a: float, sig_b: float, r: int) -> np.ndarray:
+    lib = load_library()
+    buf = (c_int32 * (81 * 81))()
+    n = lib.rd_level_weights(sig_a, sig_b, r, buf, 81 * 81)
+    if n < 0:
+        raise RdError(RD_E_INVAL, "rd_level_weights")
+    w = int(round(n ** 0.5))
+    return np.frombuffer(buf, dtype=np.int32, count=n).copy().reshape(w, w)
+
+
+def rd_peak_threshold(peak_frac: float, r: int) -> int:
+    return int(load_library().rd_peak_threshold(peak_frac, r))
+
+
+# ---- the detector ------------------------------------------------------------------
+class Detector:
+    """One rd_ctx: method parameters, maximum frame size and batch."""
+
+    def __init__(self, params: dict, max_H: int, max_W: int, max_batch: int = 1):
+        import torch  # device memory and streams
+        self.torch = torch
+        self.lib = load_library()
+        self.params = dict(params)
+        self.max_H, self.max_W, self.max_batch = max_H, max_W, max_batch
+        ctx = c_void_p()
+        p = make_params(**params)
+        st = self.lib.rd_create(ctypes.byref(p), max_H, max_W, max_batch, ctypes.byref(ctx))
+        if st != RD_OK:
+            raise RdError(st, self.lib.rd_last_error(None).decode())
+        self.ctx = ctx
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
+        self.ring_cap = max_batch * PEAK_CAP
+        self.rings = torch.empty(self.ring_cap * 10, dtype=torch.int32, device=dev)
+        self.counts = torch.empty(max_batch, dtype=torch.int32, device=dev)
+        self.offsets = torch.empty(max_batch, dtype=torch.int32, device=dev)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None and self.ctx.value:
+            self.lib.rd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _err(self, st):
+        return RdError(st, self.lib.rd_last_error(self.ctx).decode())
+
+    @staticmethod
+    def dtype_code(t) -> int:
+        import torch
+        if t == torch.uint8:
+            return RD_U8
+        if t == torch.uint16:
+            return RD_U16
+        raise TypeError(f"unsupported frame dtype {t}")
+
+    def detect_async(self, frames, stream=None):
+        """Enqueue rd_detect on device frames [n, H, W] (uint8 / uint16)."""
+        torch = self.torch
+        if not frames.is_cuda or not frames.is_contiguous():
+            raise ValueError("frames must be a contiguous CUDA tensor")
+        n, H, W = frames.shape
+        s = stream if stream is not None else torch.cuda.current_stream()
+        st = self.lib.rd_detect(self.ctx, c_void_p(frames.data_ptr()), n, H, W, self.dtype_code(frames.dtype),
+                                c_void_p(s.cuda_stream), c_void_p(self.rings.data_ptr()), self.ring_cap,
+                                c_void_p(self.counts.data_ptr()), c_void_p(self.offsets.data_ptr()))
+        if st != RD_OK:
+            raise self._err(st)
+        return n
+
+    def stats(self) -> rd_stats:
+        out = rd_stats()
+        st = self.lib.rd_get_stats(self.ctx, ctypes.byref(out))
+        if st not in (RD_OK, RD_E_OVERFLOW):
+            raise self._err(st)
+        return out
+
+    def detect(self, frames, stream=None, check=True):
+        """rd_detect + sync; returns (list of per-frame ring arrays, stats)."""
+        n = self.detect_async(frames, stream)
+        stats = self.stats()
+        if check and stats.overflow:
+            raise RdError(RD_E_OVERFLOW, f"capacity overflow mask {stats.overflow}")
+        counts = self.counts[:n].cpu().numpy()
+        offs = self.offsets[:n].cpu().numpy()
+        total = int(min(counts.sum(), self.ring_cap))
+        rings = self.rings[: total * 10].cpu().numpy().view(RING_NP)
+        return [rings[o:o + c] for o, c in zip(offs, counts)], stats
+
+    def detect_host(self, frames_host: np.ndarray, stream=None):
+        """rd_detect_host: host frames in, host rings out (copies inside)."""
+        torch = self.torch
+        n, H, W = frames_host.shape
+        code = RD_U8 if frames_host.dtype == np.uint8 else RD_U16
+        if frames_host.dtype not in (np.uint8, np.uint16) or not frames_host.flags.c_contiguous:
+            raise TypeError("frames must be a C-contiguous uint8/uint16 array")
+        rings = np.empty(self.ring_cap, dtype=RING_NP)
+        counts = np.empty(n, dtype=np.int32)
+        offs = np.empty(n, dtype=np.int32)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        st = self.lib.rd_detect_host(self.ctx, c_void_p(frames_host.ctypes.data), n, H, W, code,
+                                     c_void_p(s.cuda_stream), c_void_p(rings.ctypes.data), self.ring_cap,
+                                     c_void_p(counts.ctypes.data), c_void_p(offs.ctypes.data))
+        if st not in (RD_OK, RD_E_OVERFLOW):
+            raise self._err(st)
+        return rings, counts, offs, st
+
+    def set_timing(self, on: bool):
+        st = self.lib.rd_set_timing(self.ctx, 1 if on else 0)
+        if st != RD_OK:
+            raise self._err(st)
+
+    def timing(self) -> np.ndarray:
+        """Stage durations (ms) of the last call: stencil, refine, bins, vote, fit."""
+        buf = (c_float * 8)()
+        n = self.lib.rd_get_timing(self.ctx, buf, 8)
+        if n < 0:
+            raise self._err(RD_E_INVAL)
+        return np.frombuffer(buf, dtype=np.float32, count=n).copy()
+
+    def debug_ridges(self, f: int = 0):
+        """Ridge pixels of frame f of the last call: xy [n, 2], dir [n, 2], hess [n, 3]."""
+        n = self.lib.rd_debug_ridges(self.ctx, f, None, None, None, 0)
+        if n < 0:
+            raise self._err(RD_E_INVAL)
+        xy = np.empty((n, 2), dtype=np.int32)
+        d = np.empty((n, 2), dtype=np.float32)
+        h = np.empty((n, 3), dtype=np.int64)
+        m = self.lib.rd_debug_ridges(self.ctx, f, xy.ctypes.data_as(POINTER(c_int32)),
+                                     d.ctypes.data_as(POINTER(c_float)), h.ctypes.data_as(POINTER(c_int64)), n)
+        return xy, d, h
+
+    def debug_capture(self, acc=None, sm=None):
+        st = self.lib.rd_debug_capture(self.ctx, c_void_p(acc.data_ptr() if acc is not None else 0),
+                                       c_void_p(sm.data_ptr() if sm is not None else 0))
+        if st != RD_OK:
+            raise self._err(st)

@@ -48,9 +48,11 @@ class Frame:
 
 
 def _render(H, W, rings, profile, background):
-    """Sum ring profiles (functions of rho - R) on a flat background."""
+    """Sum ring profiles (functions of rho - R) on a flat background.
+    ``profile`` is one function for all rings or a list with one per ring."""
     img = np.full((H, W), float(background))
-    for cx, cy, R in rings:
+    profiles = profile if isinstance(profile, (list, tuple)) else [profile] * len(rings)
+    for (cx, cy, R), profile in zip(rings, profiles):
         ext = R + 12.0
         x0, x1 = max(0, int(np.floor(cx - ext))), min(W, int(np.ceil(cx + ext)) + 1)
         y0, y1 = max(0, int(np.floor(cy - ext))), min(H, int(np.ceil(cy + ext)) + 1)
@@ -116,9 +118,7 @@ def plain_full(seed=1002, H: int = 1024, W: int = 1024, n_rings: int = 150) -> F
     R = rng.uniform(10.0, 80.0, size=n_rings)
     K = rng.integers(2, 4, size=n_rings)
     rings = np.stack([cx, cy, R], axis=1)
-    img = np.full((H, W), 400.0)
-    for i in range(n_rings):
-        img += _render(H, W, rings[i:i + 1], _fringed_ring(600.0, 1.5, int(K[i])), 0.0)
+    img = _render(H, W, rings, [_fringed_ring(600.0, 1.5, int(k)) for k in K], 400.0)
     img = rng.poisson(img).astype(np.float64) + rng.normal(0.0, 10.0, size=img.shape)
     img = np.clip(np.rint(img), 0, 4095).astype(np.uint16)
     return Frame(img, rings, dict(PLAIN_FULL_PARAMS))

@@ -1,0 +1,91 @@
+"""The C ABI library builds, loads and exports every declared symbol; its
+host-side weight tables equal the oracle's (CPU only, no GPU work)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import ringdet as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1310_1371_gb300 import rd
+    return rd.load_library(build=True)
+
+
+def declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"\b(rd_[a-z_0-9]+)\s*\(", txt)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert "rd_create" in names and "rd_detect" in names and "rd_detect_host" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+@pytest.mark.parametrize("sigma", [0.7, 1.0, 1.5, 2.0, 2.5, 3.0, 3.3, 4.0])
+def test_gaussian_taps_match_oracle(lib, sigma):
+    from paper_1310_1371_gb300 import rd
+    s32 = float(np.float32(sigma))
+    assert np.array_equal(rd.rd_gaussian_taps(s32), O.gaussian_taps(s32))
+
+
+@pytest.mark.parametrize("sig_a,sig_b", [(0.05, 0.25), (0.1, 0.5), (0.0, 1.0), (0.07, 0.13)])
+def test_level_weights_match_oracle(lib, sig_a, sig_b):
+    from paper_1310_1371_gb300 import rd
+    a, b = float(np.float32(sig_a)), float(np.float32(sig_b))
+    for r in range(1, 162):
+        if np.ceil(3 * (a * r + b)) > 40:
+            break
+        assert np.array_equal(rd.rd_level_weights(a, b, r), O.smoothing_weights(r, a, b)), r
+
+
+@pytest.mark.parametrize("frac", [0.0, 0.2, 0.35, 0.5, 0.91])
+def test_peak_threshold_matches_oracle(lib, frac):
+    from paper_1310_1371_gb300 import rd
+    f = float(np.float32(frac))
+    for r in range(1, 251):
+        thr = O.peak_threshold(f, r)
+        n = rd.rd_peak_threshold(f, r)
+        # smallest integer N with N > thr
+        assert n > thr and n - 1 <= thr, (r, n, thr)
+
+
+def test_create_rejects_bad_params(lib):
+    from paper_1310_1371_gb300 import rd
+    good = dict(sigma=2.0, r_min=5, r_max=40, ridge_thresh=-1.0, peak_frac=0.35, vote_thresh=3)
+    bad = [dict(good, sigma=0.0), dict(good, sigma=5.0), dict(good, r_min=1), dict(good, r_max=4),
+           dict(good, ridge_thresh=0.5), dict(good, peak_frac=-1.0), dict(good, vote_thresh=-1),
+           dict(good, r_max=600)]
+    for kw in bad:
+        p = rd.make_params(**kw)
+        ctx = ctypes.c_void_p()
+        st = lib.rd_create(ctypes.byref(p), 256, 256, 1, ctypes.byref(ctx))
+        assert st == rd.RD_E_INVAL, kw
+        assert ctx.value is None
+        assert lib.rd_last_error(None)
+    p = rd.make_params(**good)
+    ctx = ctypes.c_void_p()
+    assert lib.rd_create(ctypes.byref(p), 8, 256, 1, ctypes.byref(ctx)) == rd.RD_E_INVAL
+    assert lib.rd_create(ctypes.byref(p), 256, 256, 0, ctypes.byref(ctx)) == rd.RD_E_INVAL
+
+
+def test_null_context_calls_fail_cleanly(lib):
+    from paper_1310_1371_gb300 import rd
+    assert lib.rd_destroy(None) == rd.RD_E_INVAL
+    assert lib.rd_detect(None, None, 1, 64, 64, 0, None, None, 0, None, None) == rd.RD_E_INVAL
+    st = rd.rd_stats()
+    assert lib.rd_get_stats(None, ctypes.byref(st)) == rd.RD_E_INVAL
+    assert lib.rd_debug_ridges(None, 0, None, None, None, 0) == -1
