@@ -119,13 +119,41 @@ __global__ void k_scan_add(int* out, const int* block_sums, long long n) {
 }
 
 // ---- K4 ---------------------------------------------------------------------
+// Capacities of the per-level "modified" lists (the paper's registering of
+// modified elements): voxels touched by a vote, and hotspots per level.  A
+// level that overflows a list is handled densely (same result, slower).
+constexpr int TOUCH_CAP = 2048;
+constexpr int HOT_CAP = 768;
 
 size_t vote_smem_bytes(int max_rw, int T, int max_qn) {
   int rw2 = T + 2;
-  return (size_t)max_rw * max_rw * 4 + (size_t)3 * rw2 * rw2 * 4 + (size_t)max_qn * 8 + (size_t)rw2 * rw2 * 2 + 64;
+  size_t words = ((size_t)max_rw * max_rw + 1) / 2;
+  return (size_t)max_qn * 8 + (size_t)3 * rw2 * rw2 * 4 + words * 4 + TOUCH_CAP * 2 + 4 * HOT_CAP * 2 + 64;
 }
 
-__global__ void __launch_bounds__(VOTE_THREADS) k_vote(VoteArgs a) {
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc));
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
+
+// warp-aggregated append of `val` to list[cap] with counter *cnt
+__device__ __forceinline__ void warp_push(bool pred, uint16_t val, int* cnt, uint16_t* list, int cap, int lane) {
+  unsigned m = __ballot_sync(0xffffffffu, pred);
+  if (!m) return;
+  int leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(cnt, __popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (pred) {
+    int k = base + __popc(m & ((1u << lane) - 1u));
+    if (k < cap) list[k] = val;
+  }
+}
+
+__device__ __forceinline__ uint32_t a16(const uint32_t* w, int i) { return (w[i >> 1] >> ((i & 1) << 4)) & 0xffffu; }
+
+__global__ void __launch_bounds__(VOTE_THREADS, 2) k_vote(VoteArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int b = blockIdx.x;
   const int cnt_raw = a.bin_cnt[b];
@@ -141,113 +169,180 @@ __global__ void __launch_bounds__(VOTE_THREADS) k_vote(VoteArgs a) {
   const int f = t / a.n_aty;
   const long long off = a.bin_off[b];
   const int cnt = (int)max(0LL, min((long long)cnt_raw, a.pool_cap - off));
-  if (threadIdx.x == 0 && cnt < cnt_raw) atomicOr(&a.stats->overflow, 2);
   const int4 sl = a.slabs[s];
   const int lo = sl.x, hi = sl.y, h = sl.z;
   const int T = a.T, RW = T + 2 * h, RW2 = T + 2;
   const int ox = tx * T - h, oy = ty * T - h;  // image coords of the slab's (0, 0)
   const int H = a.H, W = a.W;
+  const unsigned vthr = (unsigned)a.vote_thresh;
 
-  uint32_t* sA = reinterpret_cast<uint32_t*>(smem);                    // RW*RW (max_rw^2)
-  uint32_t* sN = sA + a.max_rw * a.max_rw;                             // 3 * RW2*RW2
-  int32_t* sQ = reinterpret_cast<int32_t*>(sN + 3 * RW2 * RW2);        // max_qn
-  int32_t* sQo = sQ + a.max_qn;                                        // max_qn
-  uint16_t* sHot = reinterpret_cast<uint16_t*>(sQo + a.max_qn);        // RW2*RW2
-  __shared__ int s_nhot;
+  int2* sQq = reinterpret_cast<int2*>(smem);                                   // max_qn (weight, offset)
+  uint32_t* sN = reinterpret_cast<uint32_t*>(sQq + a.max_qn);                  // 3 slots of RW2^2
+  uint32_t* sAw = sN + 3 * RW2 * RW2;                                          // RW^2 u16 counts
+  const int nAw = (a.max_rw * a.max_rw + 1) / 2;
+  uint16_t* sA16 = reinterpret_cast<uint16_t*>(sAw);
+  uint16_t* sTouch = reinterpret_cast<uint16_t*>(sAw + nAw);                   // TOUCH_CAP
+  uint16_t* sHot = sTouch + TOUCH_CAP;                                         // 4 x HOT_CAP, (vy << 8 | vx)
+  __shared__ int s_ntouch[2], s_nhot[4], s_dense[4];
   __shared__ unsigned long long s_votes, s_fb;
+
+  if (cnt < cnt_raw && tid == 0) atomicOr(&a.stats->overflow, 2);
+  for (int i = tid; i < (RW * RW + 1) / 2; i += VOTE_THREADS) sAw[i] = 0;
+  for (int i = tid; i < 3 * RW2 * RW2; i += VOTE_THREADS) sN[i] = 0;
   if (tid == 0) {
+    s_ntouch[0] = s_ntouch[1] = 0;
+    for (int k = 0; k < 4; ++k) s_nhot[k] = s_dense[k] = 0;
     s_votes = 0;
     s_fb = 0;
   }
+  __syncthreads();
 
   const size_t fbase = (size_t)f * a.rl.cap;
-  const int lv0 = a.r_min - 1;  // level index origin
+  const int lv0 = a.r_min - 1;
+  const int rounds = (cnt + VOTE_THREADS - 1) / VOTE_THREADS;
 
   for (int r = lo - 1; r <= hi + 1; ++r) {
     const int li = r - lv0;
     const int Rs = a.q_rad[li];
-    const int Wq = 2 * Rs + 1, nq = Wq * Wq;
-    for (int i = tid; i < RW * RW; i += VOTE_THREADS) sA[i] = 0;
-    for (int i = tid; i < nq; i += VOTE_THREADS) {
-      int dy = i / Wq, dx = i - dy * Wq;
-      sQ[i] = a.q_tab[a.q_off[li] + i];
-      sQo[i] = (dy - Rs) * RW + (dx - Rs);
-    }
-    if (tid == 0) s_nhot = 0;
-    __syncthreads();
+    const int nq = (2 * Rs + 1) * (2 * Rs + 1);
+    const int lst = r & 3, slot = r % 3;
+    // weights and slab-relative offsets of this level, copied asynchronously
+    const int2* gq = a.qq_tab + a.qq_off[s * (SLAB_LEVELS + 2) + (r - lo + 1)];
+    for (int i = tid; i < nq; i += VOTE_THREADS) cp_async8(&sQq[i], &gq[i]);
+    asm volatile("cp.async.commit_group;\n" ::);
 
-    // ---- cast this level's votes
+    // ---- phase 1a: clear level r-3's smoothed sums out of the slot
+    {
+      const int ol = (r + 1) & 3;  // list of level r - 3
+      uint32_t* os = sN + slot * RW2 * RW2;
+      if (s_dense[ol]) {
+        for (int i = tid; i < RW2 * RW2; i += VOTE_THREADS) os[i] = 0;
+      } else {
+        const int n = s_nhot[ol];
+        for (int k = tid; k < n; k += VOTE_THREADS) {
+          int v = sHot[ol * HOT_CAP + k];
+          os[(v >> 8) * RW2 + (v & 0xff)] = 0;
+        }
+      }
+    }
+
+    // ---- phase 1b: cast this level's votes into the slab
     const bool owned = (r >= lo && r <= hi) || (r == lo - 1 && lo == a.r_min) || (r == hi + 1 && hi == a.r_max);
     unsigned nv = 0, nfb = 0;
     const float rf = (float)r;
-    for (int e = tid; e < cnt; e += VOTE_THREADS) {
-      uint32_t ent = a.pool[off + e];
-      int i = (int)(ent >> 1);
-      bool neg = ent & 1u;
-      size_t g = fbase + i;
-      uint32_t xy = a.rl.xy[g];
-      float4 d = a.rl.dir[g];
-      float2 kv = a.rl.kvote[g];
-      int px = (int)(xy & 0xffffu), py = (int)(xy >> 16);
-      float sr = neg ? -rf : rf;
-      int vx = vote_offset(sr, rf, d.x, d.z, kv.x, kv.y);
-      int vy = vote_offset(sr, rf, d.y, d.w, kv.x, kv.y);
-      int bx, by;
-      if (vx == INT_MIN || vy == INT_MIN) {
-        ++nfb;
-        Eig64 e64 = eigen64(a.rl.hess[3 * g], a.rl.hess[3 * g + 1], a.rl.hess[3 * g + 2], a.D64);
-        double X = e64.X, Y = e64.Y;
-        if (X * (double)d.x + Y * (double)d.y < 0.0) {
-          X = -X;
-          Y = -Y;
+    for (int j = 0; j < rounds; ++j) {
+      const int e = j * VOTE_THREADS + tid;
+      bool hit = false;
+      int la = 0;
+      if (e < cnt) {
+        uint32_t ent = a.pool[off + e];
+        int i = (int)(ent >> 1);
+        bool neg = ent & 1u;
+        size_t g = fbase + i;
+        uint32_t xy = a.rl.xy[g];
+        float4 d = a.rl.dir[g];
+        float2 kv = a.rl.kvote[g];
+        int px = (int)(xy & 0xffffu), py = (int)(xy >> 16);
+        float sr = neg ? -rf : rf;
+        int vx = vote_offset(sr, rf, d.x, d.z, kv.x, kv.y);
+        int vy = vote_offset(sr, rf, d.y, d.w, kv.x, kv.y);
+        int bx, by;
+        if (vx == INT_MIN || vy == INT_MIN) {
+          ++nfb;
+          Eig64 e64 = eigen64(a.rl.hess[3 * g], a.rl.hess[3 * g + 1], a.rl.hess[3 * g + 2], a.D64);
+          double X = e64.X, Y = e64.Y;
+          if (X * (double)d.x + Y * (double)d.y < 0.0) {
+            X = -X;
+            Y = -Y;
+          }
+          bx = vote_bin64(px, (double)sr, X);
+          by = vote_bin64(py, (double)sr, Y);
+        } else {
+          bx = px + vx;
+          by = py + vy;
         }
-        bx = vote_bin64(px, (double)sr, X);
-        by = vote_bin64(py, (double)sr, Y);
-      } else {
-        bx = px + vx;
-        by = py + vy;
+        int lx = bx - ox, ly = by - oy;
+        if (bx >= 0 && bx < W && by >= 0 && by < H && lx >= 0 && lx < RW && ly >= 0 && ly < RW) {
+          hit = true;
+          la = ly * RW + lx;
+          if (owned && lx >= h && lx < h + T && ly >= h && ly < h + T) ++nv;
+        }
       }
-      if (bx < 0 || bx >= W || by < 0 || by >= H) continue;
-      int lx = bx - ox, ly = by - oy;
-      if (lx < 0 || lx >= RW || ly < 0 || ly >= RW) continue;
-      atomicAdd(&sA[ly * RW + lx], 1u);
-      if (owned && lx >= h && lx < h + T && ly >= h && ly < h + T) ++nv;
+      unsigned oldc = 0;
+      if (hit) {
+        unsigned sh = (la & 1) << 4;
+        oldc = (atomicAdd(&sAw[la >> 1], 1u << sh) >> sh) & 0xffffu;
+      }
+      warp_push(hit && oldc == 0, (uint16_t)la, &s_ntouch[r & 1], sTouch, TOUCH_CAP, lane);
+      int vyr = 0, vxr = 0;
+      bool hot = false;
+      if (hit && oldc == vthr) {
+        int ly = la / RW, lx = la - ly * RW;
+        vyr = ly - h + 1;
+        vxr = lx - h + 1;
+        hot = vyr >= 0 && vyr < RW2 && vxr >= 0 && vxr < RW2;
+      }
+      warp_push(hot, (uint16_t)((vyr << 8) | vxr), &s_nhot[lst], sHot + lst * HOT_CAP, HOT_CAP, lane);
     }
     if (nv) atomicAdd(&s_votes, (unsigned long long)nv);
     if (nfb) atomicAdd(&s_fb, (unsigned long long)nfb);
+    cp_async_wait_all();
     __syncthreads();
 
-    // ---- hotspots of this level on the tile plus a one-voxel ring
-    uint32_t* slot = sN + (r % 3) * RW2 * RW2;
-    for (int v = tid; v < RW2 * RW2; v += VOTE_THREADS) {
-      int vy_ = v / RW2, vx_ = v - vy_ * RW2;
-      int gx = tx * T - 1 + vx_, gy = ty * T - 1 + vy_;
-      uint32_t av = 0;
-      if (gx >= 0 && gx < W && gy >= 0 && gy < H) av = sA[(vy_ + h - 1) * RW + (vx_ + h - 1)];
-      slot[v] = 0;
-      if ((long long)av > (long long)a.vote_thresh) {
-        int k = atomicAdd(&s_nhot, 1);
-        sHot[k] = (uint16_t)v;
-      }
+    // ---- phase 2: radius-dependent smoothing at this level's hotspots
+    uint32_t* cur = sN + slot * RW2 * RW2;
+    const int nhot = s_nhot[lst];
+    if (tid == 0) {
+      // counters whose last reader has passed a barrier and whose next writer
+      // is two barriers away: the touch counter of level r + 1 and the list
+      // of level r - 3 (cleared in phase 1a above), reused by level r + 1
+      s_ntouch[(r + 1) & 1] = 0;
+      s_nhot[(r + 1) & 3] = 0;
+      s_dense[(r + 1) & 3] = 0;
     }
-    __syncthreads();
-
-    // ---- radius-dependent smoothing at the hotspots (one warp per hotspot)
-    const int nhot = s_nhot;
-    for (int k = warp; k < nhot; k += NW) {
-      int v = sHot[k];
-      int vy_ = v / RW2, vx_ = v - vy_ * RW2;
-      int center = (vy_ + h - 1) * RW + (vx_ + h - 1);
-      unsigned long long acc = 0;
-      for (int q = lane; q < nq; q += 32) acc += (unsigned long long)(uint32_t)sQ[q] * sA[center + sQo[q]];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) {
-        if (acc > 0xffffffffULL) {
-          atomicOr(&a.stats->overflow, 16);
-          acc = 0xffffffffULL;
+    if (nhot <= HOT_CAP) {
+      for (int k = warp; k < nhot; k += NW) {
+        int v = sHot[lst * HOT_CAP + k];
+        int vyr = v >> 8, vxr = v & 0xff;
+        int center = (vyr + h - 1) * RW + (vxr + h - 1);
+        unsigned long long acc = 0;
+        for (int q = lane; q < nq; q += 32) {
+          int2 w = sQq[q];
+          acc += (unsigned long long)(uint32_t)w.x * a16(sAw, center + w.y);
         }
-        slot[v] = (uint32_t)acc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+          if (acc > 0xffffffffULL) {
+            atomicOr(&a.stats->overflow, 16);
+            acc = 0xffffffffULL;
+          }
+          cur[vyr * RW2 + vxr] = (uint32_t)acc;
+        }
+      }
+    } else {
+      // dense fallback: every in-image voxel of the ring region
+      if (tid == 0) s_dense[lst] = 1;
+      for (int v = warp; v < RW2 * RW2; v += NW) {
+        int vyr = v / RW2, vxr = v - vyr * RW2;
+        int gx = tx * T - 1 + vxr, gy = ty * T - 1 + vyr;
+        if (gx < 0 || gx >= W || gy < 0 || gy >= H) continue;
+        int center = (vyr + h - 1) * RW + (vxr + h - 1);
+        if (a16(sAw, center) <= vthr) continue;
+        unsigned long long acc = 0;
+        for (int q = lane; q < nq; q += 32) {
+          int2 w = sQq[q];
+          acc += (unsigned long long)(uint32_t)w.x * a16(sAw, center + w.y);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+          if (acc > 0xffffffffULL) {
+            atomicOr(&a.stats->overflow, 16);
+            acc = 0xffffffffULL;
+          }
+          cur[v] = (uint32_t)acc;
+        }
       }
     }
     __syncthreads();
@@ -257,21 +352,34 @@ __global__ void __launch_bounds__(VOTE_THREADS) k_vote(VoteArgs a) {
         int iy = v / T, ix = v - iy * T;
         int gx = tx * T + ix, gy = ty * T + iy;
         if (gx < W && gy < H) {
-          a.dbg_acc[((size_t)li * H + gy) * W + gx] = (int32_t)sA[(iy + h) * RW + (ix + h)];
-          if (a.dbg_sm) a.dbg_sm[((size_t)li * H + gy) * W + gx] = slot[(iy + 1) * RW2 + ix + 1];
+          a.dbg_acc[((size_t)li * H + gy) * W + gx] = (int32_t)a16(sAw, (iy + h) * RW + (ix + h));
+          if (a.dbg_sm) a.dbg_sm[((size_t)li * H + gy) * W + gx] = cur[(iy + 1) * RW2 + ix + 1];
         }
       }
+      __syncthreads();  // the capture reads the slab before phase 3b undoes it
     }
 
-    // ---- peak test of level r - 1 (levels r - 2, r - 1, r are in the buffer)
+    // ---- phase 3a: peak test of level r - 1 (levels r - 2, r - 1, r are in the slots)
     const int rp = r - 1;
     if (rp >= lo && rp <= hi) {
-      const uint32_t* Nlo = sN + ((rp + 2) % 3) * RW2 * RW2;  // level rp - 1
+      const uint32_t* Nlo = sN + ((rp + 2) % 3) * RW2 * RW2;
       const uint32_t* Nmid = sN + (rp % 3) * RW2 * RW2;
-      const uint32_t* Nhi = slot;                             // level rp + 1
+      const uint32_t* Nhi = cur;
       const unsigned long long thr = a.nthr[rp - lv0];
-      for (int v = tid; v < T * T; v += VOTE_THREADS) {
-        int iy = v / T, ix = v - iy * T;
+      const int pl = rp & 3;
+      const bool dense = s_dense[pl] != 0;
+      const int n = dense ? T * T : s_nhot[pl];
+      for (int k = tid; k < n; k += VOTE_THREADS) {
+        int iy, ix;
+        if (dense) {
+          iy = k / T;
+          ix = k - iy * T;
+        } else {
+          int v = sHot[pl * HOT_CAP + k];
+          iy = (v >> 8) - 1;
+          ix = (v & 0xff) - 1;
+          if (iy < 0 || iy >= T || ix < 0 || ix >= T) continue;
+        }
         int gx = tx * T + ix, gy = ty * T + iy;
         if (gx >= W || gy >= H) continue;
         int c = (iy + 1) * RW2 + ix + 1;
@@ -293,17 +401,24 @@ __global__ void __launch_bounds__(VOTE_THREADS) k_vote(VoteArgs a) {
             }
         }
         if (ok) {
-          int k = atomicAdd(&a.peak_count[f], 1);
-          if (k < a.peak_cap)
-            a.peaks[(size_t)f * a.peak_cap + k] = make_int4(gx, gy, rp, (int)nv0);
+          int kk = atomicAdd(&a.peak_count[f], 1);
+          if (kk < a.peak_cap)
+            a.peaks[(size_t)f * a.peak_cap + kk] = make_int4(gx, gy, rp, (int)nv0);
           else
             atomicOr(&a.stats->overflow, 4);
           atomicAdd(&a.stats->peaks, 1ULL);
         }
       }
     }
-    // the next level's first barrier orders these reads before the buffer
-    // slot is overwritten
+
+    // ---- phase 3b: undo this level's votes (touched voxels only)
+    const int ntouch = s_ntouch[r & 1];
+    if (ntouch <= TOUCH_CAP) {
+      for (int k = tid; k < ntouch; k += VOTE_THREADS) sA16[sTouch[k]] = 0;
+    } else {
+      for (int i = tid; i < (RW * RW + 1) / 2; i += VOTE_THREADS) sAw[i] = 0;
+    }
+    __syncthreads();
   }
   __syncthreads();
   if (tid == 0) {

@@ -36,9 +36,9 @@ struct rd_ctx {
   std::vector<int4> h_slabs;
   // device buffers
   int4* slabs = nullptr;
-  int* q_off = nullptr;
   int* q_rad = nullptr;
-  int32_t* q_tab = nullptr;
+  int* qq_off = nullptr;
+  int2* qq_tab = nullptr;
   unsigned long long* nthr = nullptr;
   RidgeList rl{};
   int* bin_cnt = nullptr;
@@ -134,7 +134,7 @@ static rd_status fail(rd_ctx* c, rd_status s, const std::string& m) {
 }
 
 static void free_all(rd_ctx* c) {
-  void* ptrs[] = {c->slabs, c->q_off, c->q_rad, c->q_tab, c->nthr, c->rl.xy, c->rl.dir, c->rl.kvote, c->rl.hess,
+  void* ptrs[] = {c->slabs, c->q_rad, c->qq_off, c->qq_tab, c->nthr, c->rl.xy, c->rl.dir, c->rl.kvote, c->rl.hess,
                   c->rl.count, c->rl.tile_off, c->rl.tile_cnt, c->bin_cnt, c->bin_off, c->bin_fill, c->block_sums,
                   c->bin_total, c->pool, c->peaks, c->peak_count, c->stats, c->stage_frames, c->stage_rings,
                   c->stage_counts, c->stage_offsets};
@@ -153,7 +153,7 @@ static std::string validate(const rd_params* p) {
   if (p->r_min < 2 || p->r_max < p->r_min || p->r_max > 250) return "need 2 <= r_min <= r_max <= 250";
   if (!(p->ridge_thresh <= 0.0f)) return "ridge_thresh must be <= 0";
   if (!(p->peak_frac >= 0.0f) || !std::isfinite(p->peak_frac)) return "peak_frac must be finite and >= 0";
-  if (p->vote_thresh < 0) return "vote_thresh must be >= 0";
+  if (p->vote_thresh < 0 || p->vote_thresh > 65534) return "vote_thresh must be in [0, 65534]";
   if (!(p->annulus_w >= 0.0f) || p->annulus_w > 64.0f) return "annulus_w must be in [0, 64]";
   if (!(p->sig_a >= 0.0f) || !std::isfinite(p->sig_a) || !std::isfinite(p->sig_b)) return "sig_a must be >= 0";
   if (!(level_sigma(p->sig_a, p->sig_b, p->r_min - 1) > 0.0)) return "sigma(r) must be > 0 for every level";
@@ -218,6 +218,21 @@ extern "C" rd_status rd_create(const rd_params* params, int max_H, int max_W, in
     c->max_rw = std::max(c->max_rw, ACC_T + 2 * h);
   }
   c->n_slabs = (int)c->h_slabs.size();
+  // per slab: (weight, offset) of every tap of its voting levels; offsets are
+  // relative to the window centre in the slab's shared-memory layout
+  std::vector<int> h_qqoff((size_t)c->n_slabs * (SLAB_LEVELS + 2), 0);
+  std::vector<int2> h_qqtab;
+  for (int si = 0; si < c->n_slabs; ++si) {
+    const int4 sl = c->h_slabs[si];
+    const int RW = ACC_T + 2 * sl.z;
+    for (int r = sl.x - 1; r <= sl.y + 1; ++r) {
+      const int li = r - lv0, Rs = h_qrad[li], Wq = 2 * Rs + 1;
+      h_qqoff[(size_t)si * (SLAB_LEVELS + 2) + (r - sl.x + 1)] = (int)h_qqtab.size();
+      const int32_t* q = h_qtab.data() + h_qoff[li];
+      for (int dy = 0; dy < Wq; ++dy)
+        for (int dx = 0; dx < Wq; ++dx) h_qqtab.push_back(make_int2(q[dy * Wq + dx], (dy - Rs) * RW + (dx - Rs)));
+    }
+  }
   if (vote_smem_bytes(c->max_rw, ACC_T, c->max_qn) > 227 * 1024) {
     delete c;
     return fail(nullptr, RD_E_INVAL, "radius range needs more shared memory than one SM has");
@@ -231,8 +246,9 @@ extern "C" rd_status rd_create(const rd_params* params, int max_H, int max_W, in
   const size_t nrec = (size_t)c->rl.cap * max_batch;
   c->n_bins_max = (long long)max_batch * n_atx * n_aty * c->n_slabs;
   c->pool_cap = std::min<long long>((long long)max_batch * max_H * max_W * 2, (1LL << 31) - 1);
-  bool ok = dalloc(&c->slabs, c->n_slabs) && dalloc(&c->q_off, c->n_levels) && dalloc(&c->q_rad, c->n_levels) &&
-            dalloc(&c->q_tab, h_qtab.size()) && dalloc(&c->nthr, c->n_levels) && dalloc(&c->rl.xy, nrec) &&
+  bool ok = dalloc(&c->slabs, c->n_slabs) && dalloc(&c->q_rad, c->n_levels) &&
+            dalloc(&c->qq_off, h_qqoff.size()) && dalloc(&c->qq_tab, h_qqtab.size()) &&
+            dalloc(&c->nthr, c->n_levels) && dalloc(&c->rl.xy, nrec) &&
             dalloc(&c->rl.dir, nrec) && dalloc(&c->rl.kvote, nrec) && dalloc(&c->rl.hess, 3 * nrec) &&
             dalloc(&c->rl.count, max_batch) && dalloc(&c->rl.tile_off, (size_t)max_batch * n_stx * n_sty) &&
             dalloc(&c->rl.tile_cnt, (size_t)max_batch * n_stx * n_sty) && dalloc(&c->bin_cnt, c->n_bins_max) &&
@@ -250,10 +266,11 @@ extern "C" rd_status rd_create(const rd_params* params, int max_H, int max_W, in
     return fail(nullptr, RD_E_NOMEM, "device allocation failed");
   }
   cudaError_t e = cudaMemcpy(c->slabs, c->h_slabs.data(), sizeof(int4) * c->n_slabs, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(c->q_off, h_qoff.data(), sizeof(int) * c->n_levels, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(c->q_rad, h_qrad.data(), sizeof(int) * c->n_levels, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
-    e = cudaMemcpy(c->q_tab, h_qtab.data(), sizeof(int32_t) * h_qtab.size(), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(c->qq_off, h_qqoff.data(), sizeof(int) * h_qqoff.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c->qq_tab, h_qqtab.data(), sizeof(int2) * h_qqtab.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(c->nthr, h_nthr.data(), sizeof(unsigned long long) * c->n_levels, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(c->stats, 0, sizeof(DevStats));
@@ -357,9 +374,9 @@ extern "C" rd_status rd_detect(rd_ctx* c, const void* frames_dev, int n, int H, 
   va.bin_off = c->bin_off;
   va.pool = c->pool;
   va.pool_cap = c->pool_cap;
-  va.q_off = c->q_off;
   va.q_rad = c->q_rad;
-  va.q_tab = c->q_tab;
+  va.qq_off = c->qq_off;
+  va.qq_tab = c->qq_tab;
   va.nthr = c->nthr;
   va.r_min = c->p.r_min;
   va.r_max = c->p.r_max;

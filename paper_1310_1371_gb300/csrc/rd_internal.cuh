@@ -93,9 +93,9 @@ struct VoteArgs {
   const int* bin_off;
   const uint32_t* pool;
   long long pool_cap;
-  const int* q_off;          // per voting level (index r - (r_min - 1)): offset into q_tab
-  const int* q_rad;          // per voting level: R_s
-  const int32_t* q_tab;      // concatenated (2R_s+1)^2 weights, row-major (dy, dx)
+  const int* q_rad;          // per voting level (index r - (r_min - 1)): R_s
+  const int* qq_off;         // per (slab, level lo-1 .. hi+1): offset into qq_tab
+  const int2* qq_tab;        // (weight, slab-relative smem offset) per window tap, row-major (dy, dx)
   const unsigned long long* nthr;  // per voting level: smallest N passing the float threshold
   int r_min, r_max, vote_thresh;
   int4* peaks;               // per frame: (x, y, r, N)

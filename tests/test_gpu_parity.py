@@ -76,10 +76,12 @@ def assert_ridges_match(ridge, image, p):
     ys, xs = ref_xy[:, 1], ref_xy[:, 0]
     assert np.array_equal(h[:, 0], hxx[ys, xs]) and np.array_equal(h[:, 1], hyy[ys, xs])
     assert np.array_equal(h[:, 2], hxy[ys, xs])
+    if len(xy) == 0:
+        return
     # direction: same line (sign conventions agree except where X == 0 to
     # within rounding), within float32 rounding of the exact direction
     dot = np.abs((d.astype(np.float64) * ref_X).sum(1))
-    assert np.all(dot > 1 - 1e-12)
+    assert np.all(dot > 1 - 1e-6)
     assert np.abs(np.abs(d) - np.abs(ref_X)).max() < 1.2e-7
 
 
