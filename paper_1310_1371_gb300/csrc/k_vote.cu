@@ -119,17 +119,28 @@ __global__ void k_scan_add(int* out, const int* block_sums, long long n) {
 }
 
 // ---- K4 ---------------------------------------------------------------------
-// Capacities of the per-level "modified" lists (the paper's registering of
-// modified elements): voxels touched by a vote, and hotspots per level.  A
-// level that overflows a list is handled densely (same result, slower).
-constexpr int TOUCH_CAP = 2048;
+// Capacity of the per-level hotspot lists (the paper's registering of
+// modified elements).  A level that overflows its list is handled densely
+// (same result, slower).
 constexpr int HOT_CAP = 768;
+constexpr int ECACHE = 4;   // bin entries a thread keeps in registers across levels
 
-size_t vote_smem_bytes(int max_rw, int T, int max_qn) {
-  int rw2 = T + 2;
-  size_t words = ((size_t)max_rw * max_rw + 1) / 2;
-  return (size_t)max_qn * 8 + (size_t)3 * rw2 * rw2 * 4 + words * 4 + TOUCH_CAP * 2 + 4 * HOT_CAP * 2 + 64;
+// Shared-memory layout of K4; every region starts on a 16-byte boundary.
+struct VoteSmem {
+  size_t q, n, a, hot, total;
+};
+__host__ __device__ __forceinline__ size_t round16(size_t x) { return (x + 15) & ~(size_t)15; }
+__host__ __device__ __forceinline__ VoteSmem vote_smem_layout(int max_rw, int T, int max_qn) {
+  const size_t rw2 = (size_t)T + 2;
+  VoteSmem L;
+  L.q = 0;                                                        // int2 (weight, offset) x max_qn
+  L.n = round16((size_t)max_qn * 8);                              // u32 x 3 slots x rw2^2
+  L.a = L.n + round16(3 * rw2 * rw2 * 4);                         // u16 counts x max_rw^2
+  L.hot = L.a + round16((((size_t)max_rw * max_rw + 1) / 2) * 4);  // u16 x 4 x HOT_CAP
+  L.total = L.hot + round16((size_t)4 * HOT_CAP * 2);
+  return L;
 }
+size_t vote_smem_bytes(int max_rw, int T, int max_qn) { return vote_smem_layout(max_rw, T, max_qn).total; }
 
 __device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
   unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
@@ -153,6 +164,67 @@ __device__ __forceinline__ void warp_push(bool pred, uint16_t val, int* cnt, uin
 
 __device__ __forceinline__ uint32_t a16(const uint32_t* w, int i) { return (w[i >> 1] >> ((i & 1) << 4)) & 0xffffu; }
 
+// A bin entry as a thread holds it across the levels of its slab.
+struct VEnt {
+  uint32_t xy;     // x | y << 16
+  uint32_t ent;    // ridge index << 1 | negative sign
+  float X, Y, kf;  // direction (hi parts) and fast-path margin coefficient
+};
+
+__device__ __forceinline__ VEnt load_ent(const VoteArgs& a, size_t fbase, long long off, int e) {
+  VEnt v;
+  v.ent = a.pool[off + e];
+  size_t g = fbase + (v.ent >> 1);
+  v.xy = a.rl.xy[g];
+  float4 d = a.rl.dir[g];
+  v.X = d.x;
+  v.Y = d.y;
+  v.kf = a.rl.kvote[g].x;
+  return v;
+}
+
+constexpr float ROUND_MAGIC = 12582912.0f;  // 1.5 * 2^23: adding it rounds |t| < 2^22 to an integer
+constexpr int ROUND_MAGIC_BITS = 0x4B400000;
+
+// Bin offsets (floor(sr X + 1/2), floor(sr Y + 1/2)) of one vote.  Fast path:
+// round to nearest with the magic constant; the result equals the half-up
+// rounding of the double-precision definition when the exact remainder is
+// more than the error margin away from 1/2.  Otherwise the double-float and
+// then the double-precision paths decide.  Returns the number of FP64
+// fallbacks taken (0 or 1).
+__device__ __forceinline__ int vote_bins(const VoteArgs& a, size_t fbase, const VEnt& v, float rf, int& ox, int& oy) {
+  const float sr = (v.ent & 1u) ? -rf : rf;
+  const float m = __fmaf_rn(rf, v.kf, 1e-10f);
+  const float tx = __fmul_rn(sr, v.X), ty = __fmul_rn(sr, v.Y);
+  const float fx = __fadd_rn(tx, ROUND_MAGIC), fy = __fadd_rn(ty, ROUND_MAGIC);
+  const float dx = __fsub_rn(tx, __fsub_rn(fx, ROUND_MAGIC));  // exact remainder in [-1/2, 1/2]
+  const float dy = __fsub_rn(ty, __fsub_rn(fy, ROUND_MAGIC));
+  ox = __float_as_int(fx) - ROUND_MAGIC_BITS;
+  oy = __float_as_int(fy) - ROUND_MAGIC_BITS;
+  if (__fadd_rn(fabsf(dx), m) < 0.5f && __fadd_rn(fabsf(dy), m) < 0.5f) return 0;
+  // slow path: double-float refinement, then the double-precision definition
+  const size_t g = fbase + (v.ent >> 1);
+  const float4 d = a.rl.dir[g];
+  const float2 kv = a.rl.kvote[g];
+  int vx = vote_offset(sr, rf, d.x, d.z, kv.x, kv.y);
+  int vy = vote_offset(sr, rf, d.y, d.w, kv.x, kv.y);
+  if (vx != INT_MIN && vy != INT_MIN) {
+    ox = vx;
+    oy = vy;
+    return 0;
+  }
+  const int px = (int)(v.xy & 0xffffu), py = (int)(v.xy >> 16);
+  Eig64 e64 = eigen64(a.rl.hess[3 * g], a.rl.hess[3 * g + 1], a.rl.hess[3 * g + 2], a.D64);
+  double X = e64.X, Y = e64.Y;
+  if (X * (double)d.x + Y * (double)d.y < 0.0) {
+    X = -X;
+    Y = -Y;
+  }
+  ox = vote_bin64(px, (double)sr, X) - px;
+  oy = vote_bin64(py, (double)sr, Y) - py;
+  return 1;
+}
+
 __global__ void __launch_bounds__(VOTE_THREADS, 2) k_vote(VoteArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int b = blockIdx.x;
@@ -172,34 +244,42 @@ __global__ void __launch_bounds__(VOTE_THREADS, 2) k_vote(VoteArgs a) {
   const int4 sl = a.slabs[s];
   const int lo = sl.x, hi = sl.y, h = sl.z;
   const int T = a.T, RW = T + 2 * h, RW2 = T + 2;
-  const int ox = tx * T - h, oy = ty * T - h;  // image coords of the slab's (0, 0)
+  const int ox0 = tx * T - h, oy0 = ty * T - h;  // image coords of the slab's (0, 0)
   const int H = a.H, W = a.W;
   const unsigned vthr = (unsigned)a.vote_thresh;
 
-  int2* sQq = reinterpret_cast<int2*>(smem);                                   // max_qn (weight, offset)
-  uint32_t* sN = reinterpret_cast<uint32_t*>(sQq + a.max_qn);                  // 3 slots of RW2^2
-  uint32_t* sAw = sN + 3 * RW2 * RW2;                                          // RW^2 u16 counts
-  const int nAw = (a.max_rw * a.max_rw + 1) / 2;
-  uint16_t* sA16 = reinterpret_cast<uint16_t*>(sAw);
-  uint16_t* sTouch = reinterpret_cast<uint16_t*>(sAw + nAw);                   // TOUCH_CAP
-  uint16_t* sHot = sTouch + TOUCH_CAP;                                         // 4 x HOT_CAP, (vy << 8 | vx)
-  __shared__ int s_ntouch[2], s_nhot[4], s_dense[4];
+  const VoteSmem L = vote_smem_layout(a.max_rw, T, a.max_qn);
+  int2* sQq = reinterpret_cast<int2*>(smem + L.q);                             // max_qn (weight, offset)
+  uint32_t* sN = reinterpret_cast<uint32_t*>(smem + L.n);                      // 3 slots of RW2^2
+  uint32_t* sAw = reinterpret_cast<uint32_t*>(smem + L.a);                     // RW^2 u16 counts
+  const int nAw4 = (((RW * RW + 1) / 2) + 3) / 4;                              // uint4 words in use (<= region)
+  uint16_t* sHot = reinterpret_cast<uint16_t*>(smem + L.hot);                  // 4 x HOT_CAP, (vy << 8 | vx)
+  __shared__ int s_nhot[4], s_dense[4];
   __shared__ unsigned long long s_votes, s_fb;
 
   if (cnt < cnt_raw && tid == 0) atomicOr(&a.stats->overflow, 2);
-  for (int i = tid; i < (RW * RW + 1) / 2; i += VOTE_THREADS) sAw[i] = 0;
+  {
+    uint4* w4 = reinterpret_cast<uint4*>(sAw);
+    for (int i = tid; i < nAw4; i += VOTE_THREADS) w4[i] = make_uint4(0, 0, 0, 0);
+  }
   for (int i = tid; i < 3 * RW2 * RW2; i += VOTE_THREADS) sN[i] = 0;
   if (tid == 0) {
-    s_ntouch[0] = s_ntouch[1] = 0;
     for (int k = 0; k < 4; ++k) s_nhot[k] = s_dense[k] = 0;
     s_votes = 0;
     s_fb = 0;
   }
-  __syncthreads();
 
   const size_t fbase = (size_t)f * a.rl.cap;
   const int lv0 = a.r_min - 1;
   const int rounds = (cnt + VOTE_THREADS - 1) / VOTE_THREADS;
+  VEnt ec[ECACHE];
+#pragma unroll
+  for (int j = 0; j < ECACHE; ++j) {
+    int e = j * VOTE_THREADS + tid;
+    if (e < cnt) ec[j] = load_ent(a, fbase, off, e);
+    else ec[j] = VEnt{0u, 0u, 0.0f, 0.0f, 0.0f};
+  }
+  __syncthreads();
 
   for (int r = lo - 1; r <= hi + 1; ++r) {
     const int li = r - lv0;
@@ -232,40 +312,27 @@ __global__ void __launch_bounds__(VOTE_THREADS, 2) k_vote(VoteArgs a) {
     const float rf = (float)r;
     for (int j = 0; j < rounds; ++j) {
       const int e = j * VOTE_THREADS + tid;
+      const bool valid = e < cnt;
+      VEnt v;
+      if (j < ECACHE) {
+#pragma unroll
+        for (int q = 0; q < ECACHE; ++q)
+          if (q == j) v = ec[q];
+      } else {
+        v = valid ? load_ent(a, fbase, off, e) : VEnt{0u, 0u, 0.0f, 0.0f, 0.0f};
+      }
       bool hit = false;
       int la = 0;
-      if (e < cnt) {
-        uint32_t ent = a.pool[off + e];
-        int i = (int)(ent >> 1);
-        bool neg = ent & 1u;
-        size_t g = fbase + i;
-        uint32_t xy = a.rl.xy[g];
-        float4 d = a.rl.dir[g];
-        float2 kv = a.rl.kvote[g];
-        int px = (int)(xy & 0xffffu), py = (int)(xy >> 16);
-        float sr = neg ? -rf : rf;
-        int vx = vote_offset(sr, rf, d.x, d.z, kv.x, kv.y);
-        int vy = vote_offset(sr, rf, d.y, d.w, kv.x, kv.y);
-        int bx, by;
-        if (vx == INT_MIN || vy == INT_MIN) {
-          ++nfb;
-          Eig64 e64 = eigen64(a.rl.hess[3 * g], a.rl.hess[3 * g + 1], a.rl.hess[3 * g + 2], a.D64);
-          double X = e64.X, Y = e64.Y;
-          if (X * (double)d.x + Y * (double)d.y < 0.0) {
-            X = -X;
-            Y = -Y;
-          }
-          bx = vote_bin64(px, (double)sr, X);
-          by = vote_bin64(py, (double)sr, Y);
-        } else {
-          bx = px + vx;
-          by = py + vy;
-        }
-        int lx = bx - ox, ly = by - oy;
-        if (bx >= 0 && bx < W && by >= 0 && by < H && lx >= 0 && lx < RW && ly >= 0 && ly < RW) {
+      if (valid) {
+        int vx, vy;
+        nfb += vote_bins(a, fbase, v, rf, vx, vy);
+        const int bx = (int)(v.xy & 0xffffu) + vx, by = (int)(v.xy >> 16) + vy;
+        const int lx = bx - ox0, ly = by - oy0;
+        if ((unsigned)bx < (unsigned)W && (unsigned)by < (unsigned)H && (unsigned)lx < (unsigned)RW &&
+            (unsigned)ly < (unsigned)RW) {
           hit = true;
           la = ly * RW + lx;
-          if (owned && lx >= h && lx < h + T && ly >= h && ly < h + T) ++nv;
+          if (owned && (unsigned)(lx - h) < (unsigned)T && (unsigned)(ly - h) < (unsigned)T) ++nv;
         }
       }
       unsigned oldc = 0;
@@ -273,7 +340,6 @@ __global__ void __launch_bounds__(VOTE_THREADS, 2) k_vote(VoteArgs a) {
         unsigned sh = (la & 1) << 4;
         oldc = (atomicAdd(&sAw[la >> 1], 1u << sh) >> sh) & 0xffffu;
       }
-      warp_push(hit && oldc == 0, (uint16_t)la, &s_ntouch[r & 1], sTouch, TOUCH_CAP, lane);
       int vyr = 0, vxr = 0;
       bool hot = false;
       if (hit && oldc == vthr) {
@@ -293,10 +359,7 @@ __global__ void __launch_bounds__(VOTE_THREADS, 2) k_vote(VoteArgs a) {
     uint32_t* cur = sN + slot * RW2 * RW2;
     const int nhot = s_nhot[lst];
     if (tid == 0) {
-      // counters whose last reader has passed a barrier and whose next writer
-      // is two barriers away: the touch counter of level r + 1 and the list
-      // of level r - 3 (cleared in phase 1a above), reused by level r + 1
-      s_ntouch[(r + 1) & 1] = 0;
+      // the list of level r - 3 (cleared in phase 1a above) is reused by level r + 1
       s_nhot[(r + 1) & 3] = 0;
       s_dense[(r + 1) & 3] = 0;
     }
@@ -356,7 +419,7 @@ __global__ void __launch_bounds__(VOTE_THREADS, 2) k_vote(VoteArgs a) {
           if (a.dbg_sm) a.dbg_sm[((size_t)li * H + gy) * W + gx] = cur[(iy + 1) * RW2 + ix + 1];
         }
       }
-      __syncthreads();  // the capture reads the slab before phase 3b undoes it
+      __syncthreads();  // the capture reads the slab before phase 3b clears it
     }
 
     // ---- phase 3a: peak test of level r - 1 (levels r - 2, r - 1, r are in the slots)
@@ -411,16 +474,13 @@ __global__ void __launch_bounds__(VOTE_THREADS, 2) k_vote(VoteArgs a) {
       }
     }
 
-    // ---- phase 3b: undo this level's votes (touched voxels only)
-    const int ntouch = s_ntouch[r & 1];
-    if (ntouch <= TOUCH_CAP) {
-      for (int k = tid; k < ntouch; k += VOTE_THREADS) sA16[sTouch[k]] = 0;
-    } else {
-      for (int i = tid; i < (RW * RW + 1) / 2; i += VOTE_THREADS) sAw[i] = 0;
+    // ---- phase 3b: clear the slab for the next level (16-byte stores)
+    {
+      uint4* w4 = reinterpret_cast<uint4*>(sAw);
+      for (int i = tid; i < nAw4; i += VOTE_THREADS) w4[i] = make_uint4(0, 0, 0, 0);
     }
     __syncthreads();
   }
-  __syncthreads();
   if (tid == 0) {
     if (s_votes) atomicAdd(&a.stats->votes, s_votes);
     if (s_fb) atomicAdd(&a.stats->fallbacks, s_fb);
