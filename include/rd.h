@@ -186,8 +186,14 @@ int       rd_get_timing(rd_ctx* ctx, float* ms, int cap);
  * rd_debug_capture makes the next rd_detect write frame 0's raw accumulator
  * (acc_dev, int32) and smoothed accumulator (sm_dev, uint32) for every voting
  * level r_min-1 .. r_max+1 as [level][H][W] device arrays (either may be
- * NULL; NULL for both turns capture off). */
+ * NULL; NULL for both turns capture off).  The smoothed accumulator is
+ * written at hotspots only; the caller zero-fills the arrays. */
 int       rd_debug_ridges(rd_ctx* ctx, int f, int32_t* xy, float* dir, int64_t* hess, int cap);
+/* rd_debug_route(ctx, 1) makes the following rd_detect calls process every
+ * accumulator tile with the dense-storage voting kernel (normally used only
+ * for tiles whose hotspots exceed the sparse kernel's capacities); the
+ * results are identical.  0 restores the normal routing. */
+rd_status rd_debug_route(rd_ctx* ctx, int all_dense);
 rd_status rd_debug_capture(rd_ctx* ctx, int32_t* acc_dev, uint32_t* sm_dev);
 
 #ifdef __cplusplus

@@ -63,7 +63,11 @@ __global__ void __launch_bounds__(256) k_bin(BinArgs a) {
               atomicAdd(&a.bin_cnt[b], 1);
             } else {
               long long pos = (long long)a.bin_off[b] + atomicAdd(&a.bin_fill[b], 1);
-              if (pos < a.pool_cap) a.pool[pos] = ((uint32_t)i << 1) | (uint32_t)sg;
+              if (pos < a.pool_cap) {
+                const uint32_t ill = a.rl.kvote[g].x > KF_CONST ? 2u : 0u;
+                a.pool[pos] = make_uint4(xy, __float_as_uint(sgn * d.x), __float_as_uint(sgn * d.y),
+                                         ((uint32_t)i << 2) | ill | (uint32_t)sg);
+              }
             }
           }
       }
@@ -133,18 +137,18 @@ __host__ __device__ __forceinline__ size_t round16(size_t x) { return (x + 15) &
 __host__ __device__ __forceinline__ VoteSmem vote_smem_layout(int max_rw, int T, int max_qn) {
   const size_t rw2 = (size_t)T + 2;
   VoteSmem L;
-  L.q = 0;                                                        // int2 (weight, offset) x max_qn
-  L.n = round16((size_t)max_qn * 8);                              // u32 x 3 slots x rw2^2
-  L.a = L.n + round16(3 * rw2 * rw2 * 4);                         // u16 counts x max_rw^2
-  L.hot = L.a + round16((((size_t)max_rw * max_rw + 1) / 2) * 4);  // u16 x 4 x HOT_CAP
+  L.q = 0;                                                 // int2 (weight, offset) x max_qn (even)
+  L.n = round16((size_t)max_qn * 8);                       // u32 x 3 slots x rw2^2
+  L.a = L.n + round16(3 * rw2 * rw2 * 4);                  // u32 counts x max_rw^2
+  L.hot = L.a + round16((size_t)max_rw * max_rw * 4);      // u16 x 4 x HOT_CAP
   L.total = L.hot + round16((size_t)4 * HOT_CAP * 2);
   return L;
 }
-size_t vote_smem_bytes(int max_rw, int T, int max_qn) { return vote_smem_layout(max_rw, T, max_qn).total; }
+size_t vote_smem_bytes(int max_rw, int T, int max_qn) { return vote_smem_layout(max_rw, T, max_qn).total + 64; }
 
-__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
   unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc));
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
 
@@ -162,8 +166,6 @@ __device__ __forceinline__ void warp_push(bool pred, uint16_t val, int* cnt, uin
   }
 }
 
-__device__ __forceinline__ uint32_t a16(const uint32_t* w, int i) { return (w[i >> 1] >> ((i & 1) << 4)) & 0xffffu; }
-
 // A bin entry as a thread holds it across the levels of its slab.
 struct VEnt {
   uint32_t xy;     // x | y << 16
@@ -172,45 +174,32 @@ struct VEnt {
 };
 
 __device__ __forceinline__ VEnt load_ent(const VoteArgs& a, size_t fbase, long long off, int e) {
+  const uint4 E = a.pool[off + e];
+  const float sg = (E.w & 1u) ? -1.0f : 1.0f;
   VEnt v;
-  v.ent = a.pool[off + e];
-  size_t g = fbase + (v.ent >> 1);
-  v.xy = a.rl.xy[g];
-  float4 d = a.rl.dir[g];
-  v.X = d.x;
-  v.Y = d.y;
-  v.kf = a.rl.kvote[g].x;
+  v.xy = E.x;
+  v.ent = ((E.w >> 2) << 1) | (E.w & 1u);
+  v.X = sg * __uint_as_float(E.y);  // back to the unsigned direction
+  v.Y = sg * __uint_as_float(E.z);
+  v.kf = (E.w & 2u) ? 1e30f : KF_CONST;
   return v;
 }
 
 constexpr float ROUND_MAGIC = 12582912.0f;  // 1.5 * 2^23: adding it rounds |t| < 2^22 to an integer
 constexpr int ROUND_MAGIC_BITS = 0x4B400000;
 
-// Bin offsets (floor(sr X + 1/2), floor(sr Y + 1/2)) of one vote.  Fast path:
-// round to nearest with the magic constant; the result equals the half-up
-// rounding of the double-precision definition when the exact remainder is
-// more than the error margin away from 1/2.  Otherwise the double-float and
-// then the double-precision paths decide.  Returns the number of FP64
-// fallbacks taken (0 or 1).
-__device__ __forceinline__ int vote_bins(const VoteArgs& a, size_t fbase, const VEnt& v, float rf, int& ox, int& oy) {
+// Slow path of one vote: double-float refinement, then the double-precision
+// definition.  Returns 1 when the FP64 definition was evaluated.
+__device__ __noinline__ int vote_bins_slow(const VoteArgs& a, size_t fbase, VEnt v, float rf, int* oxy) {
   const float sr = (v.ent & 1u) ? -rf : rf;
-  const float m = __fmaf_rn(rf, v.kf, 1e-10f);
-  const float tx = __fmul_rn(sr, v.X), ty = __fmul_rn(sr, v.Y);
-  const float fx = __fadd_rn(tx, ROUND_MAGIC), fy = __fadd_rn(ty, ROUND_MAGIC);
-  const float dx = __fsub_rn(tx, __fsub_rn(fx, ROUND_MAGIC));  // exact remainder in [-1/2, 1/2]
-  const float dy = __fsub_rn(ty, __fsub_rn(fy, ROUND_MAGIC));
-  ox = __float_as_int(fx) - ROUND_MAGIC_BITS;
-  oy = __float_as_int(fy) - ROUND_MAGIC_BITS;
-  if (__fadd_rn(fabsf(dx), m) < 0.5f && __fadd_rn(fabsf(dy), m) < 0.5f) return 0;
-  // slow path: double-float refinement, then the double-precision definition
   const size_t g = fbase + (v.ent >> 1);
   const float4 d = a.rl.dir[g];
   const float2 kv = a.rl.kvote[g];
   int vx = vote_offset(sr, rf, d.x, d.z, kv.x, kv.y);
   int vy = vote_offset(sr, rf, d.y, d.w, kv.x, kv.y);
   if (vx != INT_MIN && vy != INT_MIN) {
-    ox = vx;
-    oy = vy;
+    oxy[0] = vx;
+    oxy[1] = vy;
     return 0;
   }
   const int px = (int)(v.xy & 0xffffu), py = (int)(v.xy >> 16);
@@ -220,14 +209,48 @@ __device__ __forceinline__ int vote_bins(const VoteArgs& a, size_t fbase, const 
     X = -X;
     Y = -Y;
   }
-  ox = vote_bin64(px, (double)sr, X) - px;
-  oy = vote_bin64(py, (double)sr, Y) - py;
+  oxy[0] = vote_bin64(px, (double)sr, X) - px;
+  oxy[1] = vote_bin64(py, (double)sr, Y) - py;
   return 1;
 }
 
-__global__ void __launch_bounds__(VOTE_THREADS, 2) k_vote(VoteArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int b = blockIdx.x;
+struct CastCtx {
+  int ox0, oy0, RW, W, H, h, T;
+  bool owned;
+};
+
+// Bin offsets of one vote by round-to-nearest with the magic constant; the
+// result equals the half-up rounding of the double-precision definition when
+// the exact remainder is more than the error margin away from 1/2, otherwise
+// the slow path decides.  Returns the slab index of the vote or -1.
+__device__ __forceinline__ int cast_one(const VoteArgs& a, size_t fbase, const VEnt& v, float rf, const CastCtx& c,
+                                        unsigned& nv, unsigned& nfb) {
+  const float sr = (v.ent & 1u) ? -rf : rf;
+  const float m = __fmaf_rn(rf, v.kf, 1e-10f);
+  const float tx = __fmul_rn(sr, v.X), ty = __fmul_rn(sr, v.Y);
+  const float fx = __fadd_rn(tx, ROUND_MAGIC), fy = __fadd_rn(ty, ROUND_MAGIC);
+  const float dx = __fsub_rn(tx, __fsub_rn(fx, ROUND_MAGIC));  // exact remainder in [-1/2, 1/2]
+  const float dy = __fsub_rn(ty, __fsub_rn(fy, ROUND_MAGIC));
+  int ox = __float_as_int(fx) - ROUND_MAGIC_BITS;
+  int oy = __float_as_int(fy) - ROUND_MAGIC_BITS;
+  if (!(fmaxf(fabsf(dx), fabsf(dy)) < __fsub_rn(0.5f, m))) {
+    int oxy[2];
+    nfb += vote_bins_slow(a, fbase, v, rf, oxy);
+    ox = oxy[0];
+    oy = oxy[1];
+  }
+  const int bx = (int)(v.xy & 0xffffu) + ox, by = (int)(v.xy >> 16) + oy;
+  const int lx = bx - c.ox0, ly = by - c.oy0;
+  if ((unsigned)bx >= (unsigned)c.W || (unsigned)by >= (unsigned)c.H || (unsigned)lx >= (unsigned)c.RW ||
+      (unsigned)ly >= (unsigned)c.RW)
+    return -1;
+  if (c.owned && (unsigned)(lx - c.h) < (unsigned)c.T && (unsigned)(ly - c.h) < (unsigned)c.T) ++nv;
+  return ly * c.RW + lx;
+}
+
+// Dense per-level storage for one bin (used for bins whose hotspots or
+// peaks exceed the sparse kernel's capacities).
+__device__ __forceinline__ void dense_bin(const VoteArgs& a, int b, unsigned char* smem) {
   const int cnt_raw = a.bin_cnt[b];
   if (cnt_raw == 0) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -244,23 +267,25 @@ __global__ void __launch_bounds__(VOTE_THREADS, 2) k_vote(VoteArgs a) {
   const int4 sl = a.slabs[s];
   const int lo = sl.x, hi = sl.y, h = sl.z;
   const int T = a.T, RW = T + 2 * h, RW2 = T + 2;
-  const int ox0 = tx * T - h, oy0 = ty * T - h;  // image coords of the slab's (0, 0)
   const int H = a.H, W = a.W;
   const unsigned vthr = (unsigned)a.vote_thresh;
 
   const VoteSmem L = vote_smem_layout(a.max_rw, T, a.max_qn);
-  int2* sQq = reinterpret_cast<int2*>(smem + L.q);                             // max_qn (weight, offset)
-  uint32_t* sN = reinterpret_cast<uint32_t*>(smem + L.n);                      // 3 slots of RW2^2
-  uint32_t* sAw = reinterpret_cast<uint32_t*>(smem + L.a);                     // RW^2 u16 counts
-  const int nAw4 = (((RW * RW + 1) / 2) + 3) / 4;                              // uint4 words in use (<= region)
-  uint16_t* sHot = reinterpret_cast<uint16_t*>(smem + L.hot);                  // 4 x HOT_CAP, (vy << 8 | vx)
-  __shared__ int s_nhot[4], s_dense[4];
-  __shared__ unsigned long long s_votes, s_fb;
+  int2* sQq = reinterpret_cast<int2*>(smem + L.q);          // (weight, offset) per window tap
+  uint32_t* sN = reinterpret_cast<uint32_t*>(smem + L.n);   // 3 slots of RW2^2 smoothed sums
+  uint32_t* sA = reinterpret_cast<uint32_t*>(smem + L.a);   // RW^2 vote counts
+  uint16_t* sHot = reinterpret_cast<uint16_t*>(smem + L.hot);  // 4 x HOT_CAP, (vy << 8 | vx)
+  const int nA4 = (RW * RW + 3) / 4;
+  int* s_nhot = reinterpret_cast<int*>(smem + L.total);          // 4 counters, 4 flags, 2 x u64
+  int* s_dense = s_nhot + 4;
+  unsigned long long* s_acc64 = reinterpret_cast<unsigned long long*>(s_nhot + 8);
+  unsigned long long& s_votes = s_acc64[0];
+  unsigned long long& s_fb = s_acc64[1];
 
   if (cnt < cnt_raw && tid == 0) atomicOr(&a.stats->overflow, 2);
   {
-    uint4* w4 = reinterpret_cast<uint4*>(sAw);
-    for (int i = tid; i < nAw4; i += VOTE_THREADS) w4[i] = make_uint4(0, 0, 0, 0);
+    uint4* w4 = reinterpret_cast<uint4*>(sA);
+    for (int i = tid; i < nA4; i += VOTE_THREADS) w4[i] = make_uint4(0, 0, 0, 0);
   }
   for (int i = tid; i < 3 * RW2 * RW2; i += VOTE_THREADS) sN[i] = 0;
   if (tid == 0) {
@@ -271,24 +296,42 @@ __global__ void __launch_bounds__(VOTE_THREADS, 2) k_vote(VoteArgs a) {
 
   const size_t fbase = (size_t)f * a.rl.cap;
   const int lv0 = a.r_min - 1;
-  const int rounds = (cnt + VOTE_THREADS - 1) / VOTE_THREADS;
+  // Entry order in a bin follows the ridge list (neighbouring pixels of one
+  // arc, whose votes meet), so the lanes of a warp take entries far apart:
+  // thread k holds entries k, k + 256, ... in a lane-major numbering.
+  const int slot_of_thread = lane * NW + warp;
   VEnt ec[ECACHE];
+  int n_cached = 0;
 #pragma unroll
-  for (int j = 0; j < ECACHE; ++j) {
-    int e = j * VOTE_THREADS + tid;
-    if (e < cnt) ec[j] = load_ent(a, fbase, off, e);
-    else ec[j] = VEnt{0u, 0u, 0.0f, 0.0f, 0.0f};
+  for (int q = 0; q < ECACHE; ++q) {
+    int e = q * VOTE_THREADS + slot_of_thread;
+    if (e < cnt) {
+      ec[q] = load_ent(a, fbase, off, e);
+      n_cached = q + 1;
+    } else {
+      ec[q] = VEnt{0u, 0u, 0.0f, 0.0f, 0.0f};
+    }
   }
+  const int rounds_extra = max(0, (cnt - ECACHE * VOTE_THREADS + VOTE_THREADS - 1) / VOTE_THREADS);
+  CastCtx cc;
+  cc.ox0 = tx * T - h;
+  cc.oy0 = ty * T - h;
+  cc.RW = RW;
+  cc.W = W;
+  cc.H = H;
+  cc.h = h;
+  cc.T = T;
   __syncthreads();
 
   for (int r = lo - 1; r <= hi + 1; ++r) {
     const int li = r - lv0;
     const int Rs = a.q_rad[li];
     const int nq = (2 * Rs + 1) * (2 * Rs + 1);
+    const int nq2 = (nq + 1) >> 1;  // tap pairs (tables are padded to an even count)
     const int lst = r & 3, slot = r % 3;
     // weights and slab-relative offsets of this level, copied asynchronously
-    const int2* gq = a.qq_tab + a.qq_off[s * (SLAB_LEVELS + 2) + (r - lo + 1)];
-    for (int i = tid; i < nq; i += VOTE_THREADS) cp_async8(&sQq[i], &gq[i]);
+    const int4* gq = reinterpret_cast<const int4*>(a.qq_tab + a.qq_off[s * (SLAB_LEVELS + 2) + (r - lo + 1)]);
+    for (int i = tid; i < nq2; i += VOTE_THREADS) cp_async16(&sQq[2 * i], &gq[i]);
     asm volatile("cp.async.commit_group;\n" ::);
 
     // ---- phase 1a: clear level r-3's smoothed sums out of the slot
@@ -307,48 +350,44 @@ __global__ void __launch_bounds__(VOTE_THREADS, 2) k_vote(VoteArgs a) {
     }
 
     // ---- phase 1b: cast this level's votes into the slab
-    const bool owned = (r >= lo && r <= hi) || (r == lo - 1 && lo == a.r_min) || (r == hi + 1 && hi == a.r_max);
+    cc.owned = (r >= lo && r <= hi) || (r == lo - 1 && lo == a.r_min) || (r == hi + 1 && hi == a.r_max);
     unsigned nv = 0, nfb = 0;
     const float rf = (float)r;
-    for (int j = 0; j < rounds; ++j) {
-      const int e = j * VOTE_THREADS + tid;
-      const bool valid = e < cnt;
-      VEnt v;
-      if (j < ECACHE) {
 #pragma unroll
-        for (int q = 0; q < ECACHE; ++q)
-          if (q == j) v = ec[q];
-      } else {
-        v = valid ? load_ent(a, fbase, off, e) : VEnt{0u, 0u, 0.0f, 0.0f, 0.0f};
-      }
-      bool hit = false;
-      int la = 0;
-      if (valid) {
-        int vx, vy;
-        nfb += vote_bins(a, fbase, v, rf, vx, vy);
-        const int bx = (int)(v.xy & 0xffffu) + vx, by = (int)(v.xy >> 16) + vy;
-        const int lx = bx - ox0, ly = by - oy0;
-        if ((unsigned)bx < (unsigned)W && (unsigned)by < (unsigned)H && (unsigned)lx < (unsigned)RW &&
-            (unsigned)ly < (unsigned)RW) {
-          hit = true;
-          la = ly * RW + lx;
-          if (owned && (unsigned)(lx - h) < (unsigned)T && (unsigned)(ly - h) < (unsigned)T) ++nv;
+    for (int q = 0; q < ECACHE; ++q) {
+      int la = q < n_cached ? cast_one(a, fbase, ec[q], rf, cc, nv, nfb) : -1;
+      bool hot = false;
+      int vyx = 0;
+      if (la >= 0) {
+        unsigned old = atomicAdd(&sA[la], 1u);
+        if (old == vthr) {
+          int ly = la / RW, lx = la - ly * RW;
+          int vyr = ly - h + 1, vxr = lx - h + 1;
+          hot = (unsigned)vyr < (unsigned)RW2 && (unsigned)vxr < (unsigned)RW2;
+          vyx = (vyr << 8) | vxr;
         }
       }
-      unsigned oldc = 0;
-      if (hit) {
-        unsigned sh = (la & 1) << 4;
-        oldc = (atomicAdd(&sAw[la >> 1], 1u << sh) >> sh) & 0xffffu;
+      warp_push(hot, (uint16_t)vyx, &s_nhot[lst], sHot + lst * HOT_CAP, HOT_CAP, lane);
+    }
+    for (int j = 0; j < rounds_extra; ++j) {
+      const int e = (ECACHE + j) * VOTE_THREADS + slot_of_thread;
+      int la = -1;
+      if (e < cnt) {
+        VEnt v = load_ent(a, fbase, off, e);
+        la = cast_one(a, fbase, v, rf, cc, nv, nfb);
       }
-      int vyr = 0, vxr = 0;
       bool hot = false;
-      if (hit && oldc == vthr) {
-        int ly = la / RW, lx = la - ly * RW;
-        vyr = ly - h + 1;
-        vxr = lx - h + 1;
-        hot = vyr >= 0 && vyr < RW2 && vxr >= 0 && vxr < RW2;
+      int vyx = 0;
+      if (la >= 0) {
+        unsigned old = atomicAdd(&sA[la], 1u);
+        if (old == vthr) {
+          int ly = la / RW, lx = la - ly * RW;
+          int vyr = ly - h + 1, vxr = lx - h + 1;
+          hot = (unsigned)vyr < (unsigned)RW2 && (unsigned)vxr < (unsigned)RW2;
+          vyx = (vyr << 8) | vxr;
+        }
       }
-      warp_push(hot, (uint16_t)((vyr << 8) | vxr), &s_nhot[lst], sHot + lst * HOT_CAP, HOT_CAP, lane);
+      warp_push(hot, (uint16_t)vyx, &s_nhot[lst], sHot + lst * HOT_CAP, HOT_CAP, lane);
     }
     if (nv) atomicAdd(&s_votes, (unsigned long long)nv);
     if (nfb) atomicAdd(&s_fb, (unsigned long long)nfb);
@@ -363,49 +402,39 @@ __global__ void __launch_bounds__(VOTE_THREADS, 2) k_vote(VoteArgs a) {
       s_nhot[(r + 1) & 3] = 0;
       s_dense[(r + 1) & 3] = 0;
     }
-    if (nhot <= HOT_CAP) {
-      for (int k = warp; k < nhot; k += NW) {
+    const bool dense = nhot > HOT_CAP;
+    if (dense && tid == 0) s_dense[lst] = 1;
+    const int ntask = dense ? RW2 * RW2 : nhot;
+    const int4* sQ4 = reinterpret_cast<const int4*>(sQq);
+    for (int k = warp; k < ntask; k += NW) {
+      int vyr, vxr;
+      if (!dense) {
         int v = sHot[lst * HOT_CAP + k];
-        int vyr = v >> 8, vxr = v & 0xff;
-        int center = (vyr + h - 1) * RW + (vxr + h - 1);
-        unsigned long long acc = 0;
-        for (int q = lane; q < nq; q += 32) {
-          int2 w = sQq[q];
-          acc += (unsigned long long)(uint32_t)w.x * a16(sAw, center + w.y);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) {
-          if (acc > 0xffffffffULL) {
-            atomicOr(&a.stats->overflow, 16);
-            acc = 0xffffffffULL;
-          }
-          cur[vyr * RW2 + vxr] = (uint32_t)acc;
-        }
-      }
-    } else {
-      // dense fallback: every in-image voxel of the ring region
-      if (tid == 0) s_dense[lst] = 1;
-      for (int v = warp; v < RW2 * RW2; v += NW) {
-        int vyr = v / RW2, vxr = v - vyr * RW2;
+        vyr = v >> 8;
+        vxr = v & 0xff;
+      } else {
+        vyr = k / RW2;
+        vxr = k - vyr * RW2;
         int gx = tx * T - 1 + vxr, gy = ty * T - 1 + vyr;
         if (gx < 0 || gx >= W || gy < 0 || gy >= H) continue;
-        int center = (vyr + h - 1) * RW + (vxr + h - 1);
-        if (a16(sAw, center) <= vthr) continue;
-        unsigned long long acc = 0;
-        for (int q = lane; q < nq; q += 32) {
-          int2 w = sQq[q];
-          acc += (unsigned long long)(uint32_t)w.x * a16(sAw, center + w.y);
-        }
+        if (sA[(vyr + h - 1) * RW + (vxr + h - 1)] <= vthr) continue;
+      }
+      const uint32_t* ctr = sA + (vyr + h - 1) * RW + (vxr + h - 1);
+      unsigned long long acc0 = 0, acc1 = 0;
+      for (int q = lane; q < nq2; q += 32) {
+        int4 w = sQ4[q];  // two taps: (weight, offset), (weight, offset)
+        acc0 += (unsigned long long)(uint32_t)w.x * ctr[w.y];
+        acc1 += (unsigned long long)(uint32_t)w.z * ctr[w.w];
+      }
+      unsigned long long acc = acc0 + acc1;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) {
-          if (acc > 0xffffffffULL) {
-            atomicOr(&a.stats->overflow, 16);
-            acc = 0xffffffffULL;
-          }
-          cur[v] = (uint32_t)acc;
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) {
+        if (acc > 0xffffffffULL) {
+          atomicOr(&a.stats->overflow, 16);
+          acc = 0xffffffffULL;
         }
+        cur[vyr * RW2 + vxr] = (uint32_t)acc;
       }
     }
     __syncthreads();
@@ -415,7 +444,7 @@ __global__ void __launch_bounds__(VOTE_THREADS, 2) k_vote(VoteArgs a) {
         int iy = v / T, ix = v - iy * T;
         int gx = tx * T + ix, gy = ty * T + iy;
         if (gx < W && gy < H) {
-          a.dbg_acc[((size_t)li * H + gy) * W + gx] = (int32_t)a16(sAw, (iy + h) * RW + (ix + h));
+          a.dbg_acc[((size_t)li * H + gy) * W + gx] = (int32_t)sA[(iy + h) * RW + (ix + h)];
           if (a.dbg_sm) a.dbg_sm[((size_t)li * H + gy) * W + gx] = cur[(iy + 1) * RW2 + ix + 1];
         }
       }
@@ -430,11 +459,11 @@ __global__ void __launch_bounds__(VOTE_THREADS, 2) k_vote(VoteArgs a) {
       const uint32_t* Nhi = cur;
       const unsigned long long thr = a.nthr[rp - lv0];
       const int pl = rp & 3;
-      const bool dense = s_dense[pl] != 0;
-      const int n = dense ? T * T : s_nhot[pl];
+      const bool pdense = s_dense[pl] != 0;
+      const int n = pdense ? T * T : s_nhot[pl];
       for (int k = tid; k < n; k += VOTE_THREADS) {
         int iy, ix;
-        if (dense) {
+        if (pdense) {
           iy = k / T;
           ix = k - iy * T;
         } else {
@@ -451,14 +480,14 @@ __global__ void __launch_bounds__(VOTE_THREADS, 2) k_vote(VoteArgs a) {
         bool ok = true;
 #pragma unroll
         for (int dr = -1; dr <= 1; ++dr) {
-          const uint32_t* L = dr < 0 ? Nlo : (dr == 0 ? Nmid : Nhi);
+          const uint32_t* Lv = dr < 0 ? Nlo : (dr == 0 ? Nmid : Nhi);
           unsigned long long lhs = nv0 * (unsigned long long)(rp + dr);
 #pragma unroll
           for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
             for (int dx = -1; dx <= 1; ++dx) {
               if (dr == 0 && dy == 0 && dx == 0) continue;
-              unsigned long long rhs = (unsigned long long)L[c + dy * RW2 + dx] * (unsigned long long)rp;
+              unsigned long long rhs = (unsigned long long)Lv[c + dy * RW2 + dx] * (unsigned long long)rp;
               bool precedes = dr < 0 || (dr == 0 && (dy < 0 || (dy == 0 && dx < 0)));
               ok = ok && (precedes ? lhs > rhs : lhs >= rhs);
             }
@@ -476,12 +505,305 @@ __global__ void __launch_bounds__(VOTE_THREADS, 2) k_vote(VoteArgs a) {
 
     // ---- phase 3b: clear the slab for the next level (16-byte stores)
     {
-      uint4* w4 = reinterpret_cast<uint4*>(sAw);
-      for (int i = tid; i < nAw4; i += VOTE_THREADS) w4[i] = make_uint4(0, 0, 0, 0);
+      uint4* w4 = reinterpret_cast<uint4*>(sA);
+      for (int i = tid; i < nA4; i += VOTE_THREADS) w4[i] = make_uint4(0, 0, 0, 0);
     }
     __syncthreads();
   }
   if (tid == 0) {
+    if (s_votes) atomicAdd(&a.stats->votes, s_votes);
+    if (s_fb) atomicAdd(&a.stats->fallbacks, s_fb);
+  }
+}
+
+__global__ void __launch_bounds__(VOTE_THREADS, 2) k_vote_dense(VoteArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int n = min(*a.fb_count, a.fb_cap);
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    __syncthreads();  // the previous bin's readers are done with shared memory
+    dense_bin(a, a.fb_list[i], smem);
+  }
+}
+
+// ---- K4 (sparse) --------------------------------------------------------------
+// The common path.  Shared memory holds one level of u16 vote counts for the
+// tile plus its smoothing halo, the packed window taps of that level, and,
+// for the last four levels, the hotspot lists with their smoothed sums and a
+// small open-addressing table from voxel to list slot: the paper's
+// registering of modified elements, so that nothing proportional to the tile
+// area is kept per level and four CTAs fit on an SM.  A bin whose hotspots or
+// peaks exceed these capacities emits nothing here and is handed to
+// k_vote_dense, which computes the same result with dense per-level storage.
+constexpr int SP_HOT = 256;     // hotspots per level
+constexpr int SP_HASH = 512;    // hash slots per level (power of two, > 2 SP_HOT)
+constexpr int SP_PEAKS = 64;    // peaks buffered per CTA
+constexpr uint32_t SP_EMPTY = 0xffffffffu;
+
+struct SparseSmem {
+  size_t q, a, hash, coord, val, pk, total;
+};
+__host__ __device__ __forceinline__ SparseSmem sparse_smem_layout(int max_rw, int max_qp) {
+  SparseSmem L;
+  L.q = 0;                                                        // u32 packed taps x max_qp
+  L.a = round16((size_t)max_qp * 4);                              // u16 counts x max_rw^2
+  L.hash = L.a + round16((((size_t)max_rw * max_rw + 1) / 2) * 4);  // u32 x 4 x SP_HASH
+  L.coord = L.hash + (size_t)4 * SP_HASH * 4;                     // u16 x 4 x SP_HOT
+  L.val = L.coord + round16((size_t)4 * SP_HOT * 2);              // u32 x 4 x SP_HOT
+  L.pk = L.val + (size_t)4 * SP_HOT * 4;                          // int4 x SP_PEAKS
+  L.total = L.pk + (size_t)SP_PEAKS * 16;
+  return L;
+}
+size_t sparse_smem_bytes(int max_rw, int max_qp) { return sparse_smem_layout(max_rw, max_qp).total; }
+
+__device__ __forceinline__ uint32_t sp_hash(uint32_t key) { return (key * 2654435761u) >> (32 - 9); }
+
+__device__ __forceinline__ uint32_t sp_lookup(const uint32_t* tab, const uint32_t* val, uint32_t key) {
+  uint32_t h = sp_hash(key);
+  for (int p = 0; p < SP_HASH; ++p) {
+    const uint32_t e = tab[h];
+    if (e == SP_EMPTY) return 0u;
+    if ((e >> 16) == key) return val[e & 0xffffu];
+    h = (h + 1) & (SP_HASH - 1);
+  }
+  return 0u;
+}
+
+__global__ void __launch_bounds__(VOTE_THREADS, 4) k_vote(VoteArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int b = blockIdx.x;
+  const int cnt_raw = a.bin_cnt[b];
+  if (cnt_raw == 0) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int NW = VOTE_THREADS / 32;
+  int t = b;
+  const int s = t % a.n_slabs;
+  t /= a.n_slabs;
+  const int tx = t % a.n_atx;
+  t /= a.n_atx;
+  const int ty = t % a.n_aty;
+  const int f = t / a.n_aty;
+  const long long off = a.bin_off[b];
+  const int cnt = (int)max(0LL, min((long long)cnt_raw, a.pool_cap - off));
+  const int4 sl = a.slabs[s];
+  const int lo = sl.x, hi = sl.y, h = sl.z;
+  const int T = a.T, RW = T + 2 * h, RW2 = T + 2;
+  const int ox0 = tx * T - h, oy0 = ty * T - h;
+  const int H = a.H, W = a.W;
+  const unsigned vthr = (unsigned)a.vote_thresh;
+
+  const SparseSmem L = sparse_smem_layout(a.max_rw, a.max_qp);
+  uint32_t* sQ = reinterpret_cast<uint32_t*>(smem + L.q);
+  uint32_t* sAw = reinterpret_cast<uint32_t*>(smem + L.a);
+  const uint16_t* sA16 = reinterpret_cast<const uint16_t*>(sAw);
+  uint32_t* sHash = reinterpret_cast<uint32_t*>(smem + L.hash);
+  uint16_t* sCoord = reinterpret_cast<uint16_t*>(smem + L.coord);
+  uint32_t* sVal = reinterpret_cast<uint32_t*>(smem + L.val);
+  int4* sPk = reinterpret_cast<int4*>(smem + L.pk);
+  const int nA4 = (((RW * RW + 1) / 2) + 3) / 4;
+  __shared__ int s_nhot[4], s_npk, s_abort;
+  __shared__ unsigned long long s_votes, s_fb;
+
+  if (cnt < cnt_raw && tid == 0) atomicOr(&a.stats->overflow, 2);
+  {
+    uint4* w4 = reinterpret_cast<uint4*>(sAw);
+    for (int i = tid; i < nA4; i += VOTE_THREADS) w4[i] = make_uint4(0, 0, 0, 0);
+  }
+  for (int i = tid; i < 4 * SP_HASH; i += VOTE_THREADS) sHash[i] = SP_EMPTY;
+  if (tid == 0) {
+    for (int k = 0; k < 4; ++k) s_nhot[k] = 0;
+    s_npk = 0;
+    s_abort = a.route_dense;
+    s_votes = 0;
+    s_fb = 0;
+  }
+  const size_t fbase = (size_t)f * a.rl.cap;
+  const int lv0 = a.r_min - 1;
+  const int rounds = (cnt + VOTE_THREADS - 1) / VOTE_THREADS;
+  __syncthreads();
+
+  for (int r = lo - 1; r <= hi + 1 && !s_abort; ++r) {
+    const int li = r - lv0;
+    const int Rs = a.q_rad[li];
+    const int nq = (2 * Rs + 1) * (2 * Rs + 1);
+    const int nq4 = (nq + 3) >> 2;  // packed taps in groups of four (tables padded)
+    const int lst = r & 3;
+    const uint4* gq = reinterpret_cast<const uint4*>(a.qp_tab + a.qp_off[s * (SLAB_LEVELS + 2) + (r - lo + 1)]);
+    for (int i = tid; i < nq4; i += VOTE_THREADS) cp_async16(&sQ[4 * i], &gq[i]);
+    asm volatile("cp.async.commit_group;\n" ::);
+
+    // ---- phase 1: votes of level r; a voxel whose count passes the integer
+    //      threshold is registered as a hotspot of this level
+    const bool owned = (r >= lo && r <= hi) || (r == lo - 1 && lo == a.r_min) || (r == hi + 1 && hi == a.r_max);
+    const float rf = (float)r;
+    const float half_m = __fsub_rn(0.5f, __fmaf_rn(rf, KF_CONST, 1e-10f));
+    uint32_t* tab = sHash + lst * SP_HASH;
+    unsigned nv = 0, nfb = 0;
+    for (int j = 0; j < rounds; ++j) {
+      const int e = j * VOTE_THREADS + tid;
+      if (e >= cnt) continue;
+      const uint4 E = a.pool[off + e];
+      const float tx_ = __fmul_rn(rf, __uint_as_float(E.y)), ty_ = __fmul_rn(rf, __uint_as_float(E.z));
+      const float fx = __fadd_rn(tx_, ROUND_MAGIC), fy = __fadd_rn(ty_, ROUND_MAGIC);
+      const float dx = __fsub_rn(tx_, __fsub_rn(fx, ROUND_MAGIC));
+      const float dy = __fsub_rn(ty_, __fsub_rn(fy, ROUND_MAGIC));
+      int ox = __float_as_int(fx) - ROUND_MAGIC_BITS, oy = __float_as_int(fy) - ROUND_MAGIC_BITS;
+      if ((E.w & 2u) || !(fmaxf(fabsf(dx), fabsf(dy)) < half_m)) {
+        VEnt v;
+        v.xy = E.x;
+        v.ent = ((E.w >> 2) << 1) | (E.w & 1u);
+        v.X = v.Y = 0.0f;
+        v.kf = 0.0f;
+        int oxy[2];
+        nfb += vote_bins_slow(a, fbase, v, rf, oxy);
+        ox = oxy[0];
+        oy = oxy[1];
+      }
+      const int bx = (int)(E.x & 0xffffu) + ox, by = (int)(E.x >> 16) + oy;
+      const int lx = bx - ox0, ly = by - oy0;
+      if ((unsigned)bx >= (unsigned)W || (unsigned)by >= (unsigned)H || (unsigned)lx >= (unsigned)RW ||
+          (unsigned)ly >= (unsigned)RW)
+        continue;
+      if (owned && (unsigned)(lx - h) < (unsigned)T && (unsigned)(ly - h) < (unsigned)T) ++nv;
+      const int la = ly * RW + lx;
+      const unsigned sh = (la & 1) << 4;
+      const unsigned old = (atomicAdd(&sAw[la >> 1], 1u << sh) >> sh) & 0xffffu;
+      if (old == vthr) {
+        const int vyr = ly - h + 1, vxr = lx - h + 1;
+        if ((unsigned)vyr < (unsigned)RW2 && (unsigned)vxr < (unsigned)RW2) {
+          const int k = atomicAdd(&s_nhot[lst], 1);
+          if (k < SP_HOT) {
+            const uint32_t key = ((uint32_t)vyr << 8) | (uint32_t)vxr;
+            sCoord[lst * SP_HOT + k] = (uint16_t)key;
+            uint32_t hh = sp_hash(key);
+            for (int p = 0; p < SP_HASH; ++p) {
+              if (atomicCAS(&tab[hh], SP_EMPTY, (key << 16) | (uint32_t)k) == SP_EMPTY) break;
+              hh = (hh + 1) & (SP_HASH - 1);
+            }
+          } else {
+            s_abort = 1;
+          }
+        }
+      }
+    }
+    if (nv) atomicAdd(&s_votes, (unsigned long long)nv);
+    if (nfb) atomicAdd(&s_fb, (unsigned long long)nfb);
+    cp_async_wait_all();
+    __syncthreads();
+    if (s_abort) break;  // uniform: read after the barrier
+
+    // ---- phase 2: radius-dependent smoothing at this level's hotspots
+    const int nhot = s_nhot[lst];
+    const uint4* sQ4 = reinterpret_cast<const uint4*>(sQ);
+    for (int k = warp; k < nhot; k += NW) {
+      const uint32_t key = sCoord[lst * SP_HOT + k];
+      const uint16_t* ctr = sA16 + ((int)(key >> 8) + h - 1) * RW + ((int)(key & 0xffu) + h - 1);
+      unsigned long long acc = 0;
+      for (int q = lane; q < nq4; q += 32) {
+        const uint4 P = sQ4[q];
+        acc += (unsigned long long)(P.x >> 15) * ctr[((int)(P.x << 17)) >> 17];
+        acc += (unsigned long long)(P.y >> 15) * ctr[((int)(P.y << 17)) >> 17];
+        acc += (unsigned long long)(P.z >> 15) * ctr[((int)(P.z << 17)) >> 17];
+        acc += (unsigned long long)(P.w >> 15) * ctr[((int)(P.w << 17)) >> 17];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) {
+        if (acc > 0xffffffffULL) {
+          atomicOr(&a.stats->overflow, 16);
+          acc = 0xffffffffULL;
+        }
+        sVal[lst * SP_HOT + k] = (uint32_t)acc;
+      }
+    }
+    __syncthreads();
+
+    if (a.dbg_acc && f == 0) {
+      for (int v = tid; v < T * T; v += VOTE_THREADS) {
+        const int iy = v / T, ix = v - iy * T;
+        const int gx = tx * T + ix, gy = ty * T + iy;
+        if (gx < W && gy < H) a.dbg_acc[((size_t)li * H + gy) * W + gx] = (int32_t)sA16[(iy + h) * RW + (ix + h)];
+      }
+      if (a.dbg_sm) {
+        for (int k = tid; k < nhot; k += VOTE_THREADS) {
+          const uint32_t key = sCoord[lst * SP_HOT + k];
+          const int iy = (int)(key >> 8) - 1, ix = (int)(key & 0xffu) - 1;
+          const int gx = tx * T + ix, gy = ty * T + iy;
+          if ((unsigned)iy < (unsigned)T && (unsigned)ix < (unsigned)T && gx < W && gy < H)
+            a.dbg_sm[((size_t)li * H + gy) * W + gx] = sVal[lst * SP_HOT + k];
+        }
+      }
+      __syncthreads();  // the capture reads the slab before phase 3 clears it
+    }
+
+    // ---- phase 3: peak test of level r - 1 against levels r - 2 .. r; clear
+    //      the slab and the registers of level r - 3 for the next level
+    const int rp = r - 1;
+    if (rp >= lo && rp <= hi) {
+      const int pl = rp & 3;
+      const int n = s_nhot[pl];
+      const unsigned long long thr = a.nthr[rp - lv0];
+      for (int k = tid; k < n; k += VOTE_THREADS) {
+        const uint32_t key = sCoord[pl * SP_HOT + k];
+        const int vyr = (int)(key >> 8), vxr = (int)(key & 0xffu);
+        const int iy = vyr - 1, ix = vxr - 1;
+        if ((unsigned)iy >= (unsigned)T || (unsigned)ix >= (unsigned)T) continue;
+        const int gx = tx * T + ix, gy = ty * T + iy;
+        if (gx >= W || gy >= H) continue;
+        const unsigned long long nv0 = sVal[pl * SP_HOT + k];
+        if (nv0 < thr) continue;
+        bool ok = true;
+        for (int dr = -1; dr <= 1 && ok; ++dr) {
+          const int ll = (rp + dr) & 3;
+          const unsigned long long lhs = nv0 * (unsigned long long)(rp + dr);
+          for (int dy = -1; dy <= 1 && ok; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              if (dr == 0 && dy == 0 && dx == 0) continue;
+              const uint32_t nk = ((uint32_t)(vyr + dy) << 8) | (uint32_t)(vxr + dx);
+              const unsigned long long rhs =
+                  (unsigned long long)sp_lookup(sHash + ll * SP_HASH, sVal + ll * SP_HOT, nk) * (unsigned long long)rp;
+              const bool precedes = dr < 0 || (dr == 0 && (dy < 0 || (dy == 0 && dx < 0)));
+              if (precedes ? !(lhs > rhs) : !(lhs >= rhs)) {
+                ok = false;
+                break;
+              }
+            }
+        }
+        if (ok) {
+          const int kk = atomicAdd(&s_npk, 1);
+          if (kk < SP_PEAKS)
+            sPk[kk] = make_int4(gx, gy, rp, (int)nv0);
+          else
+            s_abort = 1;
+        }
+      }
+    }
+    {
+      uint4* w4 = reinterpret_cast<uint4*>(sAw);
+      for (int i = tid; i < nA4; i += VOTE_THREADS) w4[i] = make_uint4(0, 0, 0, 0);
+      uint32_t* nt = sHash + ((r + 1) & 3) * SP_HASH;  // level r - 3's table, reused by level r + 1
+      for (int i = tid; i < SP_HASH; i += VOTE_THREADS) nt[i] = SP_EMPTY;
+    }
+    if (tid == 0) s_nhot[(r + 1) & 3] = 0;
+    __syncthreads();
+  }
+  __syncthreads();
+  if (s_abort) {
+    if (tid == 0) {
+      const int k = atomicAdd(a.fb_count, 1);
+      if (k < a.fb_cap) a.fb_list[k] = b;
+    }
+    return;
+  }
+  const int npk = s_npk;
+  for (int k = tid; k < npk; k += VOTE_THREADS) {
+    const int kk = atomicAdd(&a.peak_count[f], 1);
+    if (kk < a.peak_cap)
+      a.peaks[(size_t)f * a.peak_cap + kk] = sPk[k];
+    else
+      atomicOr(&a.stats->overflow, 4);
+  }
+  if (tid == 0) {
+    if (npk) atomicAdd(&a.stats->peaks, (unsigned long long)npk);
     if (s_votes) atomicAdd(&a.stats->votes, s_votes);
     if (s_fb) atomicAdd(&a.stats->fallbacks, s_fb);
   }
@@ -502,9 +824,14 @@ cudaError_t launch_bins(const BinArgs& a, int n_sm, cudaStream_t st, long long n
 }
 
 cudaError_t launch_vote(const VoteArgs& a, long long n_bins, cudaStream_t st) {
-  size_t sm = vote_smem_bytes(a.max_rw, a.T, a.max_qn);
+  size_t sm = sparse_smem_bytes(a.max_rw, a.max_qp);
   cudaFuncSetAttribute(k_vote, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_vote<<<(unsigned)n_bins, VOTE_THREADS, sm, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  size_t smd = vote_smem_bytes(a.max_rw, a.T, a.max_qn);
+  cudaFuncSetAttribute(k_vote_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smd);
+  k_vote_dense<<<(unsigned)a.fb_grid, VOTE_THREADS, smd, st>>>(a);
   return cudaGetLastError();
 }
 

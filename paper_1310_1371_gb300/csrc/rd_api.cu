@@ -10,7 +10,7 @@
 //                  s = sig_a r + sig_b, |dx|, |dy| <= ceil(3 s)
 //   peak threshold S > peak_frac 2 pi  <=>  N > ((peak_frac 2 pi) 2^16) r
 #include "rd_internal.cuh"
-#include "../../include/rd.h"
+#include "rd.h"
 
 #include <cmath>
 #include <cstdio>
@@ -39,6 +39,11 @@ struct rd_ctx {
   int* q_rad = nullptr;
   int* qq_off = nullptr;
   int2* qq_tab = nullptr;
+  int* qp_off = nullptr;
+  uint32_t* qp_tab = nullptr;
+  int* fb_list = nullptr;
+  int* fb_count = nullptr;
+  int max_qp = 4;
   unsigned long long* nthr = nullptr;
   RidgeList rl{};
   int* bin_cnt = nullptr;
@@ -46,7 +51,7 @@ struct rd_ctx {
   int* bin_fill = nullptr;
   int* block_sums = nullptr;
   long long* bin_total = nullptr;
-  uint32_t* pool = nullptr;
+  uint4* pool = nullptr;
   long long pool_cap = 0, n_bins_max = 0;
   int4* peaks = nullptr;
   int* peak_count = nullptr;
@@ -57,6 +62,7 @@ struct rd_ctx {
   int last_n = 0, last_H = 0, last_W = 0;
   int32_t* dbg_acc = nullptr;
   uint32_t* dbg_sm = nullptr;
+  int route_dense = 0;
   // staging for rd_detect_host
   void* stage_frames = nullptr;
   rd_ring* stage_rings = nullptr;
@@ -134,7 +140,7 @@ static rd_status fail(rd_ctx* c, rd_status s, const std::string& m) {
 }
 
 static void free_all(rd_ctx* c) {
-  void* ptrs[] = {c->slabs, c->q_rad, c->qq_off, c->qq_tab, c->nthr, c->rl.xy, c->rl.dir, c->rl.kvote, c->rl.hess,
+  void* ptrs[] = {c->slabs, c->q_rad, c->qq_off, c->qq_tab, c->qp_off, c->qp_tab, c->fb_list, c->fb_count, c->nthr, c->rl.xy, c->rl.dir, c->rl.kvote, c->rl.hess,
                   c->rl.count, c->rl.tile_off, c->rl.tile_cnt, c->bin_cnt, c->bin_off, c->bin_fill, c->block_sums,
                   c->bin_total, c->pool, c->peaks, c->peak_count, c->stats, c->stage_frames, c->stage_rings,
                   c->stage_counts, c->stage_offsets};
@@ -205,7 +211,7 @@ extern "C" rd_status rd_create(const rd_params* params, int max_H, int max_W, in
     h_qtab.resize(h_qtab.size() + nq);
     level_weights_impl(params->sig_a, params->sig_b, r, h_qtab.data() + h_qoff[li], nq);
     h_nthr[li] = (unsigned long long)peak_threshold_impl(params->peak_frac, r);
-    c->max_qn = std::max(c->max_qn, nq);
+    c->max_qn = std::max(c->max_qn, nq + (nq & 1));
   }
   // r-slabs of SLAB_LEVELS peak levels; halo = 1 + the largest R_s of the slab's voting levels
   c->max_rw = 0;
@@ -222,6 +228,8 @@ extern "C" rd_status rd_create(const rd_params* params, int max_H, int max_W, in
   // relative to the window centre in the slab's shared-memory layout
   std::vector<int> h_qqoff((size_t)c->n_slabs * (SLAB_LEVELS + 2), 0);
   std::vector<int2> h_qqtab;
+  std::vector<int> h_qpoff((size_t)c->n_slabs * (SLAB_LEVELS + 2), 0);
+  std::vector<uint32_t> h_qptab;
   for (int si = 0; si < c->n_slabs; ++si) {
     const int4 sl = c->h_slabs[si];
     const int RW = ACC_T + 2 * sl.z;
@@ -231,9 +239,20 @@ extern "C" rd_status rd_create(const rd_params* params, int max_H, int max_W, in
       const int32_t* q = h_qtab.data() + h_qoff[li];
       for (int dy = 0; dy < Wq; ++dy)
         for (int dx = 0; dx < Wq; ++dx) h_qqtab.push_back(make_int2(q[dy * Wq + dx], (dy - Rs) * RW + (dx - Rs)));
+      if (h_qqtab.size() & 1) h_qqtab.push_back(make_int2(0, 0));  // even count: 16-byte tap pairs
+      // packed taps for the sparse kernel: weight << 15 | (offset & 0x7fff),
+      // padded with zero-weight taps to a multiple of four
+      h_qpoff[(size_t)si * (SLAB_LEVELS + 2) + (r - sl.x + 1)] = (int)h_qptab.size();
+      for (int dy = 0; dy < Wq; ++dy)
+        for (int dx = 0; dx < Wq; ++dx) {
+          const int off = (dy - Rs) * RW + (dx - Rs);
+          h_qptab.push_back(((uint32_t)q[dy * Wq + dx] << 15) | ((uint32_t)off & 0x7fffu));
+        }
+      while (h_qptab.size() & 3) h_qptab.push_back(0u);
+      c->max_qp = std::max(c->max_qp, (Wq * Wq + 3) & ~3);
     }
   }
-  if (vote_smem_bytes(c->max_rw, ACC_T, c->max_qn) > 227 * 1024) {
+  if (vote_smem_bytes(c->max_rw, ACC_T, c->max_qn) > 227 * 1024 || c->max_rw * c->max_rw > 65535 * 2) {
     delete c;
     return fail(nullptr, RD_E_INVAL, "radius range needs more shared memory than one SM has");
   }
@@ -245,9 +264,11 @@ extern "C" rd_status rd_create(const rd_params* params, int max_H, int max_W, in
   c->rl.n_sty = n_sty;
   const size_t nrec = (size_t)c->rl.cap * max_batch;
   c->n_bins_max = (long long)max_batch * n_atx * n_aty * c->n_slabs;
-  c->pool_cap = std::min<long long>((long long)max_batch * max_H * max_W * 2, (1LL << 31) - 1);
+  c->pool_cap = std::min<long long>((long long)max_batch * max_H * max_W * 3, (1LL << 31) - 1);
   bool ok = dalloc(&c->slabs, c->n_slabs) && dalloc(&c->q_rad, c->n_levels) &&
             dalloc(&c->qq_off, h_qqoff.size()) && dalloc(&c->qq_tab, h_qqtab.size()) &&
+            dalloc(&c->qp_off, h_qpoff.size()) && dalloc(&c->qp_tab, h_qptab.size()) &&
+            dalloc(&c->fb_list, c->n_bins_max) && dalloc(&c->fb_count, 1) &&
             dalloc(&c->nthr, c->n_levels) && dalloc(&c->rl.xy, nrec) &&
             dalloc(&c->rl.dir, nrec) && dalloc(&c->rl.kvote, nrec) && dalloc(&c->rl.hess, 3 * nrec) &&
             dalloc(&c->rl.count, max_batch) && dalloc(&c->rl.tile_off, (size_t)max_batch * n_stx * n_sty) &&
@@ -271,6 +292,10 @@ extern "C" rd_status rd_create(const rd_params* params, int max_H, int max_W, in
     e = cudaMemcpy(c->qq_off, h_qqoff.data(), sizeof(int) * h_qqoff.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(c->qq_tab, h_qqtab.data(), sizeof(int2) * h_qqtab.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c->qp_off, h_qpoff.data(), sizeof(int) * h_qpoff.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(c->qp_tab, h_qptab.data(), sizeof(uint32_t) * h_qptab.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(c->nthr, h_nthr.data(), sizeof(unsigned long long) * c->n_levels, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(c->stats, 0, sizeof(DevStats));
@@ -315,6 +340,7 @@ extern "C" rd_status rd_detect(rd_ctx* c, const void* frames_dev, int n, int H, 
   chk(cudaMemsetAsync(c->bin_fill, 0, sizeof(int) * n_bins, st));
   chk(cudaMemsetAsync(c->peak_count, 0, sizeof(int) * n, st));
   chk(cudaMemsetAsync(c->stats, 0, sizeof(DevStats), st));
+  chk(cudaMemsetAsync(c->fb_count, 0, sizeof(int), st));
   if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("memset: ") + cudaGetErrorString(e));
 
   auto mark = [&](int i) {
@@ -390,6 +416,14 @@ extern "C" rd_status rd_detect(rd_ctx* c, const void* frames_dev, int n, int H, 
   va.dbg_sm = c->dbg_sm;
   va.max_rw = c->max_rw;
   va.max_qn = c->max_qn;
+  va.max_qp = c->max_qp;
+  va.qp_off = c->qp_off;
+  va.qp_tab = c->qp_tab;
+  va.fb_list = c->fb_list;
+  va.fb_count = c->fb_count;
+  va.fb_cap = (int)n_bins;
+  va.fb_grid = 2 * c->n_sm;
+  va.route_dense = c->route_dense;
   chk(launch_vote(va, n_bins, st));
   mark(4);
   if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("vote: ") + cudaGetErrorString(e));
@@ -517,6 +551,12 @@ extern "C" int rd_debug_ridges(rd_ctx* c, int f, int32_t* xy, float* dir, int64_
       return -1;
   }
   return cnt;
+}
+
+extern "C" rd_status rd_debug_route(rd_ctx* c, int all_dense) {
+  if (!c) return RD_E_INVAL;
+  c->route_dense = all_dense ? 1 : 0;
+  return RD_OK;
 }
 
 extern "C" rd_status rd_debug_capture(rd_ctx* c, int32_t* acc_dev, uint32_t* sm_dev) {

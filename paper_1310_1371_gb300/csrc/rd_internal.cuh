@@ -17,7 +17,7 @@
 #include <cuda_runtime.h>
 #include <climits>
 
-#include "../../include/rd.h"
+#include "rd.h"
 
 namespace rd {
 
@@ -32,6 +32,11 @@ constexpr int VOTE_THREADS = 256;
 constexpr int MAX_RS = 40;         // level smoothing half-width ceil(3 sigma(r))
 constexpr int SLAB_LEVELS = 8;     // peak levels per r-slab
 constexpr int FIT_WARPS = 8;
+// Vote-rounding margin coefficient shared by every well-conditioned ridge
+// pixel: 1.25 (|X_lo| + e_X + 2^-24) + 2^-24 with |X_lo| <= 2^-25 and the
+// direction error e_X <= 5e-12 (condition number <= 1e3).  Pixels whose own
+// coefficient exceeds it always take the exact path.
+constexpr float KF_CONST = 1.72e-7f;
 
 struct DevStats {
   unsigned long long ridge, votes, peaks, fallbacks;
@@ -80,7 +85,7 @@ struct BinArgs {
   int* bin_cnt;
   const int* bin_off;
   int* bin_fill;
-  uint32_t* pool;
+  uint4* pool;               // per entry: x | y << 16, s X, s Y, index << 2 | ill << 1 | (s < 0)
   long long pool_cap;
   DevStats* stats;
 };
@@ -91,11 +96,17 @@ struct VoteArgs {
   const int4* slabs;
   const int* bin_cnt;
   const int* bin_off;
-  const uint32_t* pool;
+  const uint4* pool;
   long long pool_cap;
   const int* q_rad;          // per voting level (index r - (r_min - 1)): R_s
   const int* qq_off;         // per (slab, level lo-1 .. hi+1): offset into qq_tab
   const int2* qq_tab;        // (weight, slab-relative smem offset) per window tap, row-major (dy, dx)
+  const int* qp_off;         // per (slab, level): offset into qp_tab (multiple of 4)
+  const uint32_t* qp_tab;    // packed taps: weight << 15 | (offset & 0x7fff), padded to 4
+  int* fb_list;              // bins handed to the dense kernel (sparse capacities exceeded)
+  int* fb_count;
+  int fb_cap, fb_grid;
+  int route_dense;           // diagnostics: hand every bin to the dense kernel
   const unsigned long long* nthr;  // per voting level: smallest N passing the float threshold
   int r_min, r_max, vote_thresh;
   int4* peaks;               // per frame: (x, y, r, N)
@@ -105,7 +116,7 @@ struct VoteArgs {
   double D64;
   int32_t* dbg_acc;          // optional [levels][H][W] capture of frame 0
   uint32_t* dbg_sm;
-  int max_rw, max_qn;
+  int max_rw, max_qn, max_qp;
 };
 
 struct FitArgs {
@@ -130,6 +141,7 @@ cudaError_t launch_vote(const VoteArgs& a, long long n_bins, cudaStream_t st);
 cudaError_t launch_fit(const FitArgs& a, int4* peaks_mut, int* counts, int* offsets, cudaStream_t st);
 size_t stencil_smem_bytes(int R);
 size_t vote_smem_bytes(int max_rw, int T, int max_qn);
+size_t sparse_smem_bytes(int max_rw, int max_qp);
 
 // ---------------------------------------------------------------------------
 // FP64 replicas of the definition (one correctly rounded IEEE op per call)

@@ -70,6 +70,7 @@ def load_library(build: bool = False) -> ctypes.CDLL:
         "rd_debug_ridges": (c_int, [c_void_p, c_int, P(c_int32), P(c_float), P(c_int64), c_int]),
         "rd_debug_capture": (c_int, [c_void_p, c_void_p, c_void_p]),
         "rd_set_timing": (c_int, [c_void_p, c_int]),
+        "rd_debug_route": (c_int, [c_void_p, c_int]),
         "rd_get_timing": (c_int, [c_void_p, P(c_float), c_int]),
     }
     for name, (res, args) in sig.items():
@@ -237,6 +238,11 @@ class Detector:
         m = self.lib.rd_debug_ridges(self.ctx, f, xy.ctypes.data_as(POINTER(c_int32)),
                                      d.ctypes.data_as(POINTER(c_float)), h.ctypes.data_as(POINTER(c_int64)), n)
         return xy, d, h
+
+    def debug_route(self, all_dense: bool):
+        st = self.lib.rd_debug_route(self.ctx, 1 if all_dense else 0)
+        if st != RD_OK:
+            raise self._err(st)
 
     def debug_capture(self, acc=None, sm=None):
         st = self.lib.rd_debug_capture(self.ctx, c_void_p(acc.data_ptr() if acc is not None else 0),

@@ -25,12 +25,14 @@ def torch():
     return t
 
 
-def run(torch, frames, params, capture=False, max_hw=None):
+def run(torch, frames, params, capture=False, max_hw=None, dense=False):
     from paper_1310_1371_gb300 import rd
     frames = [np.ascontiguousarray(f) for f in frames]
     H, W = frames[0].shape
     mh, mw = max_hw or (H, W)
     det = rd.Detector(params, mh, mw, len(frames))
+    if dense:
+        det.debug_route(True)
     t = torch.from_numpy(np.stack(frames)).cuda()
     acc = sm = None
     if capture:
@@ -85,9 +87,9 @@ def assert_ridges_match(ridge, image, p):
     assert np.abs(np.abs(d) - np.abs(ref_X)).max() < 1.2e-7
 
 
-def check_frame(torch, image, params, capture=False):
+def check_frame(torch, image, params, capture=False, dense=False):
     p = O.Params.make(**params)
-    out = run(torch, [image], params, capture=capture)
+    out = run(torch, [image], params, capture=capture, dense=dense)
     ref = O.detect(image, p, keep=capture)
     assert_ridges_match(out["ridges"][0], image, p)
     assert out["stats"].votes == ref.votes_in
@@ -105,6 +107,18 @@ def test_plain_small_stagewise(torch):
     f = synth.plain_small()
     out, ref = check_frame(torch, f.image, f.params, capture=True)
     assert len(ref.rings) == 8
+
+
+def test_plain_small_dense_route(torch):
+    """The dense-storage voting kernel (the fallback for crowded tiles) on
+    every tile gives the same accumulators and rings."""
+    f = synth.plain_small(seed=14)
+    check_frame(torch, f.image, f.params, capture=True, dense=True)
+
+
+def test_plain_full_dense_route(torch):
+    f = synth.plain_full(seed=[1002, 3])
+    check_frame(torch, f.image, f.params, dense=True)
 
 
 @pytest.mark.parametrize("seed", [11, 12, 13])
