@@ -619,6 +619,7 @@ __global__ void __launch_bounds__(VOTE_THREADS, 4) k_vote(VoteArgs a) {
   const size_t fbase = (size_t)f * a.rl.cap;
   const int lv0 = a.r_min - 1;
   const int rounds = (cnt + VOTE_THREADS - 1) / VOTE_THREADS;
+  const uint4* __restrict__ bin = a.pool + off;  // read-only for the whole kernel
   __syncthreads();
 
   for (int r = lo - 1; r <= hi + 1 && !s_abort; ++r) {
@@ -641,7 +642,7 @@ __global__ void __launch_bounds__(VOTE_THREADS, 4) k_vote(VoteArgs a) {
     for (int j = 0; j < rounds; ++j) {
       const int e = j * VOTE_THREADS + tid;
       if (e >= cnt) continue;
-      const uint4 E = a.pool[off + e];
+      const uint4 E = __ldg(&bin[e]);
       const float tx_ = __fmul_rn(rf, __uint_as_float(E.y)), ty_ = __fmul_rn(rf, __uint_as_float(E.z));
       const float fx = __fadd_rn(tx_, ROUND_MAGIC), fy = __fadd_rn(ty_, ROUND_MAGIC);
       const float dx = __fsub_rn(tx_, __fsub_rn(fx, ROUND_MAGIC));
