@@ -97,6 +97,8 @@ typedef struct rd_stats {
   int64_t exact_fallbacks;  /* decisions re-taken in double precision             */
   int32_t overflow;         /* bit mask of RD_OVF_* capacities that overflowed    */
   int32_t n_frames;
+  int64_t hotspots;         /* voxels above the integer vote threshold            */
+  int64_t smooth_macs;      /* weight x count products of their smoothing windows */
 } rd_stats;
 
 #define RD_OVF_RIDGE 1      /* ridge list of a frame full                         */

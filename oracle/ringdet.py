@@ -419,6 +419,8 @@ class Result:
     ridge_X: np.ndarray          # [n, 2] float64 direction
     votes_in: int                # in-bounds votes over all levels
     votes_cast: int              # 2 * n_ridge * n_levels
+    hotspots: int = 0            # voxels above the integer threshold over all levels
+    smooth_macs: int = 0         # sum over hotspots of their smoothing window size
     A: dict | None = None        # level -> raw accumulator (when kept)
     N: dict | None = None        # level -> smoothed accumulator (when kept)
 
@@ -448,13 +450,18 @@ def detect(image: np.ndarray, p: Params, keep: bool = False) -> Result:
     levels = radius_levels(p.r_min, p.r_max)
     Ns, As = {}, {}
     votes_in = 0
+    hotspots = smooth_macs = 0
     peaks = []
     for r in levels:
         r = int(r)
         bx, by = cast_votes(xs, ys, ridge_X[:, 0], ridge_X[:, 1], r, H, W)
         votes_in += len(bx)
         A = accumulate(bx, by, H, W)
-        Ns[r] = smooth_hot(A, smoothing_weights(r, p.sig_a, p.sig_b), p.vote_thresh)
+        Qr = smoothing_weights(r, p.sig_a, p.sig_b)
+        Ns[r] = smooth_hot(A, Qr, p.vote_thresh)
+        n_hot = int((A > p.vote_thresh).sum())
+        hotspots += n_hot
+        smooth_macs += n_hot * Qr.size
         if keep:
             As[r] = A
         if r - 1 >= p.r_min:
@@ -467,5 +474,5 @@ def detect(image: np.ndarray, p: Params, keep: bool = False) -> Result:
         pts = annulus_members(ridge_xy, ix, iy, ir, p.annulus_w)
         cx, cy, rr, nfit, flags = kasa_fit(pts, ix, iy, ir)
         rings[i] = (cx, cy, rr, ix, iy, ir, nv / (float(1 << SMOOTH_BITS) * ir), nfit, flags)
-    return Result(rings, ridge_xy, ridge_X, votes_in, 2 * len(xs) * len(levels),
+    return Result(rings, ridge_xy, ridge_X, votes_in, 2 * len(xs) * len(levels), hotspots, smooth_macs,
                   As if keep else None, Ns if keep else None)

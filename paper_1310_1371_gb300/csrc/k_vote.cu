@@ -397,6 +397,20 @@ __device__ __forceinline__ void dense_bin(const VoteArgs& a, int b, unsigned cha
     // ---- phase 2: radius-dependent smoothing at this level's hotspots
     uint32_t* cur = sN + slot * RW2 * RW2;
     const int nhot = s_nhot[lst];
+    if (cc.owned && tid == 0) {  // algorithmic work counters: each hotspot once
+      unsigned long long own = 0;
+      for (int v = 0; v < RW2 * RW2; ++v) {
+        const int vyr = v / RW2, vxr = v - vyr * RW2;
+        const int gx = tx * T - 1 + vxr, gy = ty * T - 1 + vyr;
+        if (vyr >= 1 && vyr <= T && vxr >= 1 && vxr <= T && gx < W && gy < H &&
+            sA[(vyr + h - 1) * RW + (vxr + h - 1)] > vthr)
+          ++own;
+      }
+      if (own) {
+        atomicAdd(&a.stats->hotspots, own);
+        atomicAdd(&a.stats->smooth_macs, own * (unsigned long long)nq);
+      }
+    }
     if (tid == 0) {
       // the list of level r - 3 (cleared in phase 1a above) is reused by level r + 1
       s_nhot[(r + 1) & 3] = 0;
@@ -601,7 +615,7 @@ __global__ void __launch_bounds__(VOTE_THREADS, 4) k_vote(VoteArgs a) {
   int4* sPk = reinterpret_cast<int4*>(smem + L.pk);
   const int nA4 = (((RW * RW + 1) / 2) + 3) / 4;
   __shared__ int s_nhot[4], s_npk, s_abort;
-  __shared__ unsigned long long s_votes, s_fb;
+  __shared__ unsigned long long s_votes, s_fb, s_hot_own, s_macs;
 
   if (cnt < cnt_raw && tid == 0) atomicOr(&a.stats->overflow, 2);
   {
@@ -615,6 +629,8 @@ __global__ void __launch_bounds__(VOTE_THREADS, 4) k_vote(VoteArgs a) {
     s_abort = a.route_dense;
     s_votes = 0;
     s_fb = 0;
+    s_hot_own = 0;
+    s_macs = 0;
   }
   const size_t fbase = (size_t)f * a.rl.cap;
   const int lv0 = a.r_min - 1;
@@ -694,6 +710,16 @@ __global__ void __launch_bounds__(VOTE_THREADS, 4) k_vote(VoteArgs a) {
 
     // ---- phase 2: radius-dependent smoothing at this level's hotspots
     const int nhot = s_nhot[lst];
+    if (owned) {  // algorithmic work counters: each hotspot once
+      unsigned own = 0;
+      for (int k = tid; k < nhot; k += VOTE_THREADS) {
+        const uint32_t key = sCoord[lst * SP_HOT + k];
+        const int iy = (int)(key >> 8) - 1, ix = (int)(key & 0xffu) - 1;
+        own += ((unsigned)iy < (unsigned)T && (unsigned)ix < (unsigned)T) ? 1u : 0u;
+      }
+      if (own) atomicAdd(&s_hot_own, (unsigned long long)own);
+      if (own) atomicAdd(&s_macs, (unsigned long long)own * (unsigned long long)nq);
+    }
     const uint4* sQ4 = reinterpret_cast<const uint4*>(sQ);
     for (int k = warp; k < nhot; k += NW) {
       const uint32_t key = sCoord[lst * SP_HOT + k];
@@ -807,6 +833,8 @@ __global__ void __launch_bounds__(VOTE_THREADS, 4) k_vote(VoteArgs a) {
     if (npk) atomicAdd(&a.stats->peaks, (unsigned long long)npk);
     if (s_votes) atomicAdd(&a.stats->votes, s_votes);
     if (s_fb) atomicAdd(&a.stats->fallbacks, s_fb);
+    if (s_hot_own) atomicAdd(&a.stats->hotspots, s_hot_own);
+    if (s_macs) atomicAdd(&a.stats->smooth_macs, s_macs);
   }
 }
 

@@ -491,6 +491,8 @@ extern "C" rd_status rd_get_stats(rd_ctx* c, rd_stats* out) {
   out->exact_fallbacks = (int64_t)d.fallbacks;
   out->overflow = d.overflow;
   out->n_frames = c->last_n;
+  out->hotspots = (int64_t)d.hotspots;
+  out->smooth_macs = (int64_t)d.smooth_macs;
   return d.overflow ? RD_E_OVERFLOW : RD_OK;
 }
 

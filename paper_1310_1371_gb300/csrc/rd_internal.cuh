@@ -42,6 +42,7 @@ struct DevStats {
   unsigned long long ridge, votes, peaks, fallbacks;
   int overflow;
   int pad;
+  unsigned long long hotspots, smooth_macs;  // each hotspot counted once (tile interior, owned level)
 };
 
 struct GaussTaps {

@@ -35,7 +35,8 @@ class rd_ring(ctypes.Structure):
 
 class rd_stats(ctypes.Structure):
     _fields_ = [("ridge_pixels", c_int64), ("votes", c_int64), ("peaks", c_int64),
-                ("exact_fallbacks", c_int64), ("overflow", c_int32), ("n_frames", c_int32)]
+                ("exact_fallbacks", c_int64), ("overflow", c_int32), ("n_frames", c_int32),
+                ("hotspots", c_int64), ("smooth_macs", c_int64)]
 
 
 RING_NP = np.dtype([("frame", "<i4"), ("cx", "<f4"), ("cy", "<f4"), ("r", "<f4"), ("ix", "<i4"),

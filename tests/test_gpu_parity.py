@@ -93,6 +93,8 @@ def check_frame(torch, image, params, capture=False, dense=False):
     ref = O.detect(image, p, keep=capture)
     assert_ridges_match(out["ridges"][0], image, p)
     assert out["stats"].votes == ref.votes_in
+    assert out["stats"].hotspots == ref.hotspots
+    assert out["stats"].smooth_macs == ref.smooth_macs
     if capture:
         levels = O.radius_levels(p.r_min, p.r_max)
         for li, r in enumerate(levels):
