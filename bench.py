@@ -266,7 +266,9 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u16", "data": "synthetic",
             "config": {"workload": WORKLOAD, "batch_frames": B, "frames_bytes": int(imgs.nbytes),
-                       "l2": "inputs (192 MiB) larger than L2; no flush", "parallelism": f"replicas x{world}"},
+                       "l2": (f"inputs ({imgs.nbytes / 2**20:.0f} MiB) larger than L2; no flush" if imgs.nbytes > 129e6
+                              else f"inputs ({imgs.nbytes / 2**20:.0f} MiB) fit in L2: L2-warm"),
+                       "parallelism": f"replicas x{world}"},
             "mvotes_per_s": votes_per_step * args.steps * world / (ms / 1e3) / 1e6,
             "votes_per_frame": votes_per_step / B, "ridge_pixels_per_frame": ridge_per_step / B,
             "rings_per_frame": stats.peaks / B, "exact_fallbacks_per_frame": stats.exact_fallbacks / B,
