@@ -198,6 +198,52 @@ int       rd_debug_ridges(rd_ctx* ctx, int f, int32_t* xy, float* dir, int64_t* 
 rd_status rd_debug_route(rd_ctx* ctx, int all_dense);
 rd_status rd_debug_capture(rd_ctx* ctx, int32_t* acc_dev, uint32_t* sm_dev);
 
+/* ---- allocation-free directed-ridge stages --------------------------------
+ * The paper has no counterpart to this entry point.  It serves callers that
+ * cannot allocate device memory where they call the detector: acquisition
+ * loops that forbid cudaMalloc on the per-frame path (it can synchronise the
+ * whole device and its latency is unbounded), plug-ins whose host
+ * application owns every device allocation through its own pool, and
+ * processes whose device memory another framework has already reserved.
+ *
+ * rd_ridges_static runs the first stages of rd_detect on ONE frame --
+ * Gaussian smoothing, exact Hessian, directed-ridge mask, direction
+ * refinement -- and allocates nothing.  Its intermediate data (exact
+ * Hessians, per-tile record index, vote-rounding margins, counters; about
+ * 8.4 MB) live in one fixed device array inside the library, which every GPU
+ * that loads the library holds until the process exits.
+ *   params    : only sigma and ridge_thresh are read (ranges as in rd_params).
+ *   frame_dev : H x W pixels of type dtype, row-major, device, read only,
+ *               caller-owned; H, W in [max(12, ceil(4 sigma) + 4), 65535] and
+ *               H * W <= RD_STATIC_MAX_PIXELS.
+ *   xy_dev    : caller-owned device uint32[cap]: x | y << 16 per ridge pixel.
+ *   dir_dev   : caller-owned device float[4 * cap], 16-byte aligned:
+ *               (Xhi, Yhi, Xlo, Ylo) per ridge pixel, the unit direction
+ *               X- = (Xhi + Xlo, Yhi + Ylo) with canonical sign (X > 0, or
+ *               X == 0 and Y > 0).
+ *   cap       : record capacity, 0 <= cap <= RD_STATIC_MAX_RIDGE.
+ *   count_dev : caller-owned device int: the true number of ridge pixels;
+ *               when it exceeds cap, the records past cap are dropped.
+ * The records are the ridge pixels rd_detect finds in the same frame with
+ * the same parameters (rd_debug_ridges), in an unspecified order.  Work is
+ * enqueued on stream; outputs are valid once the stream has synchronised.
+ * Errors: RD_E_INVAL (NULL pointer, bad parameter, frame or cap beyond the
+ * limits, unaligned dir_dev: nothing is enqueued), RD_E_CUDA (set-up or a
+ * launch failed).  The message is in rd_static_last_error (per host thread).
+ * Set-up: the first call on each device, with that device current, looks up
+ * the array's device address (cudaGetSymbolAddress) and the SM count; make
+ * that first call before any stream capture on that device.
+ * Sharing: every call on a device uses the same array, which keeps the last
+ * call's contents (each call clears its counters on its stream before use).
+ * Calls whose GPU work overlaps -- on streams with no ordering between them,
+ * or from several host threads -- race on the array and give wrong results:
+ * order them on one stream. */
+#define RD_STATIC_MAX_PIXELS (1 << 20)  /* e.g. 1024 x 1024 */
+#define RD_STATIC_MAX_RIDGE  (1 << 18)
+rd_status   rd_ridges_static(const rd_params* params, const void* frame_dev, int H, int W, int dtype,
+                             void* stream, uint32_t* xy_dev, float* dir_dev, int cap, int* count_dev);
+const char* rd_static_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -73,6 +73,9 @@ def load_library(build: bool = False) -> ctypes.CDLL:
         "rd_set_timing": (c_int, [c_void_p, c_int]),
         "rd_debug_route": (c_int, [c_void_p, c_int]),
         "rd_get_timing": (c_int, [c_void_p, P(c_float), c_int]),
+        "rd_ridges_static": (c_int, [P(rd_params), c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
+                                     c_int, c_void_p]),
+        "rd_static_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -116,6 +119,36 @@ def rd_level_weights(sig_a: float, sig_b: float, r: int) -> np.ndarray:
 
 def rd_peak_threshold(peak_frac: float, r: int) -> int:
     return int(load_library().rd_peak_threshold(peak_frac, r))
+
+
+RD_STATIC_MAX_PIXELS = 1 << 20
+RD_STATIC_MAX_RIDGE = 1 << 18
+
+
+def rd_ridges_static(params: dict, frame, xy, dirs, count, stream=None) -> None:
+    """rd_ridges_static: directed ridge pixels of one device frame [H, W]
+    (uint8 / uint16) into caller-owned device tensors xy (int32 [cap]), dirs
+    (float32 [cap, 4]) and count (int32 [1]).  Allocates no device memory, for
+    callers that cannot; scratch is a fixed array inside the library, shared
+    by every call on the device, so calls must be ordered on one stream."""
+    import torch
+    lib = load_library()
+    for t in (frame, xy, dirs, count):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("arguments must be contiguous CUDA tensors")
+    if xy.dtype != torch.int32 or dirs.dtype != torch.float32 or count.dtype != torch.int32:
+        raise TypeError("xy and count must be int32, dirs float32")
+    cap = xy.numel()
+    if dirs.numel() < 4 * cap or count.numel() < 1:
+        raise ValueError("dirs needs 4 * cap floats and count one int")
+    H, W = frame.shape
+    s = stream if stream is not None else torch.cuda.current_stream()
+    p = make_params(**params)
+    st = lib.rd_ridges_static(ctypes.byref(p), c_void_p(frame.data_ptr()), H, W, Detector.dtype_code(frame.dtype),
+                              c_void_p(s.cuda_stream), c_void_p(xy.data_ptr()), c_void_p(dirs.data_ptr()), cap,
+                              c_void_p(count.data_ptr()))
+    if st != RD_OK:
+        raise RdError(st, lib.rd_static_last_error().decode())
 
 
 # ---- the detector ------------------------------------------------------------------
