@@ -276,11 +276,9 @@ __device__ __forceinline__ void dense_bin(const VoteArgs& a, int b, unsigned cha
   uint32_t* sA = reinterpret_cast<uint32_t*>(smem + L.a);   // RW^2 vote counts
   uint16_t* sHot = reinterpret_cast<uint16_t*>(smem + L.hot);  // 4 x HOT_CAP, (vy << 8 | vx)
   const int nA4 = (RW * RW + 3) / 4;
-  int* s_nhot = reinterpret_cast<int*>(smem + L.total);          // 4 counters, 4 flags, 2 x u64
+  int* s_nhot = reinterpret_cast<int*>(smem + L.total);          // 4 counters, 4 flags, 2 sums
   int* s_dense = s_nhot + 4;
-  unsigned long long* s_acc64 = reinterpret_cast<unsigned long long*>(s_nhot + 8);
-  unsigned long long& s_votes = s_acc64[0];
-  unsigned long long& s_fb = s_acc64[1];
+  unsigned* s_sum = reinterpret_cast<unsigned*>(s_nhot + 8);     // votes, fallbacks of this bin
 
   if (cnt < cnt_raw && tid == 0) atomicOr(&a.stats->overflow, 2);
   {
@@ -290,9 +288,10 @@ __device__ __forceinline__ void dense_bin(const VoteArgs& a, int b, unsigned cha
   for (int i = tid; i < 3 * RW2 * RW2; i += VOTE_THREADS) sN[i] = 0;
   if (tid == 0) {
     for (int k = 0; k < 4; ++k) s_nhot[k] = s_dense[k] = 0;
-    s_votes = 0;
-    s_fb = 0;
+    s_sum[0] = s_sum[1] = 0;
   }
+  // per-thread counts, reduced once at the end (a bin's totals fit 32 bits)
+  unsigned t_votes = 0, t_fb = 0;
 
   const size_t fbase = (size_t)f * a.rl.cap;
   const int lv0 = a.r_min - 1;
@@ -389,8 +388,8 @@ __device__ __forceinline__ void dense_bin(const VoteArgs& a, int b, unsigned cha
       }
       warp_push(hot, (uint16_t)vyx, &s_nhot[lst], sHot + lst * HOT_CAP, HOT_CAP, lane);
     }
-    if (nv) atomicAdd(&s_votes, (unsigned long long)nv);
-    if (nfb) atomicAdd(&s_fb, (unsigned long long)nfb);
+    t_votes += nv;
+    t_fb += nfb;
     cp_async_wait_all();
     __syncthreads();
 
@@ -524,9 +523,15 @@ __device__ __forceinline__ void dense_bin(const VoteArgs& a, int b, unsigned cha
     }
     __syncthreads();
   }
+  {
+    const unsigned wv = __reduce_add_sync(0xffffffffu, t_votes), wf = __reduce_add_sync(0xffffffffu, t_fb);
+    if (lane == 0 && wv) atomicAdd(&s_sum[0], wv);
+    if (lane == 0 && wf) atomicAdd(&s_sum[1], wf);
+  }
+  __syncthreads();
   if (tid == 0) {
-    if (s_votes) atomicAdd(&a.stats->votes, s_votes);
-    if (s_fb) atomicAdd(&a.stats->fallbacks, s_fb);
+    if (s_sum[0]) atomicAdd(&a.stats->votes, (unsigned long long)s_sum[0]);
+    if (s_sum[1]) atomicAdd(&a.stats->fallbacks, (unsigned long long)s_sum[1]);
   }
 }
 
@@ -615,7 +620,7 @@ __global__ void __launch_bounds__(VOTE_THREADS, 4) k_vote(VoteArgs a) {
   int4* sPk = reinterpret_cast<int4*>(smem + L.pk);
   const int nA4 = (((RW * RW + 1) / 2) + 3) / 4;
   __shared__ int s_nhot[4], s_npk, s_abort;
-  __shared__ unsigned long long s_votes, s_fb, s_hot_own, s_macs;
+  __shared__ unsigned s_sum[4];  // votes, fallbacks, owned hotspots, smoothing MACs of this bin
 
   if (cnt < cnt_raw && tid == 0) atomicOr(&a.stats->overflow, 2);
   {
@@ -627,11 +632,11 @@ __global__ void __launch_bounds__(VOTE_THREADS, 4) k_vote(VoteArgs a) {
     for (int k = 0; k < 4; ++k) s_nhot[k] = 0;
     s_npk = 0;
     s_abort = a.route_dense;
-    s_votes = 0;
-    s_fb = 0;
-    s_hot_own = 0;
-    s_macs = 0;
+    for (int k = 0; k < 4; ++k) s_sum[k] = 0;
   }
+  // Per-thread counts, reduced once at the end: a bin's totals fit 32 bits
+  // (votes and fallbacks <= 10 levels x its entries, MACs <= 10 x SP_HOT x 81^2).
+  unsigned t_votes = 0, t_fb = 0, t_hot = 0, t_macs = 0;
   const size_t fbase = (size_t)f * a.rl.cap;
   const int lv0 = a.r_min - 1;
   const int rounds = (cnt + VOTE_THREADS - 1) / VOTE_THREADS;
@@ -702,8 +707,8 @@ __global__ void __launch_bounds__(VOTE_THREADS, 4) k_vote(VoteArgs a) {
         }
       }
     }
-    if (nv) atomicAdd(&s_votes, (unsigned long long)nv);
-    if (nfb) atomicAdd(&s_fb, (unsigned long long)nfb);
+    t_votes += nv;
+    t_fb += nfb;
     cp_async_wait_all();
     __syncthreads();
     if (s_abort) break;  // uniform: read after the barrier
@@ -717,8 +722,8 @@ __global__ void __launch_bounds__(VOTE_THREADS, 4) k_vote(VoteArgs a) {
         const int iy = (int)(key >> 8) - 1, ix = (int)(key & 0xffu) - 1;
         own += ((unsigned)iy < (unsigned)T && (unsigned)ix < (unsigned)T) ? 1u : 0u;
       }
-      if (own) atomicAdd(&s_hot_own, (unsigned long long)own);
-      if (own) atomicAdd(&s_macs, (unsigned long long)own * (unsigned long long)nq);
+      t_hot += own;
+      t_macs += own * (unsigned)nq;
     }
     const uint4* sQ4 = reinterpret_cast<const uint4*>(sQ);
     for (int k = warp; k < nhot; k += NW) {
@@ -821,6 +826,17 @@ __global__ void __launch_bounds__(VOTE_THREADS, 4) k_vote(VoteArgs a) {
     }
     return;
   }
+  {
+    const unsigned c0 = __reduce_add_sync(0xffffffffu, t_votes), c1 = __reduce_add_sync(0xffffffffu, t_fb);
+    const unsigned c2 = __reduce_add_sync(0xffffffffu, t_hot), c3 = __reduce_add_sync(0xffffffffu, t_macs);
+    if (lane == 0) {
+      if (c0) atomicAdd(&s_sum[0], c0);
+      if (c1) atomicAdd(&s_sum[1], c1);
+      if (c2) atomicAdd(&s_sum[2], c2);
+      if (c3) atomicAdd(&s_sum[3], c3);
+    }
+  }
+  __syncthreads();
   const int npk = s_npk;
   for (int k = tid; k < npk; k += VOTE_THREADS) {
     const int kk = atomicAdd(&a.peak_count[f], 1);
@@ -831,10 +847,10 @@ __global__ void __launch_bounds__(VOTE_THREADS, 4) k_vote(VoteArgs a) {
   }
   if (tid == 0) {
     if (npk) atomicAdd(&a.stats->peaks, (unsigned long long)npk);
-    if (s_votes) atomicAdd(&a.stats->votes, s_votes);
-    if (s_fb) atomicAdd(&a.stats->fallbacks, s_fb);
-    if (s_hot_own) atomicAdd(&a.stats->hotspots, s_hot_own);
-    if (s_macs) atomicAdd(&a.stats->smooth_macs, s_macs);
+    if (s_sum[0]) atomicAdd(&a.stats->votes, (unsigned long long)s_sum[0]);
+    if (s_sum[1]) atomicAdd(&a.stats->fallbacks, (unsigned long long)s_sum[1]);
+    if (s_sum[2]) atomicAdd(&a.stats->hotspots, (unsigned long long)s_sum[2]);
+    if (s_sum[3]) atomicAdd(&a.stats->smooth_macs, (unsigned long long)s_sum[3]);
   }
 }
 
