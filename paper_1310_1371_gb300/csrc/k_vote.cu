@@ -635,7 +635,8 @@ __global__ void __launch_bounds__(VOTE_THREADS, 4) k_vote(VoteArgs a) {
     for (int k = 0; k < 4; ++k) s_sum[k] = 0;
   }
   // Per-thread counts, reduced once at the end: a bin's totals fit 32 bits
-  // (votes and fallbacks <= 10 levels x its entries, MACs <= 10 x SP_HOT x 81^2).
+  // (votes and fallbacks <= SLAB_LEVELS + 2 levels x its entries, MACs <=
+  // (SLAB_LEVELS + 2) x SP_HOT x 81^2).
   unsigned t_votes = 0, t_fb = 0, t_hot = 0, t_macs = 0;
   const size_t fbase = (size_t)f * a.rl.cap;
   const int lv0 = a.r_min - 1;

@@ -33,6 +33,7 @@ struct rd_ctx {
   double D64;
   float invD;
   int n_levels, n_slabs, max_rw, max_qn;
+  int T;  // accumulator tile edge (ACC_T, or ACC_T_SMALL when the dense kernel would not fit)
   std::vector<int4> h_slabs;
   // device buffers
   int4* slabs = nullptr;
@@ -214,16 +215,21 @@ extern "C" rd_status rd_create(const rd_params* params, int max_H, int max_W, in
     c->max_qn = std::max(c->max_qn, nq + (nq & 1));
   }
   // r-slabs of SLAB_LEVELS peak levels; halo = 1 + the largest R_s of the slab's voting levels
-  c->max_rw = 0;
+  int max_h = 0;
   for (int lo = params->r_min; lo <= params->r_max; lo += SLAB_LEVELS) {
     int hi = std::min(lo + SLAB_LEVELS - 1, params->r_max);
     int h = 0;
     for (int r = lo - 1; r <= hi + 1; ++r) h = std::max(h, h_qrad[r - lv0]);
     h += 1;
     c->h_slabs.push_back(make_int4(lo, hi, h, 0));
-    c->max_rw = std::max(c->max_rw, ACC_T + 2 * h);
+    max_h = std::max(max_h, h);
   }
   c->n_slabs = (int)c->h_slabs.size();
+  // The larger tile casts fewer halo votes per owned voxel; it is taken when
+  // the dense kernel's per-tile storage still fits one SM.
+  c->T = ACC_T;
+  if (vote_smem_bytes(ACC_T + 2 * max_h, ACC_T, c->max_qn) > 227 * 1024) c->T = ACC_T_SMALL;
+  c->max_rw = c->T + 2 * max_h;
   // per slab: (weight, offset) of every tap of its voting levels; offsets are
   // relative to the window centre in the slab's shared-memory layout
   std::vector<int> h_qqoff((size_t)c->n_slabs * (SLAB_LEVELS + 2), 0);
@@ -232,7 +238,7 @@ extern "C" rd_status rd_create(const rd_params* params, int max_H, int max_W, in
   std::vector<uint32_t> h_qptab;
   for (int si = 0; si < c->n_slabs; ++si) {
     const int4 sl = c->h_slabs[si];
-    const int RW = ACC_T + 2 * sl.z;
+    const int RW = c->T + 2 * sl.z;
     for (int r = sl.x - 1; r <= sl.y + 1; ++r) {
       const int li = r - lv0, Rs = h_qrad[li], Wq = 2 * Rs + 1;
       h_qqoff[(size_t)si * (SLAB_LEVELS + 2) + (r - sl.x + 1)] = (int)h_qqtab.size();
@@ -252,13 +258,14 @@ extern "C" rd_status rd_create(const rd_params* params, int max_H, int max_W, in
       c->max_qp = std::max(c->max_qp, (Wq * Wq + 3) & ~3);
     }
   }
-  if (vote_smem_bytes(c->max_rw, ACC_T, c->max_qn) > 227 * 1024 || c->max_rw * c->max_rw > 65535 * 2) {
+  if (vote_smem_bytes(c->max_rw, c->T, c->max_qn) > 227 * 1024 ||
+      sparse_smem_bytes(c->max_rw, c->max_qp) > 227 * 1024 || c->max_rw * c->max_rw > 65535 * 2) {
     delete c;
     return fail(nullptr, RD_E_INVAL, "radius range needs more shared memory than one SM has");
   }
   // workspaces
   const int n_stx = (max_W + ST_TW - 1) / ST_TW, n_sty = (max_H + ST_TH - 1) / ST_TH;
-  const int n_atx = (max_W + ACC_T - 1) / ACC_T, n_aty = (max_H + ACC_T - 1) / ACC_T;
+  const int n_atx = (max_W + c->T - 1) / c->T, n_aty = (max_H + c->T - 1) / c->T;
   c->rl.cap = std::max(4096, (int)std::min<long long>((long long)max_H * max_W / 4, 1LL << 24));
   c->rl.n_stx = n_stx;
   c->rl.n_sty = n_sty;
@@ -325,7 +332,7 @@ extern "C" rd_status rd_detect(rd_ctx* c, const void* frames_dev, int n, int H, 
   c->last_W = W;
 
   const int n_stx = (W + ST_TW - 1) / ST_TW, n_sty = (H + ST_TH - 1) / ST_TH;
-  const int n_atx = (W + ACC_T - 1) / ACC_T, n_aty = (H + ACC_T - 1) / ACC_T;
+  const int n_atx = (W + c->T - 1) / c->T, n_aty = (H + c->T - 1) / c->T;
   const long long n_bins = (long long)n * n_atx * n_aty * c->n_slabs;
   RidgeList rl = c->rl;
   rl.n_stx = n_stx;
@@ -374,7 +381,7 @@ extern "C" rd_status rd_detect(rd_ctx* c, const void* frames_dev, int n, int H, 
   ba.n_atx = n_atx;
   ba.n_aty = n_aty;
   ba.n_slabs = c->n_slabs;
-  ba.T = ACC_T;
+  ba.T = c->T;
   ba.slabs = c->slabs;
   ba.bin_cnt = c->bin_cnt;
   ba.bin_off = c->bin_off;
@@ -394,7 +401,7 @@ extern "C" rd_status rd_detect(rd_ctx* c, const void* frames_dev, int n, int H, 
   va.n_atx = n_atx;
   va.n_aty = n_aty;
   va.n_slabs = c->n_slabs;
-  va.T = ACC_T;
+  va.T = c->T;
   va.slabs = c->slabs;
   va.bin_cnt = c->bin_cnt;
   va.bin_off = c->bin_off;

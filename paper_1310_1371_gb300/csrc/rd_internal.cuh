@@ -27,10 +27,11 @@ constexpr int MAX_RG = 16;         // Gaussian half-width ceil(4 sigma), sigma <
 constexpr int ST_TW = 32;          // stencil tile (output pixels)
 constexpr int ST_TH = 32;
 constexpr int ST_THREADS = 256;
-constexpr int ACC_T = 64;          // accumulator tile edge
+constexpr int ACC_T = 96;          // accumulator tile edge
+constexpr int ACC_T_SMALL = 64;    // tile edge when the dense kernel needs the room (large r_max)
 constexpr int VOTE_THREADS = 256;
 constexpr int MAX_RS = 40;         // level smoothing half-width ceil(3 sigma(r))
-constexpr int SLAB_LEVELS = 8;     // peak levels per r-slab
+constexpr int SLAB_LEVELS = 12;    // peak levels per r-slab
 constexpr int FIT_WARPS = 8;
 // Vote-rounding margin coefficient shared by every well-conditioned ridge
 // pixel: 1.25 (|X_lo| + e_X + 2^-24) + 2^-24 with |X_lo| <= 2^-25 and the

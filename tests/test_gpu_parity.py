@@ -142,6 +142,24 @@ def test_ragged_frame_and_borders(torch):
     check_frame(torch, img, params, capture=True)
 
 
+def test_large_radius_range_small_tiles(torch):
+    """Search radii up to 170: the dense voting kernel's per-tile storage for
+    96-pixel accumulator tiles (window halo 28 px) no longer fits one SM, so
+    the context works on 64-pixel tiles; both voting routes must still agree
+    with the oracle, the largest ring (r = 140) included."""
+    rng = np.random.default_rng(41)
+    H = W = 320
+    yy, xx = np.mgrid[0:H, 0:W].astype(float)
+    img = np.full((H, W), 40.0)
+    for cx, cy, R in [(160.3, 158.7, 140.0), (60.2, 70.5, 20.0), (250.0, 240.0, 35.5), (120.6, 200.2, 52.0)]:
+        img += 120 * np.exp(-0.5 * ((np.hypot(xx - cx, yy - cy) - R) / 1.5) ** 2)
+    img = np.clip(np.rint(img + rng.normal(0, 8, img.shape)), 0, 255).astype(np.uint8)
+    params = dict(synth.PLAIN_SMALL_PARAMS, r_min=5, r_max=170)
+    out, ref = check_frame(torch, img, params)
+    assert len(ref.rings) == 4 and max(r[2] for r in ref.rings) > 139
+    check_frame(torch, img, params, dense=True)
+
+
 def test_flat_frame_has_nothing(torch):
     img = np.full((64, 64), 100, dtype=np.uint8)
     out, ref = check_frame(torch, img, synth.PLAIN_SMALL_PARAMS)
