@@ -65,7 +65,10 @@ __global__ void __launch_bounds__(256) k_bin(BinArgs a) {
               long long pos = (long long)a.bin_off[b] + atomicAdd(&a.bin_fill[b], 1);
               if (pos < a.pool_cap) {
                 const uint32_t ill = a.rl.kvote[g].x > KF_CONST ? 2u : 0u;
-                a.pool[pos] = make_uint4(xy, __float_as_uint(sgn * d.x), __float_as_uint(sgn * d.y),
+                // position relative to the tile region's origin (tx T - h, ty T - h)
+                const int lx0 = (int)(xy & 0xffffu) - (tx * a.T - h), ly0 = (int)(xy >> 16) - (ty * a.T - h);
+                a.pool[pos] = make_uint4(((uint32_t)ly0 << 16) | ((uint32_t)lx0 & 0xffffu),
+                                         __float_as_uint(sgn * d.x), __float_as_uint(sgn * d.y),
                                          ((uint32_t)i << 2) | ill | (uint32_t)sg);
               }
             }
@@ -168,7 +171,7 @@ __device__ __forceinline__ void warp_push(bool pred, uint16_t val, int* cnt, uin
 
 // A bin entry as a thread holds it across the levels of its slab.
 struct VEnt {
-  uint32_t xy;     // x | y << 16
+  uint32_t xy;     // position relative to the tile region: int16 x | int16 y << 16
   uint32_t ent;    // ridge index << 1 | negative sign
   float X, Y, kf;  // direction (hi parts) and fast-path margin coefficient
 };
@@ -190,7 +193,8 @@ constexpr int ROUND_MAGIC_BITS = 0x4B400000;
 
 // Slow path of one vote: double-float refinement, then the double-precision
 // definition.  Returns 1 when the FP64 definition was evaluated.
-__device__ __noinline__ int vote_bins_slow(const VoteArgs& a, size_t fbase, VEnt v, float rf, int* oxy) {
+__device__ __noinline__ int vote_bins_slow(const VoteArgs& a, size_t fbase, VEnt v, int px, int py, float rf,
+                                           int* oxy) {
   const float sr = (v.ent & 1u) ? -rf : rf;
   const size_t g = fbase + (v.ent >> 1);
   const float4 d = a.rl.dir[g];
@@ -202,7 +206,6 @@ __device__ __noinline__ int vote_bins_slow(const VoteArgs& a, size_t fbase, VEnt
     oxy[1] = vy;
     return 0;
   }
-  const int px = (int)(v.xy & 0xffffu), py = (int)(v.xy >> 16);
   Eig64 e64 = eigen64(a.rl.hess[3 * g], a.rl.hess[3 * g + 1], a.rl.hess[3 * g + 2], a.D64);
   double X = e64.X, Y = e64.Y;
   if (X * (double)d.x + Y * (double)d.y < 0.0) {
@@ -215,9 +218,13 @@ __device__ __noinline__ int vote_bins_slow(const VoteArgs& a, size_t fbase, VEnt
 }
 
 struct CastCtx {
-  int ox0, oy0, RW, W, H, h, T;
+  int ox0, oy0, RW, h, T;
+  int lxlo, lxn, lylo, lyn;  // the tile region clipped to the image: [lo, lo + n)
   bool owned;
 };
+
+__device__ __forceinline__ int ent_lx(uint32_t xy) { return (int)(int16_t)(xy & 0xffffu); }
+__device__ __forceinline__ int ent_ly(uint32_t xy) { return (int)xy >> 16; }
 
 // Bin offsets of one vote by round-to-nearest with the magic constant; the
 // result equals the half-up rounding of the double-precision definition when
@@ -235,15 +242,12 @@ __device__ __forceinline__ int cast_one(const VoteArgs& a, size_t fbase, const V
   int oy = __float_as_int(fy) - ROUND_MAGIC_BITS;
   if (!(fmaxf(fabsf(dx), fabsf(dy)) < __fsub_rn(0.5f, m))) {
     int oxy[2];
-    nfb += vote_bins_slow(a, fbase, v, rf, oxy);
+    nfb += vote_bins_slow(a, fbase, v, ent_lx(v.xy) + c.ox0, ent_ly(v.xy) + c.oy0, rf, oxy);
     ox = oxy[0];
     oy = oxy[1];
   }
-  const int bx = (int)(v.xy & 0xffffu) + ox, by = (int)(v.xy >> 16) + oy;
-  const int lx = bx - c.ox0, ly = by - c.oy0;
-  if ((unsigned)bx >= (unsigned)c.W || (unsigned)by >= (unsigned)c.H || (unsigned)lx >= (unsigned)c.RW ||
-      (unsigned)ly >= (unsigned)c.RW)
-    return -1;
+  const int lx = ent_lx(v.xy) + ox, ly = ent_ly(v.xy) + oy;
+  if ((unsigned)(lx - c.lxlo) >= (unsigned)c.lxn || (unsigned)(ly - c.lylo) >= (unsigned)c.lyn) return -1;
   if (c.owned && (unsigned)(lx - c.h) < (unsigned)c.T && (unsigned)(ly - c.h) < (unsigned)c.T) ++nv;
   return ly * c.RW + lx;
 }
@@ -316,10 +320,12 @@ __device__ __forceinline__ void dense_bin(const VoteArgs& a, int b, unsigned cha
   cc.ox0 = tx * T - h;
   cc.oy0 = ty * T - h;
   cc.RW = RW;
-  cc.W = W;
-  cc.H = H;
   cc.h = h;
   cc.T = T;
+  cc.lxlo = max(0, -cc.ox0);
+  cc.lxn = min(RW, W - cc.ox0) - cc.lxlo;
+  cc.lylo = max(0, -cc.oy0);
+  cc.lyn = min(RW, H - cc.oy0) - cc.lylo;
   __syncthreads();
 
   for (int r = lo - 1; r <= hi + 1; ++r) {
@@ -608,6 +614,9 @@ __global__ void __launch_bounds__(VOTE_THREADS, 4) k_vote(VoteArgs a) {
   const int T = a.T, RW = T + 2 * h, RW2 = T + 2;
   const int ox0 = tx * T - h, oy0 = ty * T - h;
   const int H = a.H, W = a.W;
+  // the tile region clipped to the image: [lxlo, lxlo + lxn) x [lylo, lylo + lyn)
+  const int lxlo = max(0, -ox0), lxn = min(RW, W - ox0) - lxlo;
+  const int lylo = max(0, -oy0), lyn = min(RW, H - oy0) - lylo;
   const unsigned vthr = (unsigned)a.vote_thresh;
 
   const SparseSmem L = sparse_smem_layout(a.max_rw, a.max_qp);
@@ -677,15 +686,12 @@ __global__ void __launch_bounds__(VOTE_THREADS, 4) k_vote(VoteArgs a) {
         v.X = v.Y = 0.0f;
         v.kf = 0.0f;
         int oxy[2];
-        nfb += vote_bins_slow(a, fbase, v, rf, oxy);
+        nfb += vote_bins_slow(a, fbase, v, ent_lx(E.x) + ox0, ent_ly(E.x) + oy0, rf, oxy);
         ox = oxy[0];
         oy = oxy[1];
       }
-      const int bx = (int)(E.x & 0xffffu) + ox, by = (int)(E.x >> 16) + oy;
-      const int lx = bx - ox0, ly = by - oy0;
-      if ((unsigned)bx >= (unsigned)W || (unsigned)by >= (unsigned)H || (unsigned)lx >= (unsigned)RW ||
-          (unsigned)ly >= (unsigned)RW)
-        continue;
+      const int lx = ent_lx(E.x) + ox, ly = ent_ly(E.x) + oy;
+      if ((unsigned)(lx - lxlo) >= (unsigned)lxn || (unsigned)(ly - lylo) >= (unsigned)lyn) continue;
       if (owned && (unsigned)(lx - h) < (unsigned)T && (unsigned)(ly - h) < (unsigned)T) ++nv;
       const int la = ly * RW + lx;
       const unsigned sh = (la & 1) << 4;

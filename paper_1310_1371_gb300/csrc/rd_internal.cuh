@@ -87,7 +87,8 @@ struct BinArgs {
   int* bin_cnt;
   const int* bin_off;
   int* bin_fill;
-  uint4* pool;               // per entry: x | y << 16, s X, s Y, index << 2 | ill << 1 | (s < 0)
+  uint4* pool;               // per entry: int16 x | int16 y << 16 relative to the tile region
+                             // (origin (tx T - h, ty T - h)), s X, s Y, index << 2 | ill << 1 | (s < 0)
   long long pool_cap;
   DevStats* stats;
 };
