@@ -670,10 +670,13 @@ __global__ void __launch_bounds__(VOTE_THREADS, 4) k_vote(VoteArgs a) {
     const float half_m = __fsub_rn(0.5f, __fmaf_rn(rf, KF_CONST, 1e-10f));
     uint32_t* tab = sHash + lst * SP_HASH;
     unsigned nv = 0, nfb = 0;
+    uint4 En = make_uint4(0u, 0u, 0u, 0u);  // next round's entry, loaded one round ahead
+    if (tid < cnt) En = __ldg(&bin[tid]);
     for (int j = 0; j < rounds; ++j) {
       const int e = j * VOTE_THREADS + tid;
+      const uint4 E = En;
+      if (e + VOTE_THREADS < cnt) En = __ldg(&bin[e + VOTE_THREADS]);
       if (e >= cnt) continue;
-      const uint4 E = __ldg(&bin[e]);
       const float tx_ = __fmul_rn(rf, __uint_as_float(E.y)), ty_ = __fmul_rn(rf, __uint_as_float(E.z));
       const float fx = __fadd_rn(tx_, ROUND_MAGIC), fy = __fadd_rn(ty_, ROUND_MAGIC);
       const float dx = __fsub_rn(tx_, __fsub_rn(fx, ROUND_MAGIC));
@@ -744,8 +747,12 @@ __global__ void __launch_bounds__(VOTE_THREADS, 4) k_vote(VoteArgs a) {
         acc += (unsigned long long)(P.z >> 15) * ctr[((int)(P.z << 17)) >> 17];
         acc += (unsigned long long)(P.w >> 15) * ctr[((int)(P.w << 17)) >> 17];
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      // Exact warp sum in two 32-bit reductions: a lane holds at most 208 taps
+      // of weight <= 2^16 and count < 2^16, so acc < 2^40 and both the low
+      // 24 bits and acc >> 24 sum over 32 lanes without overflow.
+      const unsigned s_lo = __reduce_add_sync(0xffffffffu, (unsigned)acc & 0xffffffu);
+      const unsigned s_hi = __reduce_add_sync(0xffffffffu, (unsigned)(acc >> 24));
+      acc = (unsigned long long)s_lo + ((unsigned long long)s_hi << 24);
       if (lane == 0) {
         if (acc > 0xffffffffULL) {
           atomicOr(&a.stats->overflow, 16);
