@@ -308,9 +308,10 @@ __global__ void __launch_bounds__(ST_THREADS) k_stencil_ridge(StencilArgs a) {
 // R = sqrt(P^2 + Bq^2): X- is proportional to (Bq, -(P + R)) for P >= 0 and
 // to (-(|P| + R), Bq) otherwise; both components are computed without
 // cancellation, so the direction is accurate to ~2^-44.
-__global__ void __launch_bounds__(256) k_ridge_refine(RidgeList rl, int n_frames) {
+__global__ void __launch_bounds__(256) k_ridge_refine(RidgeList rl) {
   const int gstride = gridDim.x * blockDim.x;
-  for (int f = 0; f < n_frames; ++f) {
+  {
+    const int f = blockIdx.y;  // one grid row per frame
     int cnt = min(rl.count[f], rl.cap);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gstride) {
       size_t g = (size_t)f * rl.cap + i;
@@ -375,7 +376,8 @@ cudaError_t launch_stencil(const StencilArgs& a, int dtype, cudaStream_t st) {
 }
 
 cudaError_t launch_refine(const RidgeList& rl, int n_frames, int n_sm, cudaStream_t st) {
-  k_ridge_refine<<<n_sm * 4, 256, 0, st>>>(rl, n_frames);
+  const dim3 grid((unsigned)max(1, (n_sm * 4 + n_frames - 1) / n_frames), (unsigned)n_frames);
+  k_ridge_refine<<<grid, 256, 0, st>>>(rl);
   return cudaGetLastError();
 }
 

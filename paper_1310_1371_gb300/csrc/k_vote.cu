@@ -17,6 +17,7 @@
 // that level's hotspots into a three-level cyclic buffer of smoothed sums,
 // and peak-tests the middle level, so the 3-d accumulator never leaves the SM.
 #include "rd_internal.cuh"
+#include <algorithm>
 #include <climits>
 
 namespace rd {
@@ -28,51 +29,110 @@ __device__ __forceinline__ int floordiv(int a, int b) { return a >= 0 ? a / b : 
 // vote positions p + s r X for r in [lo-1, hi+1] lie on a segment; a bin's
 // tile collects votes within `halo` px of the tile, and a vote bin is within
 // 1/2 px of its real position (1 px margin).
-template <bool FILL>
+struct SegTiles {
+  int tx0, ty0, w, n;  // tiles [tx0, tx0 + w) x [ty0, ty0 + n / w); n = 0 when none
+};
+
+// floor(v / T) for v > -4 T (a halo is shorter than a tile): a division by a
+// compile-time constant
+template <int T>
+__device__ __forceinline__ int tile_of(int v) {
+  return (int)((unsigned)(v + 4 * T) / (unsigned)T) - 4;
+}
+
+template <int T>
+__device__ __forceinline__ SegTiles seg_tiles(const BinArgs& a, float px, float py, float dx, float dy, float r0,
+                                              float r1, int h) {
+  SegTiles t{0, 0, 1, 0};
+  float ax0 = px + r0 * dx, ax1 = px + r1 * dx;
+  float ay0 = py + r0 * dy, ay1 = py + r1 * dy;
+  int bx0 = (int)floorf(fminf(ax0, ax1)) - 1, bx1 = (int)ceilf(fmaxf(ax0, ax1)) + 1;
+  int by0 = (int)floorf(fminf(ay0, ay1)) - 1, by1 = (int)ceilf(fmaxf(ay0, ay1)) + 1;
+  bx0 = max(bx0, 0);
+  by0 = max(by0, 0);
+  bx1 = min(bx1, a.W - 1);
+  by1 = min(by1, a.H - 1);
+  if (bx0 > bx1 || by0 > by1) return t;
+  int tx0 = max(tile_of<T>(bx0 - h), 0), tx1 = min(tile_of<T>(bx1 + h), a.n_atx - 1);
+  int ty0 = max(tile_of<T>(by0 - h), 0), ty1 = min(tile_of<T>(by1 + h), a.n_aty - 1);
+  t.tx0 = tx0;
+  t.ty0 = ty0;
+  t.w = tx1 - tx0 + 1;
+  t.n = t.w * (ty1 - ty0 + 1);
+  return t;
+}
+
+// Grid row f handles frame f.  Threads walk the ridge pixels of one slab at a
+// time, so the lanes of a warp hold neighbouring pixels, whose segments
+// mostly reach the same bins: each step the warp groups equal bins (match)
+// and the group leader makes one atomic for the group.  The entry order
+// inside a bin is immaterial downstream (votes commute; peaks are sorted
+// before the fit).
+template <bool FILL, int T>
 __global__ void __launch_bounds__(256) k_bin(BinArgs a) {
+  const int lane = threadIdx.x & 31;
   const int gstride = gridDim.x * blockDim.x;
-  for (int f = 0; f < a.n_frames; ++f) {
-    const int cnt = min(a.rl.count[f], a.rl.cap);
-    const long long total = (long long)cnt * a.n_slabs;
-    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total; it += gstride) {
-      int i = (int)(it / a.n_slabs), s = (int)(it - (long long)i * a.n_slabs);
-      size_t g = (size_t)f * a.rl.cap + i;
-      uint32_t xy = a.rl.xy[g];
-      float4 d = a.rl.dir[g];
-      float px = (float)(xy & 0xffffu), py = (float)(xy >> 16);
-      int4 sl = a.slabs[s];
-      float r0 = (float)(sl.x - 1), r1 = (float)(sl.y + 1);
-      int h = sl.z;
-      for (int sg = 0; sg < 2; ++sg) {
-        float sgn = sg == 0 ? 1.0f : -1.0f;
-        float ax0 = px + sgn * r0 * d.x, ax1 = px + sgn * r1 * d.x;
-        float ay0 = py + sgn * r0 * d.y, ay1 = py + sgn * r1 * d.y;
-        int bx0 = (int)floorf(fminf(ax0, ax1)) - 1, bx1 = (int)ceilf(fmaxf(ax0, ax1)) + 1;
-        int by0 = (int)floorf(fminf(ay0, ay1)) - 1, by1 = (int)ceilf(fmaxf(ay0, ay1)) + 1;
-        bx0 = max(bx0, 0);
-        by0 = max(by0, 0);
-        bx1 = min(bx1, a.W - 1);
-        by1 = min(by1, a.H - 1);
-        if (bx0 > bx1 || by0 > by1) continue;
-        int tx0 = max(floordiv(bx0 - h, a.T), 0), tx1 = min(floordiv(bx1 + h, a.T), a.n_atx - 1);
-        int ty0 = max(floordiv(by0 - h, a.T), 0), ty1 = min(floordiv(by1 + h, a.T), a.n_aty - 1);
-        for (int ty = ty0; ty <= ty1; ++ty)
-          for (int tx = tx0; tx <= tx1; ++tx) {
-            long long b = (((long long)f * a.n_aty + ty) * a.n_atx + tx) * a.n_slabs + s;
-            if (!FILL) {
-              atomicAdd(&a.bin_cnt[b], 1);
-            } else {
-              long long pos = (long long)a.bin_off[b] + atomicAdd(&a.bin_fill[b], 1);
-              if (pos < a.pool_cap) {
-                const uint32_t ill = a.rl.kvote[g].x > KF_CONST ? 2u : 0u;
-                // position relative to the tile region's origin (tx T - h, ty T - h)
-                const int lx0 = (int)(xy & 0xffffu) - (tx * a.T - h), ly0 = (int)(xy >> 16) - (ty * a.T - h);
-                a.pool[pos] = make_uint4(((uint32_t)ly0 << 16) | ((uint32_t)lx0 & 0xffffu),
-                                         __float_as_uint(sgn * d.x), __float_as_uint(sgn * d.y),
-                                         ((uint32_t)i << 2) | ill | (uint32_t)sg);
-              }
-            }
+  const int wbase = blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+  const int f = blockIdx.y;
+  const int cnt = min(a.rl.count[f], a.rl.cap);
+  const long long fbin = (long long)f * a.n_aty * a.n_atx * a.n_slabs;
+  for (int s = 0; s < a.n_slabs; ++s) {
+    const int4 sl = a.slabs[s];
+    const float r0 = (float)(sl.x - 1), r1 = (float)(sl.y + 1);
+    const int h = sl.z;
+    for (int base = wbase; base < cnt; base += gstride) {  // warp-uniform
+      const int i = base + lane;
+      int nb = 0;
+      SegTiles t0{0, 0, 1, 0}, t1{0, 0, 1, 0};
+      const size_t g = (size_t)f * a.rl.cap + i;
+      uint32_t xy = 0;
+      float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i < cnt) {
+        xy = a.rl.xy[g];
+        d = a.rl.dir[g];
+        const float px = (float)(xy & 0xffffu), py = (float)(xy >> 16);
+        t0 = seg_tiles<T>(a, px, py, d.x, d.y, r0, r1, h);
+        t1 = seg_tiles<T>(a, px, py, -d.x, -d.y, r0, r1, h);
+        nb = t0.n + t1.n;
+      }
+      const int maxnb = __reduce_max_sync(0xffffffffu, nb);
+      for (int k = 0; k < maxnb; ++k) {
+        unsigned key = 0xffffffffu;  // bin within the frame
+        int sg = 0, tx = 0, ty = 0;
+        if (k < nb) {
+          sg = k < t0.n ? 0 : 1;
+          const SegTiles& t = sg == 0 ? t0 : t1;
+          int kk = sg == 0 ? k : k - t0.n;
+          ty = t.ty0;
+          while (kk >= t.w) {
+            kk -= t.w;
+            ++ty;
           }
+          tx = t.tx0 + kk;
+          key = (unsigned)((ty * a.n_atx + tx) * a.n_slabs + s);
+        }
+        const unsigned grp = __match_any_sync(0xffffffffu, key);
+        if (k >= nb) continue;
+        const int leader = __ffs(grp) - 1;
+        const int n_grp = __popc(grp);
+        const long long b = fbin + key;
+        if (!FILL) {
+          if (lane == leader) atomicAdd(&a.bin_cnt[b], n_grp);
+        } else {
+          int first = 0;
+          if (lane == leader) first = atomicAdd(&a.bin_fill[b], n_grp);
+          first = __shfl_sync(grp, first, leader);
+          const long long pos = (long long)a.bin_off[b] + first + __popc(grp & ((1u << lane) - 1u));
+          if (pos < a.pool_cap) {
+            const float sgn = sg == 0 ? 1.0f : -1.0f;
+            const uint32_t ill = a.rl.kvote[g].x > KF_CONST ? 2u : 0u;
+            // position relative to the tile region's origin (tx T - h, ty T - h)
+            const int lx0 = (int)(xy & 0xffffu) - (tx * T - h), ly0 = (int)(xy >> 16) - (ty * T - h);
+            a.pool[pos] = make_uint4(((uint32_t)ly0 << 16) | ((uint32_t)lx0 & 0xffffu),
+                                     __float_as_uint(sgn * d.x), __float_as_uint(sgn * d.y),
+                                     ((uint32_t)i << 2) | ill | (uint32_t)sg);
+          }
+        }
       }
     }
   }
@@ -871,14 +931,22 @@ __global__ void __launch_bounds__(VOTE_THREADS, 4) k_vote(VoteArgs a) {
 cudaError_t launch_bins(const BinArgs& a, int n_sm, cudaStream_t st, long long n_bins, int* block_sums,
                         long long* total_dev) {
   cudaError_t e;
-  k_bin<false><<<n_sm * 8, 256, 0, st>>>(a);
+  // about 8 CTAs per SM in total, split over the frames (grid rows)
+  const dim3 grid((unsigned)std::max(1, (n_sm * 8 + a.n_frames - 1) / a.n_frames), (unsigned)a.n_frames);
+  if (a.T == ACC_T)
+    k_bin<false, ACC_T><<<grid, 256, 0, st>>>(a);
+  else
+    k_bin<false, ACC_T_SMALL><<<grid, 256, 0, st>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   int nb = (int)((n_bins + 1023) / 1024);
   k_scan_blocks<<<nb, 1024, 0, st>>>(a.bin_cnt, const_cast<int*>(a.bin_off), block_sums, n_bins);
   k_scan_sums<<<1, 1024, 0, st>>>(block_sums, nb, total_dev);
   k_scan_add<<<nb, 1024, 0, st>>>(const_cast<int*>(a.bin_off), block_sums, n_bins);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_bin<true><<<n_sm * 8, 256, 0, st>>>(a);
+  if (a.T == ACC_T)
+    k_bin<true, ACC_T><<<grid, 256, 0, st>>>(a);
+  else
+    k_bin<true, ACC_T_SMALL><<<grid, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 
