@@ -127,6 +127,28 @@ __device__ __forceinline__ int ridge_fast(const float* sK, const float* sE, int 
   return verdict;
 }
 
+// Shared-memory layout of K1 (byte offsets, all 8-byte aligned): the
+// smoothed tile L' (u64), then one region holding first the input tile and
+// the horizontal pass (u32) and later the exact Hessians (i64), then k- and
+// its error bound (f32), then the compaction scratch.
+struct StencilSmem {
+  size_t l, x, k, scan, total;
+};
+__host__ __device__ __forceinline__ StencilSmem stencil_smem_layout(int R) {
+  const int HALO = R + 3;
+  const size_t IW = ST_TW + 2 * HALO, IH = ST_TH + 2 * HALO;
+  const size_t PW = ST_TW + 6, LH = ST_TH + 6;
+  const size_t HW2 = ST_TW + 2, HH2 = ST_TH + 2;
+  const size_t in_bytes = (IH * IW + IH * PW) * 4, hess_bytes = 3 * HH2 * HW2 * 8;
+  StencilSmem L;
+  L.l = 0;
+  L.x = LH * PW * 8;
+  L.k = L.x + (((in_bytes > hess_bytes ? in_bytes : hess_bytes) + 7) & ~(size_t)7);
+  L.scan = L.k + 2 * HH2 * HW2 * 4;
+  L.total = L.scan + 16 * 4;
+  return L;
+}
+
 template <typename Tin>
 __global__ void __launch_bounds__(ST_THREADS) k_stencil_ridge(StencilArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -138,16 +160,19 @@ __global__ void __launch_bounds__(ST_THREADS) k_stencil_ridge(StencilArgs a) {
   const int HW2 = ST_TW + 2, HH2 = ST_TH + 2;
   const int H = a.H, W = a.W;
 
-  // shared memory carve-up (8-byte aligned pieces first)
-  unsigned long long* sL = reinterpret_cast<unsigned long long*>(smem);      // LH*PW
-  long long* sHxx = reinterpret_cast<long long*>(sL + LH * PW);             // HH2*HW2 each
+  // shared memory carve-up (8-byte aligned pieces first).  The input tile
+  // and the horizontal pass (sI, sP) are dead once the vertical pass is
+  // done, and the exact Hessians are written after it, so they share bytes.
+  const StencilSmem Ls = stencil_smem_layout(R);
+  unsigned long long* sL = reinterpret_cast<unsigned long long*>(smem + Ls.l);  // LH*PW
+  long long* sHxx = reinterpret_cast<long long*>(smem + Ls.x);                 // HH2*HW2 each
   long long* sHyy = sHxx + HH2 * HW2;
   long long* sHxy = sHyy + HH2 * HW2;
-  uint32_t* sI = reinterpret_cast<uint32_t*>(sHxy + HH2 * HW2);             // IH*IW
-  uint32_t* sP = sI + IH * IW;                                              // IH*PW
-  float* sK = reinterpret_cast<float*>(sP + IH * PW);                       // HH2*HW2
+  uint32_t* sI = reinterpret_cast<uint32_t*>(smem + Ls.x);                     // IH*IW
+  uint32_t* sP = sI + IH * IW;                                                 // IH*PW
+  float* sK = reinterpret_cast<float*>(smem + Ls.k);                           // HH2*HW2
   float* sE = sK + HH2 * HW2;
-  int* sScan = reinterpret_cast<int*>(sE + HH2 * HW2);                      // 8 warps + 2
+  int* sScan = reinterpret_cast<int*>(smem + Ls.scan);                         // 8 warps + 2
   __shared__ int32_t q[2 * MAX_RG + 1];
 
   if (tid < 2 * R + 1) q[tid] = a.taps.q[tid];
@@ -156,11 +181,20 @@ __global__ void __launch_bounds__(ST_THREADS) k_stencil_ridge(StencilArgs a) {
   const int x0 = blockIdx.x * ST_TW, y0 = blockIdx.y * ST_TH;
   const Tin* img = reinterpret_cast<const Tin*>(a.frames) + (size_t)f * H * W;
 
-  // ---- A: input tile with reflect-101 halo
-  for (int i = tid; i < IH * IW; i += ST_THREADS) {
-    int iy = i / IW, ix = i - iy * IW;
-    int gy = reflect101(y0 - HALO + iy, H), gx = reflect101(x0 - HALO + ix, W);
-    sI[i] = (uint32_t)img[(size_t)gy * W + gx];
+  // ---- A: input tile with reflect-101 halo, one row per warp step (only
+  //      tiles that reach past a border reflect)
+  {
+    const int lane = tid & 31, warp = tid >> 5;
+    const bool interior = x0 >= HALO && y0 >= HALO && x0 + ST_TW + HALO <= W && y0 + ST_TH + HALO <= H;
+    for (int iy = warp; iy < IH; iy += ST_THREADS / 32) {
+      const int gy = interior ? y0 - HALO + iy : reflect101(y0 - HALO + iy, H);
+      const Tin* row = img + (size_t)gy * W;
+      uint32_t* dst = sI + iy * IW;
+      for (int ix = lane; ix < IW; ix += 32) {
+        const int gx = interior ? x0 - HALO + ix : reflect101(x0 - HALO + ix, W);
+        dst[ix] = (uint32_t)row[gx];
+      }
+    }
   }
   __syncthreads();
 
@@ -353,14 +387,7 @@ __global__ void __launch_bounds__(256) k_ridge_refine(RidgeList rl) {
 template __global__ void k_stencil_ridge<uint8_t>(StencilArgs);
 template __global__ void k_stencil_ridge<uint16_t>(StencilArgs);
 
-size_t stencil_smem_bytes(int R) {
-  const int HALO = R + 3;
-  const int IW = ST_TW + 2 * HALO, IH = ST_TH + 2 * HALO;
-  const int PW = ST_TW + 6, LH = ST_TH + 6;
-  const int HW2 = ST_TW + 2, HH2 = ST_TH + 2;
-  return (size_t)LH * PW * 8 + (size_t)3 * HH2 * HW2 * 8 + (size_t)IH * IW * 4 + (size_t)IH * PW * 4 +
-         (size_t)2 * HH2 * HW2 * 4 + 16 * 4;
-}
+size_t stencil_smem_bytes(int R) { return stencil_smem_layout(R).total; }
 
 cudaError_t launch_stencil(const StencilArgs& a, int dtype, cudaStream_t st) {
   dim3 grid((a.W + ST_TW - 1) / ST_TW, (a.H + ST_TH - 1) / ST_TH, a.n);
