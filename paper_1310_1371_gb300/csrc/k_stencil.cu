@@ -64,7 +64,7 @@ __device__ __forceinline__ bool eig32_dir(float b, float hdf, float rad, float M
 // Exact (double-precision definition) ridge test of the pixel at Hessian
 // tile coordinates (hy, hx) = image (gy, gx).  Reads exact Hessians of the
 // pixel and of the bilinear corners from shared memory.
-__device__ bool ridge_exact(const long long* sHxx, const long long* sHyy, const long long* sHxy, int stride, int hy,
+__device__ __noinline__ bool ridge_exact(const long long* sHxx, const long long* sHyy, const long long* sHxy, int stride, int hy,
                             int hx, int gx, int gy, int H, int W, double D, double tau) {
   int c = hy * stride + hx;
   Eig64 e = eigen64(sHxx[c], sHyy[c], sHxy[c], D);
