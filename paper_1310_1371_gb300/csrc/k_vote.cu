@@ -690,6 +690,9 @@ __global__ void __launch_bounds__(VOTE_THREADS, 4) k_vote(VoteArgs a) {
   const int nA4 = (((RW * RW + 1) / 2) + 3) / 4;
   __shared__ int s_nhot[4], s_npk, s_abort;
   __shared__ unsigned s_sum[4];  // votes, fallbacks, owned hotspots, smoothing MACs of this bin
+  // per voting level lo-1 .. hi+1 of the slab: R_s, offset of its packed taps, peak threshold
+  __shared__ int s_rad[SLAB_LEVELS + 2], s_qpo[SLAB_LEVELS + 2];
+  __shared__ unsigned long long s_thr[SLAB_LEVELS + 2];
 
   if (cnt < cnt_raw && tid == 0) atomicOr(&a.stats->overflow, 2);
   {
@@ -703,6 +706,12 @@ __global__ void __launch_bounds__(VOTE_THREADS, 4) k_vote(VoteArgs a) {
     s_abort = a.route_dense;
     for (int k = 0; k < 4; ++k) s_sum[k] = 0;
   }
+  if (tid <= hi - lo + 2) {
+    const int li = lo - 1 + tid - (a.r_min - 1);
+    s_rad[tid] = a.q_rad[li];
+    s_qpo[tid] = a.qp_off[s * (SLAB_LEVELS + 2) + tid];
+    s_thr[tid] = a.nthr[li];
+  }
   // Per-thread counts, reduced once at the end: a bin's totals fit 32 bits
   // (votes and fallbacks <= SLAB_LEVELS + 2 levels x its entries, MACs <=
   // (SLAB_LEVELS + 2) x SP_HOT x 81^2).
@@ -715,11 +724,11 @@ __global__ void __launch_bounds__(VOTE_THREADS, 4) k_vote(VoteArgs a) {
 
   for (int r = lo - 1; r <= hi + 1 && !s_abort; ++r) {
     const int li = r - lv0;
-    const int Rs = a.q_rad[li];
+    const int Rs = s_rad[r - lo + 1];
     const int nq = (2 * Rs + 1) * (2 * Rs + 1);
     const int nq4 = (nq + 3) >> 2;  // packed taps in groups of four (tables padded)
     const int lst = r & 3;
-    const uint4* gq = reinterpret_cast<const uint4*>(a.qp_tab + a.qp_off[s * (SLAB_LEVELS + 2) + (r - lo + 1)]);
+    const uint4* gq = reinterpret_cast<const uint4*>(a.qp_tab + s_qpo[r - lo + 1]);
     for (int i = tid; i < nq4; i += VOTE_THREADS) cp_async16(&sQ[4 * i], &gq[i]);
     asm volatile("cp.async.commit_group;\n" ::);
 
@@ -764,13 +773,7 @@ __global__ void __launch_bounds__(VOTE_THREADS, 4) k_vote(VoteArgs a) {
         if ((unsigned)vyr < (unsigned)RW2 && (unsigned)vxr < (unsigned)RW2) {
           const int k = atomicAdd(&s_nhot[lst], 1);
           if (k < SP_HOT) {
-            const uint32_t key = ((uint32_t)vyr << 8) | (uint32_t)vxr;
-            sCoord[lst * SP_HOT + k] = (uint16_t)key;
-            uint32_t hh = sp_hash(key);
-            for (int p = 0; p < SP_HASH; ++p) {
-              if (atomicCAS(&tab[hh], SP_EMPTY, (key << 16) | (uint32_t)k) == SP_EMPTY) break;
-              hh = (hh + 1) & (SP_HASH - 1);
-            }
+            sCoord[lst * SP_HOT + k] = (uint16_t)(((uint32_t)vyr << 8) | (uint32_t)vxr);
           } else {
             s_abort = 1;
           }
@@ -783,17 +786,26 @@ __global__ void __launch_bounds__(VOTE_THREADS, 4) k_vote(VoteArgs a) {
     __syncthreads();
     if (s_abort) break;  // uniform: read after the barrier
 
-    // ---- phase 2: radius-dependent smoothing at this level's hotspots
+    // ---- phase 2: hash this level's hotspots (thread per hotspot; the peak
+    //      tests of levels r - 1 .. r + 1 look them up after the next barrier)
+    //      and smooth at them (warp per hotspot)
     const int nhot = s_nhot[lst];
-    if (owned) {  // algorithmic work counters: each hotspot once
+    {
       unsigned own = 0;
       for (int k = tid; k < nhot; k += VOTE_THREADS) {
         const uint32_t key = sCoord[lst * SP_HOT + k];
+        uint32_t hh = sp_hash(key);
+        for (int p = 0; p < SP_HASH; ++p) {
+          if (atomicCAS(&tab[hh], SP_EMPTY, (key << 16) | (uint32_t)k) == SP_EMPTY) break;
+          hh = (hh + 1) & (SP_HASH - 1);
+        }
         const int iy = (int)(key >> 8) - 1, ix = (int)(key & 0xffu) - 1;
         own += ((unsigned)iy < (unsigned)T && (unsigned)ix < (unsigned)T) ? 1u : 0u;
       }
-      t_hot += own;
-      t_macs += own * (unsigned)nq;
+      if (owned) {  // algorithmic work counters: each hotspot once
+        t_hot += own;
+        t_macs += own * (unsigned)nq;
+      }
     }
     const uint4* sQ4 = reinterpret_cast<const uint4*>(sQ);
     for (int k = warp; k < nhot; k += NW) {
@@ -847,7 +859,7 @@ __global__ void __launch_bounds__(VOTE_THREADS, 4) k_vote(VoteArgs a) {
     if (rp >= lo && rp <= hi) {
       const int pl = rp & 3;
       const int n = s_nhot[pl];
-      const unsigned long long thr = a.nthr[rp - lv0];
+      const unsigned long long thr = s_thr[rp - lo + 1];
       for (int k = tid; k < n; k += VOTE_THREADS) {
         const uint32_t key = sCoord[pl * SP_HOT + k];
         const int vyr = (int)(key >> 8), vxr = (int)(key & 0xffu);
