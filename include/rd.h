@@ -150,6 +150,42 @@ rd_status rd_get_stats(rd_ctx* ctx, rd_stats* out);
 
 rd_status rd_destroy(rd_ctx* ctx);
 
+/* ---- accumulator geometry and its autotuner --------------------------------
+ * The voting stage works on (frame, tile, slab) bins: tile x tile pixels of
+ * the accumulator and slab_levels consecutive peak levels, each held in one
+ * SM's shared memory (Results, "Directed ridge detection & votes
+ * collection"; the paper streams whole equi-radius levels instead).  The
+ * geometry changes speed only: results are bit-identical for every valid
+ * geometry.  tile is 64, 80 or 96; slab_levels is 4 .. 16; 0 in both fields
+ * asks for the automatic choice (the autotuner's cached choice for this frame
+ * size and radius range if there is one, else tile 96 -- 64 when 96 does not
+ * fit the radius range's windows -- and 12 levels). */
+typedef struct rd_geometry {
+  int tile;
+  int slab_levels;
+} rd_geometry;
+
+/* rd_create with an explicit geometry (NULL = automatic).  Errors as
+ * rd_create, plus RD_E_INVAL for a geometry outside the ranges above or one
+ * whose per-tile storage exceeds one SM's shared memory for this radius
+ * range. */
+rd_status rd_create_ex(const rd_params* params, int max_H, int max_W, int max_batch, const rd_geometry* geometry,
+                       rd_ctx** out);
+
+/* The geometry a context uses. */
+rd_status rd_get_geometry(const rd_ctx* ctx, rd_geometry* out);
+
+/* Time rd_detect on the caller's n device frames (H x W, dtype, as for
+ * rd_detect) for every geometry that fits (tile 64/80/96 x slab 8/12/16),
+ * with one warm-up and two timed calls each on stream, and return the
+ * fastest in *best.  The choice is also cached for this process under
+ * (H, W, r_min, r_max), where rd_create and rd_create_ex with an automatic
+ * geometry find it.  Allocates and frees a temporary context per candidate
+ * and synchronises stream.  Errors: RD_E_INVAL (as rd_create / rd_detect),
+ * RD_E_NOMEM (no candidate could allocate), RD_E_CUDA. */
+rd_status rd_autotune(const rd_params* params, const void* frames_dev, int n, int H, int W, int dtype, void* stream,
+                      rd_geometry* best);
+
 /* Last error message of ctx (or of the last failed rd_create when ctx is
  * NULL).  The string lives until the next call on the same context. */
 const char* rd_last_error(const rd_ctx* ctx);

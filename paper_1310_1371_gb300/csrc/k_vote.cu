@@ -395,7 +395,7 @@ __device__ __forceinline__ void dense_bin(const VoteArgs& a, int b, unsigned cha
     const int nq2 = (nq + 1) >> 1;  // tap pairs (tables are padded to an even count)
     const int lst = r & 3, slot = r % 3;
     // weights and slab-relative offsets of this level, copied asynchronously
-    const int4* gq = reinterpret_cast<const int4*>(a.qq_tab + a.qq_off[s * (SLAB_LEVELS + 2) + (r - lo + 1)]);
+    const int4* gq = reinterpret_cast<const int4*>(a.qq_tab + a.qq_off[s * a.slab_stride + (r - lo + 1)]);
     for (int i = tid; i < nq2; i += VOTE_THREADS) cp_async16(&sQq[2 * i], &gq[i]);
     asm volatile("cp.async.commit_group;\n" ::);
 
@@ -691,8 +691,8 @@ __global__ void __launch_bounds__(VOTE_THREADS, 4) k_vote(VoteArgs a) {
   __shared__ int s_nhot[4], s_npk, s_abort;
   __shared__ unsigned s_sum[4];  // votes, fallbacks, owned hotspots, smoothing MACs of this bin
   // per voting level lo-1 .. hi+1 of the slab: R_s, offset of its packed taps, peak threshold
-  __shared__ int s_rad[SLAB_LEVELS + 2], s_qpo[SLAB_LEVELS + 2];
-  __shared__ unsigned long long s_thr[SLAB_LEVELS + 2];
+  __shared__ int s_rad[MAX_SLAB_LEVELS + 2], s_qpo[MAX_SLAB_LEVELS + 2];
+  __shared__ unsigned long long s_thr[MAX_SLAB_LEVELS + 2];
 
   if (cnt < cnt_raw && tid == 0) atomicOr(&a.stats->overflow, 2);
   {
@@ -709,12 +709,12 @@ __global__ void __launch_bounds__(VOTE_THREADS, 4) k_vote(VoteArgs a) {
   if (tid <= hi - lo + 2) {
     const int li = lo - 1 + tid - (a.r_min - 1);
     s_rad[tid] = a.q_rad[li];
-    s_qpo[tid] = a.qp_off[s * (SLAB_LEVELS + 2) + tid];
+    s_qpo[tid] = a.qp_off[s * a.slab_stride + tid];
     s_thr[tid] = a.nthr[li];
   }
   // Per-thread counts, reduced once at the end: a bin's totals fit 32 bits
-  // (votes and fallbacks <= SLAB_LEVELS + 2 levels x its entries, MACs <=
-  // (SLAB_LEVELS + 2) x SP_HOT x 81^2).
+  // (votes and fallbacks <= MAX_SLAB_LEVELS + 2 levels x its entries, MACs <=
+  // (MAX_SLAB_LEVELS + 2) x SP_HOT x 81^2).
   unsigned t_votes = 0, t_fb = 0, t_hot = 0, t_macs = 0;
   const size_t fbase = (size_t)f * a.rl.cap;
   const int lv0 = a.r_min - 1;
@@ -947,6 +947,8 @@ cudaError_t launch_bins(const BinArgs& a, int n_sm, cudaStream_t st, long long n
   const dim3 grid((unsigned)std::max(1, (n_sm * 8 + a.n_frames - 1) / a.n_frames), (unsigned)a.n_frames);
   if (a.T == ACC_T)
     k_bin<false, ACC_T><<<grid, 256, 0, st>>>(a);
+  else if (a.T == ACC_T_MID)
+    k_bin<false, ACC_T_MID><<<grid, 256, 0, st>>>(a);
   else
     k_bin<false, ACC_T_SMALL><<<grid, 256, 0, st>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -957,6 +959,8 @@ cudaError_t launch_bins(const BinArgs& a, int n_sm, cudaStream_t st, long long n
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (a.T == ACC_T)
     k_bin<true, ACC_T><<<grid, 256, 0, st>>>(a);
+  else if (a.T == ACC_T_MID)
+    k_bin<true, ACC_T_MID><<<grid, 256, 0, st>>>(a);
   else
     k_bin<true, ACC_T_SMALL><<<grid, 256, 0, st>>>(a);
   return cudaGetLastError();

@@ -18,6 +18,9 @@
 #include <cstring>
 #include <string>
 #include <vector>
+#include <tuple>
+#include <mutex>
+#include <map>
 
 
 using namespace rd;
@@ -33,7 +36,8 @@ struct rd_ctx {
   double D64;
   float invD;
   int n_levels, n_slabs, max_rw, max_qn;
-  int T;  // accumulator tile edge (ACC_T, or ACC_T_SMALL when the dense kernel would not fit)
+  int T;  // accumulator tile edge: 64, 80 or 96
+  int S;  // peak levels per r-slab
   std::vector<int4> h_slabs;
   // device buffers
   int4* slabs = nullptr;
@@ -169,11 +173,43 @@ static std::string validate(const rd_params* p) {
 }
 
 // ---------------------------------------------------------------- C ABI
+// Geometries chosen by rd_autotune, per (H, W, r_min, r_max), for this process.
+namespace {
+struct TuneKey {
+  int H, W, r_min, r_max;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(H, W, r_min, r_max) < std::tie(o.H, o.W, o.r_min, o.r_max);
+  }
+};
+std::mutex g_tune_mutex;
+std::map<TuneKey, rd_geometry> g_tuned;
+
+bool tuned_geometry(const rd_params* p, int H, int W, rd_geometry* g) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  auto it = g_tuned.find(TuneKey{H, W, p->r_min, p->r_max});
+  if (it == g_tuned.end()) return false;
+  *g = it->second;
+  return true;
+}
+}  // namespace
+
 extern "C" rd_status rd_create(const rd_params* params, int max_H, int max_W, int max_batch, rd_ctx** out) {
+  return rd_create_ex(params, max_H, max_W, max_batch, nullptr, out);
+}
+
+extern "C" rd_status rd_create_ex(const rd_params* params, int max_H, int max_W, int max_batch,
+                                  const rd_geometry* geometry, rd_ctx** out) {
   if (!out) return fail(nullptr, RD_E_INVAL, "out is NULL");
   *out = nullptr;
   std::string v = validate(params);
   if (!v.empty()) return fail(nullptr, RD_E_INVAL, v);
+  rd_geometry geo{0, 0};
+  if (geometry) geo = *geometry;
+  const bool automatic = geo.tile == 0 && geo.slab_levels == 0;
+  if (!automatic && ((geo.tile != ACC_T && geo.tile != ACC_T_MID && geo.tile != ACC_T_SMALL) ||
+                     geo.slab_levels < 4 || geo.slab_levels > MAX_SLAB_LEVELS))
+    return fail(nullptr, RD_E_INVAL, "geometry: tile must be 64, 80 or 96 and slab_levels 4 .. 16 (or both 0)");
+  if (automatic && !tuned_geometry(params, max_H, max_W, &geo)) geo = rd_geometry{0, SLAB_LEVELS};
   const int R = gaussian_radius(params->sigma);
   if (max_H < R + 4 || max_W < R + 4 || max_H < 12 || max_W < 12 || max_H > 65535 || max_W > 65535)
     return fail(nullptr, RD_E_INVAL, "frame size must be at least max(12, ceil(4 sigma) + 4) and at most 65535");
@@ -214,10 +250,11 @@ extern "C" rd_status rd_create(const rd_params* params, int max_H, int max_W, in
     h_nthr[li] = (unsigned long long)peak_threshold_impl(params->peak_frac, r);
     c->max_qn = std::max(c->max_qn, nq + (nq & 1));
   }
-  // r-slabs of SLAB_LEVELS peak levels; halo = 1 + the largest R_s of the slab's voting levels
+  // r-slabs of S peak levels; halo = 1 + the largest R_s of the slab's voting levels
+  c->S = geo.slab_levels;
   int max_h = 0;
-  for (int lo = params->r_min; lo <= params->r_max; lo += SLAB_LEVELS) {
-    int hi = std::min(lo + SLAB_LEVELS - 1, params->r_max);
+  for (int lo = params->r_min; lo <= params->r_max; lo += c->S) {
+    int hi = std::min(lo + c->S - 1, params->r_max);
     int h = 0;
     for (int r = lo - 1; r <= hi + 1; ++r) h = std::max(h, h_qrad[r - lv0]);
     h += 1;
@@ -225,30 +262,30 @@ extern "C" rd_status rd_create(const rd_params* params, int max_H, int max_W, in
     max_h = std::max(max_h, h);
   }
   c->n_slabs = (int)c->h_slabs.size();
-  // The larger tile casts fewer halo votes per owned voxel; it is taken when
-  // the dense kernel's per-tile storage still fits one SM.
-  c->T = ACC_T;
-  if (vote_smem_bytes(ACC_T + 2 * max_h, ACC_T, c->max_qn) > 227 * 1024) c->T = ACC_T_SMALL;
+  // Automatic tile: the larger tile casts fewer halo votes per owned voxel;
+  // it is taken when the dense kernel's per-tile storage still fits one SM.
+  c->T = geo.tile;
+  if (c->T == 0) c->T = vote_smem_bytes(ACC_T + 2 * max_h, ACC_T, c->max_qn) > 227 * 1024 ? ACC_T_SMALL : ACC_T;
   c->max_rw = c->T + 2 * max_h;
   // per slab: (weight, offset) of every tap of its voting levels; offsets are
   // relative to the window centre in the slab's shared-memory layout
-  std::vector<int> h_qqoff((size_t)c->n_slabs * (SLAB_LEVELS + 2), 0);
+  std::vector<int> h_qqoff((size_t)c->n_slabs * (c->S + 2), 0);
   std::vector<int2> h_qqtab;
-  std::vector<int> h_qpoff((size_t)c->n_slabs * (SLAB_LEVELS + 2), 0);
+  std::vector<int> h_qpoff((size_t)c->n_slabs * (c->S + 2), 0);
   std::vector<uint32_t> h_qptab;
   for (int si = 0; si < c->n_slabs; ++si) {
     const int4 sl = c->h_slabs[si];
     const int RW = c->T + 2 * sl.z;
     for (int r = sl.x - 1; r <= sl.y + 1; ++r) {
       const int li = r - lv0, Rs = h_qrad[li], Wq = 2 * Rs + 1;
-      h_qqoff[(size_t)si * (SLAB_LEVELS + 2) + (r - sl.x + 1)] = (int)h_qqtab.size();
+      h_qqoff[(size_t)si * (c->S + 2) + (r - sl.x + 1)] = (int)h_qqtab.size();
       const int32_t* q = h_qtab.data() + h_qoff[li];
       for (int dy = 0; dy < Wq; ++dy)
         for (int dx = 0; dx < Wq; ++dx) h_qqtab.push_back(make_int2(q[dy * Wq + dx], (dy - Rs) * RW + (dx - Rs)));
       if (h_qqtab.size() & 1) h_qqtab.push_back(make_int2(0, 0));  // even count: 16-byte tap pairs
       // packed taps for the sparse kernel: weight << 15 | (offset & 0x7fff),
       // padded with zero-weight taps to a multiple of four
-      h_qpoff[(size_t)si * (SLAB_LEVELS + 2) + (r - sl.x + 1)] = (int)h_qptab.size();
+      h_qpoff[(size_t)si * (c->S + 2) + (r - sl.x + 1)] = (int)h_qptab.size();
       for (int dy = 0; dy < Wq; ++dy)
         for (int dx = 0; dx < Wq; ++dx) {
           const int off = (dy - Rs) * RW + (dx - Rs);
@@ -261,7 +298,7 @@ extern "C" rd_status rd_create(const rd_params* params, int max_H, int max_W, in
   if (vote_smem_bytes(c->max_rw, c->T, c->max_qn) > 227 * 1024 ||
       sparse_smem_bytes(c->max_rw, c->max_qp) > 227 * 1024 || c->max_rw * c->max_rw > 65535 * 2) {
     delete c;
-    return fail(nullptr, RD_E_INVAL, "radius range needs more shared memory than one SM has");
+    return fail(nullptr, RD_E_INVAL, "radius range and geometry need more shared memory than one SM has");
   }
   // workspaces
   const int n_stx = (max_W + ST_TW - 1) / ST_TW, n_sty = (max_H + ST_TH - 1) / ST_TH;
@@ -402,6 +439,7 @@ extern "C" rd_status rd_detect(rd_ctx* c, const void* frames_dev, int n, int H, 
   va.n_aty = n_aty;
   va.n_slabs = c->n_slabs;
   va.T = c->T;
+  va.slab_stride = c->S + 2;
   va.slabs = c->slabs;
   va.bin_cnt = c->bin_cnt;
   va.bin_off = c->bin_off;
@@ -572,5 +610,82 @@ extern "C" rd_status rd_debug_capture(rd_ctx* c, int32_t* acc_dev, uint32_t* sm_
   if (!c) return RD_E_INVAL;
   c->dbg_acc = acc_dev;
   c->dbg_sm = acc_dev ? sm_dev : nullptr;
+  return RD_OK;
+}
+
+extern "C" rd_status rd_get_geometry(const rd_ctx* c, rd_geometry* out) {
+  if (!c || !out) return RD_E_INVAL;
+  out->tile = c->T;
+  out->slab_levels = c->S;
+  return RD_OK;
+}
+
+// Autotuner: every candidate geometry runs the caller's frames through a
+// temporary context (one warm-up call, two timed calls, CUDA events on the
+// caller's stream); the fastest is returned and cached for rd_create.
+extern "C" rd_status rd_autotune(const rd_params* params, const void* frames_dev, int n, int H, int W, int dtype,
+                                 void* stream, rd_geometry* best) {
+  if (!params || !frames_dev || !best || n < 1) return fail(nullptr, RD_E_INVAL, "rd_autotune: NULL argument or n < 1");
+  std::string v = validate(params);
+  if (!v.empty()) return fail(nullptr, RD_E_INVAL, v);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int ring_cap = n * 4096;
+  rd_ring* rings = nullptr;
+  int* counts = nullptr;
+  int* offs = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  rd_status res = RD_OK;
+  if (!dalloc(&rings, (size_t)ring_cap) || !dalloc(&counts, (size_t)n) || !dalloc(&offs, (size_t)n)) {
+    res = fail(nullptr, RD_E_NOMEM, "rd_autotune: output buffers");
+  } else if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    res = fail(nullptr, RD_E_CUDA, "rd_autotune: cudaEventCreate");
+  }
+  float best_ms = 0.0f;
+  rd_geometry bg{0, 0};
+  rd_status last = RD_E_NOMEM;
+  std::string last_msg = "no candidate geometry could allocate its workspaces";
+  const int tiles[3] = {ACC_T_SMALL, ACC_T_MID, ACC_T};
+  const int slabs[3] = {8, 12, 16};
+  for (int ti = 0; ti < 3 && res == RD_OK; ++ti)
+    for (int si = 0; si < 3 && res == RD_OK; ++si) {
+      const rd_geometry g{tiles[ti], slabs[si]};
+      rd_ctx* c = nullptr;
+      rd_status s = rd_create_ex(params, H, W, n, &g, &c);
+      if (s != RD_OK) {  // does not fit this radius range, or no memory: skip
+        last = s;
+        last_msg = g_create_error;
+        continue;
+      }
+      float ms = 0.0f;
+      s = rd_detect(c, frames_dev, n, H, W, dtype, stream, rings, ring_cap, counts, offs);
+      if (s == RD_OK && cudaEventRecord(e0, st) == cudaSuccess) {
+        for (int k = 0; k < 2 && s == RD_OK; ++k) s = rd_detect(c, frames_dev, n, H, W, dtype, stream, rings, ring_cap, counts, offs);
+        if (s == RD_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                           cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+          s = RD_E_CUDA;
+      }
+      if (s != RD_OK) {
+        res = fail(nullptr, s, std::string("rd_autotune: ") + c->err);
+        rd_destroy(c);
+        break;
+      }
+      rd_destroy(c);
+      if (bg.tile == 0 || ms < best_ms) {
+        best_ms = ms;
+        bg = g;
+      }
+    }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(rings);
+  cudaFree(counts);
+  cudaFree(offs);
+  if (res != RD_OK) return res;
+  if (bg.tile == 0) return fail(nullptr, last, "rd_autotune: " + last_msg);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tuned[TuneKey{H, W, params->r_min, params->r_max}] = bg;
+  }
+  *best = bg;
   return RD_OK;
 }

@@ -27,11 +27,13 @@ constexpr int MAX_RG = 16;         // Gaussian half-width ceil(4 sigma), sigma <
 constexpr int ST_TW = 32;          // stencil tile (output pixels)
 constexpr int ST_TH = 32;
 constexpr int ST_THREADS = 256;
-constexpr int ACC_T = 96;          // accumulator tile edge
-constexpr int ACC_T_SMALL = 64;    // tile edge when the dense kernel needs the room (large r_max)
+constexpr int ACC_T = 96;          // default accumulator tile edge
+constexpr int ACC_T_MID = 80;      // the other supported tile edges
+constexpr int ACC_T_SMALL = 64;    // (64 when the dense kernel needs the room at large r_max)
 constexpr int VOTE_THREADS = 256;
 constexpr int MAX_RS = 40;         // level smoothing half-width ceil(3 sigma(r))
-constexpr int SLAB_LEVELS = 12;    // peak levels per r-slab
+constexpr int SLAB_LEVELS = 12;    // default peak levels per r-slab
+constexpr int MAX_SLAB_LEVELS = 16;
 constexpr int FIT_WARPS = 8;
 // Vote-rounding margin coefficient shared by every well-conditioned ridge
 // pixel: 1.25 (|X_lo| + e_X + 2^-24) + 2^-24 with |X_lo| <= 2^-25 and the
@@ -105,6 +107,7 @@ struct VoteArgs {
   const int* qq_off;         // per (slab, level lo-1 .. hi+1): offset into qq_tab
   const int2* qq_tab;        // (weight, slab-relative smem offset) per window tap, row-major (dy, dx)
   const int* qp_off;         // per (slab, level): offset into qp_tab (multiple of 4)
+  int slab_stride;           // entries per slab in qq_off / qp_off: slab levels + 2
   const uint32_t* qp_tab;    // packed taps: weight << 15 | (offset & 0x7fff), padded to 4
   int* fb_list;              // bins handed to the dense kernel (sparse capacities exceeded)
   int* fb_count;

@@ -33,6 +33,10 @@ class rd_ring(ctypes.Structure):
                 ("iy", c_int), ("ir", c_int), ("score", c_float), ("n_fit", c_int), ("flags", c_int)]
 
 
+class rd_geometry(ctypes.Structure):
+    _fields_ = [("tile", c_int), ("slab_levels", c_int)]
+
+
 class rd_stats(ctypes.Structure):
     _fields_ = [("ridge_pixels", c_int64), ("votes", c_int64), ("peaks", c_int64),
                 ("exact_fallbacks", c_int64), ("overflow", c_int32), ("n_frames", c_int32),
@@ -58,6 +62,9 @@ def load_library(build: bool = False) -> ctypes.CDLL:
     P = POINTER
     sig = {
         "rd_create": (c_int, [P(rd_params), c_int, c_int, c_int, P(c_void_p)]),
+        "rd_create_ex": (c_int, [P(rd_params), c_int, c_int, c_int, P(rd_geometry), P(c_void_p)]),
+        "rd_get_geometry": (c_int, [c_void_p, P(rd_geometry)]),
+        "rd_autotune": (c_int, [P(rd_params), c_void_p, c_int, c_int, c_int, c_int, c_void_p, P(rd_geometry)]),
         "rd_detect": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_int,
                               c_void_p, c_void_p]),
         "rd_detect_host": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_int,
@@ -121,6 +128,24 @@ def rd_peak_threshold(peak_frac: float, r: int) -> int:
     return int(load_library().rd_peak_threshold(peak_frac, r))
 
 
+def rd_autotune(params: dict, frames, stream=None) -> tuple[int, int]:
+    """rd_autotune on device frames [n, H, W]: the fastest (tile, slab_levels),
+    also cached in the library for contexts created afterwards."""
+    import torch
+    lib = load_library()
+    if not frames.is_cuda or not frames.is_contiguous():
+        raise ValueError("frames must be a contiguous CUDA tensor")
+    n, H, W = frames.shape
+    s = stream if stream is not None else torch.cuda.current_stream()
+    p = make_params(**params)
+    g = rd_geometry()
+    st = lib.rd_autotune(ctypes.byref(p), c_void_p(frames.data_ptr()), n, H, W, Detector.dtype_code(frames.dtype),
+                         c_void_p(s.cuda_stream), ctypes.byref(g))
+    if st != RD_OK:
+        raise RdError(st, lib.rd_last_error(None).decode())
+    return g.tile, g.slab_levels
+
+
 RD_STATIC_MAX_PIXELS = 1 << 20
 RD_STATIC_MAX_RIDGE = 1 << 18
 
@@ -155,7 +180,8 @@ def rd_ridges_static(params: dict, frame, xy, dirs, count, stream=None) -> None:
 class Detector:
     """One rd_ctx: method parameters, maximum frame size and batch."""
 
-    def __init__(self, params: dict, max_H: int, max_W: int, max_batch: int = 1):
+    def __init__(self, params: dict, max_H: int, max_W: int, max_batch: int = 1, geometry=None):
+        """geometry: None (automatic) or (tile, slab_levels) for rd_create_ex."""
         import torch  # device memory and streams
         self.torch = torch
         self.lib = load_library()
@@ -163,7 +189,9 @@ class Detector:
         self.max_H, self.max_W, self.max_batch = max_H, max_W, max_batch
         ctx = c_void_p()
         p = make_params(**params)
-        st = self.lib.rd_create(ctypes.byref(p), max_H, max_W, max_batch, ctypes.byref(ctx))
+        geo = rd_geometry(*geometry) if geometry is not None else None
+        st = self.lib.rd_create_ex(ctypes.byref(p), max_H, max_W, max_batch,
+                                   ctypes.byref(geo) if geo is not None else None, ctypes.byref(ctx))
         if st != RD_OK:
             raise RdError(st, self.lib.rd_last_error(None).decode())
         self.ctx = ctx
@@ -173,6 +201,13 @@ class Detector:
         self.rings = torch.empty(self.ring_cap * 10, dtype=torch.int32, device=dev)
         self.counts = torch.empty(max_batch, dtype=torch.int32, device=dev)
         self.offsets = torch.empty(max_batch, dtype=torch.int32, device=dev)
+
+    def geometry(self) -> tuple[int, int]:
+        g = rd_geometry()
+        st = self.lib.rd_get_geometry(self.ctx, ctypes.byref(g))
+        if st != RD_OK:
+            raise self._err(st)
+        return g.tile, g.slab_levels
 
     def close(self):
         if getattr(self, "ctx", None) is not None and self.ctx.value:

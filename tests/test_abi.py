@@ -89,3 +89,15 @@ def test_null_context_calls_fail_cleanly(lib):
     st = rd.rd_stats()
     assert lib.rd_get_stats(None, ctypes.byref(st)) == rd.RD_E_INVAL
     assert lib.rd_debug_ridges(None, 0, None, None, None, 0) == -1
+
+
+@pytest.mark.parametrize("geo", [(72, 12), (96, 3), (96, 17), (0, 8), (64, 0)])
+def test_bad_geometry_rejected(lib, geo):
+    """rd_create_ex validates the accumulator geometry before touching the GPU."""
+    from paper_1310_1371_gb300 import rd, synth
+    p = rd.make_params(**synth.PLAIN_SMALL_PARAMS)
+    g = rd.rd_geometry(*geo)
+    ctx = ctypes.c_void_p()
+    st = lib.rd_create_ex(ctypes.byref(p), 256, 256, 1, ctypes.byref(g), ctypes.byref(ctx))
+    assert st == rd.RD_E_INVAL and not ctx.value
+    assert b"geometry" in lib.rd_last_error(None)
