@@ -653,9 +653,8 @@ __device__ __forceinline__ uint32_t sp_lookup(const uint32_t* tab, const uint32_
   return 0u;
 }
 
-__global__ void __launch_bounds__(VOTE_THREADS, 4) k_vote(VoteArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int b = blockIdx.x;
+// K4 work of one bin b; called by every thread of the CTA.
+__device__ __forceinline__ void vote_bin_sparse(const VoteArgs& a, const int b, unsigned char* smem) {
   const int cnt_raw = a.bin_cnt[b];
   if (cnt_raw == 0) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -966,10 +965,57 @@ cudaError_t launch_bins(const BinArgs& a, int n_sm, cudaStream_t st, long long n
   return cudaGetLastError();
 }
 
+// K4's work queue: the non-empty bins, largest first (bucketed by the
+// leading-zero count of their entry count, i.e. by floor(log2)), so that a
+// persistent grid ends with small items.  One CTA; also resets the head.
+__global__ void __launch_bounds__(1024) k_queue(const int* bin_cnt, long long n_bins, int* queue, int* n_queue,
+                                               int* head) {
+  __shared__ int hist[33], start[33];
+  const int tid = threadIdx.x;
+  if (tid < 33) hist[tid] = 0;
+  __syncthreads();
+  for (long long b = tid; b < n_bins; b += blockDim.x) {
+    const int c = bin_cnt[b];
+    if (c > 0) atomicAdd(&hist[__clz(c)], 1);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int sum = 0;
+    for (int q = 0; q < 33; ++q) {
+      start[q] = sum;
+      sum += hist[q];
+    }
+    *n_queue = sum;
+    *head = 0;
+  }
+  __syncthreads();
+  for (long long b = tid; b < n_bins; b += blockDim.x) {
+    const int c = bin_cnt[b];
+    if (c > 0) queue[atomicAdd(&start[__clz(c)], 1)] = (int)b;
+  }
+}
+
+// Persistent K4: a fixed grid of CTAs takes bins from the work queue.
+__global__ void __launch_bounds__(VOTE_THREADS, 4) k_vote(VoteArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_item;
+  const int n_items = *a.n_queue;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(a.queue_head, 1);
+    __syncthreads();  // also: every thread is done with the previous bin's shared memory
+    const int item = s_item;
+    __syncthreads();  // s_item read by all before thread 0 takes the next item
+    if (item >= n_items) break;
+    vote_bin_sparse(a, a.queue[item], smem);
+  }
+}
+
 cudaError_t launch_vote(const VoteArgs& a, long long n_bins, cudaStream_t st) {
   size_t sm = sparse_smem_bytes(a.max_rw, a.max_qp);
   cudaFuncSetAttribute(k_vote, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_vote<<<(unsigned)n_bins, VOTE_THREADS, sm, st>>>(a);
+  k_queue<<<1, 1024, 0, st>>>(a.bin_cnt, n_bins, a.queue, a.n_queue, a.queue_head);
+  const unsigned grid = (unsigned)std::max(1LL, std::min<long long>(n_bins, a.vote_grid));
+  k_vote<<<grid, VOTE_THREADS, sm, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   size_t smd = vote_smem_bytes(a.max_rw, a.T, a.max_qn);

@@ -12,6 +12,7 @@
 #include "rd_internal.cuh"
 #include "rd.h"
 
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -47,6 +48,8 @@ struct rd_ctx {
   int* qp_off = nullptr;
   uint32_t* qp_tab = nullptr;
   int* fb_list = nullptr;
+  int* queue = nullptr;      // K4 work queue (bin indices)
+  int* queue_ctr = nullptr;  // [0] queue length, [1] head
   int* fb_count = nullptr;
   int max_qp = 4;
   unsigned long long* nthr = nullptr;
@@ -145,7 +148,7 @@ static rd_status fail(rd_ctx* c, rd_status s, const std::string& m) {
 }
 
 static void free_all(rd_ctx* c) {
-  void* ptrs[] = {c->slabs, c->q_rad, c->qq_off, c->qq_tab, c->qp_off, c->qp_tab, c->fb_list, c->fb_count, c->nthr, c->rl.xy, c->rl.dir, c->rl.kvote, c->rl.hess,
+  void* ptrs[] = {c->slabs, c->q_rad, c->qq_off, c->qq_tab, c->qp_off, c->qp_tab, c->fb_list, c->fb_count, c->queue, c->queue_ctr, c->nthr, c->rl.xy, c->rl.dir, c->rl.kvote, c->rl.hess,
                   c->rl.count, c->rl.tile_off, c->rl.tile_cnt, c->bin_cnt, c->bin_off, c->bin_fill, c->block_sums,
                   c->bin_total, c->pool, c->peaks, c->peak_count, c->stats, c->stage_frames, c->stage_rings,
                   c->stage_counts, c->stage_offsets};
@@ -309,10 +312,15 @@ extern "C" rd_status rd_create_ex(const rd_params* params, int max_H, int max_W,
   const size_t nrec = (size_t)c->rl.cap * max_batch;
   c->n_bins_max = (long long)max_batch * n_atx * n_aty * c->n_slabs;
   c->pool_cap = std::min<long long>((long long)max_batch * max_H * max_W * 3, (1LL << 31) - 1);
+  if (c->n_bins_max > INT_MAX) {
+    delete c;
+    return fail(nullptr, RD_E_INVAL, "too many accumulator bins (frames x tiles x slabs > 2^31): lower max_batch");
+  }
   bool ok = dalloc(&c->slabs, c->n_slabs) && dalloc(&c->q_rad, c->n_levels) &&
             dalloc(&c->qq_off, h_qqoff.size()) && dalloc(&c->qq_tab, h_qqtab.size()) &&
             dalloc(&c->qp_off, h_qpoff.size()) && dalloc(&c->qp_tab, h_qptab.size()) &&
-            dalloc(&c->fb_list, c->n_bins_max) && dalloc(&c->fb_count, 1) &&
+            dalloc(&c->fb_list, c->n_bins_max) && dalloc(&c->fb_count, 1) && dalloc(&c->queue, c->n_bins_max) &&
+            dalloc(&c->queue_ctr, 2) &&
             dalloc(&c->nthr, c->n_levels) && dalloc(&c->rl.xy, nrec) &&
             dalloc(&c->rl.dir, nrec) && dalloc(&c->rl.kvote, nrec) && dalloc(&c->rl.hess, 3 * nrec) &&
             dalloc(&c->rl.count, max_batch) && dalloc(&c->rl.tile_off, (size_t)max_batch * n_stx * n_sty) &&
@@ -468,6 +476,10 @@ extern "C" rd_status rd_detect(rd_ctx* c, const void* frames_dev, int n, int H, 
   va.fb_count = c->fb_count;
   va.fb_cap = (int)n_bins;
   va.fb_grid = 2 * c->n_sm;
+  va.queue = c->queue;
+  va.n_queue = c->queue_ctr;
+  va.queue_head = c->queue_ctr + 1;
+  va.vote_grid = 4 * c->n_sm;
   va.route_dense = c->route_dense;
   chk(launch_vote(va, n_bins, st));
   mark(4);

@@ -109,6 +109,10 @@ struct VoteArgs {
   const int* qp_off;         // per (slab, level): offset into qp_tab (multiple of 4)
   int slab_stride;           // entries per slab in qq_off / qp_off: slab levels + 2
   const uint32_t* qp_tab;    // packed taps: weight << 15 | (offset & 0x7fff), padded to 4
+  int* queue;                // K4 work queue: non-empty bins, largest first
+  int* n_queue;              // its length
+  int* queue_head;           // next item to take
+  int vote_grid;             // CTAs of the persistent K4 grid
   int* fb_list;              // bins handed to the dense kernel (sparse capacities exceeded)
   int* fb_count;
   int fb_cap, fb_grid;
