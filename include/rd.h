@@ -144,6 +144,17 @@ rd_status rd_detect_host(rd_ctx* ctx, const void* frames_host, int n, int H, int
                          void* stream, rd_ring* rings_host, int ring_cap,
                          int* counts_host, int* offsets_host);
 
+/* Graph mode.  rd_set_graph(ctx, 1) makes rd_detect capture its whole launch
+ * sequence (memsets and every kernel) into a CUDA graph the first time it is
+ * called with a given argument set (frames_dev, n, H, W, dtype, stream,
+ * rings_dev, ring_cap, counts_dev, offsets_dev) and replay that graph with
+ * one cudaGraphLaunch on later calls with the same arguments; the frames'
+ * contents may change between calls, their address may not (a different
+ * address captures anew).  Graph mode needs a non-default stream (RD_E_INVAL
+ * otherwise) and records no stage timing.  rd_set_graph(ctx, 0), the debug
+ * settings and rd_destroy release the captured graph. */
+rd_status rd_set_graph(rd_ctx* ctx, int on);
+
 /* Synchronise the stream of the last rd_detect on ctx and copy its device
  * counters to *out.  Returns RD_E_OVERFLOW when any RD_OVF_* bit is set. */
 rd_status rd_get_stats(rd_ctx* ctx, rd_stats* out);

@@ -12,6 +12,7 @@
 #include "rd_internal.cuh"
 #include "rd.h"
 
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -78,6 +79,12 @@ struct rd_ctx {
   int* stage_offsets = nullptr;
   // stage timing
   bool timing = false, timed = false;
+  // graph mode: the captured rd_detect launch sequence and the arguments it was captured with
+  bool graph_on = false;
+  cudaGraphExec_t gexec = nullptr;
+  const void* g_args[4] = {};
+  int g_shape[5] = {};
+  cudaStream_t g_stream = nullptr;
   cudaEvent_t ev[RD_N_STAGES + 1] = {};
   std::string err;
 };
@@ -361,9 +368,10 @@ extern "C" rd_status rd_create_ex(const rd_params* params, int max_H, int max_W,
   return RD_OK;
 }
 
-extern "C" rd_status rd_detect(rd_ctx* c, const void* frames_dev, int n, int H, int W, int dtype, void* stream,
-                               rd_ring* rings_dev, int ring_cap, int* counts_dev, int* offsets_dev) {
-  if (!c) return RD_E_INVAL;
+// Enqueue every stage of rd_detect on the stream (the body of rd_detect, and
+// what graph mode captures).
+static rd_status detect_enqueue(rd_ctx* c, const void* frames_dev, int n, int H, int W, int dtype, void* stream,
+                                rd_ring* rings_dev, int ring_cap, int* counts_dev, int* offsets_dev) {
   if (!frames_dev || !counts_dev || !offsets_dev || (ring_cap > 0 && !rings_dev) || ring_cap < 0)
     return fail(c, RD_E_INVAL, "NULL buffer or negative ring_cap");
   if (n < 1 || n > c->max_batch) return fail(c, RD_E_INVAL, "n must be in [1, max_batch]");
@@ -505,6 +513,63 @@ extern "C" rd_status rd_detect(rd_ctx* c, const void* frames_dev, int n, int H, 
   return RD_OK;
 }
 
+static void drop_graph(rd_ctx* c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gexec = nullptr;
+}
+
+extern "C" rd_status rd_detect(rd_ctx* c, const void* frames_dev, int n, int H, int W, int dtype, void* stream,
+                               rd_ring* rings_dev, int ring_cap, int* counts_dev, int* offsets_dev) {
+  if (!c) return RD_E_INVAL;
+  if (!c->graph_on) return detect_enqueue(c, frames_dev, n, H, W, dtype, stream, rings_dev, ring_cap, counts_dev,
+                                          offsets_dev);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!st) return fail(c, RD_E_INVAL, "graph mode needs a non-default stream");
+  const void* args[4] = {frames_dev, rings_dev, counts_dev, offsets_dev};
+  const int shape[5] = {n, H, W, dtype, ring_cap};
+  const bool same = c->gexec && st == c->g_stream && std::equal(args, args + 4, c->g_args) &&
+                    std::equal(shape, shape + 5, c->g_shape);
+  if (!same) {  // capture this argument set once; later identical calls replay it
+    drop_graph(c);
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+    const bool timing = c->timing;
+    c->timing = false;
+    rd_status s = detect_enqueue(c, frames_dev, n, H, W, dtype, stream, rings_dev, ring_cap, counts_dev, offsets_dev);
+    c->timing = timing;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(st, &g);
+    if (s != RD_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->gexec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      c->gexec = nullptr;
+      return fail(c, RD_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
+    std::copy(args, args + 4, c->g_args);
+    std::copy(shape, shape + 5, c->g_shape);
+    c->g_stream = st;
+  }
+  c->last_stream = st;
+  c->last_n = n;
+  c->last_H = H;
+  c->last_W = W;
+  c->timed = false;
+  cudaError_t e = cudaGraphLaunch(c->gexec, st);
+  if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
+  return RD_OK;
+}
+
+extern "C" rd_status rd_set_graph(rd_ctx* c, int on) {
+  if (!c) return RD_E_INVAL;
+  c->graph_on = on != 0;
+  drop_graph(c);
+  return RD_OK;
+}
+
 extern "C" rd_status rd_detect_host(rd_ctx* c, const void* frames_host, int n, int H, int W, int dtype, void* stream,
                                     rd_ring* rings_host, int ring_cap, int* counts_host, int* offsets_host) {
   if (!c) return RD_E_INVAL;
@@ -575,6 +640,7 @@ extern "C" int rd_get_timing(rd_ctx* c, float* ms, int cap) {
 extern "C" rd_status rd_destroy(rd_ctx* c) {
   if (!c) return RD_E_INVAL;
   cudaDeviceSynchronize();
+  drop_graph(c);
   for (int i = 0; i <= RD_N_STAGES; ++i)
     if (c->ev[i]) cudaEventDestroy(c->ev[i]);
   free_all(c);
@@ -615,6 +681,7 @@ extern "C" int rd_debug_ridges(rd_ctx* c, int f, int32_t* xy, float* dir, int64_
 extern "C" rd_status rd_debug_route(rd_ctx* c, int all_dense) {
   if (!c) return RD_E_INVAL;
   c->route_dense = all_dense ? 1 : 0;
+  drop_graph(c);
   return RD_OK;
 }
 
@@ -622,6 +689,7 @@ extern "C" rd_status rd_debug_capture(rd_ctx* c, int32_t* acc_dev, uint32_t* sm_
   if (!c) return RD_E_INVAL;
   c->dbg_acc = acc_dev;
   c->dbg_sm = acc_dev ? sm_dev : nullptr;
+  drop_graph(c);
   return RD_OK;
 }
 

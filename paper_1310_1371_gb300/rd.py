@@ -78,6 +78,7 @@ def load_library(build: bool = False) -> ctypes.CDLL:
         "rd_debug_ridges": (c_int, [c_void_p, c_int, P(c_int32), P(c_float), P(c_int64), c_int]),
         "rd_debug_capture": (c_int, [c_void_p, c_void_p, c_void_p]),
         "rd_set_timing": (c_int, [c_void_p, c_int]),
+        "rd_set_graph": (c_int, [c_void_p, c_int]),
         "rd_debug_route": (c_int, [c_void_p, c_int]),
         "rd_get_timing": (c_int, [c_void_p, P(c_float), c_int]),
         "rd_ridges_static": (c_int, [P(rd_params), c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
@@ -282,6 +283,12 @@ class Detector:
         if st not in (RD_OK, RD_E_OVERFLOW):
             raise self._err(st)
         return rings, counts, offs, st
+
+    def set_graph(self, on: bool):
+        """rd_set_graph: capture rd_detect into a CUDA graph and replay it."""
+        st = self.lib.rd_set_graph(self.ctx, 1 if on else 0)
+        if st != RD_OK:
+            raise self._err(st)
 
     def set_timing(self, on: bool):
         st = self.lib.rd_set_timing(self.ctx, 1 if on else 0)
