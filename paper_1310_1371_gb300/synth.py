@@ -129,27 +129,64 @@ def plain_full_batch(n: int, seed0: int = 1002, **kw) -> list[Frame]:
     return [plain_full(seed=[seed0, i], **kw) for i in range(n)]
 
 
-def video(n_frames: int, seed: int = 1003, H: int = 1024, W: int = 1024,
-          pool: int = 300, n_min: int = 20, n_max: int = 300) -> list[Frame]:
-    """A drifting-track video of u8 frames rendered like ``plain_small``.
-    Frame i shows the first n_i ~ U{n_min..n_max} tracks of the pool."""
+def video_tracks(n_frames: int, seed: int = 1003, H: int = 1024, W: int = 1024,
+                 pool: int = 300, n_min: int = 20, n_max: int = 300) -> list[np.ndarray]:
+    """Ring geometry of each frame of ``video``: frame i shows the first
+    n_i ~ U{n_min..n_max} tracks of a drifting pool, as [n_i, 3] (cx, cy, R)."""
     rng = np.random.default_rng(seed)
     c = rng.uniform(40.0, np.array([W - 40.0, H - 40.0]), size=(pool, 2))
     R = rng.uniform(8.0, 30.0, size=pool)
-    frames = []
+    tracks = []
     for i in range(n_frames):
-        fr = np.random.default_rng([seed, i])
-        n = int(fr.integers(n_min, n_max + 1))
-        rings = np.concatenate([c[:n], R[:n, None]], axis=1)
-        img = _render(H, W, rings, _gauss_ring(120.0, 1.5), 40.0)
-        img += fr.normal(0.0, 8.0, size=img.shape)
-        img = np.clip(np.rint(img), 0, 255).astype(np.uint8)
-        frames.append(Frame(img, rings.copy(), dict(VIDEO_PARAMS)))
+        n = int(np.random.default_rng([seed, i]).integers(n_min, n_max + 1))
+        tracks.append(np.concatenate([c[:n], R[:n, None]], axis=1))
         c = c + rng.normal(0.0, 1.5, size=c.shape)
         c[:, 0] = np.clip(c[:, 0], 0.0, W - 1.0)
         c[:, 1] = np.clip(c[:, 1], 0.0, H - 1.0)
         R = np.clip(R + rng.uniform(-0.3, 0.3, size=R.shape), 8.0, 30.0)
-    return frames
+    return tracks
+
+
+def video_frame(i: int, rings: np.ndarray, seed: int = 1003, H: int = 1024, W: int = 1024,
+                n_min: int = 20, n_max: int = 300) -> np.ndarray:
+    """Frame i of ``video`` (u8) from its ring geometry."""
+    fr = np.random.default_rng([seed, i])
+    fr.integers(n_min, n_max + 1)  # the ring count drawn by video_tracks
+    img = _render(H, W, rings, _gauss_ring(120.0, 1.5), 40.0)
+    img += fr.normal(0.0, 8.0, size=img.shape)
+    return np.clip(np.rint(img), 0, 255).astype(np.uint8)
+
+
+def video(n_frames: int, seed: int = 1003, H: int = 1024, W: int = 1024,
+          pool: int = 300, n_min: int = 20, n_max: int = 300) -> list[Frame]:
+    """A drifting-track video of u8 frames rendered like ``plain_small``.
+    Frame i shows the first n_i ~ U{n_min..n_max} tracks of the pool."""
+    tracks = video_tracks(n_frames, seed, H, W, pool, n_min, n_max)
+    return [Frame(video_frame(i, rings, seed, H, W, n_min, n_max), rings.copy(), dict(VIDEO_PARAMS))
+            for i, rings in enumerate(tracks)]
+
+
+def _video_frame_job(args):
+    return video_frame(*args)
+
+
+def video_images(n_frames: int, seed: int = 1003, H: int = 1024, W: int = 1024, workers: int = 0) -> np.ndarray:
+    """The frames of ``video`` as one [n, H, W] u8 array, rendered by a pool
+    of ``workers`` processes started with 'spawn' (0: all cores)."""
+    import multiprocessing as mp
+    import os
+    tracks = video_tracks(n_frames, seed, H, W)
+    jobs = [(i, rings, seed, H, W) for i, rings in enumerate(tracks)]
+    out = np.empty((n_frames, H, W), dtype=np.uint8)
+    workers = workers or (os.cpu_count() or 1)
+    if workers <= 1:
+        for i, j in enumerate(jobs):
+            out[i] = _video_frame_job(j)
+        return out
+    with mp.get_context("spawn").Pool(workers) as pool:
+        for i, img in enumerate(pool.imap(_video_frame_job, jobs, chunksize=4)):
+            out[i] = img
+    return out
 
 
 def diff_frames(n: int, seed: int = 1004, H: int = 512, W: int = 512, n_rings: int = 64) -> list[Frame]:
