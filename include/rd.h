@@ -43,7 +43,7 @@ extern "C" {
 
 /* Pixel type of the frames.  Integer frames are smoothed with exact integer
  * arithmetic (quantised Gaussian taps), which makes the Hessian exact. */
-typedef enum { RD_U8 = 0, RD_U16 = 1 } rd_dtype;
+typedef enum { RD_U8 = 0, RD_U16 = 1, RD_F32 = 2 /* soft-score entry points only */ } rd_dtype;
 
 typedef enum {
   RD_OK = 0,
@@ -160,6 +160,43 @@ rd_status rd_set_graph(rd_ctx* ctx, int on);
 rd_status rd_get_stats(rd_ctx* ctx, rd_stats* out);
 
 rd_status rd_destroy(rd_ctx* ctx);
+
+/* ---- differentiable soft score, its gradients and refinement --------------
+ * Not in the paper: a smooth extension of its voting and scoring steps
+ * (Results, "Directed ridge detection & votes collection" and "Local maxima
+ * detection in a noisy parameter space") used to refine rings by gradient
+ * ascent and to differentiate a ring's score with respect to the image:
+ *   Score(c, rho) = (1/rho) sum_{p in ridge} m(p) sum_{s = +-1} sum_{q in corners(v)}
+ *                   bil(v, q) exp(-|q - c|^2 / (2 sigma(rho)^2)),
+ *   v = p + s rho X-(p), m(p) = logistic((tau - k-(p)) / T), T = |tau| / 4,
+ * where the directed-ridge set of the frame (the rd_detect rule, evaluated on
+ * the frame in double precision) is held fixed, bil(v, q) are the bilinear
+ * weights of the four grid points of v's cell (points outside the image get
+ * nothing) and sigma(rho) = sig_a rho + sig_b.  c = (cx, cy) and rho = r
+ * are read from the rings' float fields; frame i's rings are the counts_dev[i]
+ * rings that follow frame i - 1's in rings_dev.  Computed in double
+ * precision; outputs are float.  Frames may be RD_U8, RD_U16 or RD_F32
+ * (rd_backward: RD_F32).  The first call on a context allocates its FP64
+ * workspaces (about 64 bytes per pixel of max_batch x max_H x max_W).
+ * Errors: RD_E_INVAL (NULL pointers, sizes above the rd_create maxima, bad
+ * dtype), RD_E_NOMEM, RD_E_CUDA.
+ *
+ * rd_soft_score writes Score of every ring to score_dev and, when
+ * dparams_dev is not NULL, (dScore/dcx, dScore/dcy, dScore/dr) per ring.
+ * rd_backward takes dscore_dev (one float per ring) and writes
+ * dimage_dev[n][H][W] = sum_i dscore_i dScore_i/dframe and, when dparams_dev
+ * is not NULL, dscore_i times each ring's parameter gradient.
+ * rd_refine moves every ring iters times by
+ *   delta = step * sigma(r)^2 / Score * grad Score   (each component at most
+ * 0.5 px; r at least 1), updating cx, cy, r of rings_dev in place; at most
+ * 4096 rings per frame. */
+rd_status rd_soft_score(rd_ctx* ctx, const void* frames_dev, int n, int H, int W, int dtype, void* stream,
+                        const rd_ring* rings_dev, const int* counts_dev, float* score_dev, float* dparams_dev);
+rd_status rd_backward(rd_ctx* ctx, const float* frames_dev, int n, int H, int W, void* stream,
+                      const rd_ring* rings_dev, const int* counts_dev, const float* dscore_dev,
+                      float* dimage_dev, float* dparams_dev);
+rd_status rd_refine(rd_ctx* ctx, const void* frames_dev, int n, int H, int W, int dtype, void* stream,
+                    rd_ring* rings_dev, const int* counts_dev, int iters, float step);
 
 /* ---- accumulator geometry and its autotuner --------------------------------
  * The voting stage works on (frame, tile, slab) bins: tile x tile pixels of

@@ -1,0 +1,466 @@
+// k_soft.cu -- the differentiable (soft) ring score, its gradients with
+// respect to the ring parameters and to the image, and gradient-ascent
+// refinement of rings.
+//
+// The paper has no differentiable form.  The score extends its voting and
+// scoring steps (Results, "Directed ridge detection & votes collection",
+// "Local maxima detection in a noisy parameter space") smoothly:
+//   Score(c, rho) = (1/rho) sum_{p in ridge} m(p) sum_{s=+-1} sum_{q in corners(v)}
+//                   bil(v, q) exp(-|q - c|^2 / (2 sigma(rho)^2)),
+//   v = p + s rho X(p),  m(p) = logistic((tau - k(p)) / T),  T = |tau| / 4,
+// with the hard directed-ridge set of the frame held fixed, grid points
+// outside the image receiving nothing, and sigma(rho) = sig_a rho + sig_b.
+// The image gradient flows through k and X to the exact-arithmetic chain
+// eigen <- 5x5 second-order Sobel / 64 <- Gaussian, each stencil with
+// reflect-101 borders; its adjoint is applied as gathers, recomputing the
+// stencil stage instead of storing per-ring state.  Everything is FP64.
+#include "rd_internal.cuh"
+
+#include <cmath>
+
+namespace rd {
+
+__device__ __forceinline__ int refl101(int i, int n) {
+  i = i < 0 ? -i : i;
+  return i >= n ? 2 * (n - 1) - i : i;
+}
+
+template <typename T>
+__device__ __forceinline__ double pix(const void* frames, size_t i) {
+  return (double)reinterpret_cast<const T*>(frames)[i];
+}
+
+// ---- S1/S2: separable Gaussian (taps Q_i / S) ---------------------------------
+template <typename T>
+__global__ void k_soft_hpass(SoftArgs a) {
+  const size_t total = (size_t)a.n * a.H * a.W;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t row = i / a.W;
+    const int x = (int)(i - row * a.W);
+    const size_t base = row * a.W;
+    double s = 0.0;
+    for (int t = -a.R; t <= a.R; ++t) s += a.g[t + a.R] * pix<T>(a.frames, base + refl101(x + t, a.W));
+    a.t0[i] = s;
+  }
+}
+
+__global__ void k_soft_vpass(SoftArgs a) {
+  const size_t plane = (size_t)a.H * a.W, total = plane * a.n;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t f = i / plane;
+    const size_t r = i - f * plane;
+    const int y = (int)(r / a.W), x = (int)(r - (size_t)y * a.W);
+    const double* src = a.t0 + f * plane + x;
+    double s = 0.0;
+    for (int t = -a.R; t <= a.R; ++t) s += a.g[t + a.R] * src[(size_t)refl101(y + t, a.H) * a.W];
+    a.t1[i] = s;
+  }
+}
+
+__constant__ double c_s5[5] = {1, 4, 6, 4, 1};
+__constant__ double c_d1[5] = {-1, -2, 0, 2, 1};
+__constant__ double c_d2[5] = {1, 0, -2, 0, 1};
+
+// eigen step (O3) in the oracle's operation order
+struct SoftEig {
+  double k, X, Y;
+  bool degenerate, use1, flip;
+};
+__device__ __forceinline__ SoftEig soft_eigen(double a, double c, double b) {
+  SoftEig e;
+  const double half_tr = d_mul(d_add(a, c), 0.5);
+  const double half_df = d_mul(d_sub(a, c), 0.5);
+  const double rad = d_sqrt(d_add(d_mul(half_df, half_df), d_mul(b, b)));
+  e.k = d_sub(half_tr, rad);
+  const double v1x = b, v1y = d_sub(e.k, a), v2x = d_sub(e.k, c), v2y = b;
+  const double n1 = d_add(d_mul(v1x, v1x), d_mul(v1y, v1y));
+  const double n2 = d_add(d_mul(v2x, v2x), d_mul(v2y, v2y));
+  e.use1 = n1 >= n2;
+  const double vx = e.use1 ? v1x : v2x, vy = e.use1 ? v1y : v2y, nn = e.use1 ? n1 : n2;
+  e.degenerate = nn == 0.0;
+  e.X = 0.0;
+  e.Y = 0.0;
+  e.flip = false;
+  if (!e.degenerate) {
+    const double nrm = d_sqrt(nn);
+    double X = d_div(vx, nrm), Y = d_div(vy, nrm);
+    e.flip = X < 0.0 || (X == 0.0 && Y < 0.0);
+    e.X = e.flip ? -X : X;
+    e.Y = e.flip ? -Y : Y;
+  }
+  return e;
+}
+
+// ---- S3: Hessian (5x5 second-order Sobel / 64 of L) and k-, X- ----------------
+__global__ void k_soft_hessian(SoftArgs a) {
+  const size_t plane = (size_t)a.H * a.W, total = plane * a.n;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t f = i / plane;
+    const size_t r = i - f * plane;
+    const int y = (int)(r / a.W), x = (int)(r - (size_t)y * a.W);
+    const double* L = a.t1 + f * plane;
+    double hxx = 0.0, hyy = 0.0, hxy = 0.0;
+    for (int dy = 0; dy < 5; ++dy) {
+      const double* row = L + (size_t)refl101(y + dy - 2, a.H) * a.W;
+      double sx = 0.0, d2x = 0.0, d1x = 0.0;
+      for (int dx = 0; dx < 5; ++dx) {
+        const double l = row[refl101(x + dx - 2, a.W)];
+        sx += c_s5[dx] * l;
+        d2x += c_d2[dx] * l;
+        d1x += c_d1[dx] * l;
+      }
+      hxx += c_s5[dy] * d2x;
+      hyy += c_d2[dy] * sx;
+      hxy += c_d1[dy] * d1x;
+    }
+    const double A = hxx / 64.0, C = hyy / 64.0, B = hxy / 64.0;
+    a.a[i] = A;
+    a.b[i] = B;
+    a.c[i] = C;
+    const SoftEig e = soft_eigen(A, C, B);
+    a.k[i] = e.k;
+    a.X[i] = e.X;
+    a.Y[i] = e.Y;
+  }
+}
+
+// ---- S4: directed-ridge mask (O4) and ridge records -----------------------------
+__global__ void k_soft_ridges(SoftArgs a) {
+  const size_t plane = (size_t)a.H * a.W, total = plane * a.n;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t f = i / plane;
+    const size_t r = i - f * plane;
+    const int y = (int)(r / a.W), x = (int)(r - (size_t)y * a.W);
+    const double kp = a.k[i], X = a.X[i], Y = a.Y[i];
+    if (!(kp < a.tau) || (X == 0.0 && Y == 0.0)) continue;
+    const double* K = a.k + f * plane;
+    bool ok = true;
+    for (int s = 0; s < 2 && ok; ++s) {
+      const double qx = s == 0 ? d_add((double)x, X) : d_sub((double)x, X);
+      const double qy = s == 0 ? d_add((double)y, Y) : d_sub((double)y, Y);
+      if (qx < 0.0 || qx > (double)(a.W - 1) || qy < 0.0 || qy > (double)(a.H - 1)) {
+        ok = false;
+        break;
+      }
+      const double x0f = floor(qx), y0f = floor(qy);
+      const double fx = d_sub(qx, x0f), fy = d_sub(qy, y0f);
+      const int x0 = (int)x0f, y0 = (int)y0f;
+      const int x1 = min(x0 + 1, a.W - 1), y1 = min(y0 + 1, a.H - 1);
+      const double kt = bilinear64(fx, fy, K[(size_t)y0 * a.W + x0], K[(size_t)y0 * a.W + x1],
+                                   K[(size_t)y1 * a.W + x0], K[(size_t)y1 * a.W + x1]);
+      ok = s == 0 ? (kp < kt) : (kp <= kt);
+    }
+    if (!ok) continue;
+    const int j = atomicAdd(&a.count[f], 1);
+    if (j >= a.cap) continue;
+    const size_t g = f * (size_t)a.cap + j;
+    const SoftEig e = soft_eigen(a.a[i], a.c[i], a.b[i]);
+    a.xy[g] = (uint32_t)x | ((uint32_t)y << 16);
+    a.flags[g] = (uint8_t)((e.use1 ? 1 : 0) | (e.flip ? 2 : 0));
+    a.rk[g] = kp;
+    a.rX[g] = X;
+    a.rY[g] = Y;
+    a.ra[g] = a.a[i];
+    a.rb[g] = a.b[i];
+    a.rc[g] = a.c[i];
+    a.rm[g] = 1.0 / (1.0 + exp(-(a.tau - kp) / a.temp));
+  }
+}
+
+cudaError_t launch_soft_stencil(const SoftArgs& a, cudaStream_t st) {
+  const unsigned grid = 152 * 8;
+  if (a.dtype == RD_U8)
+    k_soft_hpass<uint8_t><<<grid, 256, 0, st>>>(a);
+  else if (a.dtype == RD_U16)
+    k_soft_hpass<uint16_t><<<grid, 256, 0, st>>>(a);
+  else
+    k_soft_hpass<float><<<grid, 256, 0, st>>>(a);
+  k_soft_vpass<<<grid, 256, 0, st>>>(a);
+  k_soft_hessian<<<grid, 256, 0, st>>>(a);
+  k_soft_ridges<<<grid, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// ---- S5: score and gradients per ring -------------------------------------------
+// exclusive prefix of the per-frame ring counts (one CTA)
+__global__ void k_soft_offsets(const int* counts, int n, int* off) {
+  __shared__ int part[1024];
+  const int tid = threadIdx.x;
+  const int per = (n + 1023) / 1024;
+  int s = 0;
+  for (int i = tid * per; i < min(n, (tid + 1) * per); ++i) s += max(counts[i], 0);
+  part[tid] = s;
+  __syncthreads();
+  if (tid == 0) {
+    int acc = 0;
+    for (int t = 0; t < 1024; ++t) {
+      const int v = part[t];
+      part[t] = acc;
+      acc += v;
+    }
+    off[n] = acc;
+  }
+  __syncthreads();
+  int acc = part[tid];
+  for (int i = tid * per; i < min(n, (tid + 1) * per); ++i) {
+    off[i] = acc;
+    acc += max(counts[i], 0);
+  }
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  return t;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(256) k_soft_score(SoftArgs a) {
+  __shared__ double red[8];
+  const int n_rings = min(a.ring_off[a.n], a.max_rings);
+  for (int i = blockIdx.x; i < n_rings; i += gridDim.x) {
+    int lo = 0, hi = a.n;  // frame f: ring_off[f] <= i < ring_off[f + 1]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (a.ring_off[mid] <= i) lo = mid; else hi = mid;
+    }
+    const int f = lo;
+    const double cx = a.rings[i].cx, cy = a.rings[i].cy, rho = a.rings[i].r;
+    const double ds = a.dscore ? (double)a.dscore[i] : 1.0;
+    const double sig = a.sig_a * rho + a.sig_b;
+    const double den = 2.0 * sig * sig;
+    const double cut = 38.7 * sig + 1.5;  // beyond: every Gaussian factor underflows to 0
+    const int cnt = min(a.count[f], a.cap);
+    const size_t base = (size_t)f * a.cap;
+    double T = 0.0, Tcx = 0.0, Tcy = 0.0, Tsig = 0.0, Trho = 0.0;
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+      const size_t g = base + j;
+      const uint32_t xy = a.xy[g];
+      const double px = (double)(xy & 0xffffu), py = (double)(xy >> 16);
+      const double X = a.rX[g], Y = a.rY[g], m = a.rm[g];
+      double gk = 0.0, gX = 0.0, gY = 0.0;
+      for (int s = -1; s <= 1; s += 2) {
+        const double vx = px + s * rho * X, vy = py + s * rho * Y;
+        const double ex = vx - cx, ey = vy - cy;
+        if (ex * ex + ey * ey > cut * cut) continue;
+        const double x0 = floor(vx), y0 = floor(vy);
+        const double fx = vx - x0, fy = vy - y0;
+        for (int oy = 0; oy < 2; ++oy)
+          for (int ox = 0; ox < 2; ++ox) {
+            const double qx = x0 + ox, qy = y0 + oy;
+            if (qx < 0.0 || qx > (double)(a.W - 1) || qy < 0.0 || qy > (double)(a.H - 1)) continue;
+            const double wx = ox ? fx : 1.0 - fx, wy = oy ? fy : 1.0 - fy;
+            const double dxq = qx - cx, dyq = qy - cy;
+            const double d2 = dxq * dxq + dyq * dyq;
+            const double G = exp(-d2 / den);
+            const double mwG = m * wx * wy * G;
+            T += mwG;
+            Tcx += mwG * dxq;          // x 1/sig^2 below
+            Tcy += mwG * dyq;
+            Tsig += mwG * d2;          // x 1/sig^3 below
+            // d w / d v: the cell corner is fixed, w = wx wy
+            const double dwdvx = (ox ? 1.0 : -1.0) * wy, dwdvy = wx * (oy ? 1.0 : -1.0);
+            const double mG = m * G;
+            Trho += mG * (dwdvx * s * X + dwdvy * s * Y);
+            if (a.accumulate) {
+              gk += wx * wy * G;
+              gX += mG * dwdvx * s * rho;
+              gY += mG * dwdvy * s * rho;
+            }
+          }
+      }
+      if (a.accumulate && (gk != 0.0 || gX != 0.0 || gY != 0.0)) {
+        const double dm = -m * (1.0 - m) / a.temp;  // dm/dk
+        atomicAdd(&a.gk[g], ds * gk * dm / rho);
+        atomicAdd(&a.gX[g], ds * gX / rho);
+        atomicAdd(&a.gY[g], ds * gY / rho);
+      }
+    }
+    T = block_sum(T, red);
+    Tcx = block_sum(Tcx, red);
+    Tcy = block_sum(Tcy, red);
+    Tsig = block_sum(Tsig, red);
+    Trho = block_sum(Trho, red);
+    if (threadIdx.x == 0) {
+      const double s2 = sig * sig;
+      const double score = T / rho;
+      // dScore/drho: through the vote positions, sigma(rho) and the 1/rho
+      const double dT_drho = Trho + Tsig / (s2 * sig) * a.sig_a;
+      if (a.score) a.score[i] = (float)score;
+      if (a.dparams) {
+        a.dparams[3 * i + 0] = (float)(ds * Tcx / s2 / rho);
+        a.dparams[3 * i + 1] = (float)(ds * Tcy / s2 / rho);
+        a.dparams[3 * i + 2] = (float)(ds * (dT_drho / rho - T / (rho * rho)));
+      }
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_soft_score(const SoftArgs& a, const int* counts, int* ring_off, cudaStream_t st) {
+  k_soft_offsets<<<1, 1024, 0, st>>>(counts, a.n, ring_off);
+  k_soft_score<<<152 * 8, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// ---- S6: chain through the eigen step (per ridge record) -----------------------
+// k = (a + c)/2 - R, R = sqrt(((a - c)/2)^2 + b^2); X = sign * v / |v| with
+// v = (b, k - a) or (k - c, b); d(v/|v|) = (I - u u^T) dv / |v|.
+__global__ void k_soft_chain(SoftArgs a) {
+  const size_t plane = (size_t)a.H * a.W;
+  const size_t total = (size_t)a.n * a.cap;
+  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
+    const int f = (int)(g / a.cap), j = (int)(g - (size_t)f * a.cap);
+    if (j >= min(a.count[f], a.cap)) continue;
+    const double A = a.ra[g], B = a.rb[g], C = a.rc[g], k = a.rk[g];
+    const double hd = 0.5 * (A - C);
+    const double R = sqrt(hd * hd + B * B);
+    const double dka = 0.5 - 0.5 * hd / R, dkc = 0.5 + 0.5 * hd / R, dkb = -B / R;
+    const bool use1 = a.flags[g] & 1;
+    const double sgn = (a.flags[g] & 2) ? -1.0 : 1.0;
+    const double vx = use1 ? B : k - C, vy = use1 ? k - A : B;
+    const double nv = sqrt(vx * vx + vy * vy);
+    const double ux = vx / nv, uy = vy / nv;
+    // gradient with respect to v: (I - u u^T) (sgn g_X) / |v|
+    const double hx = sgn * a.gX[g], hy = sgn * a.gY[g];
+    const double dot = ux * hx + uy * hy;
+    const double gvx = (hx - ux * dot) / nv, gvy = (hy - uy * dot) / nv;
+    // dv/d(a, b, c)
+    double ga, gb, gc;
+    if (use1) {  // v = (b, k - a)
+      ga = gvy * (dka - 1.0);
+      gb = gvx + gvy * dkb;
+      gc = gvy * dkc;
+    } else {     // v = (k - c, b)
+      ga = gvx * dka;
+      gb = gvx * dkb + gvy;
+      gc = gvx * (dkc - 1.0);
+    }
+    const double gk = a.gk[g];
+    ga += gk * dka;
+    gb += gk * dkb;
+    gc += gk * dkc;
+    const uint32_t xy = a.xy[g];
+    const size_t p = (size_t)f * plane + (size_t)(xy >> 16) * a.W + (xy & 0xffffu);
+    a.a[p] = ga;  // the Hessian images now hold d/d(Lxx, Lxy, Lyy)
+    a.b[p] = gb;
+    a.c[p] = gc;
+  }
+}
+
+// ---- S7: adjoint of the reflect-101 correlations -------------------------------
+// Forward along one axis: out[i] = sum_t k[t] in[refl(i + t)], |t| <= r.
+// Adjoint at j: the outputs i whose tap t reads j directly (i + t = j), by
+// the reflection below 0 (i + t = -j, j > 0) or above N - 1
+// (i + t = 2 (N - 1) - j, j < N - 1).
+__device__ __forceinline__ double adj1d(const double* src, size_t stride, int N, int j, const double* k, int r) {
+  double s = 0.0;
+  for (int t = -r; t <= r; ++t) {
+    int i = j - t;
+    if (i >= 0 && i < N) s += k[t + r] * src[i * stride];
+    if (j > 0) {
+      i = -j - t;
+      if (i >= 0 && i < N) s += k[t + r] * src[i * stride];
+    }
+    if (j < N - 1) {
+      i = 2 * (N - 1) - j - t;
+      if (i >= 0 && i < N) s += k[t + r] * src[i * stride];
+    }
+  }
+  return s;
+}
+
+// vertical Sobel adjoints: t0 = s5_y^T dLxx, t1 = d2_y^T dLyy, k = d1_y^T dLxy
+__global__ void k_soft_adj_sobel_v(SoftArgs a) {
+  const size_t plane = (size_t)a.H * a.W, total = plane * a.n;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t f = i / plane;
+    const size_t r = i - f * plane;
+    const int y = (int)(r / a.W), x = (int)(r - (size_t)y * a.W);
+    const size_t o = f * plane + x;
+    a.t0[i] = adj1d(a.a + o, a.W, a.H, y, c_s5, 2);
+    a.t1[i] = adj1d(a.c + o, a.W, a.H, y, c_d2, 2);
+    a.k[i] = adj1d(a.b + o, a.W, a.H, y, c_d1, 2);
+  }
+}
+
+// horizontal Sobel adjoints: dL = (d2_x^T t0 + s5_x^T t1 + d1_x^T k) / 64 -> X
+__global__ void k_soft_adj_sobel_h(SoftArgs a) {
+  const size_t plane = (size_t)a.H * a.W, total = plane * a.n;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t row = i / a.W;
+    const int x = (int)(i - row * a.W);
+    const size_t o = row * a.W;
+    a.X[i] = (adj1d(a.t0 + o, 1, a.W, x, c_d2, 2) + adj1d(a.t1 + o, 1, a.W, x, c_s5, 2) +
+              adj1d(a.k + o, 1, a.W, x, c_d1, 2)) / 64.0;
+  }
+}
+
+// Gaussian adjoints: Y = g_y^T X, then dimage = g_x^T Y
+__global__ void k_soft_adj_gauss_v(SoftArgs a) {
+  const size_t plane = (size_t)a.H * a.W, total = plane * a.n;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t f = i / plane;
+    const size_t r = i - f * plane;
+    const int y = (int)(r / a.W), x = (int)(r - (size_t)y * a.W);
+    a.Y[i] = adj1d(a.X + f * plane + x, a.W, a.H, y, a.g, a.R);
+  }
+}
+
+__global__ void k_soft_adj_gauss_h(SoftArgs a) {
+  const size_t plane = (size_t)a.H * a.W, total = plane * a.n;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t row = i / a.W;
+    const int x = (int)(i - row * a.W);
+    a.dimage[i] = (float)adj1d(a.Y + row * a.W, 1, a.W, x, a.g, a.R);
+  }
+}
+
+cudaError_t launch_soft_backward_image(const SoftArgs& a, cudaStream_t st) {
+  const size_t bytes = sizeof(double) * a.n * (size_t)a.H * a.W;
+  cudaError_t e = cudaMemsetAsync(a.a, 0, bytes, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.b, 0, bytes, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.c, 0, bytes, st);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = 152 * 8;
+  k_soft_chain<<<grid, 256, 0, st>>>(a);
+  k_soft_adj_sobel_v<<<grid, 256, 0, st>>>(a);
+  k_soft_adj_sobel_h<<<grid, 256, 0, st>>>(a);
+  k_soft_adj_gauss_v<<<grid, 256, 0, st>>>(a);
+  k_soft_adj_gauss_h<<<grid, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// ---- refinement: one gradient-ascent step per ring ------------------------------
+// Newton-like scaling: the score's curvature in c is about -Score / sigma^2,
+// so delta = step * sigma(rho)^2 / Score * gradient, at most 0.5 px.
+__global__ void k_soft_refine_step(SoftArgs a) {
+  const int n_rings = min(a.ring_off[a.n], a.max_rings);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_rings; i += gridDim.x * blockDim.x) {
+    rd_ring& q = a.rings_mut[i];
+    const float sc = a.score[i];
+    if (!(sc > 0.0f)) continue;
+    const float sig = a.sig_a * q.r + a.sig_b;
+    const float scale = a.step * sig * sig / sc;
+    const float d0 = fminf(fmaxf(scale * a.dparams[3 * i + 0], -0.5f), 0.5f);
+    const float d1 = fminf(fmaxf(scale * a.dparams[3 * i + 1], -0.5f), 0.5f);
+    const float d2 = fminf(fmaxf(scale * a.dparams[3 * i + 2], -0.5f), 0.5f);
+    q.cx += d0;
+    q.cy += d1;
+    q.r = fmaxf(q.r + d2, 1.0f);
+  }
+}
+
+cudaError_t launch_soft_refine_step(const SoftArgs& a, cudaStream_t st) {
+  k_soft_refine_step<<<152, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace rd

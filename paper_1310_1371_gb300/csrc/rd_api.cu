@@ -79,6 +79,18 @@ struct rd_ctx {
   int* stage_offsets = nullptr;
   // stage timing
   bool timing = false, timed = false;
+  // soft (differentiable) path: FP64 workspaces, allocated on first use
+  bool soft_ready = false;
+  double *s_t0 = nullptr, *s_t1 = nullptr, *s_a = nullptr, *s_b = nullptr, *s_c = nullptr, *s_k = nullptr,
+         *s_X = nullptr, *s_Y = nullptr;
+  int* s_count = nullptr;
+  uint32_t* s_xy = nullptr;
+  uint8_t* s_flags = nullptr;
+  double *s_rk = nullptr, *s_rX = nullptr, *s_rY = nullptr, *s_ra = nullptr, *s_rb = nullptr, *s_rc = nullptr,
+         *s_rm = nullptr, *s_gk = nullptr, *s_gX = nullptr, *s_gY = nullptr;
+  int* s_ring_off = nullptr;
+  float* s_score = nullptr;
+  float* s_dparams = nullptr;
   // graph mode: the captured rd_detect launch sequence and the arguments it was captured with
   bool graph_on = false;
   cudaGraphExec_t gexec = nullptr;
@@ -160,6 +172,11 @@ static void free_all(rd_ctx* c) {
                   c->bin_total, c->pool, c->peaks, c->peak_count, c->stats, c->stage_frames, c->stage_rings,
                   c->stage_counts, c->stage_offsets};
   for (void* p : ptrs)
+    if (p) cudaFree(p);
+  void* soft[] = {c->s_t0, c->s_t1, c->s_a, c->s_b, c->s_c, c->s_k, c->s_X, c->s_Y, c->s_count, c->s_xy,
+                  c->s_flags, c->s_rk, c->s_rX, c->s_rY, c->s_ra, c->s_rb, c->s_rc, c->s_rm, c->s_gk, c->s_gX,
+                  c->s_gY, c->s_ring_off, c->s_score, c->s_dparams};
+  for (void* p : soft)
     if (p) cudaFree(p);
 }
 
@@ -767,5 +784,146 @@ extern "C" rd_status rd_autotune(const rd_params* params, const void* frames_dev
     g_tuned[TuneKey{H, W, params->r_min, params->r_max}] = bg;
   }
   *best = bg;
+  return RD_OK;
+}
+
+
+// ---------------------------------------------------------------- soft (differentiable) path
+static rd_status ensure_soft(rd_ctx* c) {
+  if (c->soft_ready) return RD_OK;
+  const size_t px = (size_t)c->max_batch * c->max_H * c->max_W;
+  const size_t rec = (size_t)c->max_batch * c->rl.cap;
+  const size_t rings = (size_t)c->max_batch * c->peak_cap;
+  bool ok = dalloc(&c->s_t0, px) && dalloc(&c->s_t1, px) && dalloc(&c->s_a, px) && dalloc(&c->s_b, px) &&
+            dalloc(&c->s_c, px) && dalloc(&c->s_k, px) && dalloc(&c->s_X, px) && dalloc(&c->s_Y, px) &&
+            dalloc(&c->s_count, c->max_batch) && dalloc(&c->s_xy, rec) && dalloc(&c->s_flags, rec) &&
+            dalloc(&c->s_rk, rec) && dalloc(&c->s_rX, rec) && dalloc(&c->s_rY, rec) && dalloc(&c->s_ra, rec) &&
+            dalloc(&c->s_rb, rec) && dalloc(&c->s_rc, rec) && dalloc(&c->s_rm, rec) && dalloc(&c->s_gk, rec) &&
+            dalloc(&c->s_gX, rec) && dalloc(&c->s_gY, rec) && dalloc(&c->s_ring_off, (size_t)c->max_batch + 1) &&
+            dalloc(&c->s_score, rings) && dalloc(&c->s_dparams, 3 * rings);
+  if (!ok) {
+    cudaGetLastError();
+    return fail(c, RD_E_NOMEM, "soft path: device allocation failed");
+  }
+  c->soft_ready = true;
+  return RD_OK;
+}
+
+// Validate, allocate on first use and enqueue the soft stencil stage (Gaussian,
+// Hessian, eigen, ridge records) of n frames; fills *a.
+static rd_status soft_prepare(rd_ctx* c, const void* frames, int n, int H, int W, int dtype, cudaStream_t st,
+                              const rd_ring* rings, const int* counts, SoftArgs* a) {
+  if (!frames || !rings || !counts) return fail(c, RD_E_INVAL, "NULL argument");
+  if (n < 1 || n > c->max_batch) return fail(c, RD_E_INVAL, "n must be in [1, max_batch]");
+  if (H > c->max_H || W > c->max_W || H < c->taps.R + 4 || W < c->taps.R + 4 || H < 12 || W < 12)
+    return fail(c, RD_E_INVAL, "frame size outside [max(12, ceil(4 sigma) + 4), rd_create maxima]");
+  if (dtype != RD_U8 && dtype != RD_U16 && dtype != RD_F32)
+    return fail(c, RD_E_INVAL, "dtype must be RD_U8, RD_U16 or RD_F32");
+  rd_status s = ensure_soft(c);
+  if (s != RD_OK) return s;
+  *a = SoftArgs{};
+  a->frames = frames;
+  a->dtype = dtype;
+  a->n = n;
+  a->H = H;
+  a->W = W;
+  a->R = c->taps.R;
+  long long S = 0;
+  for (int i = 0; i <= 2 * c->taps.R; ++i) S += c->taps.q[i];
+  for (int i = 0; i <= 2 * c->taps.R; ++i) a->g[i] = (double)c->taps.q[i] / (double)S;
+  a->tau = (double)c->p.ridge_thresh;
+  a->temp = std::max(std::fabs(a->tau), 1e-6) / 4.0;
+  a->sig_a = (double)c->p.sig_a;
+  a->sig_b = (double)c->p.sig_b;
+  a->t0 = c->s_t0;
+  a->t1 = c->s_t1;
+  a->a = c->s_a;
+  a->b = c->s_b;
+  a->c = c->s_c;
+  a->k = c->s_k;
+  a->X = c->s_X;
+  a->Y = c->s_Y;
+  a->cap = c->rl.cap;
+  a->count = c->s_count;
+  a->xy = c->s_xy;
+  a->flags = c->s_flags;
+  a->rk = c->s_rk;
+  a->rX = c->s_rX;
+  a->rY = c->s_rY;
+  a->ra = c->s_ra;
+  a->rb = c->s_rb;
+  a->rc = c->s_rc;
+  a->rm = c->s_rm;
+  a->gk = c->s_gk;
+  a->gX = c->s_gX;
+  a->gY = c->s_gY;
+  a->rings = rings;
+  a->ring_off = c->s_ring_off;
+  a->max_rings = INT_MAX;
+  c->last_stream = st;
+  cudaError_t e = cudaMemsetAsync(c->s_count, 0, sizeof(int) * n, st);
+  if (e == cudaSuccess) e = launch_soft_stencil(*a, st);
+  if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("soft stencil: ") + cudaGetErrorString(e));
+  return RD_OK;
+}
+
+extern "C" rd_status rd_soft_score(rd_ctx* c, const void* frames_dev, int n, int H, int W, int dtype, void* stream,
+                                   const rd_ring* rings_dev, const int* counts_dev, float* score_dev,
+                                   float* dparams_dev) {
+  if (!c) return RD_E_INVAL;
+  if (!score_dev) return fail(c, RD_E_INVAL, "score_dev is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  SoftArgs a;
+  rd_status s = soft_prepare(c, frames_dev, n, H, W, dtype, st, rings_dev, counts_dev, &a);
+  if (s != RD_OK) return s;
+  a.score = score_dev;
+  a.dparams = dparams_dev;
+  cudaError_t e = launch_soft_score(a, counts_dev, c->s_ring_off, st);
+  if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("soft score: ") + cudaGetErrorString(e));
+  return RD_OK;
+}
+
+extern "C" rd_status rd_backward(rd_ctx* c, const float* frames_dev, int n, int H, int W, void* stream,
+                                 const rd_ring* rings_dev, const int* counts_dev, const float* dscore_dev,
+                                 float* dimage_dev, float* dparams_dev) {
+  if (!c) return RD_E_INVAL;
+  if (!dscore_dev || !dimage_dev) return fail(c, RD_E_INVAL, "dscore_dev and dimage_dev must not be NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  SoftArgs a;
+  rd_status s = soft_prepare(c, frames_dev, n, H, W, RD_F32, st, rings_dev, counts_dev, &a);
+  if (s != RD_OK) return s;
+  const size_t rec = sizeof(double) * (size_t)n * c->rl.cap;
+  cudaError_t e = cudaMemsetAsync(c->s_gk, 0, rec, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->s_gX, 0, rec, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->s_gY, 0, rec, st);
+  a.dscore = dscore_dev;
+  a.dparams = dparams_dev;
+  a.accumulate = 1;
+  a.dimage = dimage_dev;
+  if (e == cudaSuccess) e = launch_soft_score(a, counts_dev, c->s_ring_off, st);
+  if (e == cudaSuccess) e = launch_soft_backward_image(a, st);
+  if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("soft backward: ") + cudaGetErrorString(e));
+  return RD_OK;
+}
+
+extern "C" rd_status rd_refine(rd_ctx* c, const void* frames_dev, int n, int H, int W, int dtype, void* stream,
+                               rd_ring* rings_dev, const int* counts_dev, int iters, float step) {
+  if (!c) return RD_E_INVAL;
+  if (iters < 0 || !(step > 0.0f)) return fail(c, RD_E_INVAL, "iters must be >= 0 and step > 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  SoftArgs a;
+  rd_status s = soft_prepare(c, frames_dev, n, H, W, dtype, st, rings_dev, counts_dev, &a);
+  if (s != RD_OK) return s;
+  a.rings_mut = rings_dev;
+  a.score = c->s_score;
+  a.dparams = c->s_dparams;
+  a.max_rings = c->max_batch * c->peak_cap;
+  a.step = step;
+  cudaError_t e = cudaSuccess;
+  for (int it = 0; it < iters && e == cudaSuccess; ++it) {
+    e = launch_soft_score(a, counts_dev, c->s_ring_off, st);
+    if (e == cudaSuccess) e = launch_soft_refine_step(a, st);
+  }
+  if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("refine: ") + cudaGetErrorString(e));
   return RD_OK;
 }

@@ -143,6 +143,43 @@ struct FitArgs {
   DevStats* stats;
 };
 
+// Soft (differentiable) score path: FP64 images and ridge records of a batch
+// of frames, allocated on first use (k_soft.cu).
+struct SoftArgs {
+  const void* frames;
+  int dtype;                  // RD_U8, RD_U16 or RD_F32
+  int n, H, W;
+  int R;                      // Gaussian half-width
+  double g[2 * MAX_RG + 1];   // Gaussian taps Q_i / S
+  double tau, temp, sig_a, sig_b;
+  // dense FP64 images, n * H * W each
+  double *t0, *t1, *a, *b, *c, *k, *X, *Y;
+  // ridge records, frame f at [f * cap, f * cap + count[f])
+  int cap;
+  int* count;
+  uint32_t* xy;               // x | y << 16
+  uint8_t* flags;             // bit 0: eigenvector candidate v1; bit 1: sign flipped
+  double *rk, *rX, *rY, *ra, *rb, *rc, *rm;
+  double *gk, *gX, *gY;       // accumulated d(sum dscore Score)/d(k, X, Y) per record
+  // rings
+  const rd_ring* rings;
+  rd_ring* rings_mut;
+  int n_rings;
+  const int* ring_off;        // exclusive prefix of the per-frame ring counts, n + 1
+  const float* dscore;        // per ring, or null (1)
+  float* score;               // per ring, or null
+  float* dparams;             // per ring 3, or null
+  float* dimage;              // n * H * W, or null
+  int accumulate;             // add record gradients (backward)
+  int max_rings;              // rings beyond this index are ignored
+  float step;                 // refine step
+};
+
+cudaError_t launch_soft_stencil(const SoftArgs& a, cudaStream_t st);
+cudaError_t launch_soft_score(const SoftArgs& a, const int* counts, int* ring_off, cudaStream_t st);
+cudaError_t launch_soft_backward_image(const SoftArgs& a, cudaStream_t st);
+cudaError_t launch_soft_refine_step(const SoftArgs& a, cudaStream_t st);
+
 cudaError_t launch_stencil(const StencilArgs& a, int dtype, cudaStream_t st);
 cudaError_t launch_refine(const RidgeList& rl, int n_frames, int n_sm, cudaStream_t st);
 cudaError_t launch_bins(const BinArgs& a, int n_sm, cudaStream_t st, long long n_bins, int* block_sums,

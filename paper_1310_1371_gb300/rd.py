@@ -15,7 +15,7 @@ import numpy as np
 
 from . import _build
 
-RD_U8, RD_U16 = 0, 1
+RD_U8, RD_U16, RD_F32 = 0, 1, 2
 RD_OK, RD_E_INVAL, RD_E_NOMEM, RD_E_CUDA, RD_E_OVERFLOW, RD_E_TIMEOUT, RD_E_BUSY = range(7)
 STATUS_NAMES = ["RD_OK", "RD_E_INVAL", "RD_E_NOMEM", "RD_E_CUDA", "RD_E_OVERFLOW", "RD_E_TIMEOUT", "RD_E_BUSY"]
 RD_RING_FIT_FAIL = 1
@@ -79,6 +79,12 @@ def load_library(build: bool = False) -> ctypes.CDLL:
         "rd_debug_capture": (c_int, [c_void_p, c_void_p, c_void_p]),
         "rd_set_timing": (c_int, [c_void_p, c_int]),
         "rd_set_graph": (c_int, [c_void_p, c_int]),
+        "rd_soft_score": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
+                                  c_void_p, c_void_p]),
+        "rd_backward": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p,
+                                c_void_p, c_void_p]),
+        "rd_refine": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_int,
+                              c_float]),
         "rd_debug_route": (c_int, [c_void_p, c_int]),
         "rd_get_timing": (c_int, [c_void_p, P(c_float), c_int]),
         "rd_ridges_static": (c_int, [P(rd_params), c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
@@ -231,7 +237,63 @@ class Detector:
             return RD_U8
         if t == torch.uint16:
             return RD_U16
+        if t == torch.float32:
+            return RD_F32
         raise TypeError(f"unsupported frame dtype {t}")
+
+    # ---- differentiable soft score (rd_soft_score, rd_backward, rd_refine) ----
+    def _soft_args(self, frames, rings, counts):
+        torch = self.torch
+        for t in (frames, rings, counts):
+            if not t.is_cuda or not t.is_contiguous():
+                raise ValueError("frames, rings and counts must be contiguous CUDA tensors")
+        if rings.dtype != torch.float32 or rings.dim() != 2 or rings.shape[1] != 10:
+            raise TypeError("rings must be a float32 [n_rings, 10] tensor of rd_ring records (see pack_rings)")
+        if counts.dtype != torch.int32:
+            raise TypeError("counts must be int32")
+        n, H, W = frames.shape
+        return n, H, W
+
+    def soft_score(self, frames, rings, counts, with_grad=False, stream=None):
+        """rd_soft_score: per-ring scores [n_rings] (and d/d(cx, cy, r) [n_rings, 3])."""
+        torch = self.torch
+        n, H, W = self._soft_args(frames, rings, counts)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        score = torch.empty(rings.shape[0], dtype=torch.float32, device=frames.device)
+        dp = torch.empty((rings.shape[0], 3), dtype=torch.float32, device=frames.device) if with_grad else None
+        st = self.lib.rd_soft_score(self.ctx, c_void_p(frames.data_ptr()), n, H, W, self.dtype_code(frames.dtype),
+                                    c_void_p(s.cuda_stream), c_void_p(rings.data_ptr()), c_void_p(counts.data_ptr()),
+                                    c_void_p(score.data_ptr()), c_void_p(dp.data_ptr() if dp is not None else 0))
+        if st != RD_OK:
+            raise self._err(st)
+        return score, dp
+
+    def backward(self, frames, rings, counts, dscore, stream=None):
+        """rd_backward: (dimage [n, H, W], dparams [n_rings, 3]) for upstream dscore [n_rings]."""
+        torch = self.torch
+        n, H, W = self._soft_args(frames, rings, counts)
+        if frames.dtype != torch.float32 or dscore.dtype != torch.float32 or not dscore.is_contiguous():
+            raise TypeError("rd_backward takes float32 frames and a contiguous float32 dscore")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        dimage = torch.empty_like(frames)
+        dp = torch.empty((rings.shape[0], 3), dtype=torch.float32, device=frames.device)
+        st = self.lib.rd_backward(self.ctx, c_void_p(frames.data_ptr()), n, H, W, c_void_p(s.cuda_stream),
+                                  c_void_p(rings.data_ptr()), c_void_p(counts.data_ptr()), c_void_p(dscore.data_ptr()),
+                                  c_void_p(dimage.data_ptr()), c_void_p(dp.data_ptr()))
+        if st != RD_OK:
+            raise self._err(st)
+        return dimage, dp
+
+    def refine(self, frames, rings, counts, iters=10, step=0.5, stream=None):
+        """rd_refine: gradient ascent on the soft score, updating rings in place."""
+        torch = self.torch
+        n, H, W = self._soft_args(frames, rings, counts)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        st = self.lib.rd_refine(self.ctx, c_void_p(frames.data_ptr()), n, H, W, self.dtype_code(frames.dtype),
+                                c_void_p(s.cuda_stream), c_void_p(rings.data_ptr()), c_void_p(counts.data_ptr()),
+                                int(iters), float(step))
+        if st != RD_OK:
+            raise self._err(st)
 
     def detect_async(self, frames, stream=None):
         """Enqueue rd_detect on device frames [n, H, W] (uint8 / uint16)."""
@@ -325,3 +387,52 @@ class Detector:
                                        c_void_p(sm.data_ptr() if sm is not None else 0))
         if st != RD_OK:
             raise self._err(st)
+
+
+# ---- rd_ring records as a float32 [n, 10] tensor and the autograd wrapper ------------
+def pack_rings(params):
+    """rd_ring records (float32 [n, 10] view) whose cx, cy, r are params [n, 3];
+    the integer fields are left zero (the soft entry points read only cx, cy, r)."""
+    import torch
+    rec = torch.zeros((params.shape[0], 10), dtype=torch.float32, device=params.device)
+    rec[:, 1:4] = params
+    return rec
+
+
+def _soft_function():
+    import torch
+
+    class SoftRingScore(torch.autograd.Function):
+        """Score of each ring [n_rings] of a batch of float32 frames [n, H, W];
+        differentiable with respect to the frames and to params [n_rings, 3]
+        (cx, cy, r); counts [n] int32 assigns consecutive rings to frames.
+        Forward: rd_soft_score; backward: rd_backward."""
+
+        @staticmethod
+        def forward(ctx, frames, params, det, counts):
+            rings = pack_rings(params.detach())
+            score, _ = det.soft_score(frames.detach().contiguous(), rings, counts)
+            ctx.save_for_backward(frames, params, counts)
+            ctx.det = det
+            return score
+
+        @staticmethod
+        def backward(ctx, dscore):
+            frames, params, counts = ctx.saved_tensors
+            dimage, dparams = ctx.det.backward(frames.detach().contiguous(), pack_rings(params.detach()), counts,
+                                               dscore.contiguous().to(torch.float32))
+            return dimage, dparams, None, None
+
+    return SoftRingScore
+
+
+_SOFT = None
+
+
+def soft_ring_score(det: "Detector", frames, params, counts):
+    """Differentiable soft ring score (torch.autograd) through rd_soft_score /
+    rd_backward; see SoftRingScore."""
+    global _SOFT
+    if _SOFT is None:
+        _SOFT = _soft_function()
+    return _SOFT.apply(frames, params, det, counts)
