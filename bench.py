@@ -16,6 +16,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -381,6 +382,113 @@ def run_video(args):
     plain.close()
 
 
+# ------------------------------------------------------------------ differentiable soft score
+DIFF_METRIC = "frames/s, soft ring score + backward (image and ring gradients), 512x512 f32, 64 rings per frame"
+
+
+def _match(truth, found, tol=3.0):
+    """Index of the found ring nearest each true ring (centre within tol px), or -1."""
+    out = np.full(len(truth), -1)
+    if len(found) == 0:
+        return out
+    for i, (cx, cy, r) in enumerate(truth):
+        d = np.hypot(found[:, 0] - cx, found[:, 1] - cy) + np.abs(found[:, 2] - r)
+        j = int(np.argmin(d))
+        if d[j] < tol:
+            out[i] = j
+    return out
+
+
+def run_diff(args):
+    """rd_soft_score (scores and ring gradients) and rd_backward (image and ring
+    gradients) on 256 float frames with 64 rings each; rd_refine from the
+    hard detector's rings, with the sub-pixel error against the true rings
+    before and after; the FP64 oracle's forward + backward on a bounded sample."""
+    from paper_1310_1371_gb300 import synth
+    n, H, W = args.diff_frames, 512, 512
+    imgs, truth = synth.diff_images(n)  # spawn pool, before any CUDA call
+    import torch
+    from paper_1310_1371_gb300 import rd
+    torch.cuda.set_device(0)
+    params = synth.DIFF_PARAMS
+    det = rd.Detector(params, H, W, n)
+    frames = torch.from_numpy(imgs).cuda()
+    # starting rings: the hard detector on the frames rounded to u16
+    f16 = torch.from_numpy(np.clip(np.rint(imgs), 0, 65535).astype(np.uint16)).cuda()
+    found, _ = det.detect(f16)
+    counts_l = [len(r) for r in found]
+    flat = np.concatenate([np.stack([r["cx"], r["cy"], r["r"]], 1) for r in found]).astype(np.float32)
+    counts = torch.tensor(counts_l, dtype=torch.int32, device="cuda")
+    rings = rd.pack_rings(torch.from_numpy(flat).cuda())
+    ones = torch.ones(len(flat), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, k):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(k):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / k
+
+    sampler = ClockSampler(0)
+    time.sleep(0.3)
+    ms_fwd = timed(lambda: det.soft_score(frames, rings, counts, with_grad=True), args.steps)
+    ms_step = timed(lambda: (det.soft_score(frames, rings, counts), det.backward(frames, rings, counts, ones)),
+                    args.steps)
+    refined = rings.clone()
+    iters = 20
+    ev0.record(stream)
+    det.refine(frames, refined, counts, iters=iters, step=0.5)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_refine = ev0.elapsed_time(ev1)
+    clocks = sampler.stop()
+    # sub-pixel error of matched rings (centre distance, radius) before and after refinement
+    ref = refined[:, 1:4].cpu().numpy()
+    err_b, err_a = [], []
+    o = 0
+    for f in range(n):
+        k = counts_l[f]
+        m = _match(truth[f], flat[o:o + k])
+        for i, j in enumerate(m):
+            if j >= 0:
+                t = truth[f, i]
+                err_b.append((math.hypot(flat[o + j, 0] - t[0], flat[o + j, 1] - t[1]), abs(flat[o + j, 2] - t[2])))
+                err_a.append((math.hypot(ref[o + j, 0] - t[0], ref[o + j, 1] - t[1]), abs(ref[o + j, 2] - t[2])))
+        o += k
+    err_b, err_a = np.array(err_b), np.array(err_a)
+    # the FP64 oracle's forward + backward on a bounded sample of frames
+    from oracle import soft as S
+    sp = S.SoftParams.make(**params)
+    t0, done, o = time.perf_counter(), 0, 0
+    while done < n and (done == 0 or time.perf_counter() - t0 < args.cpu_budget):
+        S.soft_grads(imgs[done], flat[o:o + counts_l[done]].astype(np.float64), sp)
+        o += counts_l[done]
+        done += 1
+    cpu_s = time.perf_counter() - t0
+    line = {"metric": DIFF_METRIC, "value": n / (ms_step / 1e3), "unit": "frames/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": 2, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 (f32 frames and outputs)", "data": "synthetic",
+            "config": {"workload": f"diff: {n} frames 512x512 f32, 64 rings r 10-50 with sub-pixel truth, search r 8-56",
+                       "rings": int(len(flat)), "l2": f"inputs ({imgs.nbytes / 2**20:.0f} MiB) larger than L2; no flush"},
+            "score_and_ring_grads": {"value": n / (ms_fwd / 1e3), "unit": "frames/s"},
+            "refine": {"iters": iters, "ms": ms_refine, "frames_per_s": n / (ms_refine / 1e3),
+                       "matched_rings": int(len(err_b)),
+                       "median_centre_err_px": [float(np.median(err_b[:, 0])), float(np.median(err_a[:, 0]))],
+                       "median_radius_err_px": [float(np.median(err_b[:, 1])), float(np.median(err_a[:, 1]))],
+                       "note": "[before (hard detector, Kasa fit on u16-rounded frames), after rd_refine]"},
+            "cpu_baseline": {"value": done / cpu_s, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{done} frames: FP64 soft score + autograd gradients in {cpu_s:.1f} s"},
+            "gpu_launches": 14 * args.steps, "clocks": clocks}
+    print(json.dumps(line))
+    det.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -390,7 +498,8 @@ def main():
     ap.add_argument("--batch", type=int, default=96)
     ap.add_argument("--cpu-frames", type=int, default=4)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--workload", default="plain_full", choices=["plain_full", "video"])
+    ap.add_argument("--workload", default="plain_full", choices=["plain_full", "video", "diff"])
+    ap.add_argument("--diff-frames", type=int, default=256)
     ap.add_argument("--video-frames", type=int, default=2000)
     ap.add_argument("--video-batch", type=int, default=200)
     args = ap.parse_args()
@@ -398,6 +507,8 @@ def main():
         args.warmup = 3
     if args.workload == "video":
         run_video(args)
+    elif args.workload == "diff":
+        run_diff(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -186,10 +186,12 @@ rd_status rd_destroy(rd_ctx* ctx);
  * rd_backward takes dscore_dev (one float per ring) and writes
  * dimage_dev[n][H][W] = sum_i dscore_i dScore_i/dframe and, when dparams_dev
  * is not NULL, dscore_i times each ring's parameter gradient.
- * rd_refine moves every ring iters times by
- *   delta = step * sigma(r)^2 / Score * grad Score   (each component at most
- * 0.5 px; r at least 1), updating cx, cy, r of rings_dev in place; at most
- * 4096 rings per frame. */
+ * rd_refine ascends the unnormalised vote mass r * Score of every ring (the
+ * 1/r normalisation compares rings of different radii; for one ring it
+ * would pull r inward by about sigma(r)^2 / r), iters steps of
+ *   delta = step * sigma(r)^2 / Score * (dScore/dcx, dScore/dcy, dScore/dr + Score / r)
+ * (each component at most 0.5 px; r at least 1), updating cx, cy, r of
+ * rings_dev in place; at most 4096 rings per frame. */
 rd_status rd_soft_score(rd_ctx* ctx, const void* frames_dev, int n, int H, int W, int dtype, void* stream,
                         const rd_ring* rings_dev, const int* counts_dev, float* score_dev, float* dparams_dev);
 rd_status rd_backward(rd_ctx* ctx, const float* frames_dev, int n, int H, int W, void* stream,

@@ -439,8 +439,13 @@ cudaError_t launch_soft_backward_image(const SoftArgs& a, cudaStream_t st) {
 }
 
 // ---- refinement: one gradient-ascent step per ring ------------------------------
-// Newton-like scaling: the score's curvature in c is about -Score / sigma^2,
-// so delta = step * sigma(rho)^2 / Score * gradient, at most 0.5 px.
+// The ascent is on the unnormalised vote mass rho * Score: the 1/rho of the
+// score compares rings of different radii, but for one ring it pulls the
+// maximum in rho inward by about sigma^2 / rho.  Its gradient is
+// (rho dS/dc, rho dS/drho + S); with the Newton-like scaling by the
+// curvature -rho S / sigma^2 the step is
+//   delta = step * sigma(rho)^2 / S * (dS/dcx, dS/dcy, dS/drho + S / rho),
+// each component at most 0.5 px.
 __global__ void k_soft_refine_step(SoftArgs a) {
   const int n_rings = min(a.ring_off[a.n], a.max_rings);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_rings; i += gridDim.x * blockDim.x) {
@@ -451,7 +456,7 @@ __global__ void k_soft_refine_step(SoftArgs a) {
     const float scale = a.step * sig * sig / sc;
     const float d0 = fminf(fmaxf(scale * a.dparams[3 * i + 0], -0.5f), 0.5f);
     const float d1 = fminf(fmaxf(scale * a.dparams[3 * i + 1], -0.5f), 0.5f);
-    const float d2 = fminf(fmaxf(scale * a.dparams[3 * i + 2], -0.5f), 0.5f);
+    const float d2 = fminf(fmaxf(scale * (a.dparams[3 * i + 2] + sc / q.r), -0.5f), 0.5f);
     q.cx += d0;
     q.cy += d1;
     q.r = fmaxf(q.r + d2, 1.0f);

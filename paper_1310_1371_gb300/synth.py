@@ -189,16 +189,43 @@ def video_images(n_frames: int, seed: int = 1003, H: int = 1024, W: int = 1024, 
     return out
 
 
+def diff_frame(i: int, seed: int = 1004, H: int = 512, W: int = 512, n_rings: int = 64) -> Frame:
+    """Frame i of ``diff_frames``."""
+    rng = np.random.default_rng([seed, i])
+    cx = rng.uniform(40.0, W - 40.0, size=n_rings)
+    cy = rng.uniform(40.0, H - 40.0, size=n_rings)
+    R = rng.uniform(10.0, 50.0, size=n_rings)
+    rings = np.stack([cx, cy, R], axis=1)
+    img = _render(H, W, rings, _gauss_ring(120.0, 1.5), 40.0)
+    img += rng.normal(0.0, 8.0, size=img.shape)
+    return Frame(img.astype(np.float32), rings, dict(DIFF_PARAMS))
+
+
 def diff_frames(n: int, seed: int = 1004, H: int = 512, W: int = 512, n_rings: int = 64) -> list[Frame]:
     """f32 frames with sub-pixel centres and radii, no rounding or clipping."""
-    frames = []
-    for i in range(n):
-        rng = np.random.default_rng([seed, i])
-        cx = rng.uniform(40.0, W - 40.0, size=n_rings)
-        cy = rng.uniform(40.0, H - 40.0, size=n_rings)
-        R = rng.uniform(10.0, 50.0, size=n_rings)
-        rings = np.stack([cx, cy, R], axis=1)
-        img = _render(H, W, rings, _gauss_ring(120.0, 1.5), 40.0)
-        img += rng.normal(0.0, 8.0, size=img.shape)
-        frames.append(Frame(img.astype(np.float32), rings, dict(DIFF_PARAMS)))
-    return frames
+    return [diff_frame(i, seed, H, W, n_rings) for i in range(n)]
+
+
+def _diff_frame_job(args):
+    f = diff_frame(*args)
+    return f.image, f.rings
+
+
+def diff_images(n: int, seed: int = 1004, H: int = 512, W: int = 512, n_rings: int = 64, workers: int = 0):
+    """The frames of ``diff_frames`` as ([n, H, W] f32, [n, n_rings, 3] truth),
+    rendered by a pool of ``workers`` processes started with 'spawn' (0: all cores)."""
+    import multiprocessing as mp
+    import os
+    jobs = [(i, seed, H, W, n_rings) for i in range(n)]
+    imgs = np.empty((n, H, W), dtype=np.float32)
+    truth = np.empty((n, n_rings, 3))
+    workers = workers or (os.cpu_count() or 1)
+    if workers <= 1:
+        for i, j in enumerate(jobs):
+            imgs[i], truth[i] = _diff_frame_job(j)
+        return imgs, truth
+    with mp.get_context("spawn").Pool(workers) as pool:
+        for i, (img, rings) in enumerate(pool.imap(_diff_frame_job, jobs, chunksize=4)):
+            imgs[i] = img
+            truth[i] = rings
+    return imgs, truth

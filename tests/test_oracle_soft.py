@@ -153,3 +153,23 @@ def test_closed_form_bilinear_split():
     sc = S.soft_score(rd, np.array([[12.5, 10.0, 2.5]]), P, 30, 30)[0]
     far = 0.5 * math.exp(-(5.5 ** 2) / (2 * sig * sig)) + 0.5 * math.exp(-(4.5 ** 2) / (2 * sig * sig))
     assert abs(sc - (math.exp(-0.25 / (2 * sig * sig)) + far) / 2.5) < 1e-14
+
+
+def test_unnormalised_mass_is_stationary_at_the_true_radius():
+    """For the symmetric twelve-point ring, rho * Score is even in rho - 5
+    (the votes land at c0 -/+ (rho - 5) X for opposite directions) when the
+    window width is fixed, so its rho-derivative vanishes at the true radius, while Score itself still
+    decreases there: the 1/rho normalisation biases a refinement of rho.
+    This is why refinement ascends rho * Score."""
+    rd = twelve_points()
+    h = 1e-5
+    # sigma held at sigma(5) (sig_a = 0): a growing sigma(rho) would add mass
+    # from the bilinear neighbours on one side only
+    P0 = S.SoftParams(P.sigma, P.ridge_thresh, 0.0, P.sig_a * 5.0 + P.sig_b)
+    mass = lambda rho: rho * S.soft_score(rd, np.array([[20.0, 20.0, rho]]), P0, 41, 41)[0]
+    dm = (mass(5.0 + h) - mass(5.0 - h)) / (2 * h)
+    ds = (mass(5.0 + h) / (5.0 + h) - mass(5.0 - h) / (5.0 - h)) / (2 * h)
+    assert abs(dm) < 1e-8
+    # d(T / rho)/drho = -T / rho^2 with T = 12; the votes sit h off the grid
+    # point at rho = 5 +/- h, so T = 12 - O(h) on both sides
+    assert abs(ds + 12.0 / 25.0) < 1e-4
