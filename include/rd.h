@@ -330,6 +330,50 @@ rd_status   rd_ridges_static(const rd_params* params, const void* frame_dev, int
                              void* stream, uint32_t* xy_dev, float* dir_dev, int cap, int* count_dev);
 const char* rd_static_last_error(void);
 
+/* ---- continuous-batching request server ------------------------------------
+ * Not in the paper (whose producer-consumer pool is its prior art, Methods).
+ * One server serves single-frame requests of several size classes on the
+ * current GPU.  Each class owns `slots` detector contexts with their own
+ * streams and pinned staging, all created by rd_serve_create; their device
+ * workspaces must fit mem_budget bytes (0: no limit), else RD_E_NOMEM and no
+ * server.  A scheduler thread admits queued requests into free slots, up to
+ * max_batch frames per launch, so requests arriving while others are on the
+ * GPU are admitted as slots free up and the slots' work overlaps.  A frame's
+ * rings are the ones rd_detect gives for that frame alone.
+ *   rd_serve_submit copies the class's H x W frame (dtype of the class) from
+ *     frame_host and queues it (RD_E_BUSY: queue_cap requests are waiting;
+ *     RD_E_INVAL: bad class or pointer).  Thread-safe.
+ *   rd_serve_poll waits up to wait_ms for completed requests and returns up
+ *     to max_results of them (-1 on bad arguments): ids, class, status
+ *     (RD_OK or the error of its batch), ring count, latency from submission
+ *     to results on the host (microseconds); their rings are concatenated in
+ *     rings (a result whose rings do not fit stays for the next poll, unless
+ *     it is the first, which is then truncated).  Thread-safe.
+ *   rd_serve_stats writes submitted, completed, batches launched and device
+ *     bytes of the slots.
+ *   rd_serve_destroy stops admitting, waits for the batches in flight and
+ *     frees everything; results not polled are dropped.
+ * Errors of rd_serve_create / rd_serve_submit: rd_serve_last_error (per
+ * host thread). */
+typedef struct rd_serve_class {
+  rd_params params;
+  int H, W;       /* frame size of the class's requests                       */
+  int dtype;      /* RD_U8 or RD_U16                                          */
+  int max_batch;  /* frames per launch                                        */
+  int slots;      /* batches in flight at once (contexts and streams), 1..16   */
+} rd_serve_class;
+
+typedef struct rd_server rd_server;
+
+rd_status   rd_serve_create(const rd_serve_class* classes, int n_classes, long long mem_budget, int queue_cap,
+                            rd_server** out);
+rd_status   rd_serve_submit(rd_server* server, int cls, const void* frame_host, long long request_id);
+int         rd_serve_poll(rd_server* server, long long* ids, int* classes, int* status, int* n_rings,
+                          rd_ring* rings, int rings_cap, double* latency_us, int max_results, int wait_ms);
+rd_status   rd_serve_stats(rd_server* server, long long* out4);
+rd_status   rd_serve_destroy(rd_server* server);
+const char* rd_serve_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

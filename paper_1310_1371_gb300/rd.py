@@ -90,6 +90,13 @@ def load_library(build: bool = False) -> ctypes.CDLL:
         "rd_ridges_static": (c_int, [P(rd_params), c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
                                      c_int, c_void_p]),
         "rd_static_last_error": (ctypes.c_char_p, []),
+        "rd_serve_create": (c_int, [c_void_p, c_int, ctypes.c_longlong, c_int, P(c_void_p)]),
+        "rd_serve_submit": (c_int, [c_void_p, c_int, c_void_p, ctypes.c_longlong]),
+        "rd_serve_poll": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p,
+                                  c_int, c_int]),
+        "rd_serve_stats": (c_int, [c_void_p, c_void_p]),
+        "rd_serve_destroy": (c_int, [c_void_p]),
+        "rd_serve_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -436,3 +443,73 @@ def soft_ring_score(det: "Detector", frames, params, counts):
     if _SOFT is None:
         _SOFT = _soft_function()
     return _SOFT.apply(frames, params, det, counts)
+
+
+# ---- continuous-batching server (rd_serve_*) ----------------------------------------
+class rd_serve_class(ctypes.Structure):
+    _fields_ = [("params", rd_params), ("H", c_int), ("W", c_int), ("dtype", c_int), ("max_batch", c_int),
+                ("slots", c_int)]
+
+
+class Server:
+    """rd_serve_*: continuous-batching request server.  classes: list of dicts
+    with params, H, W, dtype ('u8'/'u16'), max_batch, slots."""
+
+    def __init__(self, classes, mem_budget=0, queue_cap=4096):
+        import torch  # noqa: F401  (the CUDA context of the current device)
+        self.lib = load_library()
+        arr = (rd_serve_class * len(classes))()
+        self.frame_shapes = []
+        for i, c in enumerate(classes):
+            arr[i] = rd_serve_class(make_params(**c["params"]), int(c["H"]), int(c["W"]),
+                                    RD_U8 if c.get("dtype", "u16") == "u8" else RD_U16, int(c["max_batch"]),
+                                    int(c["slots"]))
+            self.frame_shapes.append((int(c["H"]), int(c["W"]), np.uint8 if c.get("dtype", "u16") == "u8" else np.uint16))
+        self.ptr = c_void_p()
+        st = self.lib.rd_serve_create(arr, len(classes), int(mem_budget), int(queue_cap), ctypes.byref(self.ptr))
+        if st != RD_OK:
+            raise RdError(st, self.lib.rd_serve_last_error().decode())
+
+    def submit(self, cls: int, frame: np.ndarray, request_id: int) -> int:
+        """Queue one frame; returns the status (RD_OK or RD_E_BUSY), raises on bad arguments."""
+        H, W, dt = self.frame_shapes[cls]
+        if frame.shape != (H, W) or frame.dtype != dt or not frame.flags.c_contiguous:
+            raise ValueError(f"class {cls} takes C-contiguous {H}x{W} {np.dtype(dt).name} frames")
+        st = self.lib.rd_serve_submit(self.ptr, cls, c_void_p(frame.ctypes.data), int(request_id))
+        if st not in (RD_OK, RD_E_BUSY):
+            raise RdError(st, self.lib.rd_serve_last_error().decode())
+        return st
+
+    def poll(self, max_results=256, rings_cap=1 << 20, wait_ms=0):
+        """Completed requests: list of (id, class, status, rings array, latency_us)."""
+        ids = np.empty(max_results, np.int64)
+        cls = np.empty(max_results, np.int32)
+        sts = np.empty(max_results, np.int32)
+        nr = np.empty(max_results, np.int32)
+        lat = np.empty(max_results, np.float64)
+        rings = np.empty(rings_cap, dtype=RING_NP)
+        k = self.lib.rd_serve_poll(self.ptr, ids.ctypes.data, cls.ctypes.data, sts.ctypes.data, nr.ctypes.data,
+                                   rings.ctypes.data, rings_cap, lat.ctypes.data, max_results, int(wait_ms))
+        if k < 0:
+            raise RdError(RD_E_INVAL, "rd_serve_poll")
+        out, o = [], 0
+        for i in range(k):
+            out.append((int(ids[i]), int(cls[i]), int(sts[i]), rings[o:o + nr[i]].copy(), float(lat[i])))
+            o += int(nr[i])
+        return out
+
+    def stats(self):
+        buf = np.zeros(4, np.int64)
+        self.lib.rd_serve_stats(self.ptr, buf.ctypes.data)
+        return dict(submitted=int(buf[0]), completed=int(buf[1]), batches=int(buf[2]), device_bytes=int(buf[3]))
+
+    def close(self):
+        if getattr(self, "ptr", None) is not None and self.ptr.value:
+            self.lib.rd_serve_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

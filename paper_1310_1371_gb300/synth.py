@@ -229,3 +229,53 @@ def diff_images(n: int, seed: int = 1004, H: int = 512, W: int = 512, n_rings: i
             imgs[i] = img
             truth[i] = rings
     return imgs, truth
+
+
+# Serving workload: frame sizes and the detector settings of each size class
+# (radius search range scaled with the frame size).
+SERVE_CLASSES = {
+    256: dict(PLAIN_FULL_PARAMS, r_min=5, r_max=20),
+    512: dict(PLAIN_FULL_PARAMS, r_min=5, r_max=40),
+    1024: dict(PLAIN_FULL_PARAMS, r_min=8, r_max=96),
+    2048: dict(PLAIN_FULL_PARAMS, r_min=8, r_max=160),
+}
+
+
+def serve_frame(size: int, i: int, seed: int = 1005) -> Frame:
+    """Frame i of the serving size class ``size`` (u16, rendered like
+    ``plain_full``): 10-400 rings, radii uniform inside the class's search
+    range (2 px in from each end)."""
+    p = SERVE_CLASSES[size]
+    rng = np.random.default_rng([seed, size, i])
+    n = int(rng.integers(10, 401))
+    cx = rng.uniform(0.0, size, size=n)
+    cy = rng.uniform(0.0, size, size=n)
+    R = rng.uniform(p["r_min"] + 2.0, p["r_max"] - 2.0, size=n)
+    K = rng.integers(2, 4, size=n)
+    rings = np.stack([cx, cy, R], axis=1)
+    img = _render(size, size, rings, [_fringed_ring(600.0, 1.5, int(k)) for k in K], 400.0)
+    img = rng.poisson(img).astype(np.float64) + rng.normal(0.0, 10.0, size=img.shape)
+    img = np.clip(np.rint(img), 0, 4095).astype(np.uint16)
+    return Frame(img, rings, dict(p))
+
+
+def _serve_frame_job(args):
+    return serve_frame(*args).image
+
+
+def serve_images(per_class: int, seed: int = 1005, sizes=(256, 512, 1024, 2048), workers: int = 0) -> dict:
+    """``per_class`` frames of each serving size class, {size: [frames]},
+    rendered by a pool of processes started with 'spawn' (0: all cores)."""
+    import multiprocessing as mp
+    import os
+    jobs = [(s, i, seed) for s in sizes for i in range(per_class)]
+    workers = workers or (os.cpu_count() or 1)
+    if workers <= 1:
+        imgs = [_serve_frame_job(j) for j in jobs]
+    else:
+        with mp.get_context("spawn").Pool(workers) as pool:
+            imgs = pool.map(_serve_frame_job, jobs, chunksize=1)
+    out = {s: [] for s in sizes}
+    for (s, i, _), img in zip(jobs, imgs):
+        out[s].append(img)
+    return out

@@ -101,3 +101,19 @@ def test_bad_geometry_rejected(lib, geo):
     st = lib.rd_create_ex(ctypes.byref(p), 256, 256, 1, ctypes.byref(g), ctypes.byref(ctx))
     assert st == rd.RD_E_INVAL and not ctx.value
     assert b"geometry" in lib.rd_last_error(None)
+
+
+def test_serve_create_validates_classes(lib):
+    """rd_serve_create rejects bad class descriptions before touching the GPU."""
+    from paper_1310_1371_gb300 import rd, synth
+    good = rd.rd_serve_class(rd.make_params(**synth.PLAIN_SMALL_PARAMS), 256, 256, rd.RD_U8, 4, 1)
+    for bad in (dict(slots=0), dict(slots=17), dict(max_batch=0), dict(dtype=7)):
+        c = rd.rd_serve_class(good.params, good.H, good.W, bad.get("dtype", good.dtype),
+                              bad.get("max_batch", good.max_batch), bad.get("slots", good.slots))
+        arr = (rd.rd_serve_class * 1)(c)
+        out = ctypes.c_void_p()
+        assert lib.rd_serve_create(arr, 1, 0, 16, ctypes.byref(out)) == rd.RD_E_INVAL and not out.value
+    arr = (rd.rd_serve_class * 1)(good)
+    out = ctypes.c_void_p()
+    assert lib.rd_serve_create(arr, 0, 0, 16, ctypes.byref(out)) == rd.RD_E_INVAL
+    assert lib.rd_serve_create(arr, 1, 0, 0, ctypes.byref(out)) == rd.RD_E_INVAL
