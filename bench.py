@@ -489,6 +489,83 @@ def run_diff(args):
     det.close()
 
 
+# ------------------------------------------------------------------ serving (continuous batching)
+SERVE_METRIC = "p50/p99 latency and frames/s, Poisson stream of single-frame requests (256^2-2048^2 u16)"
+
+
+def run_serve(args):
+    """A Poisson stream of single-frame requests (sizes uniform over
+    256^2 .. 2048^2, u16, 10-400 rings) through the continuous-batching
+    server; latency from submission to results on the host."""
+    import threading
+    from paper_1310_1371_gb300 import synth
+    sizes = (256, 512, 1024, 2048)
+    pool = synth.serve_images(args.serve_pool)  # spawn pool, before any CUDA call
+    import torch
+    from paper_1310_1371_gb300 import rd
+    torch.cuda.set_device(0)
+    batch = {256: 16, 512: 8, 1024: 4, 2048: 2}
+    classes = [dict(params=synth.SERVE_CLASSES[s], H=s, W=s, dtype="u16", max_batch=batch[s], slots=2) for s in sizes]
+    server = rd.Server(classes, mem_budget=int(args.serve_budget_gb * 2**30), queue_cap=8192)
+    for c, s in enumerate(sizes):  # warm-up: one request per class
+        server.submit(c, pool[s][0], -1 - c)
+    got = 0
+    while got < len(sizes):
+        got += len(server.poll(wait_ms=100))
+    n, rate = args.serve_requests, args.serve_rate
+    rng = np.random.default_rng(1005)
+    arrive = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    cls = rng.integers(0, len(sizes), size=n)
+    idx = rng.integers(0, args.serve_pool, size=n)
+    lat = np.zeros(n)
+    status = np.zeros(n, dtype=np.int32)
+    t_done = [0.0]
+
+    def collect():
+        seen = 0
+        while seen < n:
+            for rid, c, st, rings, l in server.poll(wait_ms=20):
+                lat[rid] = l
+                status[rid] = st
+                seen += 1
+            t_done[0] = time.perf_counter()
+
+    th = threading.Thread(target=collect)
+    sampler = ClockSampler(0)
+    th.start()
+    t0 = time.perf_counter()
+    busy = 0
+    for i in range(n):
+        wait = t0 + arrive[i] - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        while server.submit(int(cls[i]), pool[sizes[cls[i]]][idx[i]], i) == rd.RD_E_BUSY:
+            busy += 1
+            time.sleep(1e-4)
+    th.join()
+    clocks = sampler.stop()
+    wall = t_done[0] - t0
+    stats = server.stats()
+    server.close()
+    ms = lat / 1e3
+    per = {f"{s}x{s}": {"requests": int((cls == c).sum()), "p50_ms": float(np.percentile(ms[cls == c], 50)),
+                        "p99_ms": float(np.percentile(ms[cls == c], 99))} for c, s in enumerate(sizes)}
+    line = {"metric": SERVE_METRIC, "value": float(np.percentile(ms, 99)), "unit": "ms (p99 latency)",
+            "higher_is_better": False, "n_gpus": 1, "steps": n, "warmup": len(sizes),
+            "ms_per_step": wall * 1e3 / n, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
+            "data": "synthetic",
+            "config": {"workload": f"serve: {n} requests, Poisson {rate}/s, sizes uniform over 256..2048 squared, "
+                                   f"10-400 rings, r ranges 5-20 / 5-40 / 8-96 / 8-160",
+                       "frames_per_class_pool": args.serve_pool, "max_batch": batch, "slots_per_class": 2,
+                       "mem_budget_gb": args.serve_budget_gb},
+            "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+            "frames_per_s": n / wall, "offered_per_s": rate, "per_class": per,
+            "batches": stats["batches"] - len(sizes), "device_bytes": stats["device_bytes"],
+            "errors": int((status != 0).sum()), "submit_retries_busy": busy,
+            "gpu_launches": KERNELS_PER_CALL * (stats["batches"] - len(sizes)), "clocks": clocks}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -498,7 +575,11 @@ def main():
     ap.add_argument("--batch", type=int, default=96)
     ap.add_argument("--cpu-frames", type=int, default=4)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--workload", default="plain_full", choices=["plain_full", "video", "diff"])
+    ap.add_argument("--workload", default="plain_full", choices=["plain_full", "video", "diff", "serve"])
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-rate", type=float, default=500.0)
+    ap.add_argument("--serve-pool", type=int, default=8)
+    ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     ap.add_argument("--diff-frames", type=int, default=256)
     ap.add_argument("--video-frames", type=int, default=2000)
     ap.add_argument("--video-batch", type=int, default=200)
@@ -509,6 +590,8 @@ def main():
         run_video(args)
     elif args.workload == "diff":
         run_diff(args)
+    elif args.workload == "serve":
+        run_serve(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
