@@ -48,6 +48,8 @@ class Params:
     annulus_w: float      # annulus half-width in px (step 5; not given in the paper)
     sig_a: float          # sigma(r) = sig_a * r + sig_b (Methods: 0.05, 0.25)
     sig_b: float
+    features: str = "ridge"   # "ridge" (the method) or "edge" (Additional notes: directed edges)
+    edge_thresh: float = 0.0  # gradient-magnitude threshold of the edge variant (intensity / px)
 
     @staticmethod
     def make(**kw) -> "Params":
@@ -55,7 +57,8 @@ class Params:
         return Params(sigma=f32(kw["sigma"]), r_min=int(kw["r_min"]), r_max=int(kw["r_max"]),
                       ridge_thresh=f32(kw["ridge_thresh"]), peak_frac=f32(kw["peak_frac"]),
                       vote_thresh=int(kw["vote_thresh"]), annulus_w=f32(kw.get("annulus_w", 2.0)),
-                      sig_a=f32(kw.get("sig_a", 0.05)), sig_b=f32(kw.get("sig_b", 0.25)))
+                      sig_a=f32(kw.get("sig_a", 0.05)), sig_b=f32(kw.get("sig_b", 0.25)),
+                      features=kw.get("features", "ridge"), edge_thresh=f32(kw.get("edge_thresh", 0.0)))
 
 
 # --------------------------------------------------------------------------
@@ -438,6 +441,66 @@ def directed_ridges(image: np.ndarray, p: Params):
     return np.stack([xs, ys], axis=1).astype(np.int64), np.stack([X[ys, xs], Y[ys, xs]], axis=1)
 
 
+# --------------------------------------------------------------------------
+# Directed-edge variant (Additional notes: the Hessian is replaced by the
+# gradient, whose magnitude, replacing k-, must be a local maximum along the
+# gradient direction).  Readings: the gradient is the first-order 5x5 Sobel
+# of L' (exact integers) scaled by 1/128 (Sum s = 16 times the first-order
+# weight 8 of d1 on a unit ramp, so a linear ramp gives its slope exactly);
+# an edge pixel has |grad| > edge_thresh, |grad| > its bilinear sample at
+# p + X and >= its sample at p - X (strict/non-strict as for ridges), with
+# X = grad / |grad| in the canonical sign; |grad| = 0 is never an edge.
+# --------------------------------------------------------------------------
+def gradient_int(Lp: np.ndarray):
+    """Exact integer first-order Sobel of L': Gx' = (d1_x (x) s_y) * L',
+    Gy' = (s_x (x) d1_y) * L', reflect-101 borders."""
+    gx = _correlate1d_int(_correlate1d_int(Lp, SOBEL_D1, 1), SOBEL_S, 0)
+    gy = _correlate1d_int(_correlate1d_int(Lp, SOBEL_S, 1), SOBEL_D1, 0)
+    return gx, gy
+
+
+def gradient(image: np.ndarray, sigma: float):
+    """(Gx, Gy) = (Gx', Gy') / (128 S^2) in float64 (one division each)."""
+    Lp, S = smooth_int(image, sigma)
+    gx, gy = gradient_int(Lp)
+    D = float(128 * S * S)
+    return gx.astype(np.float64) / D, gy.astype(np.float64) / D
+
+
+def edge_direction(gx: np.ndarray, gy: np.ndarray):
+    """|grad| and its unit direction in the canonical sign (X > 0, or X == 0
+    and Y > 0), one IEEE operation per step: g = sqrt(gx gx + gy gy),
+    X = gx / g, Y = gy / g.  Degenerate where g == 0."""
+    g = np.sqrt(gx * gx + gy * gy)
+    degenerate = g == 0.0
+    with np.errstate(invalid="ignore", divide="ignore"):
+        X = gx / g
+        Y = gy / g
+    flip = (X < 0.0) | ((X == 0.0) & (Y < 0.0))
+    X = np.where(flip, -X, X)
+    Y = np.where(flip, -Y, Y)
+    X = np.where(degenerate, 0.0, X)
+    Y = np.where(degenerate, 0.0, Y)
+    return g, X, Y, degenerate
+
+
+def edge_mask(g, X, Y, degenerate, edge_thresh: float) -> np.ndarray:
+    """edge(p) <=> g(p) > edge_thresh and g(p) > g~(p + X) and
+    g(p) >= g~(p - X); bilinear samples as in ridge_mask (a maximum instead of
+    a minimum); a sample outside the frame makes the pixel a non-edge."""
+    # the ridge test of -g against the threshold -edge_thresh is the same test
+    return ridge_mask(-g, X, Y, degenerate, -edge_thresh)
+
+
+def directed_edges(image: np.ndarray, p: Params):
+    """Edge pixel coordinates (row-major) and their gradient directions."""
+    gx, gy = gradient(image, p.sigma)
+    g, X, Y, deg = edge_direction(gx, gy)
+    mask = edge_mask(g, X, Y, deg, p.edge_thresh)
+    ys, xs = np.nonzero(mask)
+    return np.stack([xs, ys], axis=1).astype(np.int64), np.stack([X[ys, xs], Y[ys, xs]], axis=1)
+
+
 def detect(image: np.ndarray, p: Params, keep: bool = False) -> Result:
     """Frame -> rings, steps O1-O9 in order.  Levels are visited in
     increasing r; the peak test of level r runs once N of level r + 1 exists
@@ -445,7 +508,7 @@ def detect(image: np.ndarray, p: Params, keep: bool = False) -> Result:
     if image.dtype.kind not in "ui":
         raise TypeError("the oracle's exact path takes integer frames")
     H, W = image.shape
-    ridge_xy, ridge_X = directed_ridges(image, p)
+    ridge_xy, ridge_X = directed_edges(image, p) if p.features == "edge" else directed_ridges(image, p)
     xs, ys = ridge_xy[:, 0], ridge_xy[:, 1]
     levels = radius_levels(p.r_min, p.r_max)
     Ns, As = {}, {}
