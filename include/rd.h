@@ -200,6 +200,25 @@ rd_status rd_backward(rd_ctx* ctx, const float* frames_dev, int n, int H, int W,
 rd_status rd_refine(rd_ctx* ctx, const void* frames_dev, int n, int H, int W, int dtype, void* stream,
                     rd_ring* rings_dev, const int* counts_dev, int iters, float step);
 
+/* ---- feature stage: directed ridges (the method) or directed edges ----------
+ * The Additional notes of the paper describe a variant for images whose
+ * features are better described by edges: the gradient replaces the
+ * Hessian, and the gradient magnitude, replacing k-, must be a local maximum
+ * along the gradient direction.  rd_set_features(ctx, RD_FEATURES_EDGE, t)
+ * makes the following rd_detect calls use directed edges: (Gx, Gy) = the
+ * first-order 5x5 Sobel of the smoothed frame / 128 (exact integers, then one
+ * division), an edge pixel has |grad| > t (intensity / px), |grad| > its
+ * bilinear sample at p + X and >= its sample at p - X, X = grad / |grad|
+ * (canonical sign); each edge pixel then votes, is scored and fitted exactly
+ * like a ridge pixel.  RD_FEATURES_RIDGE restores the method.  The first
+ * switch to edges allocates the edge workspaces (36 bytes per pixel of
+ * max_batch x max_H x max_W plus 16 bytes per record).  Errors: RD_E_INVAL
+ * (unknown features, t < 0), RD_E_NOMEM.  rd_debug_ridges then returns the
+ * edge pixels and their directions (hess = 0). */
+#define RD_FEATURES_RIDGE 0
+#define RD_FEATURES_EDGE  1
+rd_status rd_set_features(rd_ctx* ctx, int features, float edge_thresh);
+
 /* ---- accumulator geometry and its autotuner --------------------------------
  * The voting stage works on (frame, tile, slab) bins: tile x tile pixels of
  * the accumulator and slab_levels consecutive peak levels, each held in one

@@ -266,8 +266,15 @@ __device__ __noinline__ int vote_bins_slow(const VoteArgs& a, size_t fbase, VEnt
     oxy[1] = vy;
     return 0;
   }
-  Eig64 e64 = eigen64(a.rl.hess[3 * g], a.rl.hess[3 * g + 1], a.rl.hess[3 * g + 2], a.D64);
-  double X = e64.X, Y = e64.Y;
+  double X, Y;
+  if (a.rl.x64) {  // directed edges: the record keeps the exact double direction
+    X = a.rl.x64[g].x;
+    Y = a.rl.x64[g].y;
+  } else {
+    const Eig64 e64 = eigen64(a.rl.hess[3 * g], a.rl.hess[3 * g + 1], a.rl.hess[3 * g + 2], a.D64);
+    X = e64.X;
+    Y = e64.Y;
+  }
   if (X * (double)d.x + Y * (double)d.y < 0.0) {
     X = -X;
     Y = -Y;

@@ -79,6 +79,13 @@ struct rd_ctx {
   int* stage_offsets = nullptr;
   // stage timing
   bool timing = false, timed = false;
+  // feature stage: 0 directed ridges (the method), 1 directed edges (variant)
+  int features = 0;
+  double edge_thresh = 0.0;
+  uint32_t* e_hp = nullptr;
+  unsigned long long* e_L = nullptr;
+  double *e_g = nullptr, *e_X = nullptr, *e_Y = nullptr;
+  double2* e_x64 = nullptr;
   // soft (differentiable) path: FP64 workspaces, allocated on first use
   bool soft_ready = false;
   double *s_t0 = nullptr, *s_t1 = nullptr, *s_a = nullptr, *s_b = nullptr, *s_c = nullptr, *s_k = nullptr,
@@ -172,6 +179,9 @@ static void free_all(rd_ctx* c) {
                   c->bin_total, c->pool, c->peaks, c->peak_count, c->stats, c->stage_frames, c->stage_rings,
                   c->stage_counts, c->stage_offsets};
   for (void* p : ptrs)
+    if (p) cudaFree(p);
+  void* edge[] = {c->e_hp, c->e_L, c->e_g, c->e_X, c->e_Y, c->e_x64};
+  for (void* p : edge)
     if (p) cudaFree(p);
   void* soft[] = {c->s_t0, c->s_t1, c->s_a, c->s_b, c->s_c, c->s_k, c->s_X, c->s_Y, c->s_count, c->s_xy,
                   c->s_flags, c->s_rk, c->s_rX, c->s_rY, c->s_ra, c->s_rb, c->s_rc, c->s_rm, c->s_gk, c->s_gX,
@@ -437,10 +447,34 @@ static rd_status detect_enqueue(rd_ctx* c, const void* frames_dev, int n, int H,
   sa.invD = c->invD;
   sa.rl = rl;
   sa.stats = c->stats;
-  chk(launch_stencil(sa, dtype, st));
-  mark(1);
-  chk(launch_refine(rl, n, c->n_sm, st));
-  mark(2);
+  if (c->features == 1) {  // directed edges replace directed ridges
+    EdgeArgs ea;
+    ea.frames = frames_dev;
+    ea.n = n;
+    ea.H = H;
+    ea.W = W;
+    ea.taps = c->taps;
+    long long S = 0;
+    for (int i = 0; i <= 2 * c->taps.R; ++i) S += c->taps.q[i];
+    ea.D64 = (double)(128LL * S * S);
+    ea.thresh = c->edge_thresh;
+    ea.hp = c->e_hp;
+    ea.L = c->e_L;
+    ea.g = c->e_g;
+    ea.X = c->e_X;
+    ea.Y = c->e_Y;
+    rl.x64 = c->e_x64;
+    ea.rl = rl;
+    ea.stats = c->stats;
+    chk(launch_edge(ea, dtype, st));
+    mark(1);
+    mark(2);
+  } else {
+    chk(launch_stencil(sa, dtype, st));
+    mark(1);
+    chk(launch_refine(rl, n, c->n_sm, st));
+    mark(2);
+  }
   if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("stencil: ") + cudaGetErrorString(e));
 
   BinArgs ba;
@@ -925,5 +959,28 @@ extern "C" rd_status rd_refine(rd_ctx* c, const void* frames_dev, int n, int H, 
     if (e == cudaSuccess) e = launch_soft_refine_step(a, st);
   }
   if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("refine: ") + cudaGetErrorString(e));
+  return RD_OK;
+}
+
+
+// ---------------------------------------------------------------- feature stage
+extern "C" rd_status rd_set_features(rd_ctx* c, int features, float edge_thresh) {
+  if (!c) return RD_E_INVAL;
+  if (features != RD_FEATURES_RIDGE && features != RD_FEATURES_EDGE)
+    return fail(c, RD_E_INVAL, "features must be RD_FEATURES_RIDGE or RD_FEATURES_EDGE");
+  if (!(edge_thresh >= 0.0f) || !std::isfinite(edge_thresh)) return fail(c, RD_E_INVAL, "edge_thresh must be >= 0");
+  if (features == RD_FEATURES_EDGE && !c->e_hp) {
+    const size_t px = (size_t)c->max_batch * c->max_H * c->max_W;
+    const size_t rec = (size_t)c->max_batch * c->rl.cap;
+    bool ok = dalloc(&c->e_hp, px) && dalloc(&c->e_L, px) && dalloc(&c->e_g, px) && dalloc(&c->e_X, px) &&
+              dalloc(&c->e_Y, px) && dalloc(&c->e_x64, rec);
+    if (!ok) {
+      cudaGetLastError();
+      return fail(c, RD_E_NOMEM, "edge workspaces: device allocation failed");
+    }
+  }
+  c->features = features;
+  c->edge_thresh = (double)edge_thresh;
+  drop_graph(c);
   return RD_OK;
 }

@@ -62,6 +62,7 @@ struct RidgeList {
   int* count;        // per frame (atomic; may exceed cap)
   int* tile_off;     // per frame and stencil tile: first record
   int* tile_cnt;     // per frame and stencil tile: record count
+  double2* x64;      // directed-edge records: the exact double direction (null for ridges)
   int cap;
   int n_stx, n_sty;  // stencil tiles per frame
 };
@@ -142,6 +143,22 @@ struct FitArgs {
   int w_int;          // w is an integer: exact integer membership test
   DevStats* stats;
 };
+
+// Directed-edge feature stage (k_edge.cu): exact integer smoothing and
+// first-order Sobel, double-precision magnitude, direction and edge test.
+struct EdgeArgs {
+  const void* frames;
+  int n, H, W;
+  GaussTaps taps;
+  double D64;                 // 128 S^2: (Gx, Gy) = (Gx', Gy') / D
+  double thresh;              // gradient-magnitude threshold
+  uint32_t* hp;               // n * H * W: horizontal pass (exact)
+  unsigned long long* L;      // n * H * W: L' (exact)
+  double *g, *X, *Y;          // n * H * W: |grad| and its unit direction
+  RidgeList rl;
+  DevStats* stats;
+};
+cudaError_t launch_edge(const EdgeArgs& a, int dtype, cudaStream_t st);
 
 // Soft (differentiable) score path: FP64 images and ridge records of a batch
 // of frames, allocated on first use (k_soft.cu).

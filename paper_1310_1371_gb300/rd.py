@@ -79,6 +79,7 @@ def load_library(build: bool = False) -> ctypes.CDLL:
         "rd_debug_capture": (c_int, [c_void_p, c_void_p, c_void_p]),
         "rd_set_timing": (c_int, [c_void_p, c_int]),
         "rd_set_graph": (c_int, [c_void_p, c_int]),
+        "rd_set_features": (c_int, [c_void_p, c_int, c_float]),
         "rd_soft_score": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
                                   c_void_p, c_void_p]),
         "rd_backward": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p,
@@ -352,6 +353,13 @@ class Detector:
         if st not in (RD_OK, RD_E_OVERFLOW):
             raise self._err(st)
         return rings, counts, offs, st
+
+    def set_features(self, features: str = "ridge", edge_thresh: float = 0.0):
+        """rd_set_features: 'ridge' (the method) or 'edge' (directed edges)."""
+        code = {"ridge": 0, "edge": 1}[features]
+        st = self.lib.rd_set_features(self.ctx, code, float(edge_thresh))
+        if st != RD_OK:
+            raise self._err(st)
 
     def set_graph(self, on: bool):
         """rd_set_graph: capture rd_detect into a CUDA graph and replay it."""

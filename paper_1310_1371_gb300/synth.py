@@ -279,3 +279,36 @@ def serve_images(per_class: int, seed: int = 1005, sizes=(256, 512, 1024, 2048),
     for (s, i, _), img in zip(jobs, imgs):
         out[s].append(img)
     return out
+
+
+# Filled discs for the directed-edge variant (features whose edges, not
+# ridges, describe them): a logistic edge of width 1.2 px.
+DISC_SMALL_PARAMS = dict(PLAIN_SMALL_PARAMS, features="edge", edge_thresh=4.0)
+DISC_FULL_PARAMS = dict(PLAIN_FULL_PARAMS, features="edge", edge_thresh=20.0)
+
+
+def _disc(amp, width):
+    return lambda rho, R: amp / (1.0 + np.exp(np.clip((rho - R) / width, -50.0, 50.0)))
+
+
+def disc_small(seed: int = 3001, H: int = 256, W: int = 256, n_discs: int = 8) -> Frame:
+    """u8 frame with non-overlapping filled discs (R ~ U[8, 30], amplitude 120
+    on 40, edge width 1.2 px) and N(0, 8^2) noise."""
+    rng = np.random.default_rng(seed)
+    discs = _nonoverlap(rng, n_discs, 40.0, min(H, W) - 40.0, 8.0, 30.0, 6.0)
+    img = _render(H, W, discs, _disc(120.0, 1.2), 40.0)
+    img += rng.normal(0.0, 8.0, size=img.shape)
+    return Frame(np.clip(np.rint(img), 0, 255).astype(np.uint8), discs, dict(DISC_SMALL_PARAMS))
+
+
+def disc_full(seed: int = 3002, H: int = 1024, W: int = 1024, n_discs: int = 150) -> Frame:
+    """12-bit u16 frame with 150 overlapping filled discs (R ~ U[10, 80],
+    amplitude 600 on 400), Poisson shot noise and N(0, 10^2) read noise."""
+    rng = np.random.default_rng(seed)
+    cx = rng.uniform(0.0, W, size=n_discs)
+    cy = rng.uniform(0.0, H, size=n_discs)
+    R = rng.uniform(10.0, 80.0, size=n_discs)
+    discs = np.stack([cx, cy, R], axis=1)
+    img = _render(H, W, discs, _disc(600.0, 1.2), 400.0)
+    img = rng.poisson(img).astype(np.float64) + rng.normal(0.0, 10.0, size=img.shape)
+    return Frame(np.clip(np.rint(img), 0, 4095).astype(np.uint16), discs, dict(DISC_FULL_PARAMS))
