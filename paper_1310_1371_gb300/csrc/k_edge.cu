@@ -69,8 +69,10 @@ __global__ void k_edge_grad(EdgeArgs a) {
     }
     const double Gx = d_div(__ll2double_rn(gx), a.D64), Gy = d_div(__ll2double_rn(gy), a.D64);
     const double g = d_sqrt(d_add(d_mul(Gx, Gx), d_mul(Gy, Gy)));
+    // the direction is needed only where the pixel can be an edge (|grad|
+    // above the threshold); the magnitude everywhere (bilinear samples)
     double X = 0.0, Y = 0.0;
-    if (g != 0.0) {
+    if (g != 0.0 && g > a.thresh) {
       X = d_div(Gx, g);
       Y = d_div(Gy, g);
       if (X < 0.0 || (X == 0.0 && Y < 0.0)) {
