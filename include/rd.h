@@ -225,10 +225,11 @@ rd_status rd_set_features(rd_ctx* ctx, int features, float edge_thresh);
  * SM's shared memory (Results, "Directed ridge detection & votes
  * collection"; the paper streams whole equi-radius levels instead).  The
  * geometry changes speed only: results are bit-identical for every valid
- * geometry.  tile is 64, 80 or 96; slab_levels is 4 .. 16; 0 in both fields
- * asks for the automatic choice (the autotuner's cached choice for this frame
- * size and radius range if there is one, else tile 96 -- 64 when 96 does not
- * fit the radius range's windows -- and 12 levels). */
+ * geometry.  tile is 64, 80, 96 or 128; slab_levels is 4 .. 16; 0 in both
+ * fields asks for the automatic choice (the autotuner's cached choice for
+ * this frame size and radius range if there is one, else the first of
+ * 128 x 16 levels, 96 x 12 and 64 x 12 whose per-tile storage fits the
+ * radius range's smoothing windows). */
 typedef struct rd_geometry {
   int tile;
   int slab_levels;
@@ -245,9 +246,9 @@ rd_status rd_create_ex(const rd_params* params, int max_H, int max_W, int max_ba
 rd_status rd_get_geometry(const rd_ctx* ctx, rd_geometry* out);
 
 /* Time rd_detect on the caller's n device frames (H x W, dtype, as for
- * rd_detect) for every geometry that fits (tile 64/80/96 x slab 8/12/16),
- * with one warm-up and two timed calls each on stream, and return the
- * fastest in *best.  The choice is also cached for this process under
+ * rd_detect) for every geometry that fits (tile 64/80/96/128 x slab
+ * 8/12/16), with one warm-up and two timed calls each on stream, and return
+ * the fastest in *best.  The choice is also cached for this process under
  * (H, W, r_min, r_max), where rd_create and rd_create_ex with an automatic
  * geometry find it.  Allocates and frees a temporary context per candidate
  * and synchronises stream.  Errors: RD_E_INVAL (as rd_create / rd_detect),

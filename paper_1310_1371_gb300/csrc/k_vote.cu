@@ -286,6 +286,7 @@ __device__ __noinline__ int vote_bins_slow(const VoteArgs& a, size_t fbase, VEnt
 
 struct CastCtx {
   int ox0, oy0, RW, h, T;
+  int eox, eoy;  // origin the bin entries' positions are relative to
   int lxlo, lxn, lylo, lyn;  // the tile region clipped to the image: [lo, lo + n)
   bool owned;
 };
@@ -309,11 +310,11 @@ __device__ __forceinline__ int cast_one(const VoteArgs& a, size_t fbase, const V
   int oy = __float_as_int(fy) - ROUND_MAGIC_BITS;
   if (!(fmaxf(fabsf(dx), fabsf(dy)) < __fsub_rn(0.5f, m))) {
     int oxy[2];
-    nfb += vote_bins_slow(a, fbase, v, ent_lx(v.xy) + c.ox0, ent_ly(v.xy) + c.oy0, rf, oxy);
+    nfb += vote_bins_slow(a, fbase, v, ent_lx(v.xy) + c.eox, ent_ly(v.xy) + c.eoy, rf, oxy);
     ox = oxy[0];
     oy = oxy[1];
   }
-  const int lx = ent_lx(v.xy) + ox, ly = ent_ly(v.xy) + oy;
+  const int lx = ent_lx(v.xy) + c.eox + ox - c.ox0, ly = ent_ly(v.xy) + c.eoy + oy - c.oy0;
   if ((unsigned)(lx - c.lxlo) >= (unsigned)c.lxn || (unsigned)(ly - c.lylo) >= (unsigned)c.lyn) return -1;
   if (c.owned && (unsigned)(lx - c.h) < (unsigned)c.T && (unsigned)(ly - c.h) < (unsigned)c.T) ++nv;
   return ly * c.RW + lx;
@@ -321,7 +322,9 @@ __device__ __forceinline__ int cast_one(const VoteArgs& a, size_t fbase, const V
 
 // Dense per-level storage for one bin (used for bins whose hotspots or
 // peaks exceed the sparse kernel's capacities).
-__device__ __forceinline__ void dense_bin(const VoteArgs& a, int b, unsigned char* smem) {
+// The dense kernel works on tiles of T_dense pixels: the bin's own tile, or
+// (tiles larger than its storage allows) sub-tile `sub` of a 2 x 2 split.
+__device__ __forceinline__ void dense_bin(const VoteArgs& a, int b, int sub, unsigned char* smem) {
   const int cnt_raw = a.bin_cnt[b];
   if (cnt_raw == 0) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -337,11 +340,12 @@ __device__ __forceinline__ void dense_bin(const VoteArgs& a, int b, unsigned cha
   const int cnt = (int)max(0LL, min((long long)cnt_raw, a.pool_cap - off));
   const int4 sl = a.slabs[s];
   const int lo = sl.x, hi = sl.y, h = sl.z;
-  const int T = a.T, RW = T + 2 * h, RW2 = T + 2;
+  const int T = a.T_dense, RW = T + 2 * h, RW2 = T + 2;
   const int H = a.H, W = a.W;
+  const int bx0 = tx * a.T + (sub & 1) * T, by0 = ty * a.T + (sub >> 1) * T;  // the (sub-)tile's first pixel
   const unsigned vthr = (unsigned)a.vote_thresh;
 
-  const VoteSmem L = vote_smem_layout(a.max_rw, T, a.max_qn);
+  const VoteSmem L = vote_smem_layout(a.max_rw_dense, T, a.max_qn);
   int2* sQq = reinterpret_cast<int2*>(smem + L.q);          // (weight, offset) per window tap
   uint32_t* sN = reinterpret_cast<uint32_t*>(smem + L.n);   // 3 slots of RW2^2 smoothed sums
   uint32_t* sA = reinterpret_cast<uint32_t*>(smem + L.a);   // RW^2 vote counts
@@ -384,8 +388,10 @@ __device__ __forceinline__ void dense_bin(const VoteArgs& a, int b, unsigned cha
   }
   const int rounds_extra = max(0, (cnt - ECACHE * VOTE_THREADS + VOTE_THREADS - 1) / VOTE_THREADS);
   CastCtx cc;
-  cc.ox0 = tx * T - h;
-  cc.oy0 = ty * T - h;
+  cc.ox0 = bx0 - h;
+  cc.oy0 = by0 - h;
+  cc.eox = tx * a.T - h;  // the bin's entries are relative to its own region
+  cc.eoy = ty * a.T - h;
   cc.RW = RW;
   cc.h = h;
   cc.T = T;
@@ -473,7 +479,7 @@ __device__ __forceinline__ void dense_bin(const VoteArgs& a, int b, unsigned cha
       unsigned long long own = 0;
       for (int v = 0; v < RW2 * RW2; ++v) {
         const int vyr = v / RW2, vxr = v - vyr * RW2;
-        const int gx = tx * T - 1 + vxr, gy = ty * T - 1 + vyr;
+        const int gx = bx0 - 1 + vxr, gy = by0 - 1 + vyr;
         if (vyr >= 1 && vyr <= T && vxr >= 1 && vxr <= T && gx < W && gy < H &&
             sA[(vyr + h - 1) * RW + (vxr + h - 1)] > vthr)
           ++own;
@@ -501,7 +507,7 @@ __device__ __forceinline__ void dense_bin(const VoteArgs& a, int b, unsigned cha
       } else {
         vyr = k / RW2;
         vxr = k - vyr * RW2;
-        int gx = tx * T - 1 + vxr, gy = ty * T - 1 + vyr;
+        int gx = bx0 - 1 + vxr, gy = by0 - 1 + vyr;
         if (gx < 0 || gx >= W || gy < 0 || gy >= H) continue;
         if (sA[(vyr + h - 1) * RW + (vxr + h - 1)] <= vthr) continue;
       }
@@ -528,7 +534,7 @@ __device__ __forceinline__ void dense_bin(const VoteArgs& a, int b, unsigned cha
     if (a.dbg_acc && f == 0) {
       for (int v = tid; v < T * T; v += VOTE_THREADS) {
         int iy = v / T, ix = v - iy * T;
-        int gx = tx * T + ix, gy = ty * T + iy;
+        int gx = bx0 + ix, gy = by0 + iy;
         if (gx < W && gy < H) {
           a.dbg_acc[((size_t)li * H + gy) * W + gx] = (int32_t)sA[(iy + h) * RW + (ix + h)];
           if (a.dbg_sm) a.dbg_sm[((size_t)li * H + gy) * W + gx] = cur[(iy + 1) * RW2 + ix + 1];
@@ -558,7 +564,7 @@ __device__ __forceinline__ void dense_bin(const VoteArgs& a, int b, unsigned cha
           ix = (v & 0xff) - 1;
           if (iy < 0 || iy >= T || ix < 0 || ix >= T) continue;
         }
-        int gx = tx * T + ix, gy = ty * T + iy;
+        int gx = bx0 + ix, gy = by0 + iy;
         if (gx >= W || gy >= H) continue;
         int c = (iy + 1) * RW2 + ix + 1;
         unsigned long long nv0 = Nmid[c];
@@ -613,7 +619,8 @@ __global__ void __launch_bounds__(VOTE_THREADS, 2) k_vote_dense(VoteArgs a) {
   const int n = min(*a.fb_count, a.fb_cap);
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
     __syncthreads();  // the previous bin's readers are done with shared memory
-    dense_bin(a, a.fb_list[i], smem);
+    const int item = a.fb_list[i];
+    dense_bin(a, item >> 2, item & 3, smem);
   }
 }
 
@@ -913,8 +920,10 @@ __device__ __forceinline__ void vote_bin_sparse(const VoteArgs& a, const int b, 
   __syncthreads();
   if (s_abort) {
     if (tid == 0) {
-      const int k = atomicAdd(a.fb_count, 1);
-      if (k < a.fb_cap) a.fb_list[k] = b;
+      const int ns = a.T_dense < a.T ? 4 : 1;
+      const int k = atomicAdd(a.fb_count, ns);
+      for (int j = 0; j < ns; ++j)
+        if (k + j < a.fb_cap) a.fb_list[k + j] = b * 4 + j;
     }
     return;
   }
@@ -955,6 +964,8 @@ cudaError_t launch_bins(const BinArgs& a, int n_sm, cudaStream_t st, long long n
     k_bin<false, ACC_T><<<grid, 256, 0, st>>>(a);
   else if (a.T == ACC_T_MID)
     k_bin<false, ACC_T_MID><<<grid, 256, 0, st>>>(a);
+  else if (a.T == ACC_T_LARGE)
+    k_bin<false, ACC_T_LARGE><<<grid, 256, 0, st>>>(a);
   else
     k_bin<false, ACC_T_SMALL><<<grid, 256, 0, st>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -967,6 +978,8 @@ cudaError_t launch_bins(const BinArgs& a, int n_sm, cudaStream_t st, long long n
     k_bin<true, ACC_T><<<grid, 256, 0, st>>>(a);
   else if (a.T == ACC_T_MID)
     k_bin<true, ACC_T_MID><<<grid, 256, 0, st>>>(a);
+  else if (a.T == ACC_T_LARGE)
+    k_bin<true, ACC_T_LARGE><<<grid, 256, 0, st>>>(a);
   else
     k_bin<true, ACC_T_SMALL><<<grid, 256, 0, st>>>(a);
   return cudaGetLastError();
@@ -1025,7 +1038,7 @@ cudaError_t launch_vote(const VoteArgs& a, long long n_bins, cudaStream_t st) {
   k_vote<<<grid, VOTE_THREADS, sm, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  size_t smd = vote_smem_bytes(a.max_rw, a.T, a.max_qn);
+  size_t smd = vote_smem_bytes(a.max_rw_dense, a.T_dense, a.max_qn);
   cudaFuncSetAttribute(k_vote_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smd);
   k_vote_dense<<<(unsigned)a.fb_grid, VOTE_THREADS, smd, st>>>(a);
   return cudaGetLastError();

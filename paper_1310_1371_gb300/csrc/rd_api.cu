@@ -38,7 +38,8 @@ struct rd_ctx {
   double D64;
   float invD;
   int n_levels, n_slabs, max_rw, max_qn;
-  int T;  // accumulator tile edge: 64, 80 or 96
+  int T;  // accumulator tile edge: 64, 80, 96 or 128
+  int T_dense, max_rw_dense;  // the dense fallback kernel's tile edge and window
   int S;  // peak levels per r-slab
   std::vector<int4> h_slabs;
   // device buffers
@@ -243,10 +244,10 @@ extern "C" rd_status rd_create_ex(const rd_params* params, int max_H, int max_W,
   rd_geometry geo{0, 0};
   if (geometry) geo = *geometry;
   const bool automatic = geo.tile == 0 && geo.slab_levels == 0;
-  if (!automatic && ((geo.tile != ACC_T && geo.tile != ACC_T_MID && geo.tile != ACC_T_SMALL) ||
+  if (!automatic && ((geo.tile != ACC_T_LARGE && geo.tile != ACC_T && geo.tile != ACC_T_MID && geo.tile != ACC_T_SMALL) ||
                      geo.slab_levels < 4 || geo.slab_levels > MAX_SLAB_LEVELS))
-    return fail(nullptr, RD_E_INVAL, "geometry: tile must be 64, 80 or 96 and slab_levels 4 .. 16 (or both 0)");
-  if (automatic && !tuned_geometry(params, max_H, max_W, &geo)) geo = rd_geometry{0, SLAB_LEVELS};
+    return fail(nullptr, RD_E_INVAL, "geometry: tile must be 64, 80, 96 or 128 and slab_levels 4 .. 16 (or both 0)");
+  if (automatic && !tuned_geometry(params, max_H, max_W, &geo)) geo = rd_geometry{0, 0};
   const int R = gaussian_radius(params->sigma);
   if (max_H < R + 4 || max_W < R + 4 || max_H < 12 || max_W < 12 || max_H > 65535 || max_W > 65535)
     return fail(nullptr, RD_E_INVAL, "frame size must be at least max(12, ceil(4 sigma) + 4) and at most 65535");
@@ -287,6 +288,36 @@ extern "C" rd_status rd_create_ex(const rd_params* params, int max_H, int max_W,
     h_nthr[li] = (unsigned long long)peak_threshold_impl(params->peak_frac, r);
     c->max_qn = std::max(c->max_qn, nq + (nq & 1));
   }
+  // Automatic geometry: the first of 128/16, 96/12 and 64/12 whose storage
+  // fits -- for 128 the sparse kernel at three CTAs per SM; always the dense
+  // fallback's per-tile storage on one SM (it splits 128-pixel tiles into
+  // four 64-pixel ones).  Larger tiles cast fewer halo votes per owned voxel
+  // and deeper slabs recompute fewer boundary levels.
+  auto dense_tile = [](int T) { return T == ACC_T_LARGE ? ACC_T_SMALL : T; };
+  auto halo_of = [&](int S) {
+    int mh = 0;
+    for (int lo = params->r_min; lo <= params->r_max; lo += S) {
+      const int hi = std::min(lo + S - 1, params->r_max);
+      for (int r = lo - 1; r <= hi + 1; ++r) mh = std::max(mh, h_qrad[r - lv0] + 1);
+    }
+    return mh;
+  };
+  int qp_need = 4;
+  for (int li = 0; li < c->n_levels; ++li) qp_need = std::max(qp_need, ((2 * h_qrad[li] + 1) * (2 * h_qrad[li] + 1) + 3) & ~3);
+  auto fits = [&](int T, int S, bool three_per_sm) {
+    const int mh = halo_of(S), Td = dense_tile(T);
+    const size_t sp = sparse_smem_bytes(T + 2 * mh, qp_need);
+    return vote_smem_bytes(Td + 2 * mh, Td, c->max_qn) <= 227 * 1024 && sp <= 227 * 1024 &&
+           (!three_per_sm || 3 * (sp + 1024) <= 228 * 1024);
+  };
+  if (geo.tile == 0) {
+    if (fits(ACC_T_LARGE, MAX_SLAB_LEVELS, true))
+      geo = rd_geometry{ACC_T_LARGE, MAX_SLAB_LEVELS};
+    else if (fits(ACC_T, SLAB_LEVELS, false))
+      geo = rd_geometry{ACC_T, SLAB_LEVELS};
+    else
+      geo = rd_geometry{ACC_T_SMALL, SLAB_LEVELS};
+  }
   // r-slabs of S peak levels; halo = 1 + the largest R_s of the slab's voting levels
   c->S = geo.slab_levels;
   int max_h = 0;
@@ -299,11 +330,10 @@ extern "C" rd_status rd_create_ex(const rd_params* params, int max_H, int max_W,
     max_h = std::max(max_h, h);
   }
   c->n_slabs = (int)c->h_slabs.size();
-  // Automatic tile: the larger tile casts fewer halo votes per owned voxel;
-  // it is taken when the dense kernel's per-tile storage still fits one SM.
   c->T = geo.tile;
-  if (c->T == 0) c->T = vote_smem_bytes(ACC_T + 2 * max_h, ACC_T, c->max_qn) > 227 * 1024 ? ACC_T_SMALL : ACC_T;
+  c->T_dense = dense_tile(c->T);
   c->max_rw = c->T + 2 * max_h;
+  c->max_rw_dense = c->T_dense + 2 * max_h;
   // per slab: (weight, offset) of every tap of its voting levels; offsets are
   // relative to the window centre in the slab's shared-memory layout
   std::vector<int> h_qqoff((size_t)c->n_slabs * (c->S + 2), 0);
@@ -312,13 +342,14 @@ extern "C" rd_status rd_create_ex(const rd_params* params, int max_H, int max_W,
   std::vector<uint32_t> h_qptab;
   for (int si = 0; si < c->n_slabs; ++si) {
     const int4 sl = c->h_slabs[si];
-    const int RW = c->T + 2 * sl.z;
+    const int RW = c->T + 2 * sl.z;         // the sparse kernel's slab row
+    const int RWd = c->T_dense + 2 * sl.z;  // the dense kernel's slab row
     for (int r = sl.x - 1; r <= sl.y + 1; ++r) {
       const int li = r - lv0, Rs = h_qrad[li], Wq = 2 * Rs + 1;
       h_qqoff[(size_t)si * (c->S + 2) + (r - sl.x + 1)] = (int)h_qqtab.size();
       const int32_t* q = h_qtab.data() + h_qoff[li];
       for (int dy = 0; dy < Wq; ++dy)
-        for (int dx = 0; dx < Wq; ++dx) h_qqtab.push_back(make_int2(q[dy * Wq + dx], (dy - Rs) * RW + (dx - Rs)));
+        for (int dx = 0; dx < Wq; ++dx) h_qqtab.push_back(make_int2(q[dy * Wq + dx], (dy - Rs) * RWd + (dx - Rs)));
       if (h_qqtab.size() & 1) h_qqtab.push_back(make_int2(0, 0));  // even count: 16-byte tap pairs
       // packed taps for the sparse kernel: weight << 15 | (offset & 0x7fff),
       // padded with zero-weight taps to a multiple of four
@@ -332,7 +363,7 @@ extern "C" rd_status rd_create_ex(const rd_params* params, int max_H, int max_W,
       c->max_qp = std::max(c->max_qp, (Wq * Wq + 3) & ~3);
     }
   }
-  if (vote_smem_bytes(c->max_rw, c->T, c->max_qn) > 227 * 1024 ||
+  if (vote_smem_bytes(c->max_rw_dense, c->T_dense, c->max_qn) > 227 * 1024 ||
       sparse_smem_bytes(c->max_rw, c->max_qp) > 227 * 1024 || c->max_rw * c->max_rw > 65535 * 2) {
     delete c;
     return fail(nullptr, RD_E_INVAL, "radius range and geometry need more shared memory than one SM has");
@@ -346,14 +377,14 @@ extern "C" rd_status rd_create_ex(const rd_params* params, int max_H, int max_W,
   const size_t nrec = (size_t)c->rl.cap * max_batch;
   c->n_bins_max = (long long)max_batch * n_atx * n_aty * c->n_slabs;
   c->pool_cap = std::min<long long>((long long)max_batch * max_H * max_W * 3, (1LL << 31) - 1);
-  if (c->n_bins_max > INT_MAX) {
+  if (c->n_bins_max > INT_MAX / 4) {
     delete c;
     return fail(nullptr, RD_E_INVAL, "too many accumulator bins (frames x tiles x slabs > 2^31): lower max_batch");
   }
   bool ok = dalloc(&c->slabs, c->n_slabs) && dalloc(&c->q_rad, c->n_levels) &&
             dalloc(&c->qq_off, h_qqoff.size()) && dalloc(&c->qq_tab, h_qqtab.size()) &&
             dalloc(&c->qp_off, h_qpoff.size()) && dalloc(&c->qp_tab, h_qptab.size()) &&
-            dalloc(&c->fb_list, c->n_bins_max) && dalloc(&c->fb_count, 1) && dalloc(&c->queue, c->n_bins_max) &&
+            dalloc(&c->fb_list, 4 * c->n_bins_max) && dalloc(&c->fb_count, 1) && dalloc(&c->queue, c->n_bins_max) &&
             dalloc(&c->queue_ctr, 2) &&
             dalloc(&c->nthr, c->n_levels) && dalloc(&c->rl.xy, nrec) &&
             dalloc(&c->rl.dir, nrec) && dalloc(&c->rl.kvote, nrec) && dalloc(&c->rl.hess, 3 * nrec) &&
@@ -527,13 +558,15 @@ static rd_status detect_enqueue(rd_ctx* c, const void* frames_dev, int n, int H,
   va.dbg_acc = c->dbg_acc;
   va.dbg_sm = c->dbg_sm;
   va.max_rw = c->max_rw;
+  va.T_dense = c->T_dense;
+  va.max_rw_dense = c->max_rw_dense;
   va.max_qn = c->max_qn;
   va.max_qp = c->max_qp;
   va.qp_off = c->qp_off;
   va.qp_tab = c->qp_tab;
   va.fb_list = c->fb_list;
   va.fb_count = c->fb_count;
-  va.fb_cap = (int)n_bins;
+  va.fb_cap = (int)(4 * n_bins);
   va.fb_grid = 2 * c->n_sm;
   va.queue = c->queue;
   va.n_queue = c->queue_ctr;
@@ -775,9 +808,9 @@ extern "C" rd_status rd_autotune(const rd_params* params, const void* frames_dev
   rd_geometry bg{0, 0};
   rd_status last = RD_E_NOMEM;
   std::string last_msg = "no candidate geometry could allocate its workspaces";
-  const int tiles[3] = {ACC_T_SMALL, ACC_T_MID, ACC_T};
+  const int tiles[4] = {ACC_T_SMALL, ACC_T_MID, ACC_T, ACC_T_LARGE};
   const int slabs[3] = {8, 12, 16};
-  for (int ti = 0; ti < 3 && res == RD_OK; ++ti)
+  for (int ti = 0; ti < 4 && res == RD_OK; ++ti)
     for (int si = 0; si < 3 && res == RD_OK; ++si) {
       const rd_geometry g{tiles[ti], slabs[si]};
       rd_ctx* c = nullptr;

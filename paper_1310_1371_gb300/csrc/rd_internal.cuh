@@ -27,9 +27,10 @@ constexpr int MAX_RG = 16;         // Gaussian half-width ceil(4 sigma), sigma <
 constexpr int ST_TW = 32;          // stencil tile (output pixels)
 constexpr int ST_TH = 32;
 constexpr int ST_THREADS = 256;
-constexpr int ACC_T = 96;          // default accumulator tile edge
-constexpr int ACC_T_MID = 80;      // the other supported tile edges
-constexpr int ACC_T_SMALL = 64;    // (64 when the dense kernel needs the room at large r_max)
+constexpr int ACC_T_LARGE = 128;   // supported accumulator tile edges (the dense fallback
+constexpr int ACC_T = 96;          // kernel splits 128-pixel tiles into four 64-pixel ones)
+constexpr int ACC_T_MID = 80;
+constexpr int ACC_T_SMALL = 64;
 constexpr int VOTE_THREADS = 256;
 constexpr int MAX_RS = 40;         // level smoothing half-width ceil(3 sigma(r))
 constexpr int SLAB_LEVELS = 12;    // default peak levels per r-slab
@@ -128,6 +129,7 @@ struct VoteArgs {
   int32_t* dbg_acc;          // optional [levels][H][W] capture of frame 0
   uint32_t* dbg_sm;
   int max_rw, max_qn, max_qp;
+  int T_dense, max_rw_dense;  // tile edge and window of the dense fallback kernel
 };
 
 struct FitArgs {

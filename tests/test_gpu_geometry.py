@@ -37,7 +37,7 @@ def same(a, b):
             assert np.array_equal(x[k], y[k]), k
 
 
-@pytest.mark.parametrize("geometry", [(64, 8), (64, 4), (80, 12), (96, 12), (96, 16)])
+@pytest.mark.parametrize("geometry", [(64, 8), (64, 4), (80, 12), (96, 12), (96, 16), (128, 16), (128, 8)])
 def test_geometry_does_not_change_results(torch, geometry):
     frames = [synth.plain_small(seed=s).image for s in (51, 52)]
     params = synth.PLAIN_SMALL_PARAMS
@@ -58,7 +58,7 @@ def test_ragged_frame_every_geometry(torch):
     f = synth.plain_small(seed=53, H=203, W=341, n_rings=10)
     params = synth.PLAIN_SMALL_PARAMS
     base, bstats, _ = run(torch, [f.image], params, (96, 12))
-    for geometry in [(64, 8), (80, 16), (64, 5)]:
+    for geometry in [(64, 8), (80, 16), (64, 5), (128, 16)]:
         rings, stats, _ = run(torch, [f.image], params, geometry)
         same(rings, base)
         assert stats.votes == bstats.votes and stats.hotspots == bstats.hotspots
