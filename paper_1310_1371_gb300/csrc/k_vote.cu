@@ -633,6 +633,7 @@ __global__ void __launch_bounds__(VOTE_THREADS, 2) k_vote_dense(VoteArgs a) {
 // area is kept per level and four CTAs fit on an SM.  A bin whose hotspots or
 // peaks exceed these capacities emits nothing here and is handed to
 // k_vote_dense, which computes the same result with dense per-level storage.
+constexpr int SP_THREADS = 320;  // 10 warps: three CTAs per SM at 64 registers use 61440 of 65536
 constexpr int SP_HOT = 256;     // hotspots per level
 constexpr int SP_HASH = 512;    // hash slots per level (power of two, > 2 SP_HOT)
 constexpr int SP_PEAKS = 64;    // peaks buffered per CTA
@@ -672,7 +673,7 @@ __device__ __forceinline__ void vote_bin_sparse(const VoteArgs& a, const int b, 
   const int cnt_raw = a.bin_cnt[b];
   if (cnt_raw == 0) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int NW = VOTE_THREADS / 32;
+  const int NW = SP_THREADS / 32;
   int t = b;
   const int s = t % a.n_slabs;
   t /= a.n_slabs;
@@ -710,9 +711,9 @@ __device__ __forceinline__ void vote_bin_sparse(const VoteArgs& a, const int b, 
   if (cnt < cnt_raw && tid == 0) atomicOr(&a.stats->overflow, 2);
   {
     uint4* w4 = reinterpret_cast<uint4*>(sAw);
-    for (int i = tid; i < nA4; i += VOTE_THREADS) w4[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < nA4; i += SP_THREADS) w4[i] = make_uint4(0, 0, 0, 0);
   }
-  for (int i = tid; i < 4 * SP_HASH; i += VOTE_THREADS) sHash[i] = SP_EMPTY;
+  for (int i = tid; i < 4 * SP_HASH; i += SP_THREADS) sHash[i] = SP_EMPTY;
   if (tid == 0) {
     for (int k = 0; k < 4; ++k) s_nhot[k] = 0;
     s_npk = 0;
@@ -731,7 +732,7 @@ __device__ __forceinline__ void vote_bin_sparse(const VoteArgs& a, const int b, 
   unsigned t_votes = 0, t_fb = 0, t_hot = 0, t_macs = 0;
   const size_t fbase = (size_t)f * a.rl.cap;
   const int lv0 = a.r_min - 1;
-  const int rounds = (cnt + VOTE_THREADS - 1) / VOTE_THREADS;
+  const int rounds = (cnt + SP_THREADS - 1) / SP_THREADS;
   const uint4* __restrict__ bin = a.pool + off;  // read-only for the whole kernel
   __syncthreads();
 
@@ -742,7 +743,7 @@ __device__ __forceinline__ void vote_bin_sparse(const VoteArgs& a, const int b, 
     const int nq4 = (nq + 3) >> 2;  // packed taps in groups of four (tables padded)
     const int lst = r & 3;
     const uint4* gq = reinterpret_cast<const uint4*>(a.qp_tab + s_qpo[r - lo + 1]);
-    for (int i = tid; i < nq4; i += VOTE_THREADS) cp_async16(&sQ[4 * i], &gq[i]);
+    for (int i = tid; i < nq4; i += SP_THREADS) cp_async16(&sQ[4 * i], &gq[i]);
     asm volatile("cp.async.commit_group;\n" ::);
 
     // ---- phase 1: votes of level r; a voxel whose count passes the integer
@@ -755,9 +756,9 @@ __device__ __forceinline__ void vote_bin_sparse(const VoteArgs& a, const int b, 
     uint4 En = make_uint4(0u, 0u, 0u, 0u);  // next round's entry, loaded one round ahead
     if (tid < cnt) En = __ldg(&bin[tid]);
     for (int j = 0; j < rounds; ++j) {
-      const int e = j * VOTE_THREADS + tid;
+      const int e = j * SP_THREADS + tid;
       const uint4 E = En;
-      if (e + VOTE_THREADS < cnt) En = __ldg(&bin[e + VOTE_THREADS]);
+      if (e + SP_THREADS < cnt) En = __ldg(&bin[e + SP_THREADS]);
       if (e >= cnt) continue;
       const float tx_ = __fmul_rn(rf, __uint_as_float(E.y)), ty_ = __fmul_rn(rf, __uint_as_float(E.z));
       const float fx = __fadd_rn(tx_, ROUND_MAGIC), fy = __fadd_rn(ty_, ROUND_MAGIC);
@@ -805,7 +806,7 @@ __device__ __forceinline__ void vote_bin_sparse(const VoteArgs& a, const int b, 
     const int nhot = s_nhot[lst];
     {
       unsigned own = 0;
-      for (int k = tid; k < nhot; k += VOTE_THREADS) {
+      for (int k = tid; k < nhot; k += SP_THREADS) {
         const uint32_t key = sCoord[lst * SP_HOT + k];
         uint32_t hh = sp_hash(key);
         for (int p = 0; p < SP_HASH; ++p) {
@@ -849,13 +850,13 @@ __device__ __forceinline__ void vote_bin_sparse(const VoteArgs& a, const int b, 
     __syncthreads();
 
     if (a.dbg_acc && f == 0) {
-      for (int v = tid; v < T * T; v += VOTE_THREADS) {
+      for (int v = tid; v < T * T; v += SP_THREADS) {
         const int iy = v / T, ix = v - iy * T;
         const int gx = tx * T + ix, gy = ty * T + iy;
         if (gx < W && gy < H) a.dbg_acc[((size_t)li * H + gy) * W + gx] = (int32_t)sA16[(iy + h) * RW + (ix + h)];
       }
       if (a.dbg_sm) {
-        for (int k = tid; k < nhot; k += VOTE_THREADS) {
+        for (int k = tid; k < nhot; k += SP_THREADS) {
           const uint32_t key = sCoord[lst * SP_HOT + k];
           const int iy = (int)(key >> 8) - 1, ix = (int)(key & 0xffu) - 1;
           const int gx = tx * T + ix, gy = ty * T + iy;
@@ -873,7 +874,7 @@ __device__ __forceinline__ void vote_bin_sparse(const VoteArgs& a, const int b, 
       const int pl = rp & 3;
       const int n = s_nhot[pl];
       const unsigned long long thr = s_thr[rp - lo + 1];
-      for (int k = tid; k < n; k += VOTE_THREADS) {
+      for (int k = tid; k < n; k += SP_THREADS) {
         const uint32_t key = sCoord[pl * SP_HOT + k];
         const int vyr = (int)(key >> 8), vxr = (int)(key & 0xffu);
         const int iy = vyr - 1, ix = vxr - 1;
@@ -910,9 +911,9 @@ __device__ __forceinline__ void vote_bin_sparse(const VoteArgs& a, const int b, 
     }
     {
       uint4* w4 = reinterpret_cast<uint4*>(sAw);
-      for (int i = tid; i < nA4; i += VOTE_THREADS) w4[i] = make_uint4(0, 0, 0, 0);
+      for (int i = tid; i < nA4; i += SP_THREADS) w4[i] = make_uint4(0, 0, 0, 0);
       uint32_t* nt = sHash + ((r + 1) & 3) * SP_HASH;  // level r - 3's table, reused by level r + 1
-      for (int i = tid; i < SP_HASH; i += VOTE_THREADS) nt[i] = SP_EMPTY;
+      for (int i = tid; i < SP_HASH; i += SP_THREADS) nt[i] = SP_EMPTY;
     }
     if (tid == 0) s_nhot[(r + 1) & 3] = 0;
     __syncthreads();
@@ -939,7 +940,7 @@ __device__ __forceinline__ void vote_bin_sparse(const VoteArgs& a, const int b, 
   }
   __syncthreads();
   const int npk = s_npk;
-  for (int k = tid; k < npk; k += VOTE_THREADS) {
+  for (int k = tid; k < npk; k += SP_THREADS) {
     const int kk = atomicAdd(&a.peak_count[f], 1);
     if (kk < a.peak_cap)
       a.peaks[(size_t)f * a.peak_cap + kk] = sPk[k];
@@ -1016,7 +1017,7 @@ __global__ void __launch_bounds__(1024) k_queue(const int* bin_cnt, long long n_
 }
 
 // Persistent K4: a fixed grid of CTAs takes bins from the work queue.
-__global__ void __launch_bounds__(VOTE_THREADS, 4) k_vote(VoteArgs a) {
+__global__ void __launch_bounds__(SP_THREADS, 3) k_vote(VoteArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
   const int n_items = *a.n_queue;
@@ -1034,8 +1035,12 @@ cudaError_t launch_vote(const VoteArgs& a, long long n_bins, cudaStream_t st) {
   size_t sm = sparse_smem_bytes(a.max_rw, a.max_qp);
   cudaFuncSetAttribute(k_vote, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_queue<<<1, 1024, 0, st>>>(a.bin_cnt, n_bins, a.queue, a.n_queue, a.queue_head);
-  const unsigned grid = (unsigned)std::max(1LL, std::min<long long>(n_bins, a.vote_grid));
-  k_vote<<<grid, VOTE_THREADS, sm, st>>>(a);
+  // persistent grid: as many CTAs as are resident at once
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_vote, SP_THREADS, sm) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  const unsigned grid = (unsigned)std::max(1LL, std::min<long long>(n_bins, (long long)a.vote_grid * per_sm));
+  k_vote<<<grid, SP_THREADS, sm, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   size_t smd = vote_smem_bytes(a.max_rw_dense, a.T_dense, a.max_qn);

@@ -571,7 +571,7 @@ static rd_status detect_enqueue(rd_ctx* c, const void* frames_dev, int n, int H,
   va.queue = c->queue;
   va.n_queue = c->queue_ctr;
   va.queue_head = c->queue_ctr + 1;
-  va.vote_grid = 4 * c->n_sm;
+  va.vote_grid = c->n_sm;  // times the resident CTAs per SM (launch_vote)
   va.route_dense = c->route_dense;
   chk(launch_vote(va, n_bins, st));
   mark(4);

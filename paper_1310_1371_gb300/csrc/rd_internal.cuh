@@ -114,7 +114,7 @@ struct VoteArgs {
   int* queue;                // K4 work queue: non-empty bins, largest first
   int* n_queue;              // its length
   int* queue_head;           // next item to take
-  int vote_grid;             // CTAs of the persistent K4 grid
+  int vote_grid;             // SMs; the persistent K4 grid is this times the resident CTAs per SM
   int* fb_list;              // bins handed to the dense kernel (sparse capacities exceeded)
   int* fb_count;
   int fb_cap, fb_grid;
