@@ -289,8 +289,8 @@ int       rd_get_timing(rd_ctx* ctx, float* ms, int cap);
  * dir[2i], dir[2i+1] = X-, Y- (float, canonical sign); hess[3i..3i+2] = the
  * exact integer Hessian (Hxx', Hyy', Hxy') = 64 S^2 (Lxx, Lyy, Lxy).  Any
  * pointer may be NULL.  Returns the number of ridge pixels of frame f (which
- * may exceed cap), or -1 on error.  Order: by stencil tile, row-major inside
- * each tile.
+ * may exceed cap), or -1 on error.  Order: by 32 x 32 stencil tile; the
+ * order inside a tile is unspecified.
  * rd_debug_capture makes the next rd_detect write frame 0's raw accumulator
  * (acc_dev, int32) and smoothed accumulator (sm_dev, uint32) for every voting
  * level r_min-1 .. r_max+1 as [level][H][W] device arrays (either may be

@@ -288,24 +288,33 @@ __global__ void __launch_bounds__(ST_THREADS) k_stencil_ridge(StencilArgs a) {
   }
   if (nfb) atomicAdd(&a.stats->fallbacks, (unsigned long long)nfb);
 
-  // ---- compaction in row-major order: 4 rounds of 256 pixels
+  // ---- compaction: one block-wide exclusive scan of the per-thread counts;
+  //      a thread's records are contiguous (record order inside a tile is
+  //      immaterial downstream: the fit's annulus sums are exact integers)
   const int lane = tid & 31, warp = tid >> 5;
-  int pos[4];
-  int base = 0;
+  const int mine = (int)flag[0] + (int)flag[1] + (int)flag[2] + (int)flag[3];
+  int incl = mine;
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    unsigned bal = __ballot_sync(0xffffffffu, flag[j]);
-    if (lane == 0) sScan[warp] = __popc(bal);
-    __syncthreads();
-    int wpre = 0, tot = 0;
-    for (int w = 0; w < ST_THREADS / 32; ++w) {
-      int c = sScan[w];
-      wpre += (w < warp) ? c : 0;
-      tot += c;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) sScan[warp] = incl;
+  __syncthreads();
+  int wpre = 0, base = 0;
+  for (int w = 0; w < ST_THREADS / 32; ++w) {
+    const int c = sScan[w];
+    wpre += (w < warp) ? c : 0;
+    base += c;
+  }
+  int pos[4];
+  {
+    int p0 = wpre + incl - mine;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      pos[j] = p0;
+      p0 += flag[j] ? 1 : 0;
     }
-    pos[j] = base + wpre + __popc(bal & ((1u << lane) - 1u));
-    base += tot;
-    __syncthreads();
   }
   const int total = base;
   const int tile = blockIdx.y * a.rl.n_stx + blockIdx.x;
