@@ -203,20 +203,38 @@ def run_ours(args):
     value = B * args.steps * world / (ms / 1e3)
     votes_per_step = stats.votes
 
-    # ---- end to end through rd_detect_host (pinned host frames, host rings)
-    pinned = torch.from_numpy(imgs).pin_memory()
-    host = pinned.numpy()
-    det.detect_host(host)
+    # ---- end to end through rd_detect_host (pinned host frames in, host rings
+    #      out): two callers, each with its own context, stream and pinned
+    #      frames, so that one call's copies overlap the other's kernels, as a
+    #      client streaming batches would
+    import threading
+    det2 = rd.Detector(params, H, W, B)
+    dets = [det, det2]
+    hosts = [torch.from_numpy(imgs).pin_memory().numpy() for _ in range(2)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    for i in range(2):
+        dets[i].detect_host(hosts[i], streams[i])
     torch.cuda.synchronize()
-    e2e_steps = max(3, args.steps // 4)
+    e2e_steps = max(4, args.steps // 4)
+    e2e_steps += e2e_steps % 2
+    d2h_per = [0, 0]
+
+    def caller(i):
+        for _ in range(e2e_steps // 2):
+            rings, counts, offs, stt = dets[i].detect_host(hosts[i], streams[i])
+            d2h_per[i] = 8 * B + 40 * int(counts.sum())
+
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
-    d2h = 0
-    for _ in range(e2e_steps):
-        rings, counts, offs, stt = det.detect_host(host)
-        d2h = 8 * B + 40 * int(counts.sum())
+    workers = [threading.Thread(target=caller, args=(i,)) for i in range(2)]
+    for w in workers:
+        w.start()
+    for w in workers:
+        w.join()
     e2e_s = time.perf_counter() - t0
+    d2h = max(d2h_per)
+    det2.close()
     if dist:
         t = torch.tensor([e2e_s], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -284,7 +302,8 @@ def run_ours(args):
                              "sample": f"{ndone} frames of the workload in {cpu_dt:.1f} s",
                              "mvotes_per_s": cpu_mv},
             "e2e": {"value": e2e_value, "unit": "frames/s", "h2d_bytes_per_step": int(imgs.nbytes),
-                    "d2h_bytes_per_step": int(d2h), "api": "rd_detect_host", "steps": e2e_steps},
+                    "d2h_bytes_per_step": int(d2h), "api": "rd_detect_host", "steps": e2e_steps,
+                    "callers": "2 host threads, each its own context, stream and pinned frames"},
             "gpu_launches": KERNELS_PER_CALL * args.steps,
             "clocks": clocks,
         }
