@@ -36,8 +36,7 @@ KERNELS_PER_CALL = 13   # stencil, refine, bin count, 3 scan, bin fill, queue, v
 STAGES = ["stencil_ridge", "ridge_refine", "vote_bin", "vote_accumulate_peaks", "sort_fit"]
 
 
-def env_rank():
-    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+from paper_1310_1371_gb300.replicas import env_rank, frame_seeds, job_rate, max_over_ranks  # noqa: E402
 
 
 def _one_frame(seed):
@@ -50,7 +49,7 @@ def make_frames(n, rank):
     spawn-started process pool before any CUDA call."""
     import concurrent.futures as cf
     import multiprocessing as mp
-    seeds = [[1002 + 1000 * rank, i] for i in range(n)]
+    seeds = frame_seeds(rank, n)
     workers = max(1, min(16, (os.cpu_count() or 2) - 1))
     with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
         return list(ex.map(_one_frame, seeds))
@@ -195,12 +194,10 @@ def run_ours(args):
         det.detect_async(frames)
         stage_ms += det.timing()
     det.set_timing(False)
+    ms = max_over_ranks(ms, dist, "cuda")
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
-    value = B * args.steps * world / (ms / 1e3)
+    value = job_rate(B * args.steps, world, ms / 1e3)
     votes_per_step = stats.votes
 
     # ---- end to end through rd_detect_host (pinned host frames in, host rings
@@ -235,11 +232,8 @@ def run_ours(args):
     e2e_s = time.perf_counter() - t0
     d2h = max(d2h_per)
     det2.close()
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = B * e2e_steps * world / e2e_s
+    e2e_s = max_over_ranks(e2e_s, dist, "cuda")
+    e2e_value = job_rate(B * e2e_steps, world, e2e_s)
 
     if rank == 0:
         # ---- roofline of the dominant stage ("Kernels and their rooflines")
