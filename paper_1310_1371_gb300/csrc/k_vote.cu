@@ -626,8 +626,9 @@ __global__ void __launch_bounds__(VOTE_THREADS, 2) k_vote_dense(VoteArgs a) {
 
 // ---- K4 (sparse) --------------------------------------------------------------
 // The common path.  Shared memory holds one level of u16 vote counts for the
-// tile plus its smoothing halo, the packed window taps of that level, and,
-// for the last four levels, the hotspot lists with their smoothed sums and a
+// tile plus its smoothing halo, the window taps of that level (by rotation
+// orbits of four equal weights), and, for the last four levels, the hotspot
+// lists with their smoothed sums and a
 // small open-addressing table from voxel to list slot: the paper's
 // registering of modified elements, so that nothing proportional to the tile
 // area is kept per level and four CTAs fit on an SM.  A bin whose hotspots or
@@ -644,7 +645,7 @@ struct SparseSmem {
 };
 __host__ __device__ __forceinline__ SparseSmem sparse_smem_layout(int max_rw, int max_qp) {
   SparseSmem L;
-  L.q = 0;                                                        // u32 packed taps x max_qp
+  L.q = 0;                                                        // u32 x max_qp: centre + tap orbits
   L.a = round16((size_t)max_qp * 4);                              // u16 counts x max_rw^2
   L.hash = L.a + round16((((size_t)max_rw * max_rw + 1) / 2) * 4);  // u32 x 4 x SP_HASH
   L.coord = L.hash + (size_t)4 * SP_HASH * 4;                     // u16 x 4 x SP_HOT
@@ -704,7 +705,7 @@ __device__ __forceinline__ void vote_bin_sparse(const VoteArgs& a, const int b, 
   const int nA4 = (((RW * RW + 1) / 2) + 3) / 4;
   __shared__ int s_nhot[4], s_npk, s_abort;
   __shared__ unsigned s_sum[4];  // votes, fallbacks, owned hotspots, smoothing MACs of this bin
-  // per voting level lo-1 .. hi+1 of the slab: R_s, offset of its packed taps, peak threshold
+  // per voting level lo-1 .. hi+1 of the slab: R_s, offset of its tap orbits, peak threshold
   __shared__ int s_rad[MAX_SLAB_LEVELS + 2], s_qpo[MAX_SLAB_LEVELS + 2];
   __shared__ unsigned long long s_thr[MAX_SLAB_LEVELS + 2];
 
@@ -740,10 +741,10 @@ __device__ __forceinline__ void vote_bin_sparse(const VoteArgs& a, const int b, 
     const int li = r - lv0;
     const int Rs = s_rad[r - lo + 1];
     const int nq = (2 * Rs + 1) * (2 * Rs + 1);
-    const int nq4 = (nq + 3) >> 2;  // packed taps in groups of four (tables padded)
+    const int ng = Rs * (Rs + 1);  // rotation orbits of four taps, after the centre entry
     const int lst = r & 3;
     const uint4* gq = reinterpret_cast<const uint4*>(a.qp_tab + s_qpo[r - lo + 1]);
-    for (int i = tid; i < nq4; i += SP_THREADS) cp_async16(&sQ[4 * i], &gq[i]);
+    for (int i = tid; i <= ng; i += SP_THREADS) cp_async16(&sQ[4 * i], &gq[i]);
     asm volatile("cp.async.commit_group;\n" ::);
 
     // ---- phase 1: votes of level r; a voxel whose count passes the integer
@@ -821,30 +822,49 @@ __device__ __forceinline__ void vote_bin_sparse(const VoteArgs& a, const int b, 
         t_macs += own * (unsigned)nq;
       }
     }
-    const uint4* sQ4 = reinterpret_cast<const uint4*>(sQ);
-    for (int k = warp; k < nhot; k += NW) {
-      const uint32_t key = sCoord[lst * SP_HOT + k];
-      const uint16_t* ctr = sA16 + ((int)(key >> 8) + h - 1) * RW + ((int)(key & 0xffu) + h - 1);
-      unsigned long long acc = 0;
-      for (int q = lane; q < nq4; q += 32) {
-        const uint4 P = sQ4[q];
-        acc += (unsigned long long)(P.x >> 15) * ctr[((int)(P.x << 17)) >> 17];
-        acc += (unsigned long long)(P.y >> 15) * ctr[((int)(P.y << 17)) >> 17];
-        acc += (unsigned long long)(P.z >> 15) * ctr[((int)(P.z << 17)) >> 17];
-        acc += (unsigned long long)(P.w >> 15) * ctr[((int)(P.w << 17)) >> 17];
-      }
-      // Exact warp sum in two 32-bit reductions: a lane holds at most 208 taps
-      // of weight <= 2^16 and count < 2^16, so acc < 2^40 and both the low
-      // 24 bits and acc >> 24 sum over 32 lanes without overflow.
-      const unsigned s_lo = __reduce_add_sync(0xffffffffu, (unsigned)acc & 0xffffffu);
-      const unsigned s_hi = __reduce_add_sync(0xffffffffu, (unsigned)(acc >> 24));
-      acc = (unsigned long long)s_lo + ((unsigned long long)s_hi << 24);
-      if (lane == 0) {
-        if (acc > 0xffffffffULL) {
-          atomicOr(&a.stats->overflow, 16);
-          acc = 0xffffffffULL;
+    // A hotspot takes 8, 16 or 32 lanes, the fewest that hold one orbit
+    // each where the window allows (uniform over the level).
+    {
+      const uint4* sG = reinterpret_cast<const uint4*>(sQ);
+      const int lg = ng <= 8 ? 3 : (ng <= 16 ? 4 : 5);
+      const int L = 1 << lg, per = 32 >> lg;
+      const int sl = lane & (L - 1);
+      for (int kb = warp * per; kb < nhot; kb += NW * per) {
+        const int k = kb + (lane >> lg);
+        unsigned long long acc = 0;
+        if (k < nhot) {
+          const uint32_t key = sCoord[lst * SP_HOT + k];
+          const uint16_t* ctr = sA16 + ((int)(key >> 8) + h - 1) * RW + ((int)(key & 0xffu) + h - 1);
+          if (sl == 0) acc = (unsigned long long)sG[0].z * ctr[0];
+          for (int q = 1 + sl; q <= ng; q += L) {
+            const uint4 G = sG[q];
+            const int o1 = (int)G.x, o2 = (int)G.y;
+            const unsigned c4 = (unsigned)ctr[o1] + (unsigned)ctr[-o1] + (unsigned)ctr[o2] + (unsigned)ctr[-o2];
+            acc += (unsigned long long)G.z * c4;
+          }
         }
-        sVal[lst * SP_HOT + k] = (uint32_t)acc;
+        // Exact sum over the hotspot's lanes in two 32-bit parts: an orbit
+        // adds at most 2^16 x 4 x (2^16 - 1) < 2^34 and the centre < 2^32, so
+        // a lane's acc < 2^50 for any window that fits in shared memory, and
+        // both its low 24 bits and acc >> 24 sum over 32 lanes in 32 bits.
+        unsigned s_lo = (unsigned)acc & 0xffffffu, s_hi = (unsigned)(acc >> 24);
+        if (lg == 5) {
+          s_lo = __reduce_add_sync(0xffffffffu, s_lo);
+          s_hi = __reduce_add_sync(0xffffffffu, s_hi);
+        } else {
+          for (int o = L >> 1; o > 0; o >>= 1) {
+            s_lo += __shfl_xor_sync(0xffffffffu, s_lo, o);
+            s_hi += __shfl_xor_sync(0xffffffffu, s_hi, o);
+          }
+        }
+        if (sl == 0 && k < nhot) {
+          acc = (unsigned long long)s_lo + ((unsigned long long)s_hi << 24);
+          if (acc > 0xffffffffULL) {
+            atomicOr(&a.stats->overflow, 16);
+            acc = 0xffffffffULL;
+          }
+          sVal[lst * SP_HOT + k] = (uint32_t)acc;
+        }
       }
     }
     __syncthreads();

@@ -303,7 +303,7 @@ extern "C" rd_status rd_create_ex(const rd_params* params, int max_H, int max_W,
     return mh;
   };
   int qp_need = 4;
-  for (int li = 0; li < c->n_levels; ++li) qp_need = std::max(qp_need, ((2 * h_qrad[li] + 1) * (2 * h_qrad[li] + 1) + 3) & ~3);
+  for (int li = 0; li < c->n_levels; ++li) qp_need = std::max(qp_need, 4 * (1 + h_qrad[li] * (h_qrad[li] + 1)));
   auto fits = [&](int T, int S, bool three_per_sm) {
     const int mh = halo_of(S), Td = dense_tile(T);
     const size_t sp = sparse_smem_bytes(T + 2 * mh, qp_need);
@@ -351,16 +351,25 @@ extern "C" rd_status rd_create_ex(const rd_params* params, int max_H, int max_W,
       for (int dy = 0; dy < Wq; ++dy)
         for (int dx = 0; dx < Wq; ++dx) h_qqtab.push_back(make_int2(q[dy * Wq + dx], (dy - Rs) * RWd + (dx - Rs)));
       if (h_qqtab.size() & 1) h_qqtab.push_back(make_int2(0, 0));  // even count: 16-byte tap pairs
-      // packed taps for the sparse kernel: weight << 15 | (offset & 0x7fff),
-      // padded with zero-weight taps to a multiple of four
+      // taps for the sparse kernel in rotation orbits: Q depends on
+      // dx^2 + dy^2 only, so the four taps (dx, dy), (-dy, dx), (-dx, -dy),
+      // (dy, -dx) share one weight.  Entry 0 is the centre {0, 0, Q(0,0), 0};
+      // then, for dx in 1..Rs and dy in 0..Rs (one tap of every orbit),
+      // {o1, o2, Q, 0} with o1 = dy RW + dx and o2 = dx RW - dy: the orbit is
+      // at offsets +-o1 and +-o2 from the centre.
       h_qpoff[(size_t)si * (c->S + 2) + (r - sl.x + 1)] = (int)h_qptab.size();
-      for (int dy = 0; dy < Wq; ++dy)
-        for (int dx = 0; dx < Wq; ++dx) {
-          const int off = (dy - Rs) * RW + (dx - Rs);
-          h_qptab.push_back(((uint32_t)q[dy * Wq + dx] << 15) | ((uint32_t)off & 0x7fffu));
+      auto qat = [&](int dx, int dy) { return (uint32_t)q[(dy + Rs) * Wq + (dx + Rs)]; };
+      h_qptab.insert(h_qptab.end(), {0u, 0u, qat(0, 0), 0u});
+      for (int dx = 1; dx <= Rs; ++dx)
+        for (int dy = 0; dy <= Rs; ++dy) {
+          const uint32_t w = qat(dx, dy);
+          if (qat(-dy, dx) != w || qat(-dx, -dy) != w || qat(dy, -dx) != w) {
+            delete c;
+            return fail(nullptr, RD_E_INVAL, "smoothing weights are not invariant under quarter turns");
+          }
+          h_qptab.insert(h_qptab.end(), {(uint32_t)(dy * RW + dx), (uint32_t)(dx * RW - dy), w, 0u});
         }
-      while (h_qptab.size() & 3) h_qptab.push_back(0u);
-      c->max_qp = std::max(c->max_qp, (Wq * Wq + 3) & ~3);
+      c->max_qp = std::max(c->max_qp, 4 * (1 + Rs * (Rs + 1)));
     }
   }
   if (vote_smem_bytes(c->max_rw_dense, c->T_dense, c->max_qn) > 227 * 1024 ||

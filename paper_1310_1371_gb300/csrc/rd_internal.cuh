@@ -110,7 +110,7 @@ struct VoteArgs {
   const int2* qq_tab;        // (weight, slab-relative smem offset) per window tap, row-major (dy, dx)
   const int* qp_off;         // per (slab, level): offset into qp_tab (multiple of 4)
   int slab_stride;           // entries per slab in qq_off / qp_off: slab levels + 2
-  const uint32_t* qp_tab;    // packed taps: weight << 15 | (offset & 0x7fff), padded to 4
+  const uint32_t* qp_tab;    // per level: {0, 0, Q(0,0), 0}, then {o1, o2, Q, 0} per orbit of four taps
   int* queue;                // K4 work queue: non-empty bins, largest first
   int* n_queue;              // its length
   int* queue_head;           // next item to take
