@@ -134,12 +134,16 @@ __device__ __forceinline__ int ridge_fast(const float* sK, const float* sE, int 
 struct StencilSmem {
   size_t l, x, k, scan, total;
 };
+// Row strides of the input tile and of the horizontal pass are odd, so that
+// the lanes of a warp, which take consecutive rows there, hit distinct banks.
+__host__ __device__ __forceinline__ int odd_stride(int w) { return w | 1; }
+
 __host__ __device__ __forceinline__ StencilSmem stencil_smem_layout(int R) {
   const int HALO = R + 3;
-  const size_t IW = ST_TW + 2 * HALO, IH = ST_TH + 2 * HALO;
-  const size_t PW = ST_TW + 6, LH = ST_TH + 6;
+  const size_t IW = odd_stride(ST_TW + 2 * HALO), IH = ST_TH + 2 * HALO;
+  const size_t PW = ST_TW + 6, PWs = odd_stride(ST_TW + 6), LH = ST_TH + 6;
   const size_t HW2 = ST_TW + 2, HH2 = ST_TH + 2;
-  const size_t in_bytes = (IH * IW + IH * PW) * 4, hess_bytes = 3 * HH2 * HW2 * 8;
+  const size_t in_bytes = (IH * IW + IH * PWs) * 4, hess_bytes = 3 * HH2 * HW2 * 8;
   StencilSmem L;
   L.l = 0;
   L.x = LH * PW * 8;
@@ -149,14 +153,16 @@ __host__ __device__ __forceinline__ StencilSmem stencil_smem_layout(int R) {
   return L;
 }
 
-template <typename Tin>
-__global__ void __launch_bounds__(ST_THREADS) k_stencil_ridge(StencilArgs a) {
+// RC > 0: the Gaussian half-width R is the compile-time RC (taps unrolled,
+// two outputs per thread from a register window); RC = 0: R from the taps.
+template <typename Tin, int RC>
+__global__ void __launch_bounds__(ST_THREADS, 4) k_stencil_ridge(StencilArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x;
-  const int R = a.taps.R;
+  const int R = RC > 0 ? RC : a.taps.R;
   const int HALO = R + 3;
-  const int IW = ST_TW + 2 * HALO, IH = ST_TH + 2 * HALO;
-  const int PW = ST_TW + 6, LH = ST_TH + 6;
+  const int IW = odd_stride(ST_TW + 2 * HALO), IH = ST_TH + 2 * HALO;
+  const int PW = ST_TW + 6, PWs = odd_stride(ST_TW + 6), LH = ST_TH + 6;
   const int HW2 = ST_TW + 2, HH2 = ST_TH + 2;
   const int H = a.H, W = a.W;
 
@@ -169,7 +175,7 @@ __global__ void __launch_bounds__(ST_THREADS) k_stencil_ridge(StencilArgs a) {
   long long* sHyy = sHxx + HH2 * HW2;
   long long* sHxy = sHyy + HH2 * HW2;
   uint32_t* sI = reinterpret_cast<uint32_t*>(smem + Ls.x);                     // IH*IW
-  uint32_t* sP = sI + IH * IW;                                                 // IH*PW
+  uint32_t* sP = sI + IH * IW;                                                 // IH*PWs
   float* sK = reinterpret_cast<float*>(smem + Ls.k);                           // HH2*HW2
   float* sE = sK + HH2 * HW2;
   int* sScan = reinterpret_cast<int*>(smem + Ls.scan);                         // 8 warps + 2
@@ -186,11 +192,12 @@ __global__ void __launch_bounds__(ST_THREADS) k_stencil_ridge(StencilArgs a) {
   {
     const int lane = tid & 31, warp = tid >> 5;
     const bool interior = x0 >= HALO && y0 >= HALO && x0 + ST_TW + HALO <= W && y0 + ST_TH + HALO <= H;
+    const int IWn = ST_TW + 2 * HALO;  // columns loaded (IW is the padded stride)
     for (int iy = warp; iy < IH; iy += ST_THREADS / 32) {
       const int gy = interior ? y0 - HALO + iy : reflect101(y0 - HALO + iy, H);
       const Tin* row = img + (size_t)gy * W;
       uint32_t* dst = sI + iy * IW;
-      for (int ix = lane; ix < IW; ix += 32) {
+      for (int ix = lane; ix < IWn; ix += 32) {
         const int gx = interior ? x0 - HALO + ix : reflect101(x0 - HALO + ix, W);
         dst[ix] = (uint32_t)row[gx];
       }
@@ -199,23 +206,67 @@ __global__ void __launch_bounds__(ST_THREADS) k_stencil_ridge(StencilArgs a) {
   __syncthreads();
 
   // ---- B: horizontal Gaussian, exact u32 (sum Q_i I < 2^31)
-  for (int i = tid; i < IH * PW; i += ST_THREADS) {
-    int iy = i / PW, px = i - iy * PW;
-    const uint32_t* row = sI + iy * IW + px;
-    uint32_t acc = (uint32_t)q[R] * row[R];
-    for (int j = 0; j < R; ++j) acc += (uint32_t)q[j] * (row[j] + row[2 * R - j]);
-    sP[i] = acc;
+  if constexpr (RC > 0) {
+    // two adjacent outputs per thread from 2R + 2 inputs; lanes take rows
+    constexpr int NW = 2 * RC + 2;
+    const int NP = PW / 2;
+    for (int i = tid; i < IH * NP; i += ST_THREADS) {
+      const int pp = i / IH, iy = i - pp * IH;
+      const uint32_t* row = sI + iy * IW + 2 * pp;
+      uint32_t w[NW];
+#pragma unroll
+      for (int k = 0; k < NW; ++k) w[k] = row[k];
+      uint32_t acc0 = (uint32_t)a.taps.q[RC] * w[RC], acc1 = (uint32_t)a.taps.q[RC] * w[RC + 1];
+#pragma unroll
+      for (int j = 0; j < RC; ++j) {
+        acc0 += (uint32_t)a.taps.q[j] * (w[j] + w[2 * RC - j]);
+        acc1 += (uint32_t)a.taps.q[j] * (w[j + 1] + w[2 * RC + 1 - j]);
+      }
+      sP[iy * PWs + 2 * pp] = acc0;
+      sP[iy * PWs + 2 * pp + 1] = acc1;
+    }
+  } else {
+    for (int i = tid; i < IH * PW; i += ST_THREADS) {
+      int iy = i / PW, px = i - iy * PW;
+      const uint32_t* row = sI + iy * IW + px;
+      uint32_t acc = (uint32_t)q[R] * row[R];
+      for (int j = 0; j < R; ++j) acc += (uint32_t)q[j] * (row[j] + row[2 * R - j]);
+      sP[iy * PWs + px] = acc;
+    }
   }
   __syncthreads();
 
   // ---- C: vertical Gaussian, exact u64: L' = sum_i sum_j Q_i Q_j I
-  for (int i = tid; i < LH * PW; i += ST_THREADS) {
-    int ly = i / PW, px = i - ly * PW;
-    const uint32_t* col = sP + ly * PW + px;
-    unsigned long long acc = (unsigned long long)(uint32_t)q[R] * col[R * PW];
-    for (int j = 0; j < R; ++j)
-      acc += (unsigned long long)(uint32_t)q[j] * (unsigned long long)(col[j * PW] + col[(2 * R - j) * PW]);
-    sL[i] = acc;
+  //      (a pair Q_j (P_j + P_2R-j) of horizontal sums stays below 2^32)
+  if constexpr (RC > 0) {
+    // two vertically adjacent outputs per thread; lanes take columns
+    constexpr int NW = 2 * RC + 2;
+    const int NL = LH / 2;
+    for (int i = tid; i < NL * PW; i += ST_THREADS) {
+      const int lp = i / PW, px = i - lp * PW;
+      const uint32_t* col = sP + (2 * lp) * PWs + px;
+      uint32_t w[NW];
+#pragma unroll
+      for (int k = 0; k < NW; ++k) w[k] = col[k * PWs];
+      unsigned long long acc0 = (unsigned long long)(uint32_t)a.taps.q[RC] * w[RC];
+      unsigned long long acc1 = (unsigned long long)(uint32_t)a.taps.q[RC] * w[RC + 1];
+#pragma unroll
+      for (int j = 0; j < RC; ++j) {
+        acc0 += (unsigned long long)(uint32_t)a.taps.q[j] * (unsigned long long)(w[j] + w[2 * RC - j]);
+        acc1 += (unsigned long long)(uint32_t)a.taps.q[j] * (unsigned long long)(w[j + 1] + w[2 * RC + 1 - j]);
+      }
+      sL[(2 * lp) * PW + px] = acc0;
+      sL[(2 * lp + 1) * PW + px] = acc1;
+    }
+  } else {
+    for (int i = tid; i < LH * PW; i += ST_THREADS) {
+      int ly = i / PW, px = i - ly * PW;
+      const uint32_t* col = sP + ly * PWs + px;
+      unsigned long long acc = (unsigned long long)(uint32_t)q[R] * col[R * PWs];
+      for (int j = 0; j < R; ++j)
+        acc += (unsigned long long)(uint32_t)q[j] * (unsigned long long)(col[j * PWs] + col[(2 * R - j) * PWs]);
+      sL[i] = acc;
+    }
   }
   __syncthreads();
 
@@ -393,21 +444,25 @@ __global__ void __launch_bounds__(256) k_ridge_refine(RidgeList rl) {
   }
 }
 
-template __global__ void k_stencil_ridge<uint8_t>(StencilArgs);
-template __global__ void k_stencil_ridge<uint16_t>(StencilArgs);
-
 size_t stencil_smem_bytes(int R) { return stencil_smem_layout(R).total; }
+
+template <typename Tin, int RC>
+static void launch_stencil_t(const StencilArgs& a, dim3 grid, size_t sm, cudaStream_t st) {
+  cudaFuncSetAttribute(k_stencil_ridge<Tin, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_stencil_ridge<Tin, RC><<<grid, ST_THREADS, sm, st>>>(a);
+}
+
+// Gaussian half-width compiled in: R = ceil(4 sigma) = 8 for sigma in (1.75, 2]
+constexpr int ST_RC = 8;
 
 cudaError_t launch_stencil(const StencilArgs& a, int dtype, cudaStream_t st) {
   dim3 grid((a.W + ST_TW - 1) / ST_TW, (a.H + ST_TH - 1) / ST_TH, a.n);
   size_t sm = stencil_smem_bytes(a.taps.R);
-  if (dtype == 0) {
-    cudaFuncSetAttribute(k_stencil_ridge<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_stencil_ridge<uint8_t><<<grid, ST_THREADS, sm, st>>>(a);
-  } else {
-    cudaFuncSetAttribute(k_stencil_ridge<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_stencil_ridge<uint16_t><<<grid, ST_THREADS, sm, st>>>(a);
-  }
+  const bool fixed = a.taps.R == ST_RC;
+  if (dtype == 0)
+    fixed ? launch_stencil_t<uint8_t, ST_RC>(a, grid, sm, st) : launch_stencil_t<uint8_t, 0>(a, grid, sm, st);
+  else
+    fixed ? launch_stencil_t<uint16_t, ST_RC>(a, grid, sm, st) : launch_stencil_t<uint16_t, 0>(a, grid, sm, st);
   return cudaGetLastError();
 }
 
