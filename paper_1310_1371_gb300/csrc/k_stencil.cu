@@ -36,10 +36,12 @@ __device__ __forceinline__ void eig32_k(float a, float b, float c, float& k, flo
 
 // Stable FP32 X- (no cancellation: the large component is |hdf| + rad) with a
 // bound eX on each component's distance to the exact direction (same sign).
-// exact_axis: the Hessian's off-diagonal is exactly 0, so X- is exactly an
-// axis in every precision and eX = 0.
-__device__ __forceinline__ bool eig32_dir(float b, float hdf, float rad, float M, bool exact_axis, float& X,
-                                          float& Y, float& eX) {
+// delta bounds the inputs' absolute error (see hess32): v = (b, -w) or
+// (-w, b), w = |hdf| + rad, moves by at most sqrt(1 + (1 + sqrt 2)^2) delta
+// < 2.62 delta, and v / |v| by twice that over |v|.  Returns false where
+// |v| is too small for a bound (the exactly degenerate case among them).
+__device__ __forceinline__ bool eig32_dir(float b, float hdf, float rad, float M, float delta, float& X, float& Y,
+                                          float& eX) {
   float w = fabsf(hdf) + rad;
   float vx, vy;
   if (hdf >= 0.0f) {
@@ -50,28 +52,52 @@ __device__ __forceinline__ bool eig32_dir(float b, float hdf, float rad, float M
     vy = b;
   }
   float nrm = sqrtf(vx * vx + vy * vy);
-  if (!(nrm > 0.0f)) return false;
+  if (!(nrm > 4.0f * delta) || !(nrm > 0.0f)) return false;
   X = vx / nrm;
   Y = vy / nrm;
   if (X < 0.0f || (X == 0.0f && Y < 0.0f)) {
     X = -X;
     Y = -Y;
   }
-  eX = exact_axis ? 0.0f : (M * (16.0f * U32)) / nrm + 4.0f * U32;
+  eX = (M * (16.0f * U32)) / nrm + 4.0f * U32 + 6.0f * delta / (nrm - 3.0f * delta);
   return true;
 }
 
-// Exact (double-precision definition) ridge test of the pixel at Hessian
-// tile coordinates (hy, hx) = image (gy, gx).  Reads exact Hessians of the
-// pixel and of the bilinear corners from shared memory.
-__device__ __noinline__ bool ridge_exact(const long long* sHxx, const long long* sHyy, const long long* sHxy, int stride, int hy,
-                            int hx, int gx, int gy, int H, int W, double D, double tau) {
-  int c = hy * stride + hx;
-  Eig64 e = eigen64(sHxx[c], sHyy[c], sHxy[c], D);
-  if (!(e.k < tau) || e.degenerate) return false;
+// Exact Hessian H' = 64 S^2 (Lxx, Lyy, Lxy) at Hessian-tile coordinates
+// (hy, hx): the 5x5 second-order Sobel stencils of the exact smoothed tile
+// L' (u64, row stride PW), whose rows hy .. hy + 4 and columns hx .. hx + 4
+// it reads.
+__device__ __forceinline__ void hess_exact(const unsigned long long* sL, int PW, int hy, int hx, long long& hxx,
+                                           long long& hyy, long long& hxy) {
+  const long long s5[5] = {1, 4, 6, 4, 1}, d2[5] = {1, 0, -2, 0, 1}, d1[5] = {-1, -2, 0, 2, 1};
+  hxx = hyy = hxy = 0;
+#pragma unroll
+  for (int dy = 0; dy < 5; ++dy) {
+    const long long* row = reinterpret_cast<const long long*>(sL) + (hy + dy) * PW + hx;
+    const long long l0 = row[0], l1 = row[1], l2 = row[2], l3 = row[3], l4 = row[4];
+    const long long sx = l0 + 4 * (l1 + l3) + 6 * l2 + l4;
+    const long long d2x = l0 - 2 * l2 + l4;
+    const long long d1x = (l4 - l0) + 2 * (l3 - l1);
+    hxx += s5[dy] * d2x;
+    hyy += d2[dy] * sx;
+    hxy += d1[dy] * d1x;
+  }
+}
+
+// Pixels per step of the exact test (9 threads each).
+constexpr int FB_CHUNK = ST_THREADS / 9;
+
+// Exact (double-precision definition) ridge test of the pixel (gx, gy) from
+// the exact k- of its 3x3 neighbourhood kn (row-major, centre kn[4]) and its
+// exact X- = (X, Y): k- < tau, then the bilinear samples at p + X- (strict)
+// and p - X- (non-strict); a sample outside the image makes it no ridge.
+__device__ __noinline__ bool ridge_exact_nb(const double* kn, double X, double Y, bool degenerate, int gx, int gy,
+                                            int H, int W, double tau) {
+  const double k = kn[4];
+  if (!(k < tau) || degenerate) return false;
   for (int s = 0; s < 2; ++s) {
-    double qx = s == 0 ? d_add((double)gx, e.X) : d_sub((double)gx, e.X);
-    double qy = s == 0 ? d_add((double)gy, e.Y) : d_sub((double)gy, e.Y);
+    double qx = s == 0 ? d_add((double)gx, X) : d_sub((double)gx, X);
+    double qy = s == 0 ? d_add((double)gy, Y) : d_sub((double)gy, Y);
     if (qx < 0.0 || qx > (double)(W - 1) || qy < 0.0 || qy > (double)(H - 1)) return false;
     double x0f = floor(qx), y0f = floor(qy);
     double fx = d_sub(qx, x0f), fy = d_sub(qy, y0f);
@@ -79,14 +105,10 @@ __device__ __noinline__ bool ridge_exact(const long long* sHxx, const long long*
     int cx1 = min(cx0 + 1, W - 1), cy1 = min(cy0 + 1, H - 1);
     if (fx == 0.0) cx1 = cx0;  // zero-weight corner: any finite value gives the same sum
     if (fy == 0.0) cy1 = cy0;
-    int lx0 = hx + (cx0 - gx), lx1 = hx + (cx1 - gx), ly0 = hy + (cy0 - gy), ly1 = hy + (cy1 - gy);
-    int i00 = ly0 * stride + lx0, i01 = ly0 * stride + lx1, i10 = ly1 * stride + lx0, i11 = ly1 * stride + lx1;
-    double k00 = eigen64(sHxx[i00], sHyy[i00], sHxy[i00], D).k;
-    double k01 = eigen64(sHxx[i01], sHyy[i01], sHxy[i01], D).k;
-    double k10 = eigen64(sHxx[i10], sHyy[i10], sHxy[i10], D).k;
-    double k11 = eigen64(sHxx[i11], sHyy[i11], sHxy[i11], D).k;
-    double kt = bilinear64(fx, fy, k00, k01, k10, k11);
-    if (s == 0 ? !(e.k < kt) : !(e.k <= kt)) return false;
+    // |X|, |Y| <= 1, so every corner is within one pixel of (gx, gy)
+    const int i0 = (cy0 - gy + 1) * 3, i1 = (cy1 - gy + 1) * 3, j0 = cx0 - gx + 1, j1 = cx1 - gx + 1;
+    double kt = bilinear64(fx, fy, kn[i0 + j0], kn[i0 + j1], kn[i1 + j0], kn[i1 + j1]);
+    if (s == 0 ? !(k < kt) : !(k <= kt)) return false;
   }
   return true;
 }
@@ -127,12 +149,30 @@ __device__ __forceinline__ int ridge_fast(const float* sK, const float* sE, int 
   return verdict;
 }
 
-// Shared-memory layout of K1 (byte offsets, all 8-byte aligned): the
-// smoothed tile L' (u64), then one region holding first the input tile and
-// the horizontal pass (u32) and later the exact Hessians (i64), then k- and
-// its error bound (f32), then the compaction scratch.
+// FP32 Hessian entries (a, b, c) = fl(H) x fl(1/D) at Hessian-tile index c0
+// from the row filters (row stride st): the column filters s, d2 and d1
+// over rows c0, c0 + st, ..., c0 + 4 st, each operation correctly rounded in
+// the written order (no contraction).
+__device__ __forceinline__ void hess32(const float* Rs, const float* Rd2, const float* Rd1, int st, int c0, float invD,
+                                       float& fa, float& fb, float& fc) {
+  const float x0 = Rd2[c0], x1 = Rd2[c0 + st], x2 = Rd2[c0 + 2 * st], x3 = Rd2[c0 + 3 * st], x4 = Rd2[c0 + 4 * st];
+  const float hxx = __fmaf_rn(6.0f, x2, __fmaf_rn(4.0f, __fadd_rn(x1, x3), __fadd_rn(x0, x4)));
+  const float y0 = Rs[c0], y2 = Rs[c0 + 2 * st], y4 = Rs[c0 + 4 * st];
+  const float hyy = __fmaf_rn(-2.0f, y2, __fadd_rn(y0, y4));
+  const float z0 = Rd1[c0], z1 = Rd1[c0 + st], z3 = Rd1[c0 + 3 * st], z4 = Rd1[c0 + 4 * st];
+  const float hxy = __fmaf_rn(2.0f, __fsub_rn(z3, z1), __fsub_rn(z4, z0));
+  fa = __fmul_rn(hxx, invD);
+  fb = __fmul_rn(hxy, invD);
+  fc = __fmul_rn(hyy, invD);
+}
+
+// Shared-memory layout of K1 (byte offsets, all 8-byte aligned): the exact
+// smoothed tile L' (u64, alive to the end), one region holding first the
+// input tile and the horizontal pass (u32) and then the FP32 row filters of
+// L, the rounded L (f32) whose bytes later hold the pixel lists, k- and its
+// error bound (f32), and the compaction scratch.
 struct StencilSmem {
-  size_t l, x, k, scan, total;
+  unsigned l, x, f, k, scan, total;
 };
 // Row strides of the input tile and of the horizontal pass are odd, so that
 // the lanes of a warp, which take consecutive rows there, hit distinct banks.
@@ -140,14 +180,16 @@ __host__ __device__ __forceinline__ int odd_stride(int w) { return w | 1; }
 
 __host__ __device__ __forceinline__ StencilSmem stencil_smem_layout(int R) {
   const int HALO = R + 3;
-  const size_t IW = odd_stride(ST_TW + 2 * HALO), IH = ST_TH + 2 * HALO;
-  const size_t PW = ST_TW + 6, PWs = odd_stride(ST_TW + 6), LH = ST_TH + 6;
-  const size_t HW2 = ST_TW + 2, HH2 = ST_TH + 2;
-  const size_t in_bytes = (IH * IW + IH * PWs) * 4, hess_bytes = 3 * HH2 * HW2 * 8;
+  const unsigned IW = odd_stride(ST_TW + 2 * HALO), IH = ST_TH + 2 * HALO;
+  const unsigned PW = ST_TW + 6, PWs = odd_stride(ST_TW + 6), LH = ST_TH + 6;
+  const unsigned HW2 = ST_TW + 2, HH2 = ST_TH + 2;
+  const unsigned in_bytes = (IH * IW + IH * PWs) * 4, rf_bytes = 3 * LH * HW2 * 4;
+  const unsigned lf_bytes = LH * PW * 4, list_bytes = ST_TW * ST_TH * (1 + 2 + 2);
   StencilSmem L;
   L.l = 0;
   L.x = LH * PW * 8;
-  L.k = L.x + (((in_bytes > hess_bytes ? in_bytes : hess_bytes) + 7) & ~(size_t)7);
+  L.f = L.x + (((in_bytes > rf_bytes ? in_bytes : rf_bytes) + 7) & ~7u);
+  L.k = L.f + (((lf_bytes > list_bytes ? lf_bytes : list_bytes) + 7) & ~7u);
   L.scan = L.k + 2 * HH2 * HW2 * 4;
   L.total = L.scan + 16 * 4;
   return L;
@@ -168,20 +210,32 @@ __global__ void __launch_bounds__(ST_THREADS, 4) k_stencil_ridge(StencilArgs a) 
 
   // shared memory carve-up (8-byte aligned pieces first).  The input tile
   // and the horizontal pass (sI, sP) are dead once the vertical pass is
-  // done, and the exact Hessians are written after it, so they share bytes.
+  // done, and the row filters are written after it, so they share bytes;
+  // the rounded L is dead after the row filters and its bytes take the
+  // pixel lists.
   const StencilSmem Ls = stencil_smem_layout(R);
   unsigned long long* sL = reinterpret_cast<unsigned long long*>(smem + Ls.l);  // LH*PW
-  long long* sHxx = reinterpret_cast<long long*>(smem + Ls.x);                 // HH2*HW2 each
-  long long* sHyy = sHxx + HH2 * HW2;
-  long long* sHxy = sHyy + HH2 * HW2;
   uint32_t* sI = reinterpret_cast<uint32_t*>(smem + Ls.x);                     // IH*IW
   uint32_t* sP = sI + IH * IW;                                                 // IH*PWs
+  float* sRs = reinterpret_cast<float*>(smem + Ls.x);                          // LH*HW2 each
+  float* sRd2 = sRs + LH * HW2;
+  float* sRd1 = sRd2 + LH * HW2;
+  float* sLf = reinterpret_cast<float*>(smem + Ls.f);                          // LH*PW
+  uint16_t* sU = reinterpret_cast<uint16_t*>(smem + Ls.f);                     // undecided pixels
+  uint16_t* sR = sU + ST_TW * ST_TH;                                           // ridge pixels
+  uint8_t* sV = reinterpret_cast<uint8_t*>(sR + ST_TW * ST_TH);                // exact verdicts
   float* sK = reinterpret_cast<float*>(smem + Ls.k);                           // HH2*HW2
   float* sE = sK + HH2 * HW2;
   int* sScan = reinterpret_cast<int*>(smem + Ls.scan);                         // 8 warps + 2
   __shared__ int32_t q[2 * MAX_RG + 1];
+  __shared__ unsigned s_lmax;  // bits of the largest rounded L of the tile (all >= 0)
+  __shared__ int s_nu;
 
   if (tid < 2 * R + 1) q[tid] = a.taps.q[tid];
+  if (tid == 0) {
+    s_lmax = 0u;
+    s_nu = 0;
+  }
 
   const int f = blockIdx.z;
   const int x0 = blockIdx.x * ST_TW, y0 = blockIdx.y * ST_TH;
@@ -237,7 +291,9 @@ __global__ void __launch_bounds__(ST_THREADS, 4) k_stencil_ridge(StencilArgs a) 
   __syncthreads();
 
   // ---- C: vertical Gaussian, exact u64: L' = sum_i sum_j Q_i Q_j I
-  //      (a pair Q_j (P_j + P_2R-j) of horizontal sums stays below 2^32)
+  //      (a pair Q_j (P_j + P_2R-j) of horizontal sums stays below 2^32);
+  //      also L' rounded to FP32 and the tile's largest value of it
+  float lmax = 0.0f;
   if constexpr (RC > 0) {
     // two vertically adjacent outputs per thread; lanes take columns
     constexpr int NW = 2 * RC + 2;
@@ -257,6 +313,10 @@ __global__ void __launch_bounds__(ST_THREADS, 4) k_stencil_ridge(StencilArgs a) 
       }
       sL[(2 * lp) * PW + px] = acc0;
       sL[(2 * lp + 1) * PW + px] = acc1;
+      const float f0 = __ull2float_rn(acc0), f1 = __ull2float_rn(acc1);
+      sLf[(2 * lp) * PW + px] = f0;
+      sLf[(2 * lp + 1) * PW + px] = f1;
+      lmax = fmaxf(lmax, fmaxf(f0, f1));
     }
   } else {
     for (int i = tid; i < LH * PW; i += ST_THREADS) {
@@ -266,84 +326,137 @@ __global__ void __launch_bounds__(ST_THREADS, 4) k_stencil_ridge(StencilArgs a) 
       for (int j = 0; j < R; ++j)
         acc += (unsigned long long)(uint32_t)q[j] * (unsigned long long)(col[j * PWs] + col[(2 * R - j) * PWs]);
       sL[i] = acc;
+      const float fl = __ull2float_rn(acc);
+      sLf[i] = fl;
+      lmax = fmaxf(lmax, fl);
     }
+  }
+  {
+    const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(lmax));
+    if ((tid & 31) == 0) atomicMax(&s_lmax, m);
   }
   __syncthreads();
 
-  // ---- D: exact Hessian (5x5 second-order Sobel of L') and FP32 k- on the
-  //         tile plus a one-pixel ring
+  // ---- D: FP32 Hessian of the rounded L and FP32 k- with its error bound,
+  //         on the tile plus a one-pixel ring.  D1: the row filters s, d2
+  //         and d1 of each row; D2: the column filters (hess32).
+  for (int i = tid; i < LH * HW2; i += ST_THREADS) {
+    const int ly = i / HW2, hx = i - ly * HW2;
+    const float* row = sLf + ly * PW + hx;
+    const float l0 = row[0], l1 = row[1], l2 = row[2], l3 = row[3], l4 = row[4];
+    const float e = __fadd_rn(l0, l4);
+    sRs[i] = __fmaf_rn(6.0f, l2, __fmaf_rn(4.0f, __fadd_rn(l1, l3), e));
+    sRd2[i] = __fmaf_rn(-2.0f, l2, e);
+    sRd1[i] = __fmaf_rn(2.0f, __fsub_rn(l3, l1), __fsub_rn(l4, l0));
+  }
+  // Bound on |fl(H) x fl(1/D) - H'/D| for each entry (hess32), u = 2^-24,
+  // with 0 <= L' <= Lm (Lm: the tile's largest rounded L, >= L'(1 - u)).
+  // Each rounding adds at most u |its result|, times the coefficient that
+  // carries it to the entry.  With the ranges of the intermediates (e and
+  // l1 + l3 in [0, 2Lm], s in [0, 16Lm], d2 in [-2Lm, 2Lm], d1 in
+  // [-3Lm, 3Lm]) the sum is, for Lxx, 64 (conversion) + 16 x 4 (row
+  // filters) + 72 (column filter) + 2 x 64 (scaling) = 328 u Lm / D; for
+  // Lyy 64 + 4 x 36 + 64 + 128 = 400; for Lxy 36 + 6 x 6 + 36 + 72 = 180.
+  // delta = 448 u Lm / D, rounded up, covers all three with room for the
+  // second-order terms.
+  const float delta = __fmul_ru(__fmul_ru(__uint_as_float(s_lmax), a.invD), 0x1.cp-16f);  // x 448 u
+  __syncthreads();
   for (int i = tid; i < HH2 * HW2; i += ST_THREADS) {
-    int hy = i / HW2, hx = i - hy * HW2;
-    long long hxx = 0, hyy = 0, hxy = 0;
-    const long long s5[5] = {1, 4, 6, 4, 1}, d2[5] = {1, 0, -2, 0, 1}, d1[5] = {-1, -2, 0, 2, 1};
-#pragma unroll
-    for (int dy = 0; dy < 5; ++dy) {
-      const long long* row = reinterpret_cast<const long long*>(sL) + (hy + dy) * PW + hx;
-      long long l0 = row[0], l1 = row[1], l2 = row[2], l3 = row[3], l4 = row[4];
-      long long sx = l0 + 4 * (l1 + l3) + 6 * l2 + l4;
-      long long d2x = l0 - 2 * l2 + l4;
-      long long d1x = (l4 - l0) + 2 * (l3 - l1);
-      hxx += s5[dy] * d2x;
-      hyy += d2[dy] * sx;
-      hxy += d1[dy] * d1x;
-    }
-    sHxx[i] = hxx;
-    sHyy[i] = hyy;
-    sHxy[i] = hxy;
-    float fa = __ll2float_rn(hxx) * a.invD, fb = __ll2float_rn(hxy) * a.invD, fc = __ll2float_rn(hyy) * a.invD;
+    float fa, fb, fc;
+    hess32(sRs, sRd2, sRd1, HW2, i, a.invD, fa, fb, fc);
     float k, ek, hdf, rad;
     eig32_k(fa, fb, fc, k, ek, hdf, rad);
     sK[i] = k;
-    sE[i] = ek;
+    // an eigenvalue moves by at most the spectral norm of the perturbation,
+    // which is at most its Frobenius norm, <= 2 delta
+    sE[i] = __fmaf_ru(3.0f, delta, ek);
   }
   __syncthreads();
 
-  // ---- E: directed-ridge test of the tile's pixels, 4 per thread
-  bool flag[4];
+  // ---- E: directed-ridge test of the tile's pixels, 4 per thread; pixels
+  //         that FP32 cannot decide go to a list for the exact test
+  int flags = 0;  // verdict of pixel j in bits 2j, 2j + 1
   int nfb = 0;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     int pi = tid + j * ST_THREADS;
     int ty = pi / ST_TW, tx = pi - ty * ST_TW;
     int gx = x0 + tx, gy = y0 + ty;
-    bool rid = false;
+    int verdict = 0;
     if (gx < W && gy < H) {
       int hy = ty + 1, hx = tx + 1, c = hy * HW2 + hx;
-      long long hxx = sHxx[c], hyy = sHyy[c], hxy = sHxy[c];
-      bool degenerate = (hxy == 0 && hxx == hyy);
       float k = sK[c], ek = sE[c];
       float dk = k - a.tau;  // exact near the boundary (Sterbenz)
-      int verdict;
-      if (degenerate || dk >= ek) {
+      if (dk >= ek) {
         verdict = 0;
       } else if (!(dk < -ek)) {
         verdict = 2;
       } else {
-        float fa = __ll2float_rn(hxx) * a.invD, fb = __ll2float_rn(hxy) * a.invD, fc = __ll2float_rn(hyy) * a.invD;
+        float fa, fb, fc;
+        hess32(sRs, sRd2, sRd1, HW2, c, a.invD, fa, fb, fc);
         float k2, ek2, hdf, rad, X, Y, eX;
         eig32_k(fa, fb, fc, k2, ek2, hdf, rad);
         float M = fabsf(fa) + fabsf(fb) + fabsf(fc);
-        if (!eig32_dir(fb, hdf, rad, M, hxy == 0, X, Y, eX))
+        if (!eig32_dir(fb, hdf, rad, M, delta, X, Y, eX))
           verdict = 2;
         else
           verdict = ridge_fast(sK, sE, HW2, hy, hx, gx, gy, H, W, k, ek, a.tau, X, Y, eX);
       }
       if (verdict == 2) {
         ++nfb;
-        rid = ridge_exact(sHxx, sHyy, sHxy, HW2, hy, hx, gx, gy, H, W, a.D64, a.tau64);
-      } else {
-        rid = verdict == 1;
+        sU[atomicAdd(&s_nu, 1)] = (uint16_t)pi;
       }
     }
-    flag[j] = rid;
+    flags |= verdict << (2 * j);
   }
   if (nfb) atomicAdd(&a.stats->fallbacks, (unsigned long long)nfb);
+  __syncthreads();
+  {
+    // exact test of the listed pixels, FB_CHUNK at a time: first one thread
+    // per (pixel, neighbour) for the exact k- of the 3x3 neighbourhood (the
+    // bilinear corners of both samples lie in it) and the centre's X-, then
+    // one thread per pixel for the decision.  The row filters are dead now.
+    double* sKn = reinterpret_cast<double*>(smem + Ls.x);  // FB_CHUNK x 9
+    double* sXc = sKn + FB_CHUNK * 9;                      // FB_CHUNK x 2
+    uint8_t* sDg = reinterpret_cast<uint8_t*>(sXc + FB_CHUNK * 2);
+    const int nu = s_nu;
+    for (int c0 = 0; c0 < nu; c0 += FB_CHUNK) {
+      const int nc = min(FB_CHUNK, nu - c0);
+      for (int t = tid; t < nc * 9; t += ST_THREADS) {
+        const int p = t / 9, n = t - p * 9;
+        const int pi = sU[c0 + p];
+        const int ty = pi / ST_TW, tx = pi - ty * ST_TW;
+        long long ha, hc, hb;
+        hess_exact(sL, PW, ty + n / 3, tx + n % 3, ha, hc, hb);
+        const Eig64 e = eigen64(ha, hc, hb, a.D64);
+        sKn[t] = e.k;
+        if (n == 4) {
+          sXc[2 * p] = e.X;
+          sXc[2 * p + 1] = e.Y;
+          sDg[p] = e.degenerate ? 1 : 0;
+        }
+      }
+      __syncthreads();
+      for (int p = tid; p < nc; p += ST_THREADS) {
+        const int pi = sU[c0 + p];
+        const int ty = pi / ST_TW, tx = pi - ty * ST_TW;
+        sV[pi] = ridge_exact_nb(sKn + 9 * p, sXc[2 * p], sXc[2 * p + 1], sDg[p] != 0, x0 + tx, y0 + ty, H, W,
+                                a.tau64)
+                     ? 1
+                     : 0;
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (((flags >> (2 * j)) & 3) == 2) flags ^= (2 ^ (int)sV[tid + j * ST_THREADS]) << (2 * j);
 
-  // ---- compaction: one block-wide exclusive scan of the per-thread counts;
-  //      a thread's records are contiguous (record order inside a tile is
-  //      immaterial downstream: the fit's annulus sums are exact integers)
+  // ---- compaction: one block-wide exclusive scan of the per-thread counts
+  //      into a list of the tile's ridge pixels (record order inside a tile
+  //      is immaterial downstream: the fit's annulus sums are exact integers)
   const int lane = tid & 31, warp = tid >> 5;
-  const int mine = (int)flag[0] + (int)flag[1] + (int)flag[2] + (int)flag[3];
+  const int mine = __popc(flags & 0x55);  // every verdict is now 0 or 1
   int incl = mine;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -358,14 +471,11 @@ __global__ void __launch_bounds__(ST_THREADS, 4) k_stencil_ridge(StencilArgs a) 
     wpre += (w < warp) ? c : 0;
     base += c;
   }
-  int pos[4];
   {
     int p0 = wpre + incl - mine;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      pos[j] = p0;
-      p0 += flag[j] ? 1 : 0;
-    }
+    for (int j = 0; j < 4; ++j)
+      if ((flags >> (2 * j)) & 1) sR[p0++] = (uint16_t)(tid + j * ST_THREADS);
   }
   const int total = base;
   const int tile = blockIdx.y * a.rl.n_stx + blockIdx.x;
@@ -380,20 +490,19 @@ __global__ void __launch_bounds__(ST_THREADS, 4) k_stencil_ridge(StencilArgs a) 
     if (total) atomicAdd(&a.stats->ridge, (unsigned long long)total);
   }
   __syncthreads();
+  // ---- records: the pixel and its exact Hessian, list entries over threads
   const int start = sScan[8];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    if (!flag[j]) continue;
-    int o = start + pos[j];
-    if (o >= a.rl.cap) continue;
-    int pi = tid + j * ST_THREADS;
-    int ty = pi / ST_TW, tx = pi - ty * ST_TW;
-    int c = (ty + 1) * HW2 + (tx + 1);
-    size_t g = (size_t)f * a.rl.cap + o;
+  const int keep = max(0, min(total, a.rl.cap - start));
+  for (int t = tid; t < keep; t += ST_THREADS) {
+    const int pi = sR[t];
+    const int ty = pi / ST_TW, tx = pi - ty * ST_TW;
+    long long hxx, hyy, hxy;
+    hess_exact(sL, PW, ty + 1, tx + 1, hxx, hyy, hxy);
+    const size_t g = (size_t)f * a.rl.cap + start + t;
     a.rl.xy[g] = (uint32_t)(x0 + tx) | ((uint32_t)(y0 + ty) << 16);
-    a.rl.hess[3 * g + 0] = sHxx[c];
-    a.rl.hess[3 * g + 1] = sHyy[c];
-    a.rl.hess[3 * g + 2] = sHxy[c];
+    a.rl.hess[3 * g + 0] = hxx;
+    a.rl.hess[3 * g + 1] = hyy;
+    a.rl.hess[3 * g + 2] = hxy;
   }
 }
 
