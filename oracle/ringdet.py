@@ -50,6 +50,8 @@ class Params:
     sig_b: float
     features: str = "ridge"   # "ridge" (the method) or "edge" (Additional notes: directed edges)
     edge_thresh: float = 0.0  # gradient-magnitude threshold of the edge variant (intensity / px)
+    coarse: int = 1           # accumulator cell edge in px: 1, 2 or 4 (Additional notes: a lower
+                              # resolution of the circle parameter space)
 
     @staticmethod
     def make(**kw) -> "Params":
@@ -58,7 +60,8 @@ class Params:
                       ridge_thresh=f32(kw["ridge_thresh"]), peak_frac=f32(kw["peak_frac"]),
                       vote_thresh=int(kw["vote_thresh"]), annulus_w=f32(kw.get("annulus_w", 2.0)),
                       sig_a=f32(kw.get("sig_a", 0.05)), sig_b=f32(kw.get("sig_b", 0.25)),
-                      features=kw.get("features", "ridge"), edge_thresh=f32(kw.get("edge_thresh", 0.0)))
+                      features=kw.get("features", "ridge"), edge_thresh=f32(kw.get("edge_thresh", 0.0)),
+                      coarse=int(kw.get("coarse", 1) or 1))
 
 
 # --------------------------------------------------------------------------
@@ -257,18 +260,31 @@ def radius_levels(r_min: int, r_max: int) -> np.ndarray:
     return np.arange(r_min - 1, r_max + 2, dtype=np.int64)
 
 
-def cast_votes(xs, ys, X, Y, r: int, H: int, W: int):
+def cell_grid(H: int, W: int, c: int = 1) -> tuple[int, int]:
+    """Accumulator cells of a coarse parameter space: ceil(H / c) x ceil(W / c)."""
+    return -(-H // c), -(-W // c)
+
+
+def cast_votes(xs, ys, X, Y, r: int, H: int, W: int, c: int = 1):
     """Both signs vote at every radius.  Vote bin = floor(p + s r X + 1/2)
     per coordinate, each product and sum one float64 operation; votes that
-    fall outside the image are discarded.  Returns in-bounds (bx, by)."""
+    fall outside the image are discarded.  Returns in-bounds (bx, by).
+
+    Coarse parameter space (Additional notes: a lower resolution of the
+    circle parameter space; the paper gives no form, this is the reading):
+    cells of c x c px, c a power of two, cell u covering [c u - c/2, c u +
+    c/2).  The bin is floor((a + c/2) / c) with a = p + s r X, the sum a +
+    c/2 one float64 operation and the division exact; c = 1 is the rule
+    above.  A cell is kept when it lies in the cell grid (cell_grid)."""
+    Hc, Wc = cell_grid(H, W, c)
     bxs, bys = [], []
     for s in (1, -1):
         sr = float(s * r)
         ax = xs.astype(np.float64) + sr * X
         ay = ys.astype(np.float64) + sr * Y
-        bx = np.floor(ax + 0.5).astype(np.int64)
-        by = np.floor(ay + 0.5).astype(np.int64)
-        keep = (bx >= 0) & (bx < W) & (by >= 0) & (by < H)
+        bx = np.floor((ax + 0.5 * c) / c).astype(np.int64)
+        by = np.floor((ay + 0.5 * c) / c).astype(np.int64)
+        keep = (bx >= 0) & (bx < Wc) & (by >= 0) & (by < Hc)
         bxs.append(bx[keep])
         bys.append(by[keep])
     return np.concatenate(bxs), np.concatenate(bys)
@@ -289,11 +305,13 @@ def level_sigma(r: int, sig_a: float, sig_b: float) -> float:
     return sig_a * r + sig_b
 
 
-def smoothing_weights(r: int, sig_a: float, sig_b: float) -> np.ndarray:
+def smoothing_weights(r: int, sig_a: float, sig_b: float, c: int = 1) -> np.ndarray:
     """Q_r(dy, dx) = floor(2^16 exp(-(dx^2 + dy^2) / (2 sigma(r)^2)) + 1/2)
     on |dx|, |dy| <= R_s = ceil(3 sigma(r)).  Weights peak at 1 (2^16) and
-    are not normalised, so that an ideal ring scores 2 pi after 1/r."""
-    sg = level_sigma(r, sig_a, sig_b)
+    are not normalised, so that an ideal ring scores 2 pi after 1/r.  In a
+    coarse parameter space (cells of c px) the window is the same Gaussian
+    measured in cells: sigma(r) / c (exact: c is a power of two)."""
+    sg = level_sigma(r, sig_a, sig_b) / c
     Rs = int(math.ceil(3.0 * sg))
     d = np.arange(-Rs, Rs + 1, dtype=np.float64)
     d2 = d[:, None] * d[:, None] + d[None, :] * d[None, :]
@@ -501,13 +519,25 @@ def directed_edges(image: np.ndarray, p: Params):
     return np.stack([xs, ys], axis=1).astype(np.int64), np.stack([X[ys, xs], Y[ys, xs]], axis=1)
 
 
+def annulus_width(p: Params) -> float:
+    """Annulus half-width of the fit: w, plus c - 1 px in a coarse parameter
+    space (the peak's centre is then only known to within c / sqrt 2 px)."""
+    return p.annulus_w + float(p.coarse - 1)
+
+
 def detect(image: np.ndarray, p: Params, keep: bool = False) -> Result:
     """Frame -> rings, steps O1-O9 in order.  Levels are visited in
     increasing r; the peak test of level r runs once N of level r + 1 exists
-    (a plain sliding window of three levels, kept only to bound memory)."""
+    (a plain sliding window of three levels, kept only to bound memory).
+    With p.coarse = c > 1 steps O5-O8 run on the c-px cell grid and a peak
+    cell (u, v) is the centre (c u, c v) px of the fit."""
     if image.dtype.kind not in "ui":
         raise TypeError("the oracle's exact path takes integer frames")
+    if p.coarse not in (1, 2, 4):
+        raise ValueError("coarse must be 1, 2 or 4")
     H, W = image.shape
+    c = p.coarse
+    Hc, Wc = cell_grid(H, W, c)
     ridge_xy, ridge_X = directed_edges(image, p) if p.features == "edge" else directed_ridges(image, p)
     xs, ys = ridge_xy[:, 0], ridge_xy[:, 1]
     levels = radius_levels(p.r_min, p.r_max)
@@ -517,10 +547,10 @@ def detect(image: np.ndarray, p: Params, keep: bool = False) -> Result:
     peaks = []
     for r in levels:
         r = int(r)
-        bx, by = cast_votes(xs, ys, ridge_X[:, 0], ridge_X[:, 1], r, H, W)
+        bx, by = cast_votes(xs, ys, ridge_X[:, 0], ridge_X[:, 1], r, H, W, c)
         votes_in += len(bx)
-        A = accumulate(bx, by, H, W)
-        Qr = smoothing_weights(r, p.sig_a, p.sig_b)
+        A = accumulate(bx, by, Hc, Wc)
+        Qr = smoothing_weights(r, p.sig_a, p.sig_b, c)
         Ns[r] = smooth_hot(A, Qr, p.vote_thresh)
         n_hot = int((A > p.vote_thresh).sum())
         hotspots += n_hot
@@ -531,10 +561,12 @@ def detect(image: np.ndarray, p: Params, keep: bool = False) -> Result:
             peaks += find_peaks_level(Ns[r - 2], Ns[r - 1], Ns[r], r - 1, p)
             if not keep:
                 del Ns[r - 2]
+    peaks = [(c * x, c * y, r, n) for x, y, r, n in peaks]
     peaks.sort(key=lambda t: (t[2], t[1], t[0]))
     rings = np.zeros(len(peaks), dtype=RING_DTYPE)
+    w = annulus_width(p)
     for i, (ix, iy, ir, nv) in enumerate(peaks):
-        pts = annulus_members(ridge_xy, ix, iy, ir, p.annulus_w)
+        pts = annulus_members(ridge_xy, ix, iy, ir, w)
         cx, cy, rr, nfit, flags = kasa_fit(pts, ix, iy, ir)
         rings[i] = (cx, cy, rr, ix, iy, ir, nv / (float(1 << SMOOTH_BITS) * ir), nfit, flags)
     return Result(rings, ridge_xy, ridge_X, votes_in, 2 * len(xs) * len(levels), hotspots, smooth_macs,

@@ -20,7 +20,7 @@ def _larger_eigen(a, c, b):
     return -k, X, Y, deg
 
 
-def _one_sign_votes(xs, ys, X, Y, r, H, W):
+def _one_sign_votes(xs, ys, X, Y, r, H, W, c=1):
     sr = float(r)
     bx = np.floor(xs + sr * X + 0.5).astype(np.int64)
     by = np.floor(ys + sr * Y + 0.5).astype(np.int64)
@@ -28,7 +28,7 @@ def _one_sign_votes(xs, ys, X, Y, r, H, W):
     return bx[keep], by[keep]
 
 
-def _truncating_votes(xs, ys, X, Y, r, H, W):
+def _truncating_votes(xs, ys, X, Y, r, H, W, c=1):
     bxs, bys = [], []
     for s in (1, -1):
         bx = np.trunc(xs + s * r * X).astype(np.int64)
@@ -38,8 +38,8 @@ def _truncating_votes(xs, ys, X, Y, r, H, W):
     return np.concatenate(bxs), np.concatenate(bys)
 
 
-def _normalised_weights(r, a, b):
-    Q = _orig["smoothing_weights"](r, a, b)
+def _normalised_weights(r, a, b, c=1):
+    Q = _orig["smoothing_weights"](r, a, b, c)
     return np.floor(Q * 65536.0 / Q.sum() + 0.5).astype(np.int64)
 
 
@@ -107,7 +107,28 @@ def _unnormalised_taps(sigma):
     return Q
 
 
+def _coarse_floor_cells(xs, ys, X, Y, r, H, W, c=1):
+    """Coarse cells by floor(a / c) instead of the nearest centre."""
+    Hc, Wc = O.cell_grid(H, W, c)
+    bxs, bys = [], []
+    for s in (1, -1):
+        ax = xs + float(s * r) * X
+        ay = ys + float(s * r) * Y
+        bx = (np.floor(ax / c) if c > 1 else np.floor(ax + 0.5)).astype(np.int64)
+        by = (np.floor(ay / c) if c > 1 else np.floor(ay + 0.5)).astype(np.int64)
+        keep = (bx >= 0) & (bx < Wc) & (by >= 0) & (by < Hc)
+        bxs.append(bx[keep]); bys.append(by[keep])
+    return np.concatenate(bxs), np.concatenate(bys)
+
+
+def _coarse_sigma_unscaled(r, a, b, c=1):
+    """The window left in pixel units on the cell grid."""
+    return _orig["smoothing_weights"](r, a, b)
+
+
 MUTATIONS = {
+    "coarse_floor_cells": ("cast_votes", _coarse_floor_cells),
+    "coarse_sigma_unscaled": ("smoothing_weights", _coarse_sigma_unscaled),
     "larger_eigenvalue": ("eigen", _larger_eigen),
     "one_sign_votes": ("cast_votes", _one_sign_votes),
     "truncating_votes": ("cast_votes", _truncating_votes),

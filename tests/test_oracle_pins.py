@@ -348,6 +348,87 @@ def check_annulus_inclusive():
     return sorted(m[:, 1].tolist()) == [3, 5, 7]
 
 
+# ---------------------------------------------------------------- coarse parameter space
+def check_coarse_cell_is_nearest_centre():
+    """In a coarse parameter space a vote at a goes to the cell whose centre
+    c u is nearest, a cell covering [c u - c/2, c u + c/2) (so a tie goes to
+    the upper cell), brute force over candidate cells; c = 1 is the pixel
+    rule.  Radius 1 keeps s r X exact so that a is known exactly."""
+    rng = np.random.default_rng(11)
+    for c in (1, 2, 4):
+        xs = rng.integers(0, 40, 400).astype(np.int64)
+        X = np.concatenate([rng.integers(-8, 9, 200) / 8.0, rng.uniform(-1, 1, 200)])  # exact half-cells too
+        ys = np.full_like(xs, 3)
+        Y = np.zeros_like(X)
+        bx, by = O.cast_votes(xs, ys, X, Y, 1, 64, 64, c)
+        exp = []
+        for s in (1, -1):
+            for x0, dx in zip(xs, X):
+                a = float(x0) + s * dx
+                best = None
+                for u in range(-3, 70):
+                    lo, hi = c * u - c / 2.0, c * u + c / 2.0
+                    if lo <= a < hi:
+                        best = u
+                if best is not None and 0 <= best < -(-64 // c):
+                    exp.append(best)
+        if sorted(bx.tolist()) != sorted(exp) or not np.all(by == (3 + c // 2) // c):
+            return False
+    return True
+
+
+def check_coarse_weights_subsample_fine():
+    """The coarse window is the same Gaussian measured in cells: Q^c(du, dv)
+    = Q^1(c du, c dv) wherever both windows hold the tap, and its half-width
+    is ceil(3 sigma(r) / c)."""
+    a, b = np.float32(0.05), np.float32(0.25)
+    for r in (8, 20, 41, 97):
+        Q1 = O.smoothing_weights(r, a, b)
+        R1 = (len(Q1) - 1) // 2
+        for c in (2, 4):
+            Qc = O.smoothing_weights(r, a, b, c)
+            Rc = (len(Qc) - 1) // 2
+            if Rc != math.ceil(3.0 * (0.05 * r + 0.25) / c - 1e-9):
+                return False
+            for du in range(-Rc, Rc + 1):
+                for dv in range(-Rc, Rc + 1):
+                    if abs(c * du) <= R1 and abs(c * dv) <= R1 and Qc[dv + Rc, du + Rc] != Q1[c * dv + R1, c * du + R1]:
+                        return False
+    return True
+
+
+def check_coarse_spike_scores_two_pi():
+    """An ideal ring's round(2 pi r) votes in one cell still score 2 pi: the
+    coarse window also peaks at 2^16."""
+    r = 30
+    for c in (2, 4):
+        Q = O.smoothing_weights(r, np.float32(0.05), np.float32(0.25), c)
+        A = np.zeros((32, 32), dtype=np.int64)
+        n = int(round(2 * math.pi * r))
+        A[10, 15] = n
+        N = O.smooth_hot(A, Q, 3)
+        if not (N[10, 15] == 65536 * n and N.sum() == N[10, 15]):
+            return False
+    return True
+
+
+def check_coarse_truth():
+    """Cells of 2 px: every true ring of the small synthetic frame is found
+    with its peak centre within one cell and its radius within 1 px, and the
+    fit recovers the centre to a fraction of a pixel."""
+    f = synth.plain_small()
+    res = O.detect(f.image, O.Params.make(coarse=2, **f.params))
+    got = np.stack([res.rings["ix"], res.rings["iy"], res.rings["ir"]], 1).astype(float)
+    fit = np.stack([res.rings["cx"], res.rings["cy"]], 1)
+    if len(got) != len(f.rings) or np.any(got[:, :2] % 2 != 0):
+        return False
+    for cx, cy, R in f.rings:
+        m = (np.abs(got[:, :2] - [cx, cy]).max(1) <= 2.0) & (np.abs(got[:, 2] - R) <= 1.0)
+        if not m.any() or np.abs(fit[m] - [cx, cy]).max() > 0.5:
+            return False
+    return True
+
+
 PINS = {name[6:]: fn for name, fn in dict(globals()).items() if name.startswith("check_")}
 
 
