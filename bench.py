@@ -637,6 +637,95 @@ def run_discs(args):
     print(json.dumps(line))
 
 
+def _one_frame_truth(seed):
+    from paper_1310_1371_gb300 import synth
+    f = synth.plain_full(seed=seed)
+    return f.image, f.rings
+
+
+def _accuracy(rings, truth):
+    """Median |d cx|, |d cy|, |d r| of the fitted rings nearest to each true
+    ring (within 3 px in centre and radius), and the fraction of true rings
+    so matched."""
+    got = np.stack([rings["cx"], rings["cy"], rings["r"]], 1).astype(np.float64)
+    errs, hit = [], 0
+    for t in truth:
+        if len(got) == 0:
+            continue
+        d = np.abs(got - t)
+        k = int(np.argmin(d.max(1)))
+        if d[k].max() <= 3.0:
+            errs.append(d[k])
+            hit += 1
+    e = np.median(np.array(errs), 0) if errs else np.full(3, np.nan)
+    return {"median_abs_cx_px": float(e[0]), "median_abs_cy_px": float(e[1]), "median_abs_r_px": float(e[2]),
+            "recall": hit / max(1, len(truth))}
+
+
+def run_coarse(args):
+    """A coarse circle parameter space (cells of c px) on the default
+    workload's 96 frames: frames/s at c and at full resolution on the same
+    resident frames (same timing protocol), and the fitted rings' accuracy
+    against the synthetic truth for both."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    B = args.batch
+    with cf.ProcessPoolExecutor(max(1, min(16, (os.cpu_count() or 2) - 1)), mp_context=mp.get_context("spawn")) as ex:
+        got = list(ex.map(_one_frame_truth, frame_seeds(0, B)))
+    imgs = np.stack([g[0] for g in got])
+    truth = [g[1] for g in got]
+    import torch
+    from paper_1310_1371_gb300 import rd, synth
+    torch.cuda.set_device(0)
+    frames = torch.from_numpy(imgs).cuda()
+    res = {}
+    clocks = None
+    for c in (1, args.coarse):
+        params = dict(synth.PLAIN_FULL_PARAMS, coarse=c)
+        geo = (args.tile, args.slab) if (c != 1 and args.tile) else None
+        det = rd.Detector(params, H, W, B, geometry=geo)
+        for _ in range(args.warmup):
+            det.detect_async(frames)
+        if det.stats().overflow:
+            raise RuntimeError(f"capacity overflow: {det.stats().overflow}")
+        sampler = ClockSampler(0) if c != 1 else None
+        time.sleep(0.3)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(args.steps):
+            det.detect_async(frames)
+        ev1.record()
+        torch.cuda.synchronize()
+        if sampler is not None:
+            clocks = sampler.stop()
+        ms = ev0.elapsed_time(ev1)
+        rings, stats = det.detect(frames)
+        acc = [_accuracy(rings[i], truth[i]) for i in range(B)]
+        det.set_timing(True)
+        stage_ms = np.zeros(len(STAGES))
+        for _ in range(5):
+            det.detect_async(frames)
+            stage_ms += det.timing()
+        res[c] = {"frames_per_s": B * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
+                  "geometry": list(det.geometry()),
+                  "stage_ms_per_step": {k: float(v) for k, v in zip(STAGES, np.round(stage_ms / 5, 4))},
+                  "rings_per_frame": stats.peaks / B, "votes_per_frame": stats.votes / B,
+                  "hotspots_per_frame": stats.hotspots / B, "smooth_macs_per_frame": stats.smooth_macs / B,
+                  "exact_fallbacks_per_frame": stats.exact_fallbacks / B,
+                  "accuracy": {k: float(np.nanmedian([a[k] for a in acc])) for k in acc[0]}}
+        det.close()
+    c = args.coarse
+    line = {"metric": METRIC + f", {c} px parameter-space cells", "value": res[c]["frames_per_s"], "unit": "frames/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": res[c]["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u16", "data": "synthetic",
+            "config": {"workload": f"coarse: plain_full frames with a {c} px cell circle parameter space",
+                       "batch_frames": B, "l2": f"inputs ({imgs.nbytes / 2**20:.0f} MiB) larger than L2; no flush"},
+            "coarse": {str(k): v for k, v in res.items()},
+            "gpu_launches": KERNELS_PER_CALL * args.steps, "clocks": clocks}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -646,7 +735,11 @@ def main():
     ap.add_argument("--batch", type=int, default=96)
     ap.add_argument("--cpu-frames", type=int, default=4)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--workload", default="plain_full", choices=["plain_full", "video", "diff", "serve", "discs"])
+    ap.add_argument("--workload", default="plain_full",
+                    choices=["plain_full", "video", "diff", "serve", "discs", "coarse"])
+    ap.add_argument("--coarse", type=int, default=2, choices=[2, 4])
+    ap.add_argument("--tile", type=int, default=0, help="accumulator tile (cells) of the coarse run; 0: automatic")
+    ap.add_argument("--slab", type=int, default=16, help="slab levels of the coarse run with --tile")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=500.0)
     ap.add_argument("--serve-pool", type=int, default=8)
@@ -665,6 +758,8 @@ def main():
         run_serve(args)
     elif args.workload == "discs":
         run_discs(args)
+    elif args.workload == "coarse":
+        run_coarse(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

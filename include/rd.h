@@ -72,6 +72,16 @@ typedef struct rd_params {
                          | |p - c| - r | <= annulus_w are fitted (step 5)       */
   float sig_a, sig_b; /* level smoothing sigma(r) = sig_a r + sig_b, > 0 for all
                          levels (Methods: 0.05, 0.25)                            */
+  int   coarse;       /* cell edge c of the circle parameter space in px: 0 or 1
+                         (full resolution), 2 or 4 (Additional notes: a lower
+                         resolution of the parameter space for more speed per
+                         processing unit).  A vote at a = p + s r X goes to the
+                         cell floor((a + c/2) / c); the level window is the same
+                         Gaussian in cells (sigma(r) / c); a cell is a hotspot
+                         when its count exceeds vote_thresh c^2 (<= 65534); a
+                         peak cell (u, v) is the centre (c u, c v) px, fitted
+                         over the annulus of half-width annulus_w + c - 1.
+                         Radii stay in 1 px steps.                               */
 } rd_params;
 
 /* One detected ring.  (ix, iy, ir) is the integer peak of the smoothed,
@@ -293,9 +303,11 @@ int       rd_get_timing(rd_ctx* ctx, float* ms, int cap);
  * order inside a tile is unspecified.
  * rd_debug_capture makes the next rd_detect write frame 0's raw accumulator
  * (acc_dev, int32) and smoothed accumulator (sm_dev, uint32) for every voting
- * level r_min-1 .. r_max+1 as [level][H][W] device arrays (either may be
- * NULL; NULL for both turns capture off).  The smoothed accumulator is
- * written at hotspots only; the caller zero-fills the arrays. */
+ * level r_min-1 .. r_max+1 as [level][Hc][Wc] device arrays, Hc = ceil(H / c)
+ * and Wc = ceil(W / c) cells of the parameter space (c = params.coarse; the
+ * frame size when c = 1; either array may be NULL; NULL for both turns
+ * capture off).  The smoothed accumulator is written at hotspots only; the
+ * caller zero-fills the arrays. */
 int       rd_debug_ridges(rd_ctx* ctx, int f, int32_t* xy, float* dir, int64_t* hess, int cap);
 /* rd_debug_route(ctx, 1) makes the following rd_detect calls process every
  * accumulator tile with the dense-storage voting kernel (normally used only

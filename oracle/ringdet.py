@@ -519,6 +519,13 @@ def directed_edges(image: np.ndarray, p: Params):
     return np.stack([xs, ys], axis=1).astype(np.int64), np.stack([X[ys, xs], Y[ys, xs]], axis=1)
 
 
+def hot_threshold(p: Params) -> int:
+    """Integer hotspot threshold on a cell: T_int, times c^2 in a coarse
+    parameter space (reading: the threshold is a vote density per pixel of
+    the parameter space, and a cell covers c^2 pixels)."""
+    return p.vote_thresh * p.coarse * p.coarse
+
+
 def annulus_width(p: Params) -> float:
     """Annulus half-width of the fit: w, plus c - 1 px in a coarse parameter
     space (the peak's centre is then only known to within c / sqrt 2 px)."""
@@ -551,8 +558,8 @@ def detect(image: np.ndarray, p: Params, keep: bool = False) -> Result:
         votes_in += len(bx)
         A = accumulate(bx, by, Hc, Wc)
         Qr = smoothing_weights(r, p.sig_a, p.sig_b, c)
-        Ns[r] = smooth_hot(A, Qr, p.vote_thresh)
-        n_hot = int((A > p.vote_thresh).sum())
+        Ns[r] = smooth_hot(A, Qr, hot_threshold(p))
+        n_hot = int((A > hot_threshold(p)).sum())
         hotspots += n_hot
         smooth_macs += n_hot * Qr.size
         if keep:

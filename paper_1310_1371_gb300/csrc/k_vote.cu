@@ -44,8 +44,9 @@ template <int T>
 __device__ __forceinline__ SegTiles seg_tiles(const BinArgs& a, float px, float py, float dx, float dy, float r0,
                                               float r1, int h) {
   SegTiles t{0, 0, 1, 0};
-  float ax0 = px + r0 * dx, ax1 = px + r1 * dx;
-  float ay0 = py + r0 * dy, ay1 = py + r1 * dy;
+  // in cells of 2^lc px (a.inv_c = 2^-lc, exact)
+  float ax0 = (px + r0 * dx) * a.inv_c, ax1 = (px + r1 * dx) * a.inv_c;
+  float ay0 = (py + r0 * dy) * a.inv_c, ay1 = (py + r1 * dy) * a.inv_c;
   int bx0 = (int)floorf(fminf(ax0, ax1)) - 1, bx1 = (int)ceilf(fmaxf(ax0, ax1)) + 1;
   int by0 = (int)floorf(fminf(ay0, ay1)) - 1, by1 = (int)ceilf(fmaxf(ay0, ay1)) + 1;
   bx0 = max(bx0, 0);
@@ -125,12 +126,20 @@ __global__ void __launch_bounds__(256) k_bin(BinArgs a) {
           const long long pos = (long long)a.bin_off[b] + first + __popc(grp & ((1u << lane) - 1u));
           if (pos < a.pool_cap) {
             const float sgn = sg == 0 ? 1.0f : -1.0f;
-            const uint32_t ill = a.rl.kvote[g].x > KF_CONST ? 2u : 0u;
-            // position relative to the tile region's origin (tx T - h, ty T - h)
-            const int lx0 = (int)(xy & 0xffffu) - (tx * T - h), ly0 = (int)(xy >> 16) - (ty * T - h);
+            // A direction with a component exactly 0 (both parts) is an exact
+            // axis: the Hessian's off-diagonal is exactly 0, so the
+            // definition's X- is exactly (1, 0) or (0, 1) too (sqrt(x^2) = |x|
+            // in binary floating point) and every s r X- is an exact integer.
+            const bool axis = (d.x == 0.0f && d.z == 0.0f) || (d.y == 0.0f && d.w == 0.0f);
+            const float ex = axis ? (d.x == 0.0f ? 0.0f : 1.0f) : d.x;
+            const float ey = axis ? 1.0f - ex : d.y;
+            const uint32_t ill = (!axis && a.rl.kvote[g].x > KF_CONST) ? 2u : 0u;
+            // position in px relative to the tile region's origin 2^lc (tx T - h, ty T - h)
+            const int lx0 = (int)(xy & 0xffffu) - ((tx * T - h) << a.lc);
+            const int ly0 = (int)(xy >> 16) - ((ty * T - h) << a.lc);
             a.pool[pos] = make_uint4(((uint32_t)ly0 << 16) | ((uint32_t)lx0 & 0xffffu),
-                                     __float_as_uint(sgn * d.x), __float_as_uint(sgn * d.y),
-                                     ((uint32_t)i << 2) | ill | (uint32_t)sg);
+                                     __float_as_uint(sgn * ex), __float_as_uint(sgn * ey),
+                                     ((uint32_t)i << 3) | (axis ? 4u : 0u) | ill | (uint32_t)sg);
           }
         }
       }
@@ -241,10 +250,11 @@ __device__ __forceinline__ VEnt load_ent(const VoteArgs& a, size_t fbase, long l
   const float sg = (E.w & 1u) ? -1.0f : 1.0f;
   VEnt v;
   v.xy = E.x;
-  v.ent = ((E.w >> 2) << 1) | (E.w & 1u);
+  v.ent = ((E.w >> 3) << 1) | (E.w & 1u);
   v.X = sg * __uint_as_float(E.y);  // back to the unsigned direction
   v.Y = sg * __uint_as_float(E.z);
-  v.kf = (E.w & 2u) ? 1e30f : KF_CONST;
+  // exact axis: every s r X- is an exact integer, decided without a margin
+  v.kf = (E.w & 4u) ? -1.0f : ((E.w & 2u) ? 1e30f : KF_CONST);
   return v;
 }
 
@@ -252,20 +262,18 @@ constexpr float ROUND_MAGIC = 12582912.0f;  // 1.5 * 2^23: adding it rounds |t| 
 constexpr int ROUND_MAGIC_BITS = 0x4B400000;
 
 // Slow path of one vote: double-float refinement, then the double-precision
-// definition.  Returns 1 when the FP64 definition was evaluated.
-__device__ __noinline__ int vote_bins_slow(const VoteArgs& a, size_t fbase, VEnt v, int px, int py, float rf,
-                                           int* oxy) {
+// definition.  (px, py): the pixel.  Returns (ox, oy, 1 when the FP64
+// definition was evaluated).  lc = 0: the vote's bin is p + o.  lc > 0
+// (cells of c = 2^lc px): its cell is floor((p + o + c/2) / c).
+__device__ __noinline__ int3 vote_bins_slow(const VoteArgs& a, size_t fbase, VEnt v, int px, int py, float rf) {
+  const int lc = a.lc;
   const float sr = (v.ent & 1u) ? -rf : rf;
   const size_t g = fbase + (v.ent >> 1);
   const float4 d = a.rl.dir[g];
   const float2 kv = a.rl.kvote[g];
-  int vx = vote_offset(sr, rf, d.x, d.z, kv.x, kv.y);
-  int vy = vote_offset(sr, rf, d.y, d.w, kv.x, kv.y);
-  if (vx != INT_MIN && vy != INT_MIN) {
-    oxy[0] = vx;
-    oxy[1] = vy;
-    return 0;
-  }
+  const int vx = lc ? vote_floor(sr, rf, d.x, d.z, kv.x, kv.y) : vote_offset(sr, rf, d.x, d.z, kv.x, kv.y);
+  const int vy = lc ? vote_floor(sr, rf, d.y, d.w, kv.x, kv.y) : vote_offset(sr, rf, d.y, d.w, kv.x, kv.y);
+  if (vx != INT_MIN && vy != INT_MIN) return make_int3(vx, vy, 0);
   double X, Y;
   if (a.rl.x64) {  // directed edges: the record keeps the exact double direction
     X = a.rl.x64[g].x;
@@ -279,9 +287,11 @@ __device__ __noinline__ int vote_bins_slow(const VoteArgs& a, size_t fbase, VEnt
     X = -X;
     Y = -Y;
   }
-  oxy[0] = vote_bin64(px, (double)sr, X) - px;
-  oxy[1] = vote_bin64(py, (double)sr, Y) - py;
-  return 1;
+  if (lc == 0) return make_int3(vote_bin64(px, (double)sr, X) - px, vote_bin64(py, (double)sr, Y) - py, 1);
+  // an offset o with floor((p + o + c/2) / c) = the definition's cell
+  const int hc = 1 << (lc - 1);
+  return make_int3((vote_cell64(px, (double)sr, X, lc) << lc) - hc - px,
+                   (vote_cell64(py, (double)sr, Y, lc) << lc) - hc - py, 1);
 }
 
 struct CastCtx {
@@ -308,13 +318,22 @@ __device__ __forceinline__ int cast_one(const VoteArgs& a, size_t fbase, const V
   const float dy = __fsub_rn(ty, __fsub_rn(fy, ROUND_MAGIC));
   int ox = __float_as_int(fx) - ROUND_MAGIC_BITS;
   int oy = __float_as_int(fy) - ROUND_MAGIC_BITS;
-  if (!(fmaxf(fabsf(dx), fabsf(dy)) < __fsub_rn(0.5f, m))) {
-    int oxy[2];
-    nfb += vote_bins_slow(a, fbase, v, ent_lx(v.xy) + c.eox, ent_ly(v.xy) + c.eoy, rf, oxy);
-    ox = oxy[0];
-    oy = oxy[1];
+  const int lc = a.lc;
+  // lc = 0: round to nearest, certain away from half-integers; lc > 0: floor,
+  // certain away from integers
+  const bool sure = lc == 0 ? fmaxf(fabsf(dx), fabsf(dy)) < __fsub_rn(0.5f, m) : fminf(fabsf(dx), fabsf(dy)) > m;
+  if (!sure) {
+    const int3 o = vote_bins_slow(a, fbase, v, ent_lx(v.xy) + (c.eox << lc), ent_ly(v.xy) + (c.eoy << lc), rf);
+    nfb += o.z;
+    ox = o.x;
+    oy = o.y;
+  } else if (lc) {
+    ox -= dx < 0.0f ? 1 : 0;
+    oy -= dy < 0.0f ? 1 : 0;
   }
-  const int lx = ent_lx(v.xy) + c.eox + ox - c.ox0, ly = ent_ly(v.xy) + c.eoy + oy - c.oy0;
+  const int hc = (1 << lc) >> 1;
+  const int lx = ((ent_lx(v.xy) + ox + hc) >> lc) + c.eox - c.ox0;
+  const int ly = ((ent_ly(v.xy) + oy + hc) >> lc) + c.eoy - c.oy0;
   if ((unsigned)(lx - c.lxlo) >= (unsigned)c.lxn || (unsigned)(ly - c.lylo) >= (unsigned)c.lyn) return -1;
   if (c.owned && (unsigned)(lx - c.h) < (unsigned)c.T && (unsigned)(ly - c.h) < (unsigned)c.T) ++nv;
   return ly * c.RW + lx;
@@ -587,7 +606,7 @@ __device__ __forceinline__ void dense_bin(const VoteArgs& a, int b, int sub, uns
         if (ok) {
           int kk = atomicAdd(&a.peak_count[f], 1);
           if (kk < a.peak_cap)
-            a.peaks[(size_t)f * a.peak_cap + kk] = make_int4(gx, gy, rp, (int)nv0);
+            a.peaks[(size_t)f * a.peak_cap + kk] = make_int4(gx << a.lc, gy << a.lc, rp, (int)nv0);
           else
             atomicOr(&a.stats->overflow, 4);
           atomicAdd(&a.stats->peaks, 1ULL);
@@ -670,6 +689,7 @@ __device__ __forceinline__ uint32_t sp_lookup(const uint32_t* tab, const uint32_
 }
 
 // K4 work of one bin b; called by every thread of the CTA.
+template <bool COARSE>
 __device__ __forceinline__ void vote_bin_sparse(const VoteArgs& a, const int b, unsigned char* smem) {
   const int cnt_raw = a.bin_cnt[b];
   if (cnt_raw == 0) return;
@@ -751,7 +771,8 @@ __device__ __forceinline__ void vote_bin_sparse(const VoteArgs& a, const int b, 
     //      threshold is registered as a hotspot of this level
     const bool owned = (r >= lo && r <= hi) || (r == lo - 1 && lo == a.r_min) || (r == hi + 1 && hi == a.r_max);
     const float rf = (float)r;
-    const float half_m = __fsub_rn(0.5f, __fmaf_rn(rf, KF_CONST, 1e-10f));
+    const float m_r = __fmaf_rn(rf, KF_CONST, 1e-10f);
+    const float half_m = __fsub_rn(0.5f, m_r);
     uint32_t* tab = sHash + lst * SP_HASH;
     unsigned nv = 0, nfb = 0;
     uint4 En = make_uint4(0u, 0u, 0u, 0u);  // next round's entry, loaded one round ahead
@@ -766,18 +787,32 @@ __device__ __forceinline__ void vote_bin_sparse(const VoteArgs& a, const int b, 
       const float dx = __fsub_rn(tx_, __fsub_rn(fx, ROUND_MAGIC));
       const float dy = __fsub_rn(ty_, __fsub_rn(fy, ROUND_MAGIC));
       int ox = __float_as_int(fx) - ROUND_MAGIC_BITS, oy = __float_as_int(fy) - ROUND_MAGIC_BITS;
-      if ((E.w & 2u) || !(fmaxf(fabsf(dx), fabsf(dy)) < half_m)) {
+      // pixels: round to nearest, certain away from half-integers; cells:
+      // floor, certain away from integers
+      const bool sure = COARSE ? (fminf(fabsf(dx), fabsf(dy)) > m_r || (E.w & 4u)) : fmaxf(fabsf(dx), fabsf(dy)) < half_m;
+      if ((E.w & 2u) || !sure) {
         VEnt v;
         v.xy = E.x;
-        v.ent = ((E.w >> 2) << 1) | (E.w & 1u);
+        v.ent = ((E.w >> 3) << 1) | (E.w & 1u);
         v.X = v.Y = 0.0f;
         v.kf = 0.0f;
-        int oxy[2];
-        nfb += vote_bins_slow(a, fbase, v, ent_lx(E.x) + ox0, ent_ly(E.x) + oy0, rf, oxy);
-        ox = oxy[0];
-        oy = oxy[1];
+        const int3 o = vote_bins_slow(a, fbase, v, ent_lx(E.x) + (ox0 << a.lc), ent_ly(E.x) + (oy0 << a.lc), rf);
+        nfb += o.z;
+        ox = o.x;
+        oy = o.y;
+      } else if (COARSE) {
+        ox -= dx < 0.0f ? 1 : 0;
+        oy -= dy < 0.0f ? 1 : 0;
       }
-      const int lx = ent_lx(E.x) + ox, ly = ent_ly(E.x) + oy;
+      int lx, ly;
+      if (COARSE) {
+        const int hc = 1 << (a.lc - 1);
+        lx = (ent_lx(E.x) + ox + hc) >> a.lc;
+        ly = (ent_ly(E.x) + oy + hc) >> a.lc;
+      } else {
+        lx = ent_lx(E.x) + ox;
+        ly = ent_ly(E.x) + oy;
+      }
       if ((unsigned)(lx - lxlo) >= (unsigned)lxn || (unsigned)(ly - lylo) >= (unsigned)lyn) continue;
       if (owned && (unsigned)(lx - h) < (unsigned)T && (unsigned)(ly - h) < (unsigned)T) ++nv;
       const int la = ly * RW + lx;
@@ -923,7 +958,7 @@ __device__ __forceinline__ void vote_bin_sparse(const VoteArgs& a, const int b, 
         if (ok) {
           const int kk = atomicAdd(&s_npk, 1);
           if (kk < SP_PEAKS)
-            sPk[kk] = make_int4(gx, gy, rp, (int)nv0);
+            sPk[kk] = make_int4(gx << a.lc, gy << a.lc, rp, (int)nv0);
           else
             s_abort = 1;
         }
@@ -1037,6 +1072,8 @@ __global__ void __launch_bounds__(1024) k_queue(const int* bin_cnt, long long n_
 }
 
 // Persistent K4: a fixed grid of CTAs takes bins from the work queue.
+// COARSE: cells of 2^a.lc px (a.lc > 0).
+template <bool COARSE>
 __global__ void __launch_bounds__(SP_THREADS, 3) k_vote(VoteArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
@@ -1047,20 +1084,21 @@ __global__ void __launch_bounds__(SP_THREADS, 3) k_vote(VoteArgs a) {
     const int item = s_item;
     __syncthreads();  // s_item read by all before thread 0 takes the next item
     if (item >= n_items) break;
-    vote_bin_sparse(a, a.queue[item], smem);
+    vote_bin_sparse<COARSE>(a, a.queue[item], smem);
   }
 }
 
 cudaError_t launch_vote(const VoteArgs& a, long long n_bins, cudaStream_t st) {
   size_t sm = sparse_smem_bytes(a.max_rw, a.max_qp);
-  cudaFuncSetAttribute(k_vote, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  void (*kern)(VoteArgs) = a.lc ? k_vote<true> : k_vote<false>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_queue<<<1, 1024, 0, st>>>(a.bin_cnt, n_bins, a.queue, a.n_queue, a.queue_head);
   // persistent grid: as many CTAs as are resident at once
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_vote, SP_THREADS, sm) != cudaSuccess || per_sm < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SP_THREADS, sm) != cudaSuccess || per_sm < 1)
     per_sm = 1;
   const unsigned grid = (unsigned)std::max(1LL, std::min<long long>(n_bins, (long long)a.vote_grid * per_sm));
-  k_vote<<<grid, SP_THREADS, sm, st>>>(a);
+  kern<<<grid, SP_THREADS, sm, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   size_t smd = vote_smem_bytes(a.max_rw_dense, a.T_dense, a.max_qn);

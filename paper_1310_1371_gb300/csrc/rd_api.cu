@@ -38,7 +38,8 @@ struct rd_ctx {
   double D64;
   float invD;
   int n_levels, n_slabs, max_rw, max_qn;
-  int T;  // accumulator tile edge: 64, 80, 96 or 128
+  int T;  // accumulator tile edge in cells: 64, 80, 96 or 128
+  int lc;  // log2 of the parameter-space cell edge in px (rd_params.coarse)
   int T_dense, max_rw_dense;  // the dense fallback kernel's tile edge and window
   int S;  // peak levels per r-slab
   std::vector<int4> h_slabs;
@@ -132,10 +133,15 @@ static int gaussian_taps_impl(float sigma, int32_t* taps, int cap) {
 }
 
 static double level_sigma(float sig_a, float sig_b, int r) { return (double)sig_a * (double)r + (double)sig_b; }
-static int level_radius(float sig_a, float sig_b, int r) { return (int)std::ceil(3.0 * level_sigma(sig_a, sig_b, r)); }
+// window half-width in cells of c px: ceil(3 sigma(r) / c)
+static int level_radius(float sig_a, float sig_b, int r, int c = 1) {
+  return (int)std::ceil(3.0 * (level_sigma(sig_a, sig_b, r) / (double)c));
+}
 
-static int level_weights_impl(float sig_a, float sig_b, int r, int32_t* w, int cap) {
-  const double sg = level_sigma(sig_a, sig_b, r);
+// weights of level r on a grid of c-px cells: the Gaussian of sigma(r) / c
+// (c a power of two, so the division is exact)
+static int level_weights_impl(float sig_a, float sig_b, int r, int32_t* w, int cap, int c = 1) {
+  const double sg = level_sigma(sig_a, sig_b, r) / (double)c;
   const int Rs = (int)std::ceil(3.0 * sg);
   const int Wq = 2 * Rs + 1;
   if ((long long)Wq * Wq > cap) return -1;
@@ -207,6 +213,9 @@ static std::string validate(const rd_params* p) {
   if (!(p->sig_a >= 0.0f) || !std::isfinite(p->sig_a) || !std::isfinite(p->sig_b)) return "sig_a must be >= 0";
   if (!(level_sigma(p->sig_a, p->sig_b, p->r_min - 1) > 0.0)) return "sigma(r) must be > 0 for every level";
   if (level_radius(p->sig_a, p->sig_b, p->r_max + 1) > MAX_RS) return "level smoothing radius ceil(3 sigma(r)) above 40";
+  if (p->coarse != 0 && p->coarse != 1 && p->coarse != 2 && p->coarse != 4) return "coarse must be 0, 1, 2 or 4";
+  if (p->coarse > 1 && (long long)p->vote_thresh * p->coarse * p->coarse > 65534)
+    return "vote_thresh * coarse^2 must be at most 65534";
   return "";
 }
 
@@ -214,17 +223,18 @@ static std::string validate(const rd_params* p) {
 // Geometries chosen by rd_autotune, per (H, W, r_min, r_max), for this process.
 namespace {
 struct TuneKey {
-  int H, W, r_min, r_max;
+  int H, W, r_min, r_max, coarse;
   bool operator<(const TuneKey& o) const {
-    return std::tie(H, W, r_min, r_max) < std::tie(o.H, o.W, o.r_min, o.r_max);
+    return std::tie(H, W, r_min, r_max, coarse) < std::tie(o.H, o.W, o.r_min, o.r_max, o.coarse);
   }
 };
+int coarse_of(const rd_params* p) { return p->coarse > 1 ? p->coarse : 1; }
 std::mutex g_tune_mutex;
 std::map<TuneKey, rd_geometry> g_tuned;
 
 bool tuned_geometry(const rd_params* p, int H, int W, rd_geometry* g) {
   std::lock_guard<std::mutex> lock(g_tune_mutex);
-  auto it = g_tuned.find(TuneKey{H, W, p->r_min, p->r_max});
+  auto it = g_tuned.find(TuneKey{H, W, p->r_min, p->r_max, coarse_of(p)});
   if (it == g_tuned.end()) return false;
   *g = it->second;
   return true;
@@ -255,6 +265,8 @@ extern "C" rd_status rd_create_ex(const rd_params* params, int max_H, int max_W,
 
   rd_ctx* c = new rd_ctx();
   c->p = *params;
+  c->p.coarse = coarse_of(params);
+  c->lc = c->p.coarse == 4 ? 2 : (c->p.coarse == 2 ? 1 : 0);
   c->max_H = max_H;
   c->max_W = max_W;
   c->max_batch = max_batch;
@@ -279,12 +291,12 @@ extern "C" rd_status rd_create_ex(const rd_params* params, int max_H, int max_W,
   c->max_qn = 1;
   for (int li = 0; li < c->n_levels; ++li) {
     int r = lv0 + li;
-    int Rs = level_radius(params->sig_a, params->sig_b, r);
+    int Rs = level_radius(params->sig_a, params->sig_b, r, 1 << c->lc);
     int nq = (2 * Rs + 1) * (2 * Rs + 1);
     h_qoff[li] = (int)h_qtab.size();
     h_qrad[li] = Rs;
     h_qtab.resize(h_qtab.size() + nq);
-    level_weights_impl(params->sig_a, params->sig_b, r, h_qtab.data() + h_qoff[li], nq);
+    level_weights_impl(params->sig_a, params->sig_b, r, h_qtab.data() + h_qoff[li], nq, 1 << c->lc);
     h_nthr[li] = (unsigned long long)peak_threshold_impl(params->peak_frac, r);
     c->max_qn = std::max(c->max_qn, nq + (nq & 1));
   }
@@ -379,7 +391,8 @@ extern "C" rd_status rd_create_ex(const rd_params* params, int max_H, int max_W,
   }
   // workspaces
   const int n_stx = (max_W + ST_TW - 1) / ST_TW, n_sty = (max_H + ST_TH - 1) / ST_TH;
-  const int n_atx = (max_W + c->T - 1) / c->T, n_aty = (max_H + c->T - 1) / c->T;
+  const int max_Wc = ((max_W - 1) >> c->lc) + 1, max_Hc = ((max_H - 1) >> c->lc) + 1;  // cells
+  const int n_atx = (max_Wc + c->T - 1) / c->T, n_aty = (max_Hc + c->T - 1) / c->T;
   c->rl.cap = std::max(4096, (int)std::min<long long>((long long)max_H * max_W / 4, 1LL << 24));
   c->rl.n_stx = n_stx;
   c->rl.n_sty = n_sty;
@@ -452,7 +465,8 @@ static rd_status detect_enqueue(rd_ctx* c, const void* frames_dev, int n, int H,
   c->last_W = W;
 
   const int n_stx = (W + ST_TW - 1) / ST_TW, n_sty = (H + ST_TH - 1) / ST_TH;
-  const int n_atx = (W + c->T - 1) / c->T, n_aty = (H + c->T - 1) / c->T;
+  const int Wc = ((W - 1) >> c->lc) + 1, Hc = ((H - 1) >> c->lc) + 1;  // parameter-space cells
+  const int n_atx = (Wc + c->T - 1) / c->T, n_aty = (Hc + c->T - 1) / c->T;
   const long long n_bins = (long long)n * n_atx * n_aty * c->n_slabs;
   RidgeList rl = c->rl;
   rl.n_stx = n_stx;
@@ -520,8 +534,10 @@ static rd_status detect_enqueue(rd_ctx* c, const void* frames_dev, int n, int H,
   BinArgs ba;
   ba.rl = rl;
   ba.n_frames = n;
-  ba.H = H;
-  ba.W = W;
+  ba.H = Hc;
+  ba.W = Wc;
+  ba.lc = c->lc;
+  ba.inv_c = 1.0f / (float)(1 << c->lc);
   ba.n_atx = n_atx;
   ba.n_aty = n_aty;
   ba.n_slabs = c->n_slabs;
@@ -540,8 +556,9 @@ static rd_status detect_enqueue(rd_ctx* c, const void* frames_dev, int n, int H,
   VoteArgs va;
   va.rl = rl;
   va.n_frames = n;
-  va.H = H;
-  va.W = W;
+  va.H = Hc;
+  va.W = Wc;
+  va.lc = c->lc;
   va.n_atx = n_atx;
   va.n_aty = n_aty;
   va.n_slabs = c->n_slabs;
@@ -558,7 +575,7 @@ static rd_status detect_enqueue(rd_ctx* c, const void* frames_dev, int n, int H,
   va.nthr = c->nthr;
   va.r_min = c->p.r_min;
   va.r_max = c->p.r_max;
-  va.vote_thresh = c->p.vote_thresh;
+  va.vote_thresh = c->p.vote_thresh << (2 * c->lc);  // per cell: T_int c^2
   va.peaks = c->peaks;
   va.peak_cap = c->peak_cap;
   va.peak_count = c->peak_count;
@@ -597,8 +614,9 @@ static rd_status detect_enqueue(rd_ctx* c, const void* frames_dev, int n, int H,
   fa.offsets = offsets_dev;
   fa.rings = rings_dev;
   fa.ring_cap = ring_cap;
-  fa.w = c->p.annulus_w;
-  fa.w_int = (std::floor(c->p.annulus_w) == c->p.annulus_w) ? 1 : 0;
+  // a coarse peak's centre is known to within c / sqrt 2 px: the annulus widens by c - 1
+  fa.w = c->p.annulus_w + (float)((1 << c->lc) - 1);
+  fa.w_int = (std::floor(fa.w) == fa.w) ? 1 : 0;
   fa.stats = c->stats;
   chk(launch_fit(fa, c->peaks, counts_dev, offsets_dev, st));
   mark(5);
@@ -857,7 +875,7 @@ extern "C" rd_status rd_autotune(const rd_params* params, const void* frames_dev
   if (bg.tile == 0) return fail(nullptr, last, "rd_autotune: " + last_msg);
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tuned[TuneKey{H, W, params->r_min, params->r_max}] = bg;
+    g_tuned[TuneKey{H, W, params->r_min, params->r_max, coarse_of(params)}] = bg;
   }
   *best = bg;
   return RD_OK;

@@ -85,21 +85,25 @@ struct StencilArgs {
 
 struct BinArgs {
   RidgeList rl;
-  int n_frames, H, W;
+  int n_frames, H, W;          // H, W: the accumulator grid in cells (the image for lc = 0)
   int n_atx, n_aty, n_slabs, T;
+  int lc;                      // log2 of the cell edge in px (coarse parameter space); 0, 1 or 2
+  float inv_c;                 // 2^-lc
   const int4* slabs;           // (lo, hi, halo, 0): peak levels lo..hi, votes lo-1..hi+1
   int* bin_cnt;
   const int* bin_off;
   int* bin_fill;
-  uint4* pool;               // per entry: int16 x | int16 y << 16 relative to the tile region
-                             // (origin (tx T - h, ty T - h)), s X, s Y, index << 2 | ill << 1 | (s < 0)
+  uint4* pool;               // per entry: int16 x | int16 y << 16 in px relative to the tile region
+                             // (origin 2^lc (tx T - h, ty T - h)), s X, s Y,
+                             // index << 3 | exact axis << 2 | ill << 1 | (s < 0)
   long long pool_cap;
   DevStats* stats;
 };
 
 struct VoteArgs {
   RidgeList rl;
-  int n_frames, H, W, n_atx, n_aty, n_slabs, T;
+  int n_frames, H, W, n_atx, n_aty, n_slabs, T;  // H, W: the accumulator grid in cells
+  int lc;                    // log2 of the cell edge in px (coarse parameter space)
   const int4* slabs;
   const int* bin_cnt;
   const int* bin_off;
@@ -277,6 +281,14 @@ __device__ __forceinline__ int vote_bin64(int p, double sr, double X) {
   return (int)floor(d_add(a, 0.5));
 }
 
+// Cell of one coordinate in a coarse parameter space of c = 2^lc px cells:
+// floor((a + c/2) / c), a = p + sr X, the sums rounded once each and the
+// division exact.
+__device__ __forceinline__ int vote_cell64(int p, double sr, double X, int lc) {
+  double a = d_add((double)p, d_mul(sr, X));
+  return (int)floor(d_mul(d_add(a, 0.5 * (double)(1 << lc)), 1.0 / (double)(1 << lc)));
+}
+
 // ---------------------------------------------------------------------------
 // double-float (hi + lo) arithmetic with explicit round-to-nearest intrinsics
 // (no contraction can break the error-free transformations)
@@ -362,6 +374,30 @@ __device__ __forceinline__ int vote_offset(float sr, float r, float xhi, float x
   bool low_bad = p2 < __fsub_rn(-mr, e2);           // d < -mr
   bool up_ok = (p2 < 0.5f) || (q2 > __fadd_rn(mr, e2));   // 1 - d > mr
   bool up_bad = (p2 >= 0.5f) && (q2 < __fsub_rn(e2, mr)); // d > 1 + mr
+  if (low_ok && up_ok) return (int)n;
+  if (low_bad) return (int)n - 1;
+  if (up_bad) return (int)n + 1;
+  return INT_MIN;
+}
+
+// floor(sr X_def) with the same margins (a coarse parameter space bins votes
+// by cells whose edges are at integer offsets from the pixel), or INT_MIN
+// when the margins cannot decide.
+__device__ __forceinline__ int vote_floor(float sr, float r, float xhi, float xlo, float kfast, float kref) {
+  float t = __fmul_rn(sr, xhi);
+  float n = floorf(t);
+  float p = __fsub_rn(t, n);  // exact: distance above the lower boundary, in [0, 1)
+  float m = __fmaf_rn(r, kfast, 1e-10f);
+  if (p > m && (p < 0.5f || __fsub_rn(1.0f, p) > m)) return (int)n;
+  dfl tp = two_prod(sr, xhi);
+  float e2 = __fmaf_rn(sr, xlo, tp.lo);
+  float p2 = __fsub_rn(tp.hi, n);  // exact
+  float q2 = __fsub_rn(1.0f, p2);  // exact when p2 >= 1/2
+  float mr = __fmaf_rn(r, kref, 1e-10f);
+  bool low_ok = p2 > __fsub_rn(mr, e2);
+  bool low_bad = p2 < __fsub_rn(-mr, e2);
+  bool up_ok = (p2 < 0.5f) || (q2 > __fadd_rn(mr, e2));
+  bool up_bad = (p2 >= 0.5f) && (q2 < __fsub_rn(e2, mr));
   if (low_ok && up_ok) return (int)n;
   if (low_bad) return (int)n - 1;
   if (up_bad) return (int)n + 1;

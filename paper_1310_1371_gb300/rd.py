@@ -25,7 +25,7 @@ PEAK_CAP = 4096   # per-frame peak capacity of a context
 class rd_params(ctypes.Structure):
     _fields_ = [("sigma", c_float), ("r_min", c_int), ("r_max", c_int), ("ridge_thresh", c_float),
                 ("peak_frac", c_float), ("vote_thresh", c_int), ("annulus_w", c_float),
-                ("sig_a", c_float), ("sig_b", c_float)]
+                ("sig_a", c_float), ("sig_b", c_float), ("coarse", c_int)]
 
 
 class rd_ring(ctypes.Structure):
@@ -116,7 +116,7 @@ class RdError(RuntimeError):
 def make_params(**kw) -> rd_params:
     return rd_params(float(kw["sigma"]), int(kw["r_min"]), int(kw["r_max"]), float(kw["ridge_thresh"]),
                      float(kw["peak_frac"]), int(kw["vote_thresh"]), float(kw.get("annulus_w", 2.0)),
-                     float(kw.get("sig_a", 0.05)), float(kw.get("sig_b", 0.25)))
+                     float(kw.get("sig_a", 0.05)), float(kw.get("sig_b", 0.25)), int(kw.get("coarse", 1) or 1))
 
 
 # ---- host-only helpers -----------------------------------------------------------

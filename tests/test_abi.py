@@ -68,7 +68,7 @@ def test_create_rejects_bad_params(lib):
     good = dict(sigma=2.0, r_min=5, r_max=40, ridge_thresh=-1.0, peak_frac=0.35, vote_thresh=3)
     bad = [dict(good, sigma=0.0), dict(good, sigma=5.0), dict(good, r_min=1), dict(good, r_max=4),
            dict(good, ridge_thresh=0.5), dict(good, peak_frac=-1.0), dict(good, vote_thresh=-1),
-           dict(good, r_max=600)]
+           dict(good, r_max=600), dict(good, coarse=3), dict(good, coarse=8), dict(good, coarse=-2)]
     for kw in bad:
         p = rd.make_params(**kw)
         ctx = ctypes.c_void_p()
