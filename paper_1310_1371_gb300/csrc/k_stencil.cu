@@ -247,13 +247,44 @@ __global__ void __launch_bounds__(ST_THREADS, 4) k_stencil_ridge(StencilArgs a) 
     const int lane = tid & 31, warp = tid >> 5;
     const bool interior = x0 >= HALO && y0 >= HALO && x0 + ST_TW + HALO <= W && y0 + ST_TH + HALO <= H;
     const int IWn = ST_TW + 2 * HALO;  // columns loaded (IW is the padded stride)
-    for (int iy = warp; iy < IH; iy += ST_THREADS / 32) {
-      const int gy = interior ? y0 - HALO + iy : reflect101(y0 - HALO + iy, H);
-      const Tin* row = img + (size_t)gy * W;
-      uint32_t* dst = sI + iy * IW;
-      for (int ix = lane; ix < IWn; ix += 32) {
-        const int gx = interior ? x0 - HALO + ix : reflect101(x0 - HALO + ix, W);
-        dst[ix] = (uint32_t)row[gx];
+    if constexpr (RC > 0) {
+      // all of a thread's loads are issued before its first store, so that
+      // their latencies overlap
+      constexpr int IHc = ST_TH + 2 * (RC + 3), IWc = ST_TW + 2 * (RC + 3);
+      constexpr int NR = (IHc + ST_THREADS / 32 - 1) / (ST_THREADS / 32), NC = (IWc + 31) / 32;
+      uint32_t v[NR][NC];
+#pragma unroll
+      for (int k = 0; k < NR; ++k) {
+        // rows and columns past the tile re-read its last row / column (every
+        // address stays inside the tile's footprint); they are not stored
+        const int iy = min(warp + k * (ST_THREADS / 32), IHc - 1);
+        const int gy = interior ? y0 - HALO + iy : reflect101(y0 - HALO + iy, H);
+        const Tin* row = img + (size_t)gy * W;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const int ix = min(lane + 32 * c, IWc - 1);
+          const int gx = interior ? x0 - HALO + ix : reflect101(x0 - HALO + ix, W);
+          v[k][c] = (uint32_t)row[gx];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < NR; ++k) {
+        const int iy = warp + k * (ST_THREADS / 32);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const int ix = lane + 32 * c;
+          if (iy < IHc && ix < IWc) sI[iy * IW + ix] = v[k][c];
+        }
+      }
+    } else {
+      for (int iy = warp; iy < IH; iy += ST_THREADS / 32) {
+        const int gy = interior ? y0 - HALO + iy : reflect101(y0 - HALO + iy, H);
+        const Tin* row = img + (size_t)gy * W;
+        uint32_t* dst = sI + iy * IW;
+        for (int ix = lane; ix < IWn; ix += 32) {
+          const int gx = interior ? x0 - HALO + ix : reflect101(x0 - HALO + ix, W);
+          dst[ix] = (uint32_t)row[gx];
+        }
       }
     }
   }

@@ -111,3 +111,33 @@ def test_accuracy_against_truth(torch):
         errs[c] = np.median(np.array(e), 0)
     for c in (1, 2, 4):
         assert np.all(errs[c] < 0.35), (c, errs[c])
+
+
+def test_directed_edges_coarse(torch):
+    """The directed-edge features (exact axes are common there: integer
+    gradients with one component exactly 0) voting into 2 px cells."""
+    from tests.test_gpu_edge import check as check_edge
+    f = synth.disc_small(seed=3002)
+    rings, ref = check_edge(torch, f.image, dict(f.params, coarse=2))
+    assert len(ref.rings) >= 6
+
+
+def test_batched_and_graph_replay(torch):
+    """Several frames in one call and a CUDA-graph replay give each frame's
+    single-frame result (cells of 4 px)."""
+    from paper_1310_1371_gb300 import rd
+    frames = [synth.plain_small(seed=s) for s in (21, 22, 23)]
+    params = dict(frames[0].params, coarse=4)
+    H, W = frames[0].image.shape
+    t = torch.from_numpy(np.stack([f.image for f in frames])).cuda()
+    det = rd.Detector(params, H, W, len(frames))
+    det.set_graph(True)
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    first, _ = det.detect(t, stream=stream)  # captured
+    again, _ = det.detect(t, stream=stream)  # replayed graph
+    det.close()
+    for i, f in enumerate(frames):
+        ref = O.detect(f.image, O.Params.make(**params))
+        for got in (first[i], again[i]):
+            assert_rings_match(got, ref.rings)
