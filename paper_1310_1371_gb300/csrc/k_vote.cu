@@ -658,6 +658,7 @@ constexpr int SP_HOT = 256;     // hotspots per level
 constexpr int SP_HASH = 512;    // hash slots per level (power of two, > 2 SP_HOT)
 constexpr int SP_PEAKS = 64;    // peaks buffered per CTA
 constexpr uint32_t SP_EMPTY = 0xffffffffu;
+constexpr int SP_SLOW = 32;     // votes per warp and level left to the exact path after the loop
 
 struct SparseSmem {
   size_t q, a, hash, coord, val, pk, total;
@@ -724,6 +725,7 @@ __device__ __forceinline__ void vote_bin_sparse(const VoteArgs& a, const int b, 
   int4* sPk = reinterpret_cast<int4*>(smem + L.pk);
   const int nA4 = (((RW * RW + 1) / 2) + 3) / 4;
   __shared__ int s_nhot[4], s_npk, s_abort;
+  __shared__ int s_nslow[SP_THREADS / 32], s_slow[SP_THREADS / 32][SP_SLOW];
   __shared__ unsigned s_sum[4];  // votes, fallbacks, owned hotspots, smoothing MACs of this bin
   // per voting level lo-1 .. hi+1 of the slab: R_s, offset of its tap orbits, peak threshold
   __shared__ int s_rad[MAX_SLAB_LEVELS + 2], s_qpo[MAX_SLAB_LEVELS + 2];
@@ -741,6 +743,7 @@ __device__ __forceinline__ void vote_bin_sparse(const VoteArgs& a, const int b, 
     s_abort = a.route_dense;
     for (int k = 0; k < 4; ++k) s_sum[k] = 0;
   }
+  if (lane == 0) s_nslow[warp] = 0;
   if (tid <= hi - lo + 2) {
     const int li = lo - 1 + tid - (a.r_min - 1);
     s_rad[tid] = a.q_rad[li];
@@ -777,43 +780,10 @@ __device__ __forceinline__ void vote_bin_sparse(const VoteArgs& a, const int b, 
     unsigned nv = 0, nfb = 0;
     uint4 En = make_uint4(0u, 0u, 0u, 0u);  // next round's entry, loaded one round ahead
     if (tid < cnt) En = __ldg(&bin[tid]);
-    for (int j = 0; j < rounds; ++j) {
-      const int e = j * SP_THREADS + tid;
-      const uint4 E = En;
-      if (e + SP_THREADS < cnt) En = __ldg(&bin[e + SP_THREADS]);
-      if (e >= cnt) continue;
-      const float tx_ = __fmul_rn(rf, __uint_as_float(E.y)), ty_ = __fmul_rn(rf, __uint_as_float(E.z));
-      const float fx = __fadd_rn(tx_, ROUND_MAGIC), fy = __fadd_rn(ty_, ROUND_MAGIC);
-      const float dx = __fsub_rn(tx_, __fsub_rn(fx, ROUND_MAGIC));
-      const float dy = __fsub_rn(ty_, __fsub_rn(fy, ROUND_MAGIC));
-      int ox = __float_as_int(fx) - ROUND_MAGIC_BITS, oy = __float_as_int(fy) - ROUND_MAGIC_BITS;
-      // pixels: round to nearest, certain away from half-integers; cells:
-      // floor, certain away from integers
-      const bool sure = COARSE ? (fminf(fabsf(dx), fabsf(dy)) > m_r || (E.w & 4u)) : fmaxf(fabsf(dx), fabsf(dy)) < half_m;
-      if ((E.w & 2u) || !sure) {
-        VEnt v;
-        v.xy = E.x;
-        v.ent = ((E.w >> 3) << 1) | (E.w & 1u);
-        v.X = v.Y = 0.0f;
-        v.kf = 0.0f;
-        const int3 o = vote_bins_slow(a, fbase, v, ent_lx(E.x) + (ox0 << a.lc), ent_ly(E.x) + (oy0 << a.lc), rf);
-        nfb += o.z;
-        ox = o.x;
-        oy = o.y;
-      } else if (COARSE) {
-        ox -= dx < 0.0f ? 1 : 0;
-        oy -= dy < 0.0f ? 1 : 0;
-      }
-      int lx, ly;
-      if (COARSE) {
-        const int hc = 1 << (a.lc - 1);
-        lx = (ent_lx(E.x) + ox + hc) >> a.lc;
-        ly = (ent_ly(E.x) + oy + hc) >> a.lc;
-      } else {
-        lx = ent_lx(E.x) + ox;
-        ly = ent_ly(E.x) + oy;
-      }
-      if ((unsigned)(lx - lxlo) >= (unsigned)lxn || (unsigned)(ly - lylo) >= (unsigned)lyn) continue;
+    // One vote into the slab: bounds, ownership count, packed-u16 atomic,
+    // hotspot registration on the increment that crosses the threshold.
+    auto cast = [&](int lx, int ly) {
+      if ((unsigned)(lx - lxlo) >= (unsigned)lxn || (unsigned)(ly - lylo) >= (unsigned)lyn) return;
       if (owned && (unsigned)(lx - h) < (unsigned)T && (unsigned)(ly - h) < (unsigned)T) ++nv;
       const int la = ly * RW + lx;
       const unsigned sh = (la & 1) << 4;
@@ -829,6 +799,58 @@ __device__ __forceinline__ void vote_bin_sparse(const VoteArgs& a, const int b, 
           }
         }
       }
+    };
+    for (int j = 0; j < rounds; ++j) {
+      const int e = j * SP_THREADS + tid;
+      const uint4 E = En;
+      if (e + SP_THREADS < cnt) En = __ldg(&bin[e + SP_THREADS]);
+      if (e >= cnt) continue;
+      const float tx_ = __fmul_rn(rf, __uint_as_float(E.y)), ty_ = __fmul_rn(rf, __uint_as_float(E.z));
+      const float fx = __fadd_rn(tx_, ROUND_MAGIC), fy = __fadd_rn(ty_, ROUND_MAGIC);
+      const float dx = __fsub_rn(tx_, __fsub_rn(fx, ROUND_MAGIC));
+      const float dy = __fsub_rn(ty_, __fsub_rn(fy, ROUND_MAGIC));
+      int ox = __float_as_int(fx) - ROUND_MAGIC_BITS, oy = __float_as_int(fy) - ROUND_MAGIC_BITS;
+      // pixels: round to nearest, certain away from half-integers; cells:
+      // floor, certain away from integers
+      const bool sure = COARSE ? (fminf(fabsf(dx), fabsf(dy)) > m_r || (E.w & 4u)) : fmaxf(fabsf(dx), fabsf(dy)) < half_m;
+      if ((E.w & 2u) || !sure) {  // the exact path takes it after the loop
+        const int k = atomicAdd(&s_nslow[warp], 1);
+        if (k < SP_SLOW)
+          s_slow[warp][k] = e;
+        else
+          s_abort = 1;
+        continue;
+      }
+      if (COARSE) {
+        ox -= dx < 0.0f ? 1 : 0;
+        oy -= dy < 0.0f ? 1 : 0;
+        const int hc = 1 << (a.lc - 1);
+        cast((ent_lx(E.x) + ox + hc) >> a.lc, (ent_ly(E.x) + oy + hc) >> a.lc);
+      } else {
+        cast(ent_lx(E.x) + ox, ent_ly(E.x) + oy);
+      }
+    }
+    __syncwarp();
+    {
+      const int ns = min(s_nslow[warp], SP_SLOW);
+      for (int k = lane; k < ns; k += 32) {
+        const uint4 E = __ldg(&bin[s_slow[warp][k]]);
+        VEnt v;
+        v.xy = E.x;
+        v.ent = ((E.w >> 3) << 1) | (E.w & 1u);
+        v.X = v.Y = 0.0f;
+        v.kf = 0.0f;
+        const int3 o = vote_bins_slow(a, fbase, v, ent_lx(E.x) + (ox0 << a.lc), ent_ly(E.x) + (oy0 << a.lc), rf);
+        nfb += o.z;
+        if (COARSE) {
+          const int hc = 1 << (a.lc - 1);
+          cast((ent_lx(E.x) + o.x + hc) >> a.lc, (ent_ly(E.x) + o.y + hc) >> a.lc);
+        } else {
+          cast(ent_lx(E.x) + o.x, ent_ly(E.x) + o.y);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) s_nslow[warp] = 0;
     }
     t_votes += nv;
     t_fb += nfb;
