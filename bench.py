@@ -161,7 +161,8 @@ def run_ours(args):
     params = synth.PLAIN_FULL_PARAMS
     imgs = np.stack(make_frames(B, rank))
     frames = torch.from_numpy(imgs).cuda()
-    det = rd.Detector(params, H, W, B)
+    geo = (args.tile, args.slab) if args.tile else None  # None: the automatic geometry
+    det = rd.Detector(params, H, W, B, geometry=geo)
     stream = torch.cuda.current_stream()
 
     # warm-up (also the parity smoke of this launch: overflow must not occur)
@@ -205,7 +206,7 @@ def run_ours(args):
     #      frames, so that one call's copies overlap the other's kernels, as a
     #      client streaming batches would
     import threading
-    det2 = rd.Detector(params, H, W, B)
+    det2 = rd.Detector(params, H, W, B, geometry=geo)
     dets = [det, det2]
     hosts = [torch.from_numpy(imgs).pin_memory().numpy() for _ in range(2)]
     streams = [torch.cuda.Stream(), torch.cuda.Stream()]
@@ -284,7 +285,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "batch_frames": B, "frames_bytes": int(imgs.nbytes),
                        "l2": (f"inputs ({imgs.nbytes / 2**20:.0f} MiB) larger than L2; no flush" if imgs.nbytes > 129e6
                               else f"inputs ({imgs.nbytes / 2**20:.0f} MiB) fit in L2: L2-warm"),
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}", "geometry": list(det.geometry())},
             "mvotes_per_s": votes_per_step * args.steps * world / (ms / 1e3) / 1e6,
             "votes_per_frame": votes_per_step / B, "ridge_pixels_per_frame": ridge_per_step / B,
             "rings_per_frame": stats.peaks / B, "exact_fallbacks_per_frame": stats.exact_fallbacks / B,
@@ -738,8 +739,9 @@ def main():
     ap.add_argument("--workload", default="plain_full",
                     choices=["plain_full", "video", "diff", "serve", "discs", "coarse"])
     ap.add_argument("--coarse", type=int, default=2, choices=[2, 4])
-    ap.add_argument("--tile", type=int, default=0, help="accumulator tile (cells) of the coarse run; 0: automatic")
-    ap.add_argument("--slab", type=int, default=16, help="slab levels of the coarse run with --tile")
+    ap.add_argument("--tile", type=int, default=0,
+                    help="accumulator tile (cells) of the default and coarse workloads; 0: automatic")
+    ap.add_argument("--slab", type=int, default=16, help="slab levels with --tile")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=500.0)
     ap.add_argument("--serve-pool", type=int, default=8)

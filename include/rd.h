@@ -235,10 +235,10 @@ rd_status rd_set_features(rd_ctx* ctx, int features, float edge_thresh);
  * SM's shared memory (Results, "Directed ridge detection & votes
  * collection"; the paper streams whole equi-radius levels instead).  The
  * geometry changes speed only: results are bit-identical for every valid
- * geometry.  tile is 64, 80, 96 or 128; slab_levels is 4 .. 16; 0 in both
+ * geometry.  tile is 64, 80, 96 or 128; slab_levels is 4 .. 64; 0 in both
  * fields asks for the automatic choice (the autotuner's cached choice for
  * this frame size and radius range if there is one, else the first of
- * 128 x 16 levels, 96 x 12 and 64 x 12 whose per-tile storage fits the
+ * 128 x 32 levels, 96 x 12 and 64 x 12 whose per-tile storage fits the
  * radius range's smoothing windows). */
 typedef struct rd_geometry {
   int tile;

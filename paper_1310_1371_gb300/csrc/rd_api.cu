@@ -256,7 +256,7 @@ extern "C" rd_status rd_create_ex(const rd_params* params, int max_H, int max_W,
   const bool automatic = geo.tile == 0 && geo.slab_levels == 0;
   if (!automatic && ((geo.tile != ACC_T_LARGE && geo.tile != ACC_T && geo.tile != ACC_T_MID && geo.tile != ACC_T_SMALL) ||
                      geo.slab_levels < 4 || geo.slab_levels > MAX_SLAB_LEVELS))
-    return fail(nullptr, RD_E_INVAL, "geometry: tile must be 64, 80, 96 or 128 and slab_levels 4 .. 16 (or both 0)");
+    return fail(nullptr, RD_E_INVAL, "geometry: tile must be 64, 80, 96 or 128 and slab_levels 4 .. 64 (or both 0)");
   if (automatic && !tuned_geometry(params, max_H, max_W, &geo)) geo = rd_geometry{0, 0};
   const int R = gaussian_radius(params->sigma);
   if (max_H < R + 4 || max_W < R + 4 || max_H < 12 || max_W < 12 || max_H > 65535 || max_W > 65535)
@@ -300,7 +300,7 @@ extern "C" rd_status rd_create_ex(const rd_params* params, int max_H, int max_W,
     h_nthr[li] = (unsigned long long)peak_threshold_impl(params->peak_frac, r);
     c->max_qn = std::max(c->max_qn, nq + (nq & 1));
   }
-  // Automatic geometry: the first of 128/16, 96/12 and 64/12 whose storage
+  // Automatic geometry: the first of 128/32, 96/12 and 64/12 whose storage
   // fits -- for 128 the sparse kernel at three CTAs per SM; always the dense
   // fallback's per-tile storage on one SM (it splits 128-pixel tiles into
   // four 64-pixel ones).  Larger tiles cast fewer halo votes per owned voxel
@@ -323,8 +323,8 @@ extern "C" rd_status rd_create_ex(const rd_params* params, int max_H, int max_W,
            (!three_per_sm || 3 * (sp + 1024) <= 228 * 1024);
   };
   if (geo.tile == 0) {
-    if (fits(ACC_T_LARGE, MAX_SLAB_LEVELS, true))
-      geo = rd_geometry{ACC_T_LARGE, MAX_SLAB_LEVELS};
+    if (fits(ACC_T_LARGE, DEFAULT_SLAB_LEVELS, true))
+      geo = rd_geometry{ACC_T_LARGE, DEFAULT_SLAB_LEVELS};
     else if (fits(ACC_T, SLAB_LEVELS, false))
       geo = rd_geometry{ACC_T, SLAB_LEVELS};
     else
@@ -836,9 +836,9 @@ extern "C" rd_status rd_autotune(const rd_params* params, const void* frames_dev
   rd_status last = RD_E_NOMEM;
   std::string last_msg = "no candidate geometry could allocate its workspaces";
   const int tiles[4] = {ACC_T_SMALL, ACC_T_MID, ACC_T, ACC_T_LARGE};
-  const int slabs[3] = {8, 12, 16};
+  const int slabs[4] = {8, 16, 24, 32};
   for (int ti = 0; ti < 4 && res == RD_OK; ++ti)
-    for (int si = 0; si < 3 && res == RD_OK; ++si) {
+    for (int si = 0; si < 4 && res == RD_OK; ++si) {
       const rd_geometry g{tiles[ti], slabs[si]};
       rd_ctx* c = nullptr;
       rd_status s = rd_create_ex(params, H, W, n, &g, &c);

@@ -34,7 +34,8 @@ constexpr int ACC_T_SMALL = 64;
 constexpr int VOTE_THREADS = 256;
 constexpr int MAX_RS = 40;         // level smoothing half-width ceil(3 sigma(r))
 constexpr int SLAB_LEVELS = 12;    // default peak levels per r-slab
-constexpr int MAX_SLAB_LEVELS = 16;
+constexpr int MAX_SLAB_LEVELS = 64;
+constexpr int DEFAULT_SLAB_LEVELS = 32;  // the automatic geometry's slab depth
 constexpr int FIT_WARPS = 8;
 // Vote-rounding margin coefficient shared by every well-conditioned ridge
 // pixel: 1.25 (|X_lo| + e_X + 2^-24) + 2^-24 with |X_lo| <= 2^-25 and the

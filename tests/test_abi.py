@@ -91,7 +91,7 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.rd_debug_ridges(None, 0, None, None, None, 0) == -1
 
 
-@pytest.mark.parametrize("geo", [(72, 12), (96, 3), (96, 17), (0, 8), (64, 0)])
+@pytest.mark.parametrize("geo", [(72, 12), (96, 3), (96, 65), (0, 8), (64, 0)])
 def test_bad_geometry_rejected(lib, geo):
     """rd_create_ex validates the accumulator geometry before touching the GPU."""
     from paper_1310_1371_gb300 import rd, synth

@@ -37,7 +37,8 @@ def same(a, b):
             assert np.array_equal(x[k], y[k]), k
 
 
-@pytest.mark.parametrize("geometry", [(64, 8), (64, 4), (80, 12), (96, 12), (96, 16), (128, 16), (128, 8)])
+@pytest.mark.parametrize("geometry", [(64, 8), (64, 4), (80, 12), (96, 12), (96, 16), (128, 16), (128, 8),
+                                      (128, 32), (128, 64), (64, 40)])
 def test_geometry_does_not_change_results(torch, geometry):
     frames = [synth.plain_small(seed=s).image for s in (51, 52)]
     params = synth.PLAIN_SMALL_PARAMS
@@ -70,7 +71,7 @@ def test_autotune_choice_is_used(torch):
     params = dict(synth.PLAIN_SMALL_PARAMS, r_max=39)  # a key no other test tunes
     t = torch.from_numpy(np.stack(frames)).cuda()
     best = rd.rd_autotune(params, t)
-    assert best[0] in (64, 80, 96) and best[1] in (8, 12, 16)
+    assert best[0] in (64, 80, 96, 128) and best[1] in (8, 16, 24, 32)
     det = rd.Detector(params, 256, 256, 4)  # automatic geometry: the tuned one
     assert det.geometry() == best
     rings, _ = det.detect(t)
