@@ -84,6 +84,47 @@ __device__ __forceinline__ void hess_exact(const unsigned long long* sL, int PW,
   }
 }
 
+// Exact first-order 5x5 Sobel of L' at Hessian-tile coordinates (hy, hx):
+// (Gx', Gy') = 128 S^2 (Gx, Gy).
+__device__ __forceinline__ void grad_exact(const unsigned long long* sL, int PW, int hy, int hx, long long& gx,
+                                           long long& gy) {
+  const long long s5[5] = {1, 4, 6, 4, 1}, d1[5] = {-1, -2, 0, 2, 1};
+  gx = gy = 0;
+#pragma unroll
+  for (int dy = 0; dy < 5; ++dy) {
+    const long long* row = reinterpret_cast<const long long*>(sL) + (hy + dy) * PW + hx;
+    const long long l0 = row[0], l1 = row[1], l2 = row[2], l3 = row[3], l4 = row[4];
+    const long long sx = l0 + 4 * (l1 + l3) + 6 * l2 + l4;
+    const long long d1x = (l4 - l0) + 2 * (l3 - l1);
+    gx += s5[dy] * d1x;
+    gy += d1[dy] * sx;
+  }
+}
+
+// The directed-edge definition in double precision (Additional notes: the
+// gradient replaces the Hessian): (Gx, Gy) = (Gx', Gy') / D, |grad| =
+// sqrt(Gx^2 + Gy^2), and where |grad| > thresh (and > 0) the unit direction
+// with X > 0 or (X = 0 and Y > 0), else (0, 0); one correctly rounded
+// operation per step.
+struct Grad64 {
+  double g, X, Y;
+};
+__device__ __forceinline__ Grad64 grad64(long long gx, long long gy, double D, double thresh) {
+  const double Gx = d_div(__ll2double_rn(gx), D), Gy = d_div(__ll2double_rn(gy), D);
+  Grad64 r;
+  r.g = d_sqrt(d_add(d_mul(Gx, Gx), d_mul(Gy, Gy)));
+  r.X = r.Y = 0.0;
+  if (r.g != 0.0 && r.g > thresh) {
+    r.X = d_div(Gx, r.g);
+    r.Y = d_div(Gy, r.g);
+    if (r.X < 0.0 || (r.X == 0.0 && r.Y < 0.0)) {
+      r.X = -r.X;
+      r.Y = -r.Y;
+    }
+  }
+  return r;
+}
+
 // Pixels per step of the exact test (9 threads each).
 constexpr int FB_CHUNK = ST_THREADS / 9;
 
@@ -166,6 +207,18 @@ __device__ __forceinline__ void hess32(const float* Rs, const float* Rd2, const 
   fc = __fmul_rn(hyy, invD);
 }
 
+// FP32 gradient (Gx, Gy) = fl(G') x fl(1/D) at Hessian-tile index c0 from
+// the row filters: the column filter s of d1 rows, and d1 of s rows.
+__device__ __forceinline__ void grad32(const float* Rs, const float* Rd1, int st, int c0, float invD, float& gx,
+                                       float& gy) {
+  const float x0 = Rd1[c0], x1 = Rd1[c0 + st], x2 = Rd1[c0 + 2 * st], x3 = Rd1[c0 + 3 * st], x4 = Rd1[c0 + 4 * st];
+  const float Gx = __fmaf_rn(6.0f, x2, __fmaf_rn(4.0f, __fadd_rn(x1, x3), __fadd_rn(x0, x4)));
+  const float y0 = Rs[c0], y1 = Rs[c0 + st], y3 = Rs[c0 + 3 * st], y4 = Rs[c0 + 4 * st];
+  const float Gy = __fmaf_rn(2.0f, __fsub_rn(y3, y1), __fsub_rn(y4, y0));
+  gx = __fmul_rn(Gx, invD);
+  gy = __fmul_rn(Gy, invD);
+}
+
 // Shared-memory layout of K1 (byte offsets, all 8-byte aligned): the exact
 // smoothed tile L' (u64, alive to the end), one region holding first the
 // input tile and the horizontal pass (u32) and then the FP32 row filters of
@@ -197,7 +250,9 @@ __host__ __device__ __forceinline__ StencilSmem stencil_smem_layout(int R) {
 
 // RC > 0: the Gaussian half-width R is the compile-time RC (taps unrolled,
 // two outputs per thread from a register window); RC = 0: R from the taps.
-template <typename Tin, int RC>
+// EDGE: directed edges (Additional notes) -- the gradient replaces the
+// Hessian and -|grad| takes the place of k- in every test below.
+template <typename Tin, int RC, bool EDGE>
 __global__ void __launch_bounds__(ST_THREADS, 4) k_stencil_ridge(StencilArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x;
@@ -390,17 +445,30 @@ __global__ void __launch_bounds__(ST_THREADS, 4) k_stencil_ridge(StencilArgs a) 
   // Lyy 64 + 4 x 36 + 64 + 128 = 400; for Lxy 36 + 6 x 6 + 36 + 72 = 180.
   // delta = 448 u Lm / D, rounded up, covers all three with room for the
   // second-order terms.
-  const float delta = __fmul_ru(__fmul_ru(__uint_as_float(s_lmax), a.invD), 0x1.cp-16f);  // x 448 u
+  // Directed edges: Gx 96 (conversion) + 16 x 6 (row filters) + 108 (column
+  // filter) + 96 (scaling) = 396 u Lm / D, Gy 96 + 6 x 36 + 96 + 96 = 504;
+  // delta = 576 u Lm / D.
+  const float delta = __fmul_ru(__fmul_ru(__uint_as_float(s_lmax), a.invD), EDGE ? 0x1.2p-15f : 0x1.cp-16f);
   __syncthreads();
   for (int i = tid; i < HH2 * HW2; i += ST_THREADS) {
-    float fa, fb, fc;
-    hess32(sRs, sRd2, sRd1, HW2, i, a.invD, fa, fb, fc);
-    float k, ek, hdf, rad;
-    eig32_k(fa, fb, fc, k, ek, hdf, rad);
-    sK[i] = k;
-    // an eigenvalue moves by at most the spectral norm of the perturbation,
-    // which is at most its Frobenius norm, <= 2 delta
-    sE[i] = __fmaf_ru(3.0f, delta, ek);
+    if constexpr (EDGE) {
+      float gx, gy;
+      grad32(sRs, sRd1, HW2, i, a.invD, gx, gy);
+      const float g = __fsqrt_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)));
+      sK[i] = -g;
+      // |grad| is 1-Lipschitz: the inputs move it by <= sqrt 2 delta; four
+      // roundings by <= 4 u |grad|
+      sE[i] = __fmaf_ru(1.5f, delta, 4.0f * U32 * g);
+    } else {
+      float fa, fb, fc;
+      hess32(sRs, sRd2, sRd1, HW2, i, a.invD, fa, fb, fc);
+      float k, ek, hdf, rad;
+      eig32_k(fa, fb, fc, k, ek, hdf, rad);
+      sK[i] = k;
+      // an eigenvalue moves by at most the spectral norm of the perturbation,
+      // which is at most its Frobenius norm, <= 2 delta
+      sE[i] = __fmaf_ru(3.0f, delta, ek);
+    }
   }
   __syncthreads();
 
@@ -423,15 +491,31 @@ __global__ void __launch_bounds__(ST_THREADS, 4) k_stencil_ridge(StencilArgs a) 
       } else if (!(dk < -ek)) {
         verdict = 2;
       } else {
-        float fa, fb, fc;
-        hess32(sRs, sRd2, sRd1, HW2, c, a.invD, fa, fb, fc);
-        float k2, ek2, hdf, rad, X, Y, eX;
-        eig32_k(fa, fb, fc, k2, ek2, hdf, rad);
-        float M = fabsf(fa) + fabsf(fb) + fabsf(fc);
-        if (!eig32_dir(fb, hdf, rad, M, delta, X, Y, eX))
-          verdict = 2;
-        else
-          verdict = ridge_fast(sK, sE, HW2, hy, hx, gx, gy, H, W, k, ek, a.tau, X, Y, eX);
+        float X, Y, eX;
+        bool dir_ok;
+        if constexpr (EDGE) {
+          // unit gradient: (Gx, Gy) moves by <= sqrt 2 delta, so X by <=
+          // 2 sqrt 2 delta / |grad| plus the roundings
+          float gxf, gyf;
+          grad32(sRs, sRd1, HW2, c, a.invD, gxf, gyf);
+          const float g = -k;
+          dir_ok = g > 4.0f * delta && g > 0.0f;
+          X = __fdiv_rn(gxf, g);
+          Y = __fdiv_rn(gyf, g);
+          if (X < 0.0f || (X == 0.0f && Y < 0.0f)) {
+            X = -X;
+            Y = -Y;
+          }
+          eX = 3.0f * delta / (g - 2.0f * delta) + 4.0f * U32;
+        } else {
+          float fa, fb, fc;
+          hess32(sRs, sRd2, sRd1, HW2, c, a.invD, fa, fb, fc);
+          float k2, ek2, hdf, rad;
+          eig32_k(fa, fb, fc, k2, ek2, hdf, rad);
+          float M = fabsf(fa) + fabsf(fb) + fabsf(fc);
+          dir_ok = eig32_dir(fb, hdf, rad, M, delta, X, Y, eX);
+        }
+        verdict = dir_ok ? ridge_fast(sK, sE, HW2, hy, hx, gx, gy, H, W, k, ek, a.tau, X, Y, eX) : 2;
       }
       if (verdict == 2) {
         ++nfb;
@@ -457,14 +541,26 @@ __global__ void __launch_bounds__(ST_THREADS, 4) k_stencil_ridge(StencilArgs a) 
         const int p = t / 9, n = t - p * 9;
         const int pi = sU[c0 + p];
         const int ty = pi / ST_TW, tx = pi - ty * ST_TW;
-        long long ha, hc, hb;
-        hess_exact(sL, PW, ty + n / 3, tx + n % 3, ha, hc, hb);
-        const Eig64 e = eigen64(ha, hc, hb, a.D64);
-        sKn[t] = e.k;
-        if (n == 4) {
-          sXc[2 * p] = e.X;
-          sXc[2 * p + 1] = e.Y;
-          sDg[p] = e.degenerate ? 1 : 0;
+        if constexpr (EDGE) {
+          long long gxi, gyi;
+          grad_exact(sL, PW, ty + n / 3, tx + n % 3, gxi, gyi);
+          const Grad64 e = grad64(gxi, gyi, a.D64, -a.tau64);
+          sKn[t] = -e.g;
+          if (n == 4) {
+            sXc[2 * p] = e.X;
+            sXc[2 * p + 1] = e.Y;
+            sDg[p] = (e.X == 0.0 && e.Y == 0.0) ? 1 : 0;
+          }
+        } else {
+          long long ha, hc, hb;
+          hess_exact(sL, PW, ty + n / 3, tx + n % 3, ha, hc, hb);
+          const Eig64 e = eigen64(ha, hc, hb, a.D64);
+          sKn[t] = e.k;
+          if (n == 4) {
+            sXc[2 * p] = e.X;
+            sXc[2 * p + 1] = e.Y;
+            sDg[p] = e.degenerate ? 1 : 0;
+          }
         }
       }
       __syncthreads();
@@ -521,19 +617,37 @@ __global__ void __launch_bounds__(ST_THREADS, 4) k_stencil_ridge(StencilArgs a) 
     if (total) atomicAdd(&a.stats->ridge, (unsigned long long)total);
   }
   __syncthreads();
-  // ---- records: the pixel and its exact Hessian, list entries over threads
+  // ---- records: the pixel and its exact Hessian (ridges) or exact direction
+  //      (edges), list entries over threads
   const int start = sScan[8];
   const int keep = max(0, min(total, a.rl.cap - start));
   for (int t = tid; t < keep; t += ST_THREADS) {
     const int pi = sR[t];
     const int ty = pi / ST_TW, tx = pi - ty * ST_TW;
-    long long hxx, hyy, hxy;
-    hess_exact(sL, PW, ty + 1, tx + 1, hxx, hyy, hxy);
     const size_t g = (size_t)f * a.rl.cap + start + t;
     a.rl.xy[g] = (uint32_t)(x0 + tx) | ((uint32_t)(y0 + ty) << 16);
-    a.rl.hess[3 * g + 0] = hxx;
-    a.rl.hess[3 * g + 1] = hyy;
-    a.rl.hess[3 * g + 2] = hxy;
+    if constexpr (EDGE) {
+      long long gxi, gyi;
+      grad_exact(sL, PW, ty + 1, tx + 1, gxi, gyi);
+      const Grad64 e = grad64(gxi, gyi, a.D64, -a.tau64);
+      // the double direction as a float pair (|X - (hi + lo)| <= 2^-49) and
+      // the vote-rounding margins of an exact direction
+      const float xh = __double2float_rn(e.X), yh = __double2float_rn(e.Y);
+      const float xl = __double2float_rn(e.X - (double)xh), yl = __double2float_rn(e.Y - (double)yh);
+      const float eXr = 7.105427e-15f;  // 2^-47
+      a.rl.dir[g] = make_float4(xh, yh, xl, yl);
+      a.rl.kvote[g] = make_float2(1.25f * (fmaxf(fabsf(xl), fabsf(yl)) + eXr + U32) + U32, 1.25f * eXr + 2.842171e-14f);
+      a.rl.hess[3 * g + 0] = 0;
+      a.rl.hess[3 * g + 1] = 0;
+      a.rl.hess[3 * g + 2] = 0;
+      a.rl.x64[g] = make_double2(e.X, e.Y);
+    } else {
+      long long hxx, hyy, hxy;
+      hess_exact(sL, PW, ty + 1, tx + 1, hxx, hyy, hxy);
+      a.rl.hess[3 * g + 0] = hxx;
+      a.rl.hess[3 * g + 1] = hyy;
+      a.rl.hess[3 * g + 2] = hxy;
+    }
   }
 }
 
@@ -586,23 +700,31 @@ __global__ void __launch_bounds__(256) k_ridge_refine(RidgeList rl) {
 
 size_t stencil_smem_bytes(int R) { return stencil_smem_layout(R).total; }
 
-template <typename Tin, int RC>
-static void launch_stencil_t(const StencilArgs& a, dim3 grid, size_t sm, cudaStream_t st) {
-  cudaFuncSetAttribute(k_stencil_ridge<Tin, RC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_stencil_ridge<Tin, RC><<<grid, ST_THREADS, sm, st>>>(a);
-}
-
 // Gaussian half-width compiled in: R = ceil(4 sigma) = 8 for sigma in (1.75, 2]
 constexpr int ST_RC = 8;
+
+template <typename Tin, int RC, bool EDGE>
+static void launch_stencil_t(const StencilArgs& a, dim3 grid, size_t sm, cudaStream_t st) {
+  cudaFuncSetAttribute(k_stencil_ridge<Tin, RC, EDGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_stencil_ridge<Tin, RC, EDGE><<<grid, ST_THREADS, sm, st>>>(a);
+}
+
+template <typename Tin, bool EDGE>
+static void launch_stencil_r(const StencilArgs& a, dim3 grid, size_t sm, cudaStream_t st) {
+  if (a.taps.R == ST_RC)
+    launch_stencil_t<Tin, ST_RC, EDGE>(a, grid, sm, st);
+  else
+    launch_stencil_t<Tin, 0, EDGE>(a, grid, sm, st);
+}
+
 
 cudaError_t launch_stencil(const StencilArgs& a, int dtype, cudaStream_t st) {
   dim3 grid((a.W + ST_TW - 1) / ST_TW, (a.H + ST_TH - 1) / ST_TH, a.n);
   size_t sm = stencil_smem_bytes(a.taps.R);
-  const bool fixed = a.taps.R == ST_RC;
   if (dtype == 0)
-    fixed ? launch_stencil_t<uint8_t, ST_RC>(a, grid, sm, st) : launch_stencil_t<uint8_t, 0>(a, grid, sm, st);
+    a.edge ? launch_stencil_r<uint8_t, true>(a, grid, sm, st) : launch_stencil_r<uint8_t, false>(a, grid, sm, st);
   else
-    fixed ? launch_stencil_t<uint16_t, ST_RC>(a, grid, sm, st) : launch_stencil_t<uint16_t, 0>(a, grid, sm, st);
+    a.edge ? launch_stencil_r<uint16_t, true>(a, grid, sm, st) : launch_stencil_r<uint16_t, false>(a, grid, sm, st);
   return cudaGetLastError();
 }
 

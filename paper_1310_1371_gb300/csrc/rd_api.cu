@@ -84,10 +84,7 @@ struct rd_ctx {
   // feature stage: 0 directed ridges (the method), 1 directed edges (variant)
   int features = 0;
   double edge_thresh = 0.0;
-  uint32_t* e_hp = nullptr;
-  unsigned long long* e_L = nullptr;
-  double *e_g = nullptr, *e_X = nullptr, *e_Y = nullptr;
-  double2* e_x64 = nullptr;
+  double2* e_x64 = nullptr;  // directed edges: each record's exact direction
   // soft (differentiable) path: FP64 workspaces, allocated on first use
   bool soft_ready = false;
   double *s_t0 = nullptr, *s_t1 = nullptr, *s_a = nullptr, *s_b = nullptr, *s_c = nullptr, *s_k = nullptr,
@@ -187,7 +184,7 @@ static void free_all(rd_ctx* c) {
                   c->stage_counts, c->stage_offsets};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  void* edge[] = {c->e_hp, c->e_L, c->e_g, c->e_X, c->e_Y, c->e_x64};
+  void* edge[] = {c->e_x64};
   for (void* p : edge)
     if (p) cudaFree(p);
   void* soft[] = {c->s_t0, c->s_t1, c->s_a, c->s_b, c->s_c, c->s_k, c->s_X, c->s_Y, c->s_count, c->s_xy,
@@ -489,38 +486,30 @@ static rd_status detect_enqueue(rd_ctx* c, const void* frames_dev, int n, int H,
   };
   c->timed = c->timing;
   mark(0);
-  StencilArgs sa;
+  StencilArgs sa{};
   sa.frames = frames_dev;
   sa.n = n;
   sa.H = H;
   sa.W = W;
   sa.taps = c->taps;
+  sa.edge = 0;
   sa.tau = c->p.ridge_thresh;
   sa.tau64 = (double)c->p.ridge_thresh;
   sa.D64 = c->D64;
   sa.invD = c->invD;
   sa.rl = rl;
   sa.stats = c->stats;
-  if (c->features == 1) {  // directed edges replace directed ridges
-    EdgeArgs ea;
-    ea.frames = frames_dev;
-    ea.n = n;
-    ea.H = H;
-    ea.W = W;
-    ea.taps = c->taps;
+  if (c->features == 1) {  // directed edges replace directed ridges: -|grad| is tested as k-
     long long S = 0;
     for (int i = 0; i <= 2 * c->taps.R; ++i) S += c->taps.q[i];
-    ea.D64 = (double)(128LL * S * S);
-    ea.thresh = c->edge_thresh;
-    ea.hp = c->e_hp;
-    ea.L = c->e_L;
-    ea.g = c->e_g;
-    ea.X = c->e_X;
-    ea.Y = c->e_Y;
-    rl.x64 = c->e_x64;
-    ea.rl = rl;
-    ea.stats = c->stats;
-    chk(launch_edge(ea, dtype, st));
+    sa.edge = 1;
+    sa.tau = -(float)c->edge_thresh;
+    sa.tau64 = -c->edge_thresh;
+    sa.D64 = (double)(128LL * S * S);
+    sa.invD = (float)(1.0 / sa.D64);
+    rl.x64 = c->e_x64;  // the records keep their exact double direction
+    sa.rl = rl;
+    chk(launch_stencil(sa, dtype, st));
     mark(1);
     mark(2);
   } else {
@@ -1029,11 +1018,9 @@ extern "C" rd_status rd_set_features(rd_ctx* c, int features, float edge_thresh)
   if (features != RD_FEATURES_RIDGE && features != RD_FEATURES_EDGE)
     return fail(c, RD_E_INVAL, "features must be RD_FEATURES_RIDGE or RD_FEATURES_EDGE");
   if (!(edge_thresh >= 0.0f) || !std::isfinite(edge_thresh)) return fail(c, RD_E_INVAL, "edge_thresh must be >= 0");
-  if (features == RD_FEATURES_EDGE && !c->e_hp) {
-    const size_t px = (size_t)c->max_batch * c->max_H * c->max_W;
+  if (features == RD_FEATURES_EDGE && !c->e_x64) {
     const size_t rec = (size_t)c->max_batch * c->rl.cap;
-    bool ok = dalloc(&c->e_hp, px) && dalloc(&c->e_L, px) && dalloc(&c->e_g, px) && dalloc(&c->e_X, px) &&
-              dalloc(&c->e_Y, px) && dalloc(&c->e_x64, rec);
+    bool ok = dalloc(&c->e_x64, rec);
     if (!ok) {
       cudaGetLastError();
       return fail(c, RD_E_NOMEM, "edge workspaces: device allocation failed");

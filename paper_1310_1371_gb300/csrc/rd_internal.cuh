@@ -76,9 +76,13 @@ struct StencilArgs {
   const void* frames;
   int n, H, W;
   GaussTaps taps;
+  // directed ridges: tau and D = 64 S^2 (Lxx = Hxx' / D).  Directed edges
+  // (edge = 1): -(gradient threshold) and D = 128 S^2 ((Gx, Gy) = (Gx', Gy') / D),
+  // the stage then testing -|grad| as it tests k-.
+  int edge;
   float tau;
   double tau64;
-  double D64;     // 64 S^2: Lxx = Hxx' / D
+  double D64;
   float invD;     // fl(1 / D)
   RidgeList rl;
   DevStats* stats;
@@ -150,22 +154,6 @@ struct FitArgs {
   int w_int;          // w is an integer: exact integer membership test
   DevStats* stats;
 };
-
-// Directed-edge feature stage (k_edge.cu): exact integer smoothing and
-// first-order Sobel, double-precision magnitude, direction and edge test.
-struct EdgeArgs {
-  const void* frames;
-  int n, H, W;
-  GaussTaps taps;
-  double D64;                 // 128 S^2: (Gx, Gy) = (Gx', Gy') / D
-  double thresh;              // gradient-magnitude threshold
-  uint32_t* hp;               // n * H * W: horizontal pass (exact)
-  unsigned long long* L;      // n * H * W: L' (exact)
-  double *g, *X, *Y;          // n * H * W: |grad| and its unit direction
-  RidgeList rl;
-  DevStats* stats;
-};
-cudaError_t launch_edge(const EdgeArgs& a, int dtype, cudaStream_t st);
 
 // Soft (differentiable) score path: FP64 images and ridge records of a batch
 // of frames, allocated on first use (k_soft.cu).

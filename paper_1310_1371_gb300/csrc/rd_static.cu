@@ -124,7 +124,8 @@ extern "C" rd_status rd_ridges_static(const rd_params* p, const void* frame_dev,
 
   long long S = 0;
   for (int i = 0; i <= 2 * taps.R; ++i) S += taps.q[i];
-  StencilArgs a;
+  StencilArgs a{};
+  a.edge = 0;
   a.frames = frame_dev;
   a.n = 1;
   a.H = H;
