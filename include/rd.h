@@ -221,8 +221,8 @@ rd_status rd_refine(rd_ctx* ctx, const void* frames_dev, int n, int H, int W, in
  * bilinear sample at p + X and >= its sample at p - X, X = grad / |grad|
  * (canonical sign); each edge pixel then votes, is scored and fitted exactly
  * like a ridge pixel.  RD_FEATURES_RIDGE restores the method.  The first
- * switch to edges allocates the edge workspaces (36 bytes per pixel of
- * max_batch x max_H x max_W plus 16 bytes per record).  Errors: RD_E_INVAL
+ * switch to edges allocates the records' exact directions (16 bytes per
+ * record of max_batch frames).  Errors: RD_E_INVAL
  * (unknown features, t < 0), RD_E_NOMEM.  rd_debug_ridges then returns the
  * edge pixels and their directions (hess = 0). */
 #define RD_FEATURES_RIDGE 0
