@@ -358,8 +358,9 @@ def run_video(args):
                 plain.detect_async(vid[i:i + 1], stream)
         return out
 
-    batched_pass()  # captures the graph; warm-up
-    for i in range(3):
+    for _ in range(args.warmup):  # the first pass captures the graph
+        batched_pass()
+    for i in range(max(3, args.warmup)):
         plain.detect_async(vid[i:i + 1], stream)
     torch.cuda.synchronize()
     sampler = ClockSampler(0)
@@ -382,7 +383,7 @@ def run_video(args):
     identical = len(rb) == len(rp) == n and all(
         len(a) == len(b) and all(np.array_equal(a[k], b[k]) for k in fields) for a, b in zip(rb, rp))
     line = {"metric": VIDEO_METRIC, "value": n / (ms_b / 1e3), "unit": "frames/s", "n_gpus": 1, "steps": 1,
-            "warmup": 1, "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u8", "data": "synthetic",
             "config": {"workload": f"video: {n} frames 1024x1024 u8, 20-300 drifting rings r 8-30, search r 5-40",
                        "batch_frames": B, "geometry": list(geo), "graph": True,
@@ -439,7 +440,7 @@ def run_diff(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     def timed(fn, k):
-        for _ in range(2):
+        for _ in range(args.warmup):
             fn()
         torch.cuda.synchronize()
         ev0.record(stream)
@@ -486,7 +487,7 @@ def run_diff(args):
         done += 1
     cpu_s = time.perf_counter() - t0
     line = {"metric": DIFF_METRIC, "value": n / (ms_step / 1e3), "unit": "frames/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": 2, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64 (f32 frames and outputs)", "data": "synthetic",
             "config": {"workload": f"diff: {n} frames 512x512 f32, 64 rings r 10-50 with sub-pixel truth, search r 8-56",
                        "rings": int(len(flat)), "l2": f"inputs ({imgs.nbytes / 2**20:.0f} MiB) larger than L2; no flush"},

@@ -125,41 +125,80 @@ __global__ void k_soft_hessian(SoftArgs a) {
 }
 
 // ---- S4: directed-ridge mask (O4) and ridge records -----------------------------
-__global__ void k_soft_ridges(SoftArgs a) {
-  const size_t plane = (size_t)a.H * a.W, total = plane * a.n;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const size_t f = i / plane;
-    const size_t r = i - f * plane;
-    const int y = (int)(r / a.W), x = (int)(r - (size_t)y * a.W);
-    const double kp = a.k[i], X = a.X[i], Y = a.Y[i];
-    if (!(kp < a.tau) || (X == 0.0 && Y == 0.0)) continue;
-    const double* K = a.k + f * plane;
-    bool ok = true;
-    for (int s = 0; s < 2 && ok; ++s) {
-      const double qx = s == 0 ? d_add((double)x, X) : d_sub((double)x, X);
-      const double qy = s == 0 ? d_add((double)y, Y) : d_sub((double)y, Y);
-      if (qx < 0.0 || qx > (double)(a.W - 1) || qy < 0.0 || qy > (double)(a.H - 1)) {
-        ok = false;
-        break;
-      }
-      const double x0f = floor(qx), y0f = floor(qy);
-      const double fx = d_sub(qx, x0f), fy = d_sub(qy, y0f);
-      const int x0 = (int)x0f, y0 = (int)y0f;
-      const int x1 = min(x0 + 1, a.W - 1), y1 = min(y0 + 1, a.H - 1);
-      const double kt = bilinear64(fx, fy, K[(size_t)y0 * a.W + x0], K[(size_t)y0 * a.W + x1],
-                                   K[(size_t)y1 * a.W + x0], K[(size_t)y1 * a.W + x1]);
-      ok = s == 0 ? (kp < kt) : (kp <= kt);
-    }
-    if (!ok) continue;
-    const int j = atomicAdd(&a.count[f], 1);
-    if (j >= a.cap) continue;
-    const size_t g = f * (size_t)a.cap + j;
+// One CTA per 32 x 32 tile: the mask of its pixels, then its records
+// contiguously (order inside a tile unspecified), so that the score can
+// visit only the tiles near a ring.
+constexpr int SOFT_T = 32;
+
+__device__ __forceinline__ bool soft_is_ridge(const SoftArgs& a, size_t f, int x, int y) {
+  const size_t plane = (size_t)a.H * a.W, i = f * plane + (size_t)y * a.W + x;
+  const double kp = a.k[i], X = a.X[i], Y = a.Y[i];
+  if (!(kp < a.tau) || (X == 0.0 && Y == 0.0)) return false;
+  const double* K = a.k + f * plane;
+  for (int s = 0; s < 2; ++s) {
+    const double qx = s == 0 ? d_add((double)x, X) : d_sub((double)x, X);
+    const double qy = s == 0 ? d_add((double)y, Y) : d_sub((double)y, Y);
+    if (qx < 0.0 || qx > (double)(a.W - 1) || qy < 0.0 || qy > (double)(a.H - 1)) return false;
+    const double x0f = floor(qx), y0f = floor(qy);
+    const double fx = d_sub(qx, x0f), fy = d_sub(qy, y0f);
+    const int x0 = (int)x0f, y0 = (int)y0f;
+    const int x1 = min(x0 + 1, a.W - 1), y1 = min(y0 + 1, a.H - 1);
+    const double kt = bilinear64(fx, fy, K[(size_t)y0 * a.W + x0], K[(size_t)y0 * a.W + x1],
+                                 K[(size_t)y1 * a.W + x0], K[(size_t)y1 * a.W + x1]);
+    if (s == 0 ? !(kp < kt) : !(kp <= kt)) return false;
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(256) k_soft_ridges(SoftArgs a) {
+  __shared__ int s_warp[8], s_start;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int f = blockIdx.z, x0 = blockIdx.x * SOFT_T, y0 = blockIdx.y * SOFT_T;
+  bool flag[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int pi = tid + 256 * j, x = x0 + (pi & 31), y = y0 + (pi >> 5);
+    flag[j] = x < a.W && y < a.H && soft_is_ridge(a, f, x, y);
+  }
+  const int mine = (int)flag[0] + (int)flag[1] + (int)flag[2] + (int)flag[3];
+  int incl = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  int pre = 0, total = 0;
+  for (int w = 0; w < 8; ++w) {
+    pre += w < warp ? s_warp[w] : 0;
+    total += s_warp[w];
+  }
+  const size_t t = ((size_t)f * a.n_ty + blockIdx.y) * a.n_tx + blockIdx.x;
+  if (tid == 0) {
+    const int start = total ? atomicAdd(&a.count[f], total) : 0;
+    s_start = start;
+    a.tile_off[t] = start;
+    a.tile_cnt[t] = max(0, min(total, a.cap - start));
+  }
+  __syncthreads();
+  int j0 = s_start + pre + incl - mine;
+  const size_t plane = (size_t)a.H * a.W;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (!flag[j]) continue;
+    const int jj = j0++;
+    if (jj >= a.cap) continue;
+    const int pi = tid + 256 * j, x = x0 + (pi & 31), y = y0 + (pi >> 5);
+    const size_t i = (size_t)f * plane + (size_t)y * a.W + x;
+    const size_t g = (size_t)f * a.cap + jj;
+    const double kp = a.k[i];
     const SoftEig e = soft_eigen(a.a[i], a.c[i], a.b[i]);
     a.xy[g] = (uint32_t)x | ((uint32_t)y << 16);
     a.flags[g] = (uint8_t)((e.use1 ? 1 : 0) | (e.flip ? 2 : 0));
     a.rk[g] = kp;
-    a.rX[g] = X;
-    a.rY[g] = Y;
+    a.rX[g] = a.X[i];
+    a.rY[g] = a.Y[i];
     a.ra[g] = a.a[i];
     a.rb[g] = a.b[i];
     a.rc[g] = a.c[i];
@@ -177,7 +216,7 @@ cudaError_t launch_soft_stencil(const SoftArgs& a, cudaStream_t st) {
     k_soft_hpass<float><<<grid, 256, 0, st>>>(a);
   k_soft_vpass<<<grid, 256, 0, st>>>(a);
   k_soft_hessian<<<grid, 256, 0, st>>>(a);
-  k_soft_ridges<<<grid, 256, 0, st>>>(a);
+  k_soft_ridges<<<dim3(a.n_tx, a.n_ty, a.n), 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -222,8 +261,11 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return t;  // valid in thread 0
 }
 
+constexpr int SOFT_MAX_TILES = 256;  // tiles a ring visits through the tile index
+
 __global__ void __launch_bounds__(256) k_soft_score(SoftArgs a) {
   __shared__ double red[8];
+  __shared__ int s_off[SOFT_MAX_TILES], s_pre[SOFT_MAX_TILES + 1];
   const int n_rings = min(a.ring_off[a.n], a.max_rings);
   for (int i = blockIdx.x; i < n_rings; i += gridDim.x) {
     int lo = 0, hi = a.n;  // frame f: ring_off[f] <= i < ring_off[f + 1]
@@ -236,11 +278,51 @@ __global__ void __launch_bounds__(256) k_soft_score(SoftArgs a) {
     const double ds = a.dscore ? (double)a.dscore[i] : 1.0;
     const double sig = a.sig_a * rho + a.sig_b;
     const double den = 2.0 * sig * sig;
-    const double cut = 38.7 * sig + 1.5;  // beyond: every Gaussian factor underflows to 0
+    // Votes farther than cut from the centre are left out: each of their
+    // Gaussian factors is below e^-40.5 < 3e-18 (corners lie within sqrt 2
+    // of the vote), so all of them together change a score by < 1e-12 of
+    // its value for any frame the records fit.
+    const double cut = 9.0 * sig + 1.5;
     const int cnt = min(a.count[f], a.cap);
     const size_t base = (size_t)f * a.cap;
+    // A vote lies rho from its pixel, so only the tiles within rho + cut of
+    // the centre can contribute; their record ranges, flattened.
+    const double reach = rho + cut + 2.0;
+    const double ftx0 = floor((cx - reach) / SOFT_T), ftx1 = floor((cx + reach) / SOFT_T);
+    const double fty0 = floor((cy - reach) / SOFT_T), fty1 = floor((cy + reach) / SOFT_T);
+    const int tx0 = (int)fmax(ftx0, 0.0), tx1 = (int)fmin(ftx1, (double)(a.n_tx - 1));
+    const int ty0 = (int)fmax(fty0, 0.0), ty1 = (int)fmin(fty1, (double)(a.n_ty - 1));
+    const bool finite = isfinite(cx) && isfinite(cy) && isfinite(reach);
+    const int ntx = tx1 - tx0 + 1, nty = ty1 - ty0 + 1;
+    const bool tiled = finite && ntx > 0 && nty > 0 && ntx * nty <= SOFT_MAX_TILES;
+    int total = cnt;  // not tiled: every record of the frame
+    if (finite && (ntx <= 0 || nty <= 0)) total = 0;
+    if (tiled) {
+      const int nt = ntx * nty;
+      for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+        const size_t ti = ((size_t)f * a.n_ty + ty0 + t / ntx) * a.n_tx + tx0 + t % ntx;
+        s_off[t] = a.tile_off[ti];
+        s_pre[t + 1] = a.tile_cnt[ti];
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        s_pre[0] = 0;
+        for (int t = 0; t < nt; ++t) s_pre[t + 1] += s_pre[t];
+      }
+      __syncthreads();
+      total = s_pre[nt];
+    }
     double T = 0.0, Tcx = 0.0, Tcy = 0.0, Tsig = 0.0, Trho = 0.0;
-    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+      int j = q;
+      if (tiled) {  // the tile t with s_pre[t] <= q < s_pre[t + 1]
+        int lo = 0, hi = ntx * nty;
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (s_pre[mid] <= q) lo = mid; else hi = mid;
+        }
+        j = s_off[lo] + (q - s_pre[lo]);
+      }
       const size_t g = base + j;
       const uint32_t xy = a.xy[g];
       const double px = (double)(xy & 0xffffu), py = (double)(xy >> 16);

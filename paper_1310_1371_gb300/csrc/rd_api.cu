@@ -97,6 +97,7 @@ struct rd_ctx {
   int* s_ring_off = nullptr;
   float* s_score = nullptr;
   float* s_dparams = nullptr;
+  int *s_tile_off = nullptr, *s_tile_cnt = nullptr;
   // graph mode: the captured rd_detect launch sequence and the arguments it was captured with
   bool graph_on = false;
   cudaGraphExec_t gexec = nullptr;
@@ -189,7 +190,7 @@ static void free_all(rd_ctx* c) {
     if (p) cudaFree(p);
   void* soft[] = {c->s_t0, c->s_t1, c->s_a, c->s_b, c->s_c, c->s_k, c->s_X, c->s_Y, c->s_count, c->s_xy,
                   c->s_flags, c->s_rk, c->s_rX, c->s_rY, c->s_ra, c->s_rb, c->s_rc, c->s_rm, c->s_gk, c->s_gX,
-                  c->s_gY, c->s_ring_off, c->s_score, c->s_dparams};
+                  c->s_gY, c->s_ring_off, c->s_score, c->s_dparams, c->s_tile_off, c->s_tile_cnt};
   for (void* p : soft)
     if (p) cudaFree(p);
 }
@@ -883,7 +884,9 @@ static rd_status ensure_soft(rd_ctx* c) {
             dalloc(&c->s_rk, rec) && dalloc(&c->s_rX, rec) && dalloc(&c->s_rY, rec) && dalloc(&c->s_ra, rec) &&
             dalloc(&c->s_rb, rec) && dalloc(&c->s_rc, rec) && dalloc(&c->s_rm, rec) && dalloc(&c->s_gk, rec) &&
             dalloc(&c->s_gX, rec) && dalloc(&c->s_gY, rec) && dalloc(&c->s_ring_off, (size_t)c->max_batch + 1) &&
-            dalloc(&c->s_score, rings) && dalloc(&c->s_dparams, 3 * rings);
+            dalloc(&c->s_score, rings) && dalloc(&c->s_dparams, 3 * rings) &&
+            dalloc(&c->s_tile_off, (size_t)c->max_batch * c->rl.n_stx * c->rl.n_sty) &&
+            dalloc(&c->s_tile_cnt, (size_t)c->max_batch * c->rl.n_stx * c->rl.n_sty);
   if (!ok) {
     cudaGetLastError();
     return fail(c, RD_E_NOMEM, "soft path: device allocation failed");
@@ -928,6 +931,10 @@ static rd_status soft_prepare(rd_ctx* c, const void* frames, int n, int H, int W
   a->Y = c->s_Y;
   a->cap = c->rl.cap;
   a->count = c->s_count;
+  a->n_tx = (W + 31) / 32;
+  a->n_ty = (H + 31) / 32;
+  a->tile_off = c->s_tile_off;
+  a->tile_cnt = c->s_tile_cnt;
   a->xy = c->s_xy;
   a->flags = c->s_flags;
   a->rk = c->s_rk;

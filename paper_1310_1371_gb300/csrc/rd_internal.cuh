@@ -166,9 +166,12 @@ struct SoftArgs {
   double tau, temp, sig_a, sig_b;
   // dense FP64 images, n * H * W each
   double *t0, *t1, *a, *b, *c, *k, *X, *Y;
-  // ridge records, frame f at [f * cap, f * cap + count[f])
+  // ridge records, frame f at [f * cap, f * cap + count[f]); those of 32 x 32
+  // tile t of frame f at [tile_off, tile_off + tile_cnt) within the frame's
   int cap;
   int* count;
+  int n_tx, n_ty;             // tiles per row and column
+  int *tile_off, *tile_cnt;   // n * n_ty * n_tx
   uint32_t* xy;               // x | y << 16
   uint8_t* flags;             // bit 0: eigenvector candidate v1; bit 1: sign flipped
   double *rk, *rX, *rY, *ra, *rb, *rc, *rm;
