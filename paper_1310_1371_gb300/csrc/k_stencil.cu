@@ -244,7 +244,7 @@ __host__ __device__ __forceinline__ StencilSmem stencil_smem_layout(int R) {
   L.f = L.x + (((in_bytes > rf_bytes ? in_bytes : rf_bytes) + 7) & ~7u);
   L.k = L.f + (((lf_bytes > list_bytes ? lf_bytes : list_bytes) + 7) & ~7u);
   L.scan = L.k + 2 * HH2 * HW2 * 4;
-  L.total = L.scan + 16 * 4;
+  L.total = L.scan + (ST_THREADS / 32 + 1) * 4;
   return L;
 }
 
@@ -253,7 +253,7 @@ __host__ __device__ __forceinline__ StencilSmem stencil_smem_layout(int R) {
 // EDGE: directed edges (Additional notes) -- the gradient replaces the
 // Hessian and -|grad| takes the place of k- in every test below.
 template <typename Tin, int RC, bool EDGE>
-__global__ void __launch_bounds__(ST_THREADS, 4) k_stencil_ridge(StencilArgs a) {
+__global__ void __launch_bounds__(ST_THREADS, 1024 / ST_THREADS) k_stencil_ridge(StencilArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x;
   const int R = RC > 0 ? RC : a.taps.R;
@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(ST_THREADS, 4) k_stencil_ridge(StencilArgs a) 
   uint8_t* sV = reinterpret_cast<uint8_t*>(sR + ST_TW * ST_TH);                // exact verdicts
   float* sK = reinterpret_cast<float*>(smem + Ls.k);                           // HH2*HW2
   float* sE = sK + HH2 * HW2;
-  int* sScan = reinterpret_cast<int*>(smem + Ls.scan);                         // 8 warps + 2
+  int* sScan = reinterpret_cast<int*>(smem + Ls.scan);                         // warps + 1
   __shared__ int32_t q[2 * MAX_RG + 1];
   __shared__ unsigned s_lmax;  // bits of the largest rounded L of the tile (all >= 0)
   __shared__ int s_nu;
@@ -609,7 +609,7 @@ __global__ void __launch_bounds__(ST_THREADS, 4) k_stencil_ridge(StencilArgs a) 
   const size_t tbase = (size_t)f * a.rl.n_stx * a.rl.n_sty + tile;
   if (tid == 0) {
     int start = total ? atomicAdd(&a.rl.count[f], total) : 0;
-    sScan[8] = start;
+    sScan[ST_THREADS / 32] = start;
     int keep = max(0, min(total, a.rl.cap - start));
     if (keep < total) atomicOr(&a.stats->overflow, 1);
     a.rl.tile_off[tbase] = total ? start : 0;
@@ -619,7 +619,7 @@ __global__ void __launch_bounds__(ST_THREADS, 4) k_stencil_ridge(StencilArgs a) 
   __syncthreads();
   // ---- records: the pixel and its exact Hessian (ridges) or exact direction
   //      (edges), list entries over threads
-  const int start = sScan[8];
+  const int start = sScan[ST_THREADS / 32];
   const int keep = max(0, min(total, a.rl.cap - start));
   for (int t = tid; t < keep; t += ST_THREADS) {
     const int pi = sR[t];

@@ -885,8 +885,8 @@ static rd_status ensure_soft(rd_ctx* c) {
             dalloc(&c->s_rb, rec) && dalloc(&c->s_rc, rec) && dalloc(&c->s_rm, rec) && dalloc(&c->s_gk, rec) &&
             dalloc(&c->s_gX, rec) && dalloc(&c->s_gY, rec) && dalloc(&c->s_ring_off, (size_t)c->max_batch + 1) &&
             dalloc(&c->s_score, rings) && dalloc(&c->s_dparams, 3 * rings) &&
-            dalloc(&c->s_tile_off, (size_t)c->max_batch * c->rl.n_stx * c->rl.n_sty) &&
-            dalloc(&c->s_tile_cnt, (size_t)c->max_batch * c->rl.n_stx * c->rl.n_sty);
+            dalloc(&c->s_tile_off, (size_t)c->max_batch * ((c->max_W + 31) / 32) * ((c->max_H + 31) / 32)) &&
+            dalloc(&c->s_tile_cnt, (size_t)c->max_batch * ((c->max_W + 31) / 32) * ((c->max_H + 31) / 32));
   if (!ok) {
     cudaGetLastError();
     return fail(c, RD_E_NOMEM, "soft path: device allocation failed");
