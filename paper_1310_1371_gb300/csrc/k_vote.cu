@@ -647,12 +647,13 @@ __global__ void __launch_bounds__(VOTE_THREADS, 2) k_vote_dense(VoteArgs a) {
 // The common path.  Shared memory holds one level of u16 vote counts for the
 // tile plus its smoothing halo, the window taps of that level (by rotation
 // orbits of four equal weights), and, for the last four levels, the hotspot
-// lists with their smoothed sums and a
-// small open-addressing table from voxel to list slot: the paper's
-// registering of modified elements, so that nothing proportional to the tile
-// area is kept per level and four CTAs fit on an SM.  A bin whose hotspots or
-// peaks exceed these capacities emits nothing here and is handed to
-// k_vote_dense, which computes the same result with dense per-level storage.
+// lists with their smoothed sums and a small open-addressing table from
+// voxel to list slot: the paper's registering of modified elements, so that
+// nothing proportional to the tile area is kept beyond the current level and
+// three CTAs fit on an SM with 128-pixel tiles.  A bin whose hotspots, peaks
+// or deferred exact votes exceed these capacities emits nothing here and is
+// handed to k_vote_dense, which computes the same result with dense
+// per-level storage.
 constexpr int SP_THREADS = 320;  // 10 warps: three CTAs per SM at 64 registers use 61440 of 65536
 constexpr int SP_HOT = 256;     // hotspots per level
 constexpr int SP_HASH = 512;    // hash slots per level (power of two, > 2 SP_HOT)
