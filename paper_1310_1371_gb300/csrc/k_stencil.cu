@@ -1,6 +1,8 @@
 // k_stencil.cu -- K1: fused Gaussian smoothing, second-order Sobel Hessian,
 // principal curvature k- and direction X-, and the directed-ridge mask, in
-// one pass over the frame; K2: double-float refinement of X- per ridge pixel.
+// one pass over the frame (compiled with EDGE: the directed-edge variant of
+// the Additional notes, the gradient in place of the Hessian); K2:
+// double-float refinement of X- per ridge pixel.
 //
 // Method: Methods ("Algorithm implementation": Gaussian convolution, then the
 // 5x5 second-order Sobel operator); Results ("Directed ridge detection &
@@ -23,8 +25,9 @@ __device__ __forceinline__ int reflect101(int i, int n) {
 
 constexpr float U32 = 5.9604645e-8f;  // 2^-24
 
-// FP32 k- with a bound on |k32 - k_def| (k_def: the double-precision value).
-// Inputs a, b, c carry <= 2u relative error (conversion and scaling).
+// FP32 k- of (a, b, c) with ek bounding its FP32 evaluation error plus the
+// definition's own double rounding, 16 u (|a| + |b| + |c|); the caller adds
+// the effect of the inputs' error (3 delta, see hess32).
 __device__ __forceinline__ void eig32_k(float a, float b, float c, float& k, float& ek, float& hdf, float& rad) {
   float htr = (a + c) * 0.5f;
   hdf = (a - c) * 0.5f;

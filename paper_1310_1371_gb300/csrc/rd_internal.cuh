@@ -3,15 +3,16 @@
 //
 // Numerical contract.  Integer frames are smoothed with integer Gaussian
 // taps, so the Hessian (Hxx', Hyy', Hxy') = 64 S^2 (Lxx, Lyy, Lxy) is an exact
-// int64 (Methods: Gaussian convolution, then the 5x5 second-order Sobel).  Every
-// later decision (k- < tau, the local-minimum test along X-, the rounding of
-// each vote to a bin, annulus membership) is taken in fast FP32 arithmetic
-// together with a rigorous bound on its error; when the bound does not
-// separate the value from the decision boundary the decision is re-taken by an
-// FP64 evaluation that performs the same IEEE operations in the same order as
-// the definition (helpers named *64 below), so the decision equals that of the
+// int64 (Methods: Gaussian convolution, then the 5x5 second-order Sobel),
+// formed where a decision or a record needs it.  Every decision (k- < tau,
+// the local-minimum test along X-, the rounding of each vote to a bin,
+// annulus membership) is taken in fast FP32 arithmetic together with a
+// rigorous bound on its error; when the bound does not separate the value
+// from the decision boundary the decision is re-taken by an FP64 evaluation
+// that performs the same IEEE operations in the same order as the definition
+// (helpers named *64 below), so the decision equals that of the
 // double-precision definition.  Vote directions carry a double-float
-// (hi + lo) refinement so that only ~1e-11 of the votes reach FP64.
+// (hi + lo) refinement so that only a tiny fraction of the votes reach FP64.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -33,7 +34,7 @@ constexpr int ACC_T_MID = 80;
 constexpr int ACC_T_SMALL = 64;
 constexpr int VOTE_THREADS = 256;
 constexpr int MAX_RS = 40;         // level smoothing half-width ceil(3 sigma(r))
-constexpr int SLAB_LEVELS = 12;    // default peak levels per r-slab
+constexpr int SLAB_LEVELS = 12;    // peak levels per r-slab of the smaller-tile fallbacks
 constexpr int MAX_SLAB_LEVELS = 64;
 constexpr int DEFAULT_SLAB_LEVELS = 32;  // the automatic geometry's slab depth
 constexpr int FIT_WARPS = 8;
