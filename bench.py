@@ -9,7 +9,9 @@ so no flush is needed between steps).  Multi-GPU runs are independent
 replicas (each rank its own frames; no data exchange).
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
-bounded sample of the same workload.
+bounded sample of the same workload.  --workload video|diff|serve|discs|coarse
+measures the batched path, the soft score, the server, directed edges and the
+coarse parameter space on their own synthetic workloads.
 """
 from __future__ import annotations
 

@@ -7,7 +7,8 @@
 //   Gaussian taps  Q_i = floor(2^14 g_i + 1/2), g_i = e_i / sum(e),
 //                  e_i = exp(-(i^2) / (2 sigma sigma)), |i| <= ceil(4 sigma)
 //   level weights  floor(2^16 exp(-(dy^2 + dx^2) / (2 s s)) + 1/2),
-//                  s = sig_a r + sig_b, |dx|, |dy| <= ceil(3 s)
+//                  s = (sig_a r + sig_b) / c, |dx|, |dy| <= ceil(3 s), with c
+//                  the parameter-space cell edge in px (1 unless coarse)
 //   peak threshold S > peak_frac 2 pi  <=>  N > ((peak_frac 2 pi) 2^16) r
 #include "rd_internal.cuh"
 #include "rd.h"
