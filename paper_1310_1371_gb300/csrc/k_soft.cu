@@ -15,6 +15,7 @@
 // reflect-101 borders; its adjoint is applied as gathers, recomputing the
 // stencil stage instead of storing per-ring state.  Everything is FP64.
 #include "rd_internal.cuh"
+#include "rd_cert.cuh"
 
 #include <cmath>
 
@@ -91,76 +92,174 @@ __device__ __forceinline__ SoftEig soft_eigen(double a, double c, double b) {
   return e;
 }
 
-// ---- S3: Hessian (5x5 second-order Sobel / 64 of L) and k-, X- ----------------
-__global__ void k_soft_hessian(SoftArgs a) {
-  const size_t plane = (size_t)a.H * a.W, total = plane * a.n;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const size_t f = i / plane;
-    const size_t r = i - f * plane;
-    const int y = (int)(r / a.W), x = (int)(r - (size_t)y * a.W);
-    const double* L = a.t1 + f * plane;
-    double hxx = 0.0, hyy = 0.0, hxy = 0.0;
-    for (int dy = 0; dy < 5; ++dy) {
-      const double* row = L + (size_t)refl101(y + dy - 2, a.H) * a.W;
-      double sx = 0.0, d2x = 0.0, d1x = 0.0;
-      for (int dx = 0; dx < 5; ++dx) {
-        const double l = row[refl101(x + dx - 2, a.W)];
-        sx += c_s5[dx] * l;
-        d2x += c_d2[dx] * l;
-        d1x += c_d1[dx] * l;
-      }
-      hxx += c_s5[dy] * d2x;
-      hyy += c_d2[dy] * sx;
-      hxy += c_d1[dy] * d1x;
-    }
-    const double A = hxx / 64.0, C = hyy / 64.0, B = hxy / 64.0;
-    a.a[i] = A;
-    a.b[i] = B;
-    a.c[i] = C;
-    const SoftEig e = soft_eigen(A, C, B);
-    a.k[i] = e.k;
-    a.X[i] = e.X;
-    a.Y[i] = e.Y;
-  }
-}
-
-// ---- S4: directed-ridge mask (O4) and ridge records -----------------------------
-// One CTA per 32 x 32 tile: the mask of its pixels, then its records
-// contiguously (order inside a tile unspecified), so that the score can
+// ---- S3/S4: Hessian, k- and X- (O2-O3), directed-ridge mask (O4) and ridge
+// records, one CTA per 32 x 32 tile.  Every pixel is tested in FP32 with a
+// certified bound (the detector's stencil-stage arithmetic, rd_cert.cuh)
+// from the rounded FP64 L; the few pixels it cannot decide, and the records,
+// get the FP64 Hessian and eigen step of the definition.  Records of a tile
+// are contiguous (order inside a tile unspecified), so that the score can
 // visit only the tiles near a ring.
 constexpr int SOFT_T = 32;
+constexpr int SOFT_PW = SOFT_T + 6;  // L rows and columns of a tile: the Hessian ring + the 5x5 stencil
+constexpr int SOFT_HW = SOFT_T + 2;  // Hessian tile: the pixels and a one-pixel ring
+constexpr int SOFT_FB = 256 / 9;     // pixels per step of the exact test (9 threads each)
 
-__device__ __forceinline__ bool soft_is_ridge(const SoftArgs& a, size_t f, int x, int y) {
-  const size_t plane = (size_t)a.H * a.W, i = f * plane + (size_t)y * a.W + x;
-  const double kp = a.k[i], X = a.X[i], Y = a.Y[i];
-  if (!(kp < a.tau) || (X == 0.0 && Y == 0.0)) return false;
-  const double* K = a.k + f * plane;
-  for (int s = 0; s < 2; ++s) {
-    const double qx = s == 0 ? d_add((double)x, X) : d_sub((double)x, X);
-    const double qy = s == 0 ? d_add((double)y, Y) : d_sub((double)y, Y);
-    if (qx < 0.0 || qx > (double)(a.W - 1) || qy < 0.0 || qy > (double)(a.H - 1)) return false;
-    const double x0f = floor(qx), y0f = floor(qy);
-    const double fx = d_sub(qx, x0f), fy = d_sub(qy, y0f);
-    const int x0 = (int)x0f, y0 = (int)y0f;
-    const int x1 = min(x0 + 1, a.W - 1), y1 = min(y0 + 1, a.H - 1);
-    const double kt = bilinear64(fx, fy, K[(size_t)y0 * a.W + x0], K[(size_t)y0 * a.W + x1],
-                                 K[(size_t)y1 * a.W + x0], K[(size_t)y1 * a.W + x1]);
-    if (s == 0 ? !(kp < kt) : !(kp <= kt)) return false;
+// FP64 Hessian of L at Hessian-tile coordinates (hy, hx) (rows hy .. hy + 4
+// and columns hx .. hx + 4 of the L tile, reflect-101 already applied): the
+// 5x5 second-order Sobel / 64.
+__device__ __forceinline__ void soft_hess64(const double* sLd, int hy, int hx, double& A, double& C, double& B) {
+  double hxx = 0.0, hyy = 0.0, hxy = 0.0;
+  for (int dy = 0; dy < 5; ++dy) {
+    const double* row = sLd + (hy + dy) * SOFT_PW + hx;
+    double sx = 0.0, d2x = 0.0, d1x = 0.0;
+    for (int dx = 0; dx < 5; ++dx) {
+      const double l = row[dx];
+      sx += c_s5[dx] * l;
+      d2x += c_d2[dx] * l;
+      d1x += c_d1[dx] * l;
+    }
+    hxx += c_s5[dy] * d2x;
+    hyy += c_d2[dy] * sx;
+    hxy += c_d1[dy] * d1x;
   }
-  return true;
+  A = hxx / 64.0;
+  C = hyy / 64.0;
+  B = hxy / 64.0;
 }
 
-__global__ void __launch_bounds__(256) k_soft_ridges(SoftArgs a) {
-  __shared__ int s_warp[8], s_start;
+// reflect-101 with far indices (only for discarded outputs of partial tiles) clamped
+__device__ __forceinline__ int refl101c(int i, int n) {
+  i = i < 0 ? -i : i;
+  i = i >= n ? 2 * (n - 1) - i : i;
+  return min(max(i, 0), n - 1);
+}
+
+__global__ void __launch_bounds__(256) k_soft_mask(SoftArgs a) {
+  __shared__ double sLd[SOFT_PW * SOFT_PW];                 // FP64 L of the tile
+  __shared__ float sLf[SOFT_PW * SOFT_PW];                  // rounded to FP32
+  __shared__ __align__(16) unsigned char sRow[3 * SOFT_PW * SOFT_HW * 4];  // row filters; later the exact test's scratch
+  __shared__ float sK[SOFT_HW * SOFT_HW], sE[SOFT_HW * SOFT_HW];
+  __shared__ uint16_t sU[SOFT_T * SOFT_T], sR[SOFT_T * SOFT_T];
+  __shared__ uint8_t sV[SOFT_T * SOFT_T];
+  __shared__ int s_warp[8], s_start, s_nu;
+  __shared__ unsigned s_lmax;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int f = blockIdx.z, x0 = blockIdx.x * SOFT_T, y0 = blockIdx.y * SOFT_T;
-  bool flag[4];
+  const int H = a.H, W = a.W;
+  const size_t plane = (size_t)H * W;
+  const double* L = a.t1 + (size_t)f * plane;
+  if (tid == 0) {
+    s_nu = 0;
+    s_lmax = 0u;
+  }
+  __syncthreads();
+  // L of the tile with a 3-pixel ring (reflect-101 at the frame's borders)
+  float lmax = 0.0f;
+  for (int i = tid; i < SOFT_PW * SOFT_PW; i += 256) {
+    const int iy = i / SOFT_PW, ix = i - iy * SOFT_PW;
+    const double v = L[(size_t)refl101c(y0 - 3 + iy, H) * W + refl101c(x0 - 3 + ix, W)];
+    sLd[i] = v;
+    const float fv = __double2float_rn(v);
+    sLf[i] = fv;
+    lmax = fmaxf(lmax, fabsf(fv));
+  }
+  {
+    const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(lmax));
+    if (lane == 0) atomicMax(&s_lmax, m);
+  }
+  __syncthreads();
+  // FP32 row filters s, d2, d1 of every L row, at the Hessian tile's columns
+  float* sRs = reinterpret_cast<float*>(sRow);
+  float* sRd2 = sRs + SOFT_PW * SOFT_HW;
+  float* sRd1 = sRd2 + SOFT_PW * SOFT_HW;
+  for (int i = tid; i < SOFT_PW * SOFT_HW; i += 256) {
+    const int ly = i / SOFT_HW, hx = i - ly * SOFT_HW;
+    const float* row = sLf + ly * SOFT_PW + hx;
+    const float l0 = row[0], l1 = row[1], l2 = row[2], l3 = row[3], l4 = row[4];
+    const float e = __fadd_rn(l0, l4);
+    sRs[i] = __fmaf_rn(6.0f, l2, __fmaf_rn(4.0f, __fadd_rn(l1, l3), e));
+    sRd2[i] = __fmaf_rn(-2.0f, l2, e);
+    sRd1[i] = __fmaf_rn(2.0f, __fsub_rn(l3, l1), __fsub_rn(l4, l0));
+  }
+  // The detector's bound (hess32) for |L| <= Lm of either sign: each
+  // rounding adds at most u |its result| times the coefficient that carries
+  // it to the entry; with |e|, |l1 + l3| <= 2 Lm, |s| <= 16 Lm, |d2| <= 4 Lm,
+  // |d1| <= 6 Lm and an exact scaling by 1/64 the sums are 304 (Lxx, Lyy) and
+  // 180 (Lxy) u Lm / 64; delta = 512 u Lm / 64 = 2^-21 Lm.
+  const float delta = __fmul_ru(__uint_as_float(s_lmax), 0x1p-21f);
+  __syncthreads();
+  for (int i = tid; i < SOFT_HW * SOFT_HW; i += 256) {
+    float fa, fb, fc, k, ek, hdf, rad;
+    hess32(sRs, sRd2, sRd1, SOFT_HW, i, 0.015625f, fa, fb, fc);
+    eig32_k(fa, fb, fc, k, ek, hdf, rad);
+    sK[i] = k;
+    sE[i] = __fmaf_ru(3.0f, delta, ek);
+  }
+  __syncthreads();
+  // certified test of the tile's pixels, 4 per thread; undecided ones to a list
+  const float tau = (float)a.tau;
+  int flags = 0;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const int pi = tid + 256 * j, x = x0 + (pi & 31), y = y0 + (pi >> 5);
-    flag[j] = x < a.W && y < a.H && soft_is_ridge(a, f, x, y);
+    const int pi = tid + 256 * j, ty = pi >> 5, tx = pi & 31, gx = x0 + tx, gy = y0 + ty;
+    int verdict = 0;
+    if (gx < W && gy < H) {
+      const int hy = ty + 1, hx = tx + 1, c = hy * SOFT_HW + hx;
+      const float k = sK[c], ek = sE[c], dk = k - tau;
+      if (dk >= ek) {
+        verdict = 0;
+      } else if (!(dk < -ek)) {
+        verdict = 2;
+      } else {
+        float fa, fb, fc, k2, ek2, hdf, rad, X, Y, eX;
+        hess32(sRs, sRd2, sRd1, SOFT_HW, c, 0.015625f, fa, fb, fc);
+        eig32_k(fa, fb, fc, k2, ek2, hdf, rad);
+        const float M = fabsf(fa) + fabsf(fb) + fabsf(fc);
+        verdict = eig32_dir(fb, hdf, rad, M, delta, X, Y, eX)
+                      ? ridge_fast(sK, sE, SOFT_HW, hy, hx, gx, gy, H, W, k, ek, tau, X, Y, eX)
+                      : 2;
+      }
+      if (verdict == 2) sU[atomicAdd(&s_nu, 1)] = (uint16_t)pi;
+    }
+    flags |= verdict << (2 * j);
   }
-  const int mine = (int)flag[0] + (int)flag[1] + (int)flag[2] + (int)flag[3];
+  __syncthreads();
+  {
+    // exact test: one thread per (pixel, neighbour) for the FP64 k- of the
+    // 3x3 neighbourhood and the centre's X-, then one thread per pixel
+    double* sKn = reinterpret_cast<double*>(sRow);  // SOFT_FB x 9
+    double* sXc = sKn + SOFT_FB * 9;                // SOFT_FB x 2
+    uint8_t* sDg = reinterpret_cast<uint8_t*>(sXc + SOFT_FB * 2);
+    const int nu = s_nu;
+    for (int c0 = 0; c0 < nu; c0 += SOFT_FB) {
+      const int nc = min(SOFT_FB, nu - c0);
+      for (int t = tid; t < nc * 9; t += 256) {
+        const int p = t / 9, n = t - p * 9, pi = sU[c0 + p], ty = pi >> 5, tx = pi & 31;
+        double A, C, B;
+        soft_hess64(sLd, ty + n / 3, tx + n % 3, A, C, B);
+        const SoftEig e = soft_eigen(A, C, B);
+        sKn[t] = e.k;
+        if (n == 4) {
+          sXc[2 * p] = e.X;
+          sXc[2 * p + 1] = e.Y;
+          sDg[p] = e.degenerate ? 1 : 0;
+        }
+      }
+      __syncthreads();
+      for (int p = tid; p < nc; p += 256) {
+        const int pi = sU[c0 + p], ty = pi >> 5, tx = pi & 31;
+        sV[pi] = ridge_exact_nb(sKn + 9 * p, sXc[2 * p], sXc[2 * p + 1], sDg[p] != 0, x0 + tx, y0 + ty, H, W, a.tau)
+                     ? 1
+                     : 0;
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (((flags >> (2 * j)) & 3) == 2) flags ^= (2 ^ (int)sV[tid + 256 * j]) << (2 * j);
+  // compaction: block-wide scan of the per-thread counts into the pixel list
+  const int mine = __popc(flags & 0x55);
   int incl = mine;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -174,6 +273,12 @@ __global__ void __launch_bounds__(256) k_soft_ridges(SoftArgs a) {
     pre += w < warp ? s_warp[w] : 0;
     total += s_warp[w];
   }
+  {
+    int p0 = pre + incl - mine;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if ((flags >> (2 * j)) & 1) sR[p0++] = (uint16_t)(tid + 256 * j);
+  }
   const size_t t = ((size_t)f * a.n_ty + blockIdx.y) * a.n_tx + blockIdx.x;
   if (tid == 0) {
     const int start = total ? atomicAdd(&a.count[f], total) : 0;
@@ -182,27 +287,23 @@ __global__ void __launch_bounds__(256) k_soft_ridges(SoftArgs a) {
     a.tile_cnt[t] = max(0, min(total, a.cap - start));
   }
   __syncthreads();
-  int j0 = s_start + pre + incl - mine;
-  const size_t plane = (size_t)a.H * a.W;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    if (!flag[j]) continue;
-    const int jj = j0++;
-    if (jj >= a.cap) continue;
-    const int pi = tid + 256 * j, x = x0 + (pi & 31), y = y0 + (pi >> 5);
-    const size_t i = (size_t)f * plane + (size_t)y * a.W + x;
-    const size_t g = (size_t)f * a.cap + jj;
-    const double kp = a.k[i];
-    const SoftEig e = soft_eigen(a.a[i], a.c[i], a.b[i]);
-    a.xy[g] = (uint32_t)x | ((uint32_t)y << 16);
+  // records: the FP64 Hessian, k-, X- and the soft mask weight
+  const int start = s_start, keep = max(0, min(total, a.cap - start));
+  for (int q = tid; q < keep; q += 256) {
+    const int pi = sR[q], ty = pi >> 5, tx = pi & 31;
+    double A, C, B;
+    soft_hess64(sLd, ty + 1, tx + 1, A, C, B);
+    const SoftEig e = soft_eigen(A, C, B);
+    const size_t g = (size_t)f * a.cap + start + q;
+    a.xy[g] = (uint32_t)(x0 + tx) | ((uint32_t)(y0 + ty) << 16);
     a.flags[g] = (uint8_t)((e.use1 ? 1 : 0) | (e.flip ? 2 : 0));
-    a.rk[g] = kp;
-    a.rX[g] = a.X[i];
-    a.rY[g] = a.Y[i];
-    a.ra[g] = a.a[i];
-    a.rb[g] = a.b[i];
-    a.rc[g] = a.c[i];
-    a.rm[g] = 1.0 / (1.0 + exp(-(a.tau - kp) / a.temp));
+    a.rk[g] = e.k;
+    a.rX[g] = e.X;
+    a.rY[g] = e.Y;
+    a.ra[g] = A;
+    a.rb[g] = B;
+    a.rc[g] = C;
+    a.rm[g] = 1.0 / (1.0 + exp(-(a.tau - e.k) / a.temp));
   }
 }
 
@@ -215,8 +316,7 @@ cudaError_t launch_soft_stencil(const SoftArgs& a, cudaStream_t st) {
   else
     k_soft_hpass<float><<<grid, 256, 0, st>>>(a);
   k_soft_vpass<<<grid, 256, 0, st>>>(a);
-  k_soft_hessian<<<grid, 256, 0, st>>>(a);
-  k_soft_ridges<<<dim3(a.n_tx, a.n_ty, a.n), 256, 0, st>>>(a);
+  k_soft_mask<<<dim3(a.n_tx, a.n_ty, a.n), 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 

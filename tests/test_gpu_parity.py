@@ -233,3 +233,13 @@ def test_plain_full_batch_sampled(torch):
         ref = O.detect(frames[i], p)
         assert_rings_match(out["rings"][i], ref.rings)
         assert_ridges_match(out["ridges"][i], frames[i], p)
+
+
+def test_crowded_bins_hand_off_to_dense(torch):
+    """vote_thresh 0 makes every touched voxel a hotspot and peak_frac 0 lets
+    most of them pass the float threshold, so tiles overflow the sparse
+    kernel's hotspot and peak lists and are handed to the dense kernel mid-way
+    (the sparse kernel's abort path) -- the result is still the oracle's."""
+    f = synth.plain_small(seed=15)
+    params = dict(f.params, vote_thresh=0, peak_frac=0.0, r_min=5, r_max=20)
+    check_frame(torch, f.image, params, capture=True)
