@@ -173,3 +173,31 @@ def test_unnormalised_mass_is_stationary_at_the_true_radius():
     # d(T / rho)/drho = -T / rho^2 with T = 12; the votes sit h off the grid
     # point at rho = 5 +/- h, so T = 12 - O(h) on both sides
     assert abs(ds + 12.0 / 25.0) < 1e-4
+
+
+def test_votes_beyond_nine_sigma_are_negligible():
+    """The GPU leaves out votes farther than 9 sigma(rho) + 1.5 px from the
+    centre.  On the synthetic soft-score frames their total contribution,
+    computed term by term from the oracle's ridge set, is below 1e-12 of the
+    score (the tolerances are 1e-5 for scores and 1e-4 for gradients)."""
+    fr = synth.diff_frames(2, seed=2011, H=128, W=128, n_rings=4)
+    sp = S.SoftParams.make(**synth.DIFF_PARAMS)
+    for f in fr:
+        rd = S.ridges_float(f.image.astype(np.float64), sp)
+        m = S.logistic((sp.ridge_thresh - rd.k) / sp.temperature)
+        H, W = f.image.shape
+        full = S.soft_score(rd, f.rings, sp, H, W)
+        for (cx, cy, rho), score in zip(f.rings, full):
+            sig = sp.sig_a * rho + sp.sig_b
+            cut = 9.0 * sig + 1.5
+            left_out = 0.0
+            for s in (1.0, -1.0):
+                vx = rd.xs + s * rho * rd.X
+                vy = rd.ys + s * rho * rd.Y
+                far = (vx - cx) ** 2 + (vy - cy) ** 2 > cut * cut
+                x0, y0 = np.floor(vx[far]), np.floor(vy[far])
+                for ox in (0, 1):
+                    for oy in (0, 1):
+                        d2 = (x0 + ox - cx) ** 2 + (y0 + oy - cy) ** 2
+                        left_out += float(np.sum(m[far] * np.exp(-d2 / (2 * sig * sig))))
+            assert score > 0 and left_out / rho <= 1e-12 * score, (left_out, score)
