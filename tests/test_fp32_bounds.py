@@ -115,3 +115,54 @@ def test_float_frame_hessian_bound(seed):
     for got, ref in zip((fa, fc, fb), (lxx, lyy, lxy)):
         err = np.abs(got.astype(np.float64) - ref[2:-2, 2:-2])
         assert np.all(err <= delta), float((err / np.maximum(delta, 1e-300)).max())
+
+
+def eig32(a, b, c, delta):
+    """The stencil stage's FP32 eigen step in float32 (plain operations): k-,
+    its bound, and the unit direction with its bound (nan where no bound is
+    given)."""
+    a, b, c = (np.asarray(v, np.float32) for v in (a, b, c))
+    htr = (a + c) * f32(0.5)
+    hdf = (a - c) * f32(0.5)
+    rad = np.sqrt(hdf * hdf + b * b)
+    k = htr - rad
+    M = np.abs(a) + np.abs(b) + np.abs(c)
+    ek = M * f32(16 * U) + f32(1e-30) + f32(3.0) * f32(delta)
+    w = np.abs(hdf) + rad
+    vx = np.where(hdf >= 0, b, -w)
+    vy = np.where(hdf >= 0, -w, b)
+    nrm = np.sqrt(vx * vx + vy * vy)
+    ok = (nrm > f32(4.0) * f32(delta)) & (nrm > 0)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        X, Y = vx / nrm, vy / nrm
+        flip = (X < 0) | ((X == 0) & (Y < 0))
+        X, Y = np.where(flip, -X, X), np.where(flip, -Y, Y)
+        eX = (M * f32(16 * U)) / nrm + f32(4 * U) + f32(6.0) * f32(delta) / (nrm - f32(3.0) * f32(delta))
+    return k, ek, X, Y, np.where(ok, eX, np.nan)
+
+
+def test_eigen_bounds():
+    """|k32 - k_def| <= ek and, where a bound is given and X_def is clear of
+    the canonical-sign ambiguity (|X| > eX, the region the ridge test treats
+    as undecided anyway), |X32 - X_def|, |Y32 - Y_def| <= eX; inputs exact
+    in float32 (delta 0) and perturbed by up to delta."""
+    rng = np.random.default_rng(7)
+    n = 200000
+    scale = 10.0 ** rng.uniform(-3, 3, n)
+    a = (rng.normal(size=n) * scale).astype(np.float32)
+    c = np.where(rng.random(n) < 0.2, a, (rng.normal(size=n) * scale).astype(np.float32))  # near-degenerate
+    b = np.where(rng.random(n) < 0.2, (rng.normal(size=n) * scale * 1e-6).astype(np.float32),
+                 (rng.normal(size=n) * scale).astype(np.float32))
+    for rel in (0.0, 1e-5):
+        delta = rel * (np.abs(a) + np.abs(b) + np.abs(c)).astype(np.float64)
+        # the FP32 stage sees (a, b, c); the definition's values are within delta of them
+        da = a.astype(np.float64) + rng.uniform(-1, 1, n) * delta
+        db = b.astype(np.float64) + rng.uniform(-1, 1, n) * delta
+        dc = c.astype(np.float64) + rng.uniform(-1, 1, n) * delta
+        kd, Xd, Yd, deg = O.eigen(da, dc, db)
+        k32, ek, X32, Y32, eX = eig32(a, b, c, delta.astype(np.float32))
+        assert np.all(np.abs(k32.astype(np.float64) - kd) <= ek.astype(np.float64))
+        sel = np.isfinite(eX) & ~deg & (np.abs(Xd) > eX)
+        assert sel.mean() > 0.5
+        assert np.all(np.abs(X32[sel].astype(np.float64) - Xd[sel]) <= eX[sel])
+        assert np.all(np.abs(Y32[sel].astype(np.float64) - Yd[sel]) <= eX[sel])
