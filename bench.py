@@ -222,42 +222,43 @@ def run_ours(args):
     votes_per_step = stats.votes
 
     # ---- end to end through rd_detect_host (pinned host frames in, host rings
-    #      out): two callers, each with its own context, stream and pinned
-    #      frames, so that one call's copies overlap the other's kernels, as a
+    #      out): several callers, each with its own context, stream and pinned
+    #      frames, so that one call's copies overlap another's kernels, as a
     #      client streaming batches would
     import threading
-    det2 = rd.Detector(params, H, W, B, geometry=geo)
-    dets = [det, det2]
-    hosts = [torch.from_numpy(imgs).pin_memory().numpy() for _ in range(2)]
-    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
-    for i in range(2):
+    nc = max(1, args.e2e_callers)
+    dets = [det] + [rd.Detector(params, H, W, B, geometry=geo) for _ in range(nc - 1)]
+    hosts = [torch.from_numpy(imgs).pin_memory().numpy() for _ in range(nc)]
+    streams = [torch.cuda.Stream() for _ in range(nc)]
+    for i in range(nc):
         dets[i].detect_host(hosts[i], streams[i])
     torch.cuda.synchronize()
-    e2e_steps = max(4, args.steps // 4)
-    e2e_steps += e2e_steps % 2
-    d2h_per = [0, 0]
+    e2e_steps = max(2 * nc, args.steps // 4)
+    e2e_steps -= e2e_steps % nc
+    d2h_per = [0] * nc
 
     def caller(i):
-        for _ in range(e2e_steps // 2):
+        for _ in range(e2e_steps // nc):
             rings, counts, offs, stt = dets[i].detect_host(hosts[i], streams[i])
             d2h_per[i] = 8 * B + 40 * int(counts.sum())
 
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
-    workers = [threading.Thread(target=caller, args=(i,)) for i in range(2)]
+    workers = [threading.Thread(target=caller, args=(i,)) for i in range(nc)]
     for w in workers:
         w.start()
     for w in workers:
         w.join()
     e2e_s = time.perf_counter() - t0
     d2h = max(d2h_per)
-    det2.close()
+    for d in dets[1:]:
+        d.close()
     e2e_s = max_over_ranks(e2e_s, dist, "cuda")
     e2e_value = job_rate(B * e2e_steps, world, e2e_s)
 
     if rank == 0:
-        # ---- roofline of the dominant stage ("Kernels and their rooflines")
+        # ---- roofline of the dominant stage (K4) and of the stencil stage (K1)
         per_launch = stage_ms / args.steps
         dom = int(np.argmax(per_launch))
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
@@ -319,7 +320,7 @@ def run_ours(args):
                              "mvotes_per_s": cpu_mv},
             "e2e": {"value": e2e_value, "unit": "frames/s", "h2d_bytes_per_step": int(imgs.nbytes),
                     "d2h_bytes_per_step": int(d2h), "api": "rd_detect_host", "steps": e2e_steps,
-                    "callers": "2 host threads, each its own context, stream and pinned frames"},
+                    "callers": f"{nc} host threads, each its own context, stream and pinned frames"},
             "gpu_launches": KERNELS_PER_CALL * args.steps,
             "clocks": clocks,
         }
@@ -761,6 +762,7 @@ def main():
     ap.add_argument("--workload", default="plain_full",
                     choices=["plain_full", "video", "diff", "serve", "discs", "coarse"])
     ap.add_argument("--coarse", type=int, default=2, choices=[2, 4])
+    ap.add_argument("--e2e-callers", type=int, default=4, help="host threads of the end-to-end measurement")
     ap.add_argument("--tile", type=int, default=0,
                     help="accumulator tile (cells) of the default and coarse workloads; 0: automatic")
     ap.add_argument("--slab", type=int, default=16, help="slab levels with --tile")
