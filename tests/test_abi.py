@@ -117,3 +117,63 @@ def test_serve_create_validates_classes(lib):
     out = ctypes.c_void_p()
     assert lib.rd_serve_create(arr, 0, 0, 16, ctypes.byref(out)) == rd.RD_E_INVAL
     assert lib.rd_serve_create(arr, 1, 0, 0, ctypes.byref(out)) == rd.RD_E_INVAL
+
+
+_STRUCTS = ("rd_params", "rd_ring", "rd_stats", "rd_geometry", "rd_serve_class")
+
+_C_CALLER = r"""
+#include <stddef.h>
+#include <stdio.h>
+#include "rd.h"
+#define OFF(T, f) printf(#T " " #f " %d\n", (int)offsetof(T, f))
+#define SIZE(T) printf(#T " sizeof %d\n", (int)sizeof(T))
+int main(void) {
+    int32_t taps[64];
+    int i, n = rd_gaussian_taps(2.0f, taps, 64);
+    rd_params p = {0};
+    rd_ctx* ctx = NULL;
+    rd_status st;
+    printf("taps");
+    for (i = 0; i < n; ++i) printf(" %d", (int)taps[i]);
+    printf("\n");
+    st = rd_create(&p, 64, 64, 1, &ctx);          /* sigma = 0: rejected before any device work */
+    printf("create %d %d\n", (int)st, ctx == NULL);
+@LAYOUT@
+    return 0;
+}
+"""
+
+
+def test_plain_c_caller(lib, tmp_path):
+    """The header is plain C99 (no C++ in the declarations) and a C program
+    links against the library; every struct the binding marshals has, in C,
+    the binding's size and the binding's offset for each of its fields."""
+    import shutil
+    import subprocess
+    from paper_1310_1371_gb300 import rd
+    from paper_1310_1371_gb300 import _build
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    layout = []
+    for name in _STRUCTS:
+        layout.append(f"    SIZE({name});")
+        layout += [f"    OFF({name}, {f[0]});" for f in getattr(rd, name)._fields_]
+    src = tmp_path / "caller.c"
+    src.write_text(_C_CALLER.replace("@LAYOUT@", "\n".join(layout)))
+    exe = tmp_path / "caller"
+    libdir = os.path.dirname(_build.LIB)
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-L", libdir, "-lrd", f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines()
+    taps = [int(v) for v in out[0].split()[1:]]
+    assert taps == O.gaussian_taps(2.0).tolist()
+    assert out[1] == "create 1 1"                                     # RD_E_INVAL, no context
+    seen = 0
+    for line in out[2:]:
+        name, field, value = line.split()
+        cls = getattr(rd, name)
+        want = ctypes.sizeof(cls) if field == "sizeof" else getattr(cls, field).offset
+        assert int(value) == want, (name, field)
+        seen += 1
+    assert seen == sum(1 + len(getattr(rd, n)._fields_) for n in _STRUCTS)
