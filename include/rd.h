@@ -48,12 +48,17 @@ typedef enum { RD_U8 = 0, RD_U16 = 1, RD_F32 = 2 /* soft-score entry points only
 typedef enum {
   RD_OK = 0,
   RD_E_INVAL = 1,     /* bad argument: the call did nothing                      */
-  RD_E_NOMEM = 2,     /* device allocation failed at rd_create                   */
+  RD_E_NOMEM = 2,     /* a device (or host) allocation failed                    */
   RD_E_CUDA = 3,      /* a CUDA runtime call failed; see rd_last_error           */
   RD_E_OVERFLOW = 4,  /* a capacity was exceeded; counts are true, lists truncated */
   RD_E_TIMEOUT = 5,   /* a bounded device wait gave up                           */
-  RD_E_BUSY = 6       /* the context is in use by an unfinished call             */
+  RD_E_BUSY = 6,      /* the context is in use by an unfinished call             */
+  RD_E_HOST = 7       /* another host-side failure (a thread could not start)    */
 } rd_status;
+/* No C++ exception leaves the library: a failure inside an entry point is
+ * returned as RD_E_NOMEM or RD_E_HOST (-1 from the entry points that return a
+ * count), with its message in that entry point's last-error string, and what
+ * the call had acquired is released. */
 
 /* Method parameters (the C struct holds floats; the detector widens them to
  * double wherever it computes in double). */
@@ -255,12 +260,12 @@ rd_status rd_create_ex(const rd_params* params, int max_H, int max_W, int max_ba
 /* The geometry a context uses. */
 rd_status rd_get_geometry(const rd_ctx* ctx, rd_geometry* out);
 
-/* Time rd_detect on the caller's n device frames (H x W, dtype, as for
- * rd_detect) for every geometry that fits (tile 64/80/96/128 x slab
- * 8/12/16), with one warm-up and two timed calls each on stream, and return
- * the fastest in *best.  The choice is also cached for this process under
- * (H, W, r_min, r_max), where rd_create and rd_create_ex with an automatic
- * geometry find it.  Allocates and frees a temporary context per candidate
+/* Time rd_detect on the caller's n device frames (1 <= n <= 65535; H x W,
+ * dtype, as for rd_detect) for every geometry that fits (tile 64/80/96/128 x
+ * slab 8/16/24/32), with one warm-up and two timed calls each on stream, and
+ * return the fastest in *best.  The choice is also cached for this process
+ * under (H, W, r_min, r_max, coarse), where rd_create and rd_create_ex with an
+ * automatic geometry find it.  Allocates and frees a temporary context per candidate
  * and synchronises stream.  Errors: RD_E_INVAL (as rd_create / rd_detect),
  * RD_E_NOMEM (no candidate could allocate), RD_E_CUDA. */
 rd_status rd_autotune(const rd_params* params, const void* frames_dev, int n, int H, int W, int dtype, void* stream,
@@ -287,8 +292,8 @@ int64_t rd_peak_threshold(float peak_frac, int r);
  * its stream around its stages; rd_get_timing waits for the last call and
  * writes the stage durations in milliseconds to ms[0 .. RD_N_STAGES-1]:
  * stencil + ridge mask, direction refinement, vote binning, voting + peak
- * epilogue, sort + circle fit.  Returns the number of stages written, or -1
- * (timing off, or no call yet). */
+ * epilogue, sort + circle fit.  Returns the number of stages written,
+ * min(cap, RD_N_STAGES), or -1 (timing off, no call yet, or cap < 0). */
 #define RD_N_STAGES 5
 rd_status rd_set_timing(rd_ctx* ctx, int on);
 int       rd_get_timing(rd_ctx* ctx, float* ms, int cap);
@@ -391,7 +396,7 @@ typedef struct rd_serve_class {
   rd_params params;
   int H, W;       /* frame size of the class's requests                       */
   int dtype;      /* RD_U8 or RD_U16                                          */
-  int max_batch;  /* frames per launch                                        */
+  int max_batch;  /* frames per launch, 1..65535                              */
   int slots;      /* batches in flight at once (contexts and streams), 1..16   */
 } rd_serve_class;
 

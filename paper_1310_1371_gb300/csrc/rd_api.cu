@@ -11,6 +11,7 @@
 //                  the parameter-space cell edge in px (1 unless coarse)
 //   peak threshold S > peak_frac 2 pi  <=>  N > ((peak_frac 2 pi) 2^16) r
 #include "rd_internal.cuh"
+#include "rd_abi_guard.h"
 #include "rd.h"
 
 #include <algorithm>
@@ -246,205 +247,211 @@ extern "C" rd_status rd_create(const rd_params* params, int max_H, int max_W, in
 
 extern "C" rd_status rd_create_ex(const rd_params* params, int max_H, int max_W, int max_batch,
                                   const rd_geometry* geometry, rd_ctx** out) {
-  if (!out) return fail(nullptr, RD_E_INVAL, "out is NULL");
-  *out = nullptr;
-  std::string v = validate(params);
-  if (!v.empty()) return fail(nullptr, RD_E_INVAL, v);
-  rd_geometry geo{0, 0};
-  if (geometry) geo = *geometry;
-  const bool automatic = geo.tile == 0 && geo.slab_levels == 0;
-  if (!automatic && ((geo.tile != ACC_T_LARGE && geo.tile != ACC_T && geo.tile != ACC_T_MID && geo.tile != ACC_T_SMALL) ||
-                     geo.slab_levels < 4 || geo.slab_levels > MAX_SLAB_LEVELS))
-    return fail(nullptr, RD_E_INVAL, "geometry: tile must be 64, 80, 96 or 128 and slab_levels 4 .. 64 (or both 0)");
-  if (automatic && !tuned_geometry(params, max_H, max_W, &geo)) geo = rd_geometry{0, 0};
-  const int R = gaussian_radius(params->sigma);
-  if (max_H < R + 4 || max_W < R + 4 || max_H < 12 || max_W < 12 || max_H > 65535 || max_W > 65535)
-    return fail(nullptr, RD_E_INVAL, "frame size must be at least max(12, ceil(4 sigma) + 4) and at most 65535");
-  if (max_batch < 1 || max_batch > 65535) return fail(nullptr, RD_E_INVAL, "max_batch must be in [1, 65535]");
+  return rd_abi::guard(&g_create_error, [&]() -> rd_status {
+    if (!out) return fail(nullptr, RD_E_INVAL, "out is NULL");
+    *out = nullptr;
+    std::string v = validate(params);
+    if (!v.empty()) return fail(nullptr, RD_E_INVAL, v);
+    rd_geometry geo{0, 0};
+    if (geometry) geo = *geometry;
+    const bool automatic = geo.tile == 0 && geo.slab_levels == 0;
+    if (!automatic && ((geo.tile != ACC_T_LARGE && geo.tile != ACC_T && geo.tile != ACC_T_MID && geo.tile != ACC_T_SMALL) ||
+                       geo.slab_levels < 4 || geo.slab_levels > MAX_SLAB_LEVELS))
+      return fail(nullptr, RD_E_INVAL, "geometry: tile must be 64, 80, 96 or 128 and slab_levels 4 .. 64 (or both 0)");
+    if (automatic && !tuned_geometry(params, max_H, max_W, &geo)) geo = rd_geometry{0, 0};
+    const int R = gaussian_radius(params->sigma);
+    if (max_H < R + 4 || max_W < R + 4 || max_H < 12 || max_W < 12 || max_H > 65535 || max_W > 65535)
+      return fail(nullptr, RD_E_INVAL, "frame size must be at least max(12, ceil(4 sigma) + 4) and at most 65535");
+    if (max_batch < 1 || max_batch > 65535) return fail(nullptr, RD_E_INVAL, "max_batch must be in [1, 65535]");
 
-  rd_ctx* c = new rd_ctx();
-  c->p = *params;
-  c->p.coarse = coarse_of(params);
-  c->lc = c->p.coarse == 4 ? 2 : (c->p.coarse == 2 ? 1 : 0);
-  c->max_H = max_H;
-  c->max_W = max_W;
-  c->max_batch = max_batch;
-  if (cudaGetDevice(&c->device) != cudaSuccess ||
-      cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
-    delete c;
-    return fail(nullptr, RD_E_CUDA, "no CUDA device");
-  }
-  // Gaussian taps and the Hessian scale D = 64 S^2
-  c->taps.R = R;
-  gaussian_taps_impl(params->sigma, c->taps.q, 2 * MAX_RG + 1);
-  long long S = 0;
-  for (int i = 0; i <= 2 * R; ++i) S += c->taps.q[i];
-  c->D64 = (double)(64LL * S * S);
-  c->invD = (float)(1.0 / c->D64);
-  // levels, weights, thresholds
-  const int lv0 = params->r_min - 1, lv1 = params->r_max + 1;
-  c->n_levels = lv1 - lv0 + 1;
-  std::vector<int> h_qoff(c->n_levels), h_qrad(c->n_levels);
-  std::vector<int32_t> h_qtab;
-  std::vector<unsigned long long> h_nthr(c->n_levels, 0);
-  c->max_qn = 1;
-  for (int li = 0; li < c->n_levels; ++li) {
-    int r = lv0 + li;
-    int Rs = level_radius(params->sig_a, params->sig_b, r, 1 << c->lc);
-    int nq = (2 * Rs + 1) * (2 * Rs + 1);
-    h_qoff[li] = (int)h_qtab.size();
-    h_qrad[li] = Rs;
-    h_qtab.resize(h_qtab.size() + nq);
-    level_weights_impl(params->sig_a, params->sig_b, r, h_qtab.data() + h_qoff[li], nq, 1 << c->lc);
-    h_nthr[li] = (unsigned long long)peak_threshold_impl(params->peak_frac, r);
-    c->max_qn = std::max(c->max_qn, nq + (nq & 1));
-  }
-  // Automatic geometry: the first of 128/32, 96/12 and 64/12 whose storage
-  // fits -- for 128 the sparse kernel at three CTAs per SM; always the dense
-  // fallback's per-tile storage on one SM (it splits 128-pixel tiles into
-  // four 64-pixel ones).  Larger tiles cast fewer halo votes per owned voxel
-  // and deeper slabs recompute fewer boundary levels.
-  auto dense_tile = [](int T) { return T == ACC_T_LARGE ? ACC_T_SMALL : T; };
-  auto halo_of = [&](int S) {
-    int mh = 0;
-    for (int lo = params->r_min; lo <= params->r_max; lo += S) {
-      const int hi = std::min(lo + S - 1, params->r_max);
-      for (int r = lo - 1; r <= hi + 1; ++r) mh = std::max(mh, h_qrad[r - lv0] + 1);
-    }
-    return mh;
-  };
-  int qp_need = 4;
-  for (int li = 0; li < c->n_levels; ++li) qp_need = std::max(qp_need, 4 * (1 + h_qrad[li] * (h_qrad[li] + 1)));
-  auto fits = [&](int T, int S, bool three_per_sm) {
-    const int mh = halo_of(S), Td = dense_tile(T);
-    const size_t sp = sparse_smem_bytes(T + 2 * mh, qp_need);
-    return vote_smem_bytes(Td + 2 * mh, Td, c->max_qn) <= 227 * 1024 && sp <= 227 * 1024 &&
-           (!three_per_sm || 3 * (sp + 1024) <= 228 * 1024);
-  };
-  if (geo.tile == 0) {
-    if (fits(ACC_T_LARGE, DEFAULT_SLAB_LEVELS, true))
-      geo = rd_geometry{ACC_T_LARGE, DEFAULT_SLAB_LEVELS};
-    else if (fits(ACC_T, SLAB_LEVELS, false))
-      geo = rd_geometry{ACC_T, SLAB_LEVELS};
-    else
-      geo = rd_geometry{ACC_T_SMALL, SLAB_LEVELS};
-  }
-  // r-slabs of S peak levels; halo = 1 + the largest R_s of the slab's voting levels
-  c->S = geo.slab_levels;
-  int max_h = 0;
-  for (int lo = params->r_min; lo <= params->r_max; lo += c->S) {
-    int hi = std::min(lo + c->S - 1, params->r_max);
-    int h = 0;
-    for (int r = lo - 1; r <= hi + 1; ++r) h = std::max(h, h_qrad[r - lv0]);
-    h += 1;
-    c->h_slabs.push_back(make_int4(lo, hi, h, 0));
-    max_h = std::max(max_h, h);
-  }
-  c->n_slabs = (int)c->h_slabs.size();
-  c->T = geo.tile;
-  c->T_dense = dense_tile(c->T);
-  c->max_rw = c->T + 2 * max_h;
-  c->max_rw_dense = c->T_dense + 2 * max_h;
-  // per slab: (weight, offset) of every tap of its voting levels; offsets are
-  // relative to the window centre in the slab's shared-memory layout
-  std::vector<int> h_qqoff((size_t)c->n_slabs * (c->S + 2), 0);
-  std::vector<int2> h_qqtab;
-  std::vector<int> h_qpoff((size_t)c->n_slabs * (c->S + 2), 0);
-  std::vector<uint32_t> h_qptab;
-  for (int si = 0; si < c->n_slabs; ++si) {
-    const int4 sl = c->h_slabs[si];
-    const int RW = c->T + 2 * sl.z;         // the sparse kernel's slab row
-    const int RWd = c->T_dense + 2 * sl.z;  // the dense kernel's slab row
-    for (int r = sl.x - 1; r <= sl.y + 1; ++r) {
-      const int li = r - lv0, Rs = h_qrad[li], Wq = 2 * Rs + 1;
-      h_qqoff[(size_t)si * (c->S + 2) + (r - sl.x + 1)] = (int)h_qqtab.size();
-      const int32_t* q = h_qtab.data() + h_qoff[li];
-      for (int dy = 0; dy < Wq; ++dy)
-        for (int dx = 0; dx < Wq; ++dx) h_qqtab.push_back(make_int2(q[dy * Wq + dx], (dy - Rs) * RWd + (dx - Rs)));
-      if (h_qqtab.size() & 1) h_qqtab.push_back(make_int2(0, 0));  // even count: 16-byte tap pairs
-      // taps for the sparse kernel in rotation orbits: Q depends on
-      // dx^2 + dy^2 only, so the four taps (dx, dy), (-dy, dx), (-dx, -dy),
-      // (dy, -dx) share one weight.  Entry 0 is the centre {0, 0, Q(0,0), 0};
-      // then, for dx in 1..Rs and dy in 0..Rs (one tap of every orbit),
-      // {o1, o2, Q, 0} with o1 = dy RW + dx and o2 = dx RW - dy: the orbit is
-      // at offsets +-o1 and +-o2 from the centre.
-      h_qpoff[(size_t)si * (c->S + 2) + (r - sl.x + 1)] = (int)h_qptab.size();
-      auto qat = [&](int dx, int dy) { return (uint32_t)q[(dy + Rs) * Wq + (dx + Rs)]; };
-      h_qptab.insert(h_qptab.end(), {0u, 0u, qat(0, 0), 0u});
-      for (int dx = 1; dx <= Rs; ++dx)
-        for (int dy = 0; dy <= Rs; ++dy) {
-          const uint32_t w = qat(dx, dy);
-          if (qat(-dy, dx) != w || qat(-dx, -dy) != w || qat(dy, -dx) != w) {
-            delete c;
-            return fail(nullptr, RD_E_INVAL, "smoothing weights are not invariant under quarter turns");
-          }
-          h_qptab.insert(h_qptab.end(), {(uint32_t)(dy * RW + dx), (uint32_t)(dx * RW - dy), w, 0u});
+    // Until the context is handed out, every exit (an error return or an
+    // exception) frees what it holds.
+    struct Owner {
+      rd_ctx* c;
+      ~Owner() {
+        if (c) {
+          free_all(c);
+          delete c;
         }
-      c->max_qp = std::max(c->max_qp, 4 * (1 + Rs * (Rs + 1)));
+      }
+    } own{new rd_ctx()};
+    rd_ctx* c = own.c;
+    c->p = *params;
+    c->p.coarse = coarse_of(params);
+    c->lc = c->p.coarse == 4 ? 2 : (c->p.coarse == 2 ? 1 : 0);
+    c->max_H = max_H;
+    c->max_W = max_W;
+    c->max_batch = max_batch;
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+      return fail(nullptr, RD_E_CUDA, "no CUDA device");
     }
-  }
-  if (vote_smem_bytes(c->max_rw_dense, c->T_dense, c->max_qn) > 227 * 1024 ||
-      sparse_smem_bytes(c->max_rw, c->max_qp) > 227 * 1024 || c->max_rw * c->max_rw > 65535 * 2) {
-    delete c;
-    return fail(nullptr, RD_E_INVAL, "radius range and geometry need more shared memory than one SM has");
-  }
-  // workspaces
-  const int n_stx = (max_W + ST_TW - 1) / ST_TW, n_sty = (max_H + ST_TH - 1) / ST_TH;
-  const int max_Wc = ((max_W - 1) >> c->lc) + 1, max_Hc = ((max_H - 1) >> c->lc) + 1;  // cells
-  const int n_atx = (max_Wc + c->T - 1) / c->T, n_aty = (max_Hc + c->T - 1) / c->T;
-  c->rl.cap = std::max(4096, (int)std::min<long long>((long long)max_H * max_W / 4, 1LL << 24));
-  c->rl.n_stx = n_stx;
-  c->rl.n_sty = n_sty;
-  const size_t nrec = (size_t)c->rl.cap * max_batch;
-  c->n_bins_max = (long long)max_batch * n_atx * n_aty * c->n_slabs;
-  c->pool_cap = std::min<long long>((long long)max_batch * max_H * max_W * 3, (1LL << 31) - 1);
-  if (c->n_bins_max > INT_MAX / 4) {
-    delete c;
-    return fail(nullptr, RD_E_INVAL, "too many accumulator bins (frames x tiles x slabs > 2^31): lower max_batch");
-  }
-  bool ok = dalloc(&c->slabs, c->n_slabs) && dalloc(&c->q_rad, c->n_levels) &&
-            dalloc(&c->qq_off, h_qqoff.size()) && dalloc(&c->qq_tab, h_qqtab.size()) &&
-            dalloc(&c->qp_off, h_qpoff.size()) && dalloc(&c->qp_tab, h_qptab.size()) &&
-            dalloc(&c->fb_list, 4 * c->n_bins_max) && dalloc(&c->fb_count, 1) && dalloc(&c->queue, c->n_bins_max) &&
-            dalloc(&c->queue_ctr, 2) &&
-            dalloc(&c->nthr, c->n_levels) && dalloc(&c->rl.xy, nrec) &&
-            dalloc(&c->rl.dir, nrec) && dalloc(&c->rl.kvote, nrec) && dalloc(&c->rl.hess, 3 * nrec) &&
-            dalloc(&c->rl.count, max_batch) && dalloc(&c->rl.tile_off, (size_t)max_batch * n_stx * n_sty) &&
-            dalloc(&c->rl.tile_cnt, (size_t)max_batch * n_stx * n_sty) && dalloc(&c->bin_cnt, c->n_bins_max) &&
-            dalloc(&c->bin_off, c->n_bins_max) && dalloc(&c->bin_fill, c->n_bins_max) &&
-            dalloc(&c->block_sums, (c->n_bins_max + 1023) / 1024 + 1) && dalloc(&c->bin_total, 1) &&
-            dalloc(&c->pool, c->pool_cap) && dalloc(&c->peaks, (size_t)max_batch * c->peak_cap) &&
-            dalloc(&c->peak_count, max_batch) && dalloc(&c->stats, 1) &&
-            dalloc((unsigned char**)&c->stage_frames, (size_t)max_batch * max_H * max_W * 2) &&
-            dalloc(&c->stage_rings, (size_t)max_batch * c->peak_cap) && dalloc(&c->stage_counts, max_batch) &&
-            dalloc(&c->stage_offsets, max_batch);
-  if (!ok) {
-    cudaGetLastError();
-    free_all(c);
-    delete c;
-    return fail(nullptr, RD_E_NOMEM, "device allocation failed");
-  }
-  cudaError_t e = cudaMemcpy(c->slabs, c->h_slabs.data(), sizeof(int4) * c->n_slabs, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(c->q_rad, h_qrad.data(), sizeof(int) * c->n_levels, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(c->qq_off, h_qqoff.data(), sizeof(int) * h_qqoff.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(c->qq_tab, h_qqtab.data(), sizeof(int2) * h_qqtab.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(c->qp_off, h_qpoff.data(), sizeof(int) * h_qpoff.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(c->qp_tab, h_qptab.data(), sizeof(uint32_t) * h_qptab.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(c->nthr, h_nthr.data(), sizeof(unsigned long long) * c->n_levels, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemset(c->stats, 0, sizeof(DevStats));
-  if (e != cudaSuccess) {
-    std::string m = std::string("table upload failed: ") + cudaGetErrorString(e);
-    free_all(c);
-    delete c;
-    return fail(nullptr, RD_E_CUDA, m);
-  }
-  *out = c;
-  return RD_OK;
+    // Gaussian taps and the Hessian scale D = 64 S^2
+    c->taps.R = R;
+    gaussian_taps_impl(params->sigma, c->taps.q, 2 * MAX_RG + 1);
+    long long S = 0;
+    for (int i = 0; i <= 2 * R; ++i) S += c->taps.q[i];
+    c->D64 = (double)(64LL * S * S);
+    c->invD = (float)(1.0 / c->D64);
+    // levels, weights, thresholds
+    const int lv0 = params->r_min - 1, lv1 = params->r_max + 1;
+    c->n_levels = lv1 - lv0 + 1;
+    std::vector<int> h_qoff(c->n_levels), h_qrad(c->n_levels);
+    std::vector<int32_t> h_qtab;
+    std::vector<unsigned long long> h_nthr(c->n_levels, 0);
+    c->max_qn = 1;
+    for (int li = 0; li < c->n_levels; ++li) {
+      int r = lv0 + li;
+      int Rs = level_radius(params->sig_a, params->sig_b, r, 1 << c->lc);
+      int nq = (2 * Rs + 1) * (2 * Rs + 1);
+      h_qoff[li] = (int)h_qtab.size();
+      h_qrad[li] = Rs;
+      h_qtab.resize(h_qtab.size() + nq);
+      level_weights_impl(params->sig_a, params->sig_b, r, h_qtab.data() + h_qoff[li], nq, 1 << c->lc);
+      h_nthr[li] = (unsigned long long)peak_threshold_impl(params->peak_frac, r);
+      c->max_qn = std::max(c->max_qn, nq + (nq & 1));
+    }
+    // Automatic geometry: the first of 128/32, 96/12 and 64/12 whose storage
+    // fits -- for 128 the sparse kernel at three CTAs per SM; always the dense
+    // fallback's per-tile storage on one SM (it splits 128-pixel tiles into
+    // four 64-pixel ones).  Larger tiles cast fewer halo votes per owned voxel
+    // and deeper slabs recompute fewer boundary levels.
+    auto dense_tile = [](int T) { return T == ACC_T_LARGE ? ACC_T_SMALL : T; };
+    auto halo_of = [&](int S) {
+      int mh = 0;
+      for (int lo = params->r_min; lo <= params->r_max; lo += S) {
+        const int hi = std::min(lo + S - 1, params->r_max);
+        for (int r = lo - 1; r <= hi + 1; ++r) mh = std::max(mh, h_qrad[r - lv0] + 1);
+      }
+      return mh;
+    };
+    int qp_need = 4;
+    for (int li = 0; li < c->n_levels; ++li) qp_need = std::max(qp_need, 4 * (1 + h_qrad[li] * (h_qrad[li] + 1)));
+    auto fits = [&](int T, int S, bool three_per_sm) {
+      const int mh = halo_of(S), Td = dense_tile(T);
+      const size_t sp = sparse_smem_bytes(T + 2 * mh, qp_need);
+      return vote_smem_bytes(Td + 2 * mh, Td, c->max_qn) <= 227 * 1024 && sp <= 227 * 1024 &&
+             (!three_per_sm || 3 * (sp + 1024) <= 228 * 1024);
+    };
+    if (geo.tile == 0) {
+      if (fits(ACC_T_LARGE, DEFAULT_SLAB_LEVELS, true))
+        geo = rd_geometry{ACC_T_LARGE, DEFAULT_SLAB_LEVELS};
+      else if (fits(ACC_T, SLAB_LEVELS, false))
+        geo = rd_geometry{ACC_T, SLAB_LEVELS};
+      else
+        geo = rd_geometry{ACC_T_SMALL, SLAB_LEVELS};
+    }
+    // r-slabs of S peak levels; halo = 1 + the largest R_s of the slab's voting levels
+    c->S = geo.slab_levels;
+    int max_h = 0;
+    for (int lo = params->r_min; lo <= params->r_max; lo += c->S) {
+      int hi = std::min(lo + c->S - 1, params->r_max);
+      int h = 0;
+      for (int r = lo - 1; r <= hi + 1; ++r) h = std::max(h, h_qrad[r - lv0]);
+      h += 1;
+      c->h_slabs.push_back(make_int4(lo, hi, h, 0));
+      max_h = std::max(max_h, h);
+    }
+    c->n_slabs = (int)c->h_slabs.size();
+    c->T = geo.tile;
+    c->T_dense = dense_tile(c->T);
+    c->max_rw = c->T + 2 * max_h;
+    c->max_rw_dense = c->T_dense + 2 * max_h;
+    // per slab: (weight, offset) of every tap of its voting levels; offsets are
+    // relative to the window centre in the slab's shared-memory layout
+    std::vector<int> h_qqoff((size_t)c->n_slabs * (c->S + 2), 0);
+    std::vector<int2> h_qqtab;
+    std::vector<int> h_qpoff((size_t)c->n_slabs * (c->S + 2), 0);
+    std::vector<uint32_t> h_qptab;
+    for (int si = 0; si < c->n_slabs; ++si) {
+      const int4 sl = c->h_slabs[si];
+      const int RW = c->T + 2 * sl.z;         // the sparse kernel's slab row
+      const int RWd = c->T_dense + 2 * sl.z;  // the dense kernel's slab row
+      for (int r = sl.x - 1; r <= sl.y + 1; ++r) {
+        const int li = r - lv0, Rs = h_qrad[li], Wq = 2 * Rs + 1;
+        h_qqoff[(size_t)si * (c->S + 2) + (r - sl.x + 1)] = (int)h_qqtab.size();
+        const int32_t* q = h_qtab.data() + h_qoff[li];
+        for (int dy = 0; dy < Wq; ++dy)
+          for (int dx = 0; dx < Wq; ++dx) h_qqtab.push_back(make_int2(q[dy * Wq + dx], (dy - Rs) * RWd + (dx - Rs)));
+        if (h_qqtab.size() & 1) h_qqtab.push_back(make_int2(0, 0));  // even count: 16-byte tap pairs
+        // taps for the sparse kernel in rotation orbits: Q depends on
+        // dx^2 + dy^2 only, so the four taps (dx, dy), (-dy, dx), (-dx, -dy),
+        // (dy, -dx) share one weight.  Entry 0 is the centre {0, 0, Q(0,0), 0};
+        // then, for dx in 1..Rs and dy in 0..Rs (one tap of every orbit),
+        // {o1, o2, Q, 0} with o1 = dy RW + dx and o2 = dx RW - dy: the orbit is
+        // at offsets +-o1 and +-o2 from the centre.
+        h_qpoff[(size_t)si * (c->S + 2) + (r - sl.x + 1)] = (int)h_qptab.size();
+        auto qat = [&](int dx, int dy) { return (uint32_t)q[(dy + Rs) * Wq + (dx + Rs)]; };
+        h_qptab.insert(h_qptab.end(), {0u, 0u, qat(0, 0), 0u});
+        for (int dx = 1; dx <= Rs; ++dx)
+          for (int dy = 0; dy <= Rs; ++dy) {
+            const uint32_t w = qat(dx, dy);
+            if (qat(-dy, dx) != w || qat(-dx, -dy) != w || qat(dy, -dx) != w) {
+              return fail(nullptr, RD_E_INVAL, "smoothing weights are not invariant under quarter turns");
+            }
+            h_qptab.insert(h_qptab.end(), {(uint32_t)(dy * RW + dx), (uint32_t)(dx * RW - dy), w, 0u});
+          }
+        c->max_qp = std::max(c->max_qp, 4 * (1 + Rs * (Rs + 1)));
+      }
+    }
+    if (vote_smem_bytes(c->max_rw_dense, c->T_dense, c->max_qn) > 227 * 1024 ||
+        sparse_smem_bytes(c->max_rw, c->max_qp) > 227 * 1024 || c->max_rw * c->max_rw > 65535 * 2) {
+      return fail(nullptr, RD_E_INVAL, "radius range and geometry need more shared memory than one SM has");
+    }
+    // workspaces
+    const int n_stx = (max_W + ST_TW - 1) / ST_TW, n_sty = (max_H + ST_TH - 1) / ST_TH;
+    const int max_Wc = ((max_W - 1) >> c->lc) + 1, max_Hc = ((max_H - 1) >> c->lc) + 1;  // cells
+    const int n_atx = (max_Wc + c->T - 1) / c->T, n_aty = (max_Hc + c->T - 1) / c->T;
+    c->rl.cap = std::max(4096, (int)std::min<long long>((long long)max_H * max_W / 4, 1LL << 24));
+    c->rl.n_stx = n_stx;
+    c->rl.n_sty = n_sty;
+    const size_t nrec = (size_t)c->rl.cap * max_batch;
+    c->n_bins_max = (long long)max_batch * n_atx * n_aty * c->n_slabs;
+    c->pool_cap = std::min<long long>((long long)max_batch * max_H * max_W * 3, (1LL << 31) - 1);
+    if (c->n_bins_max > INT_MAX / 4) {
+      return fail(nullptr, RD_E_INVAL, "too many accumulator bins (frames x tiles x slabs > 2^31): lower max_batch");
+    }
+    bool ok = dalloc(&c->slabs, c->n_slabs) && dalloc(&c->q_rad, c->n_levels) &&
+              dalloc(&c->qq_off, h_qqoff.size()) && dalloc(&c->qq_tab, h_qqtab.size()) &&
+              dalloc(&c->qp_off, h_qpoff.size()) && dalloc(&c->qp_tab, h_qptab.size()) &&
+              dalloc(&c->fb_list, 4 * c->n_bins_max) && dalloc(&c->fb_count, 1) && dalloc(&c->queue, c->n_bins_max) &&
+              dalloc(&c->queue_ctr, 2) &&
+              dalloc(&c->nthr, c->n_levels) && dalloc(&c->rl.xy, nrec) &&
+              dalloc(&c->rl.dir, nrec) && dalloc(&c->rl.kvote, nrec) && dalloc(&c->rl.hess, 3 * nrec) &&
+              dalloc(&c->rl.count, max_batch) && dalloc(&c->rl.tile_off, (size_t)max_batch * n_stx * n_sty) &&
+              dalloc(&c->rl.tile_cnt, (size_t)max_batch * n_stx * n_sty) && dalloc(&c->bin_cnt, c->n_bins_max) &&
+              dalloc(&c->bin_off, c->n_bins_max) && dalloc(&c->bin_fill, c->n_bins_max) &&
+              dalloc(&c->block_sums, (c->n_bins_max + 1023) / 1024 + 1) && dalloc(&c->bin_total, 1) &&
+              dalloc(&c->pool, c->pool_cap) && dalloc(&c->peaks, (size_t)max_batch * c->peak_cap) &&
+              dalloc(&c->peak_count, max_batch) && dalloc(&c->stats, 1) &&
+              dalloc((unsigned char**)&c->stage_frames, (size_t)max_batch * max_H * max_W * 2) &&
+              dalloc(&c->stage_rings, (size_t)max_batch * c->peak_cap) && dalloc(&c->stage_counts, max_batch) &&
+              dalloc(&c->stage_offsets, max_batch);
+    if (!ok) {
+      cudaGetLastError();
+      return fail(nullptr, RD_E_NOMEM, "device allocation failed");
+    }
+    cudaError_t e = cudaMemcpy(c->slabs, c->h_slabs.data(), sizeof(int4) * c->n_slabs, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->q_rad, h_qrad.data(), sizeof(int) * c->n_levels, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(c->qq_off, h_qqoff.data(), sizeof(int) * h_qqoff.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(c->qq_tab, h_qqtab.data(), sizeof(int2) * h_qqtab.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(c->qp_off, h_qpoff.data(), sizeof(int) * h_qpoff.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(c->qp_tab, h_qptab.data(), sizeof(uint32_t) * h_qptab.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(c->nthr, h_nthr.data(), sizeof(unsigned long long) * c->n_levels, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(c->stats, 0, sizeof(DevStats));
+    if (e != cudaSuccess) {
+      std::string m = std::string("table upload failed: ") + cudaGetErrorString(e);
+      return fail(nullptr, RD_E_CUDA, m);
+    }
+    own.c = nullptr;
+    *out = c;
+    return RD_OK;
+  });
 }
 
 // Enqueue every stage of rd_detect on the stream (the body of rd_detect, and
@@ -622,47 +629,49 @@ static void drop_graph(rd_ctx* c) {
 
 extern "C" rd_status rd_detect(rd_ctx* c, const void* frames_dev, int n, int H, int W, int dtype, void* stream,
                                rd_ring* rings_dev, int ring_cap, int* counts_dev, int* offsets_dev) {
-  if (!c) return RD_E_INVAL;
-  if (!c->graph_on) return detect_enqueue(c, frames_dev, n, H, W, dtype, stream, rings_dev, ring_cap, counts_dev,
-                                          offsets_dev);
-  cudaStream_t st = (cudaStream_t)stream;
-  if (!st) return fail(c, RD_E_INVAL, "graph mode needs a non-default stream");
-  const void* args[4] = {frames_dev, rings_dev, counts_dev, offsets_dev};
-  const int shape[5] = {n, H, W, dtype, ring_cap};
-  const bool same = c->gexec && st == c->g_stream && std::equal(args, args + 4, c->g_args) &&
-                    std::equal(shape, shape + 5, c->g_shape);
-  if (!same) {  // capture this argument set once; later identical calls replay it
-    drop_graph(c);
-    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
-    if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
-    const bool timing = c->timing;
-    c->timing = false;
-    rd_status s = detect_enqueue(c, frames_dev, n, H, W, dtype, stream, rings_dev, ring_cap, counts_dev, offsets_dev);
-    c->timing = timing;
-    cudaGraph_t g = nullptr;
-    e = cudaStreamEndCapture(st, &g);
-    if (s != RD_OK) {
+  return rd_abi::guard(c ? &c->err : &g_create_error, [&]() -> rd_status {
+    if (!c) return RD_E_INVAL;
+    if (!c->graph_on) return detect_enqueue(c, frames_dev, n, H, W, dtype, stream, rings_dev, ring_cap, counts_dev,
+                                            offsets_dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!st) return fail(c, RD_E_INVAL, "graph mode needs a non-default stream");
+    const void* args[4] = {frames_dev, rings_dev, counts_dev, offsets_dev};
+    const int shape[5] = {n, H, W, dtype, ring_cap};
+    const bool same = c->gexec && st == c->g_stream && std::equal(args, args + 4, c->g_args) &&
+                      std::equal(shape, shape + 5, c->g_shape);
+    if (!same) {  // capture this argument set once; later identical calls replay it
+      drop_graph(c);
+      cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+      if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+      const bool timing = c->timing;
+      c->timing = false;
+      rd_status s = detect_enqueue(c, frames_dev, n, H, W, dtype, stream, rings_dev, ring_cap, counts_dev, offsets_dev);
+      c->timing = timing;
+      cudaGraph_t g = nullptr;
+      e = cudaStreamEndCapture(st, &g);
+      if (s != RD_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&c->gexec, g, 0);
       if (g) cudaGraphDestroy(g);
-      return s;
+      if (e != cudaSuccess) {
+        c->gexec = nullptr;
+        return fail(c, RD_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+      }
+      std::copy(args, args + 4, c->g_args);
+      std::copy(shape, shape + 5, c->g_shape);
+      c->g_stream = st;
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->gexec, g, 0);
-    if (g) cudaGraphDestroy(g);
-    if (e != cudaSuccess) {
-      c->gexec = nullptr;
-      return fail(c, RD_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-    }
-    std::copy(args, args + 4, c->g_args);
-    std::copy(shape, shape + 5, c->g_shape);
-    c->g_stream = st;
-  }
-  c->last_stream = st;
-  c->last_n = n;
-  c->last_H = H;
-  c->last_W = W;
-  c->timed = false;
-  cudaError_t e = cudaGraphLaunch(c->gexec, st);
-  if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
-  return RD_OK;
+    c->last_stream = st;
+    c->last_n = n;
+    c->last_H = H;
+    c->last_W = W;
+    c->timed = false;
+    cudaError_t e = cudaGraphLaunch(c->gexec, st);
+    if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
+    return RD_OK;
+  });
 }
 
 extern "C" rd_status rd_set_graph(rd_ctx* c, int on) {
@@ -674,64 +683,70 @@ extern "C" rd_status rd_set_graph(rd_ctx* c, int on) {
 
 extern "C" rd_status rd_detect_host(rd_ctx* c, const void* frames_host, int n, int H, int W, int dtype, void* stream,
                                     rd_ring* rings_host, int ring_cap, int* counts_host, int* offsets_host) {
-  if (!c) return RD_E_INVAL;
-  if (!frames_host || !counts_host || !offsets_host || (ring_cap > 0 && !rings_host) || ring_cap < 0)
-    return fail(c, RD_E_INVAL, "NULL buffer or negative ring_cap");
-  if (n < 1 || n > c->max_batch || H < 1 || W < 1 || H > c->max_H || W > c->max_W)
-    return fail(c, RD_E_INVAL, "batch or frame size above the rd_create maxima");
-  if (ring_cap > c->max_batch * c->peak_cap) return fail(c, RD_E_INVAL, "ring_cap above max_batch * 4096");
-  if (dtype != RD_U8 && dtype != RD_U16) return fail(c, RD_E_INVAL, "dtype must be RD_U8 or RD_U16");
-  cudaStream_t st = (cudaStream_t)stream;
-  size_t bytes = (size_t)n * H * W * (dtype == RD_U8 ? 1 : 2);
-  cudaError_t e = cudaMemcpyAsync(c->stage_frames, frames_host, bytes, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("frames copy: ") + cudaGetErrorString(e));
-  rd_status s = rd_detect(c, c->stage_frames, n, H, W, dtype, stream, c->stage_rings, ring_cap, c->stage_counts,
-                          c->stage_offsets);
-  if (s != RD_OK) return s;
-  e = cudaMemcpyAsync(counts_host, c->stage_counts, sizeof(int) * n, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(offsets_host, c->stage_offsets, sizeof(int) * n, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e == cudaSuccess && ring_cap > 0) {
-    long long used = (long long)offsets_host[n - 1] + counts_host[n - 1];
-    used = std::min<long long>(used, ring_cap);
-    if (used > 0)
-      e = cudaMemcpyAsync(rings_host, c->stage_rings, sizeof(rd_ring) * used, cudaMemcpyDeviceToHost, st);
-  }
-  if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("result copy: ") + cudaGetErrorString(e));
-  rd_stats stats;
-  return rd_get_stats(c, &stats);
+  return rd_abi::guard(c ? &c->err : &g_create_error, [&]() -> rd_status {
+    if (!c) return RD_E_INVAL;
+    if (!frames_host || !counts_host || !offsets_host || (ring_cap > 0 && !rings_host) || ring_cap < 0)
+      return fail(c, RD_E_INVAL, "NULL buffer or negative ring_cap");
+    if (n < 1 || n > c->max_batch || H < 1 || W < 1 || H > c->max_H || W > c->max_W)
+      return fail(c, RD_E_INVAL, "batch or frame size above the rd_create maxima");
+    if (ring_cap > c->max_batch * c->peak_cap) return fail(c, RD_E_INVAL, "ring_cap above max_batch * 4096");
+    if (dtype != RD_U8 && dtype != RD_U16) return fail(c, RD_E_INVAL, "dtype must be RD_U8 or RD_U16");
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t bytes = (size_t)n * H * W * (dtype == RD_U8 ? 1 : 2);
+    cudaError_t e = cudaMemcpyAsync(c->stage_frames, frames_host, bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("frames copy: ") + cudaGetErrorString(e));
+    rd_status s = rd_detect(c, c->stage_frames, n, H, W, dtype, stream, c->stage_rings, ring_cap, c->stage_counts,
+                            c->stage_offsets);
+    if (s != RD_OK) return s;
+    e = cudaMemcpyAsync(counts_host, c->stage_counts, sizeof(int) * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(offsets_host, c->stage_offsets, sizeof(int) * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && ring_cap > 0) {
+      long long used = (long long)offsets_host[n - 1] + counts_host[n - 1];
+      used = std::min<long long>(used, ring_cap);
+      if (used > 0)
+        e = cudaMemcpyAsync(rings_host, c->stage_rings, sizeof(rd_ring) * used, cudaMemcpyDeviceToHost, st);
+    }
+    if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("result copy: ") + cudaGetErrorString(e));
+    rd_stats stats;
+    return rd_get_stats(c, &stats);
+  });
 }
 
 extern "C" rd_status rd_get_stats(rd_ctx* c, rd_stats* out) {
-  if (!c || !out) return RD_E_INVAL;
-  cudaError_t e = cudaStreamSynchronize(c->last_stream);
-  DevStats d{};
-  if (e == cudaSuccess) e = cudaMemcpy(&d, c->stats, sizeof(DevStats), cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("stats: ") + cudaGetErrorString(e));
-  out->ridge_pixels = (int64_t)d.ridge;
-  out->votes = (int64_t)d.votes;
-  out->peaks = (int64_t)d.peaks;
-  out->exact_fallbacks = (int64_t)d.fallbacks;
-  out->overflow = d.overflow;
-  out->n_frames = c->last_n;
-  out->hotspots = (int64_t)d.hotspots;
-  out->smooth_macs = (int64_t)d.smooth_macs;
-  return d.overflow ? RD_E_OVERFLOW : RD_OK;
+  return rd_abi::guard(c ? &c->err : &g_create_error, [&]() -> rd_status {
+    if (!c || !out) return RD_E_INVAL;
+    cudaError_t e = cudaStreamSynchronize(c->last_stream);
+    DevStats d{};
+    if (e == cudaSuccess) e = cudaMemcpy(&d, c->stats, sizeof(DevStats), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("stats: ") + cudaGetErrorString(e));
+    out->ridge_pixels = (int64_t)d.ridge;
+    out->votes = (int64_t)d.votes;
+    out->peaks = (int64_t)d.peaks;
+    out->exact_fallbacks = (int64_t)d.fallbacks;
+    out->overflow = d.overflow;
+    out->n_frames = c->last_n;
+    out->hotspots = (int64_t)d.hotspots;
+    out->smooth_macs = (int64_t)d.smooth_macs;
+    return d.overflow ? RD_E_OVERFLOW : RD_OK;
+  });
 }
 
 extern "C" rd_status rd_set_timing(rd_ctx* c, int on) {
-  if (!c) return RD_E_INVAL;
-  if (on && !c->ev[0]) {
-    for (int i = 0; i <= RD_N_STAGES; ++i)
-      if (cudaEventCreate(&c->ev[i]) != cudaSuccess) return fail(c, RD_E_CUDA, "cudaEventCreate failed");
-  }
-  c->timing = on != 0;
-  return RD_OK;
+  return rd_abi::guard(c ? &c->err : &g_create_error, [&]() -> rd_status {
+    if (!c) return RD_E_INVAL;
+    if (on && !c->ev[0]) {
+      for (int i = 0; i <= RD_N_STAGES; ++i)
+        if (cudaEventCreate(&c->ev[i]) != cudaSuccess) return fail(c, RD_E_CUDA, "cudaEventCreate failed");
+    }
+    c->timing = on != 0;
+    return RD_OK;
+  });
 }
 
 extern "C" int rd_get_timing(rd_ctx* c, float* ms, int cap) {
-  if (!c || !ms || !c->timed || !c->ev[0]) return -1;
+  if (!c || !ms || cap < 0 || !c->timed || !c->ev[0]) return -1;
   if (cudaEventSynchronize(c->ev[RD_N_STAGES]) != cudaSuccess) return -1;
   int n = std::min(cap, RD_N_STAGES);
   for (int i = 0; i < n; ++i)
@@ -753,31 +768,33 @@ extern "C" rd_status rd_destroy(rd_ctx* c) {
 extern "C" const char* rd_last_error(const rd_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
 
 extern "C" int rd_debug_ridges(rd_ctx* c, int f, int32_t* xy, float* dir, int64_t* hess, int cap) {
-  if (!c || f < 0 || f >= c->last_n || cap < 0) return -1;
-  if (cudaStreamSynchronize(c->last_stream) != cudaSuccess) return -1;
-  int cnt = 0;
-  if (cudaMemcpy(&cnt, c->rl.count + f, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
-  int n = std::min(std::min(cnt, c->rl.cap), cap);
-  size_t base = (size_t)f * c->rl.cap;
-  if (n > 0) {
-    std::vector<uint32_t> hxy(n);
-    std::vector<float4> hdir(n);
-    if (cudaMemcpy(hxy.data(), c->rl.xy + base, 4 * n, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
-    if (cudaMemcpy(hdir.data(), c->rl.dir + base, 16 * n, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
-    for (int i = 0; i < n; ++i) {
-      if (xy) {
-        xy[2 * i] = (int32_t)(hxy[i] & 0xffffu);
-        xy[2 * i + 1] = (int32_t)(hxy[i] >> 16);
+  return rd_abi::guard_count(c ? &c->err : &g_create_error, [&]() -> int {
+    if (!c || f < 0 || f >= c->last_n || cap < 0) return -1;
+    if (cudaStreamSynchronize(c->last_stream) != cudaSuccess) return -1;
+    int cnt = 0;
+    if (cudaMemcpy(&cnt, c->rl.count + f, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+    int n = std::min(std::min(cnt, c->rl.cap), cap);
+    size_t base = (size_t)f * c->rl.cap;
+    if (n > 0) {
+      std::vector<uint32_t> hxy(n);
+      std::vector<float4> hdir(n);
+      if (cudaMemcpy(hxy.data(), c->rl.xy + base, 4 * n, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+      if (cudaMemcpy(hdir.data(), c->rl.dir + base, 16 * n, cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+      for (int i = 0; i < n; ++i) {
+        if (xy) {
+          xy[2 * i] = (int32_t)(hxy[i] & 0xffffu);
+          xy[2 * i + 1] = (int32_t)(hxy[i] >> 16);
+        }
+        if (dir) {
+          dir[2 * i] = hdir[i].x;
+          dir[2 * i + 1] = hdir[i].y;
+        }
       }
-      if (dir) {
-        dir[2 * i] = hdir[i].x;
-        dir[2 * i + 1] = hdir[i].y;
-      }
+      if (hess && cudaMemcpy(hess, c->rl.hess + 3 * base, 24 * (size_t)n, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return -1;
     }
-    if (hess && cudaMemcpy(hess, c->rl.hess + 3 * base, 24 * (size_t)n, cudaMemcpyDeviceToHost) != cudaSuccess)
-      return -1;
-  }
-  return cnt;
+    return cnt;
+  });
 }
 
 extern "C" rd_status rd_debug_route(rd_ctx* c, int all_dense) {
@@ -807,69 +824,72 @@ extern "C" rd_status rd_get_geometry(const rd_ctx* c, rd_geometry* out) {
 // caller's stream); the fastest is returned and cached for rd_create.
 extern "C" rd_status rd_autotune(const rd_params* params, const void* frames_dev, int n, int H, int W, int dtype,
                                  void* stream, rd_geometry* best) {
-  if (!params || !frames_dev || !best || n < 1) return fail(nullptr, RD_E_INVAL, "rd_autotune: NULL argument or n < 1");
-  std::string v = validate(params);
-  if (!v.empty()) return fail(nullptr, RD_E_INVAL, v);
-  cudaStream_t st = (cudaStream_t)stream;
-  const int ring_cap = n * 4096;
-  rd_ring* rings = nullptr;
-  int* counts = nullptr;
-  int* offs = nullptr;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  rd_status res = RD_OK;
-  if (!dalloc(&rings, (size_t)ring_cap) || !dalloc(&counts, (size_t)n) || !dalloc(&offs, (size_t)n)) {
-    res = fail(nullptr, RD_E_NOMEM, "rd_autotune: output buffers");
-  } else if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
-    res = fail(nullptr, RD_E_CUDA, "rd_autotune: cudaEventCreate");
-  }
-  float best_ms = 0.0f;
-  rd_geometry bg{0, 0};
-  rd_status last = RD_E_NOMEM;
-  std::string last_msg = "no candidate geometry could allocate its workspaces";
-  const int tiles[4] = {ACC_T_SMALL, ACC_T_MID, ACC_T, ACC_T_LARGE};
-  const int slabs[4] = {8, 16, 24, 32};
-  for (int ti = 0; ti < 4 && res == RD_OK; ++ti)
-    for (int si = 0; si < 4 && res == RD_OK; ++si) {
-      const rd_geometry g{tiles[ti], slabs[si]};
-      rd_ctx* c = nullptr;
-      rd_status s = rd_create_ex(params, H, W, n, &g, &c);
-      if (s != RD_OK) {  // does not fit this radius range, or no memory: skip
-        last = s;
-        last_msg = g_create_error;
-        continue;
-      }
-      float ms = 0.0f;
-      s = rd_detect(c, frames_dev, n, H, W, dtype, stream, rings, ring_cap, counts, offs);
-      if (s == RD_OK && cudaEventRecord(e0, st) == cudaSuccess) {
-        for (int k = 0; k < 2 && s == RD_OK; ++k) s = rd_detect(c, frames_dev, n, H, W, dtype, stream, rings, ring_cap, counts, offs);
-        if (s == RD_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                           cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-          s = RD_E_CUDA;
-      }
-      if (s != RD_OK) {
-        res = fail(nullptr, s, std::string("rd_autotune: ") + c->err);
-        rd_destroy(c);
-        break;
-      }
-      rd_destroy(c);
-      if (bg.tile == 0 || ms < best_ms) {
-        best_ms = ms;
-        bg = g;
-      }
+  return rd_abi::guard(&g_create_error, [&]() -> rd_status {
+    if (!params || !frames_dev || !best || n < 1 || n > 65535)
+      return fail(nullptr, RD_E_INVAL, "rd_autotune: NULL argument or n outside [1, 65535]");
+    std::string v = validate(params);
+    if (!v.empty()) return fail(nullptr, RD_E_INVAL, v);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int ring_cap = n * 4096;
+    rd_ring* rings = nullptr;
+    int* counts = nullptr;
+    int* offs = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    rd_status res = RD_OK;
+    if (!dalloc(&rings, (size_t)ring_cap) || !dalloc(&counts, (size_t)n) || !dalloc(&offs, (size_t)n)) {
+      res = fail(nullptr, RD_E_NOMEM, "rd_autotune: output buffers");
+    } else if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+      res = fail(nullptr, RD_E_CUDA, "rd_autotune: cudaEventCreate");
     }
-  if (e0) cudaEventDestroy(e0);
-  if (e1) cudaEventDestroy(e1);
-  cudaFree(rings);
-  cudaFree(counts);
-  cudaFree(offs);
-  if (res != RD_OK) return res;
-  if (bg.tile == 0) return fail(nullptr, last, "rd_autotune: " + last_msg);
-  {
-    std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tuned[TuneKey{H, W, params->r_min, params->r_max, coarse_of(params)}] = bg;
-  }
-  *best = bg;
-  return RD_OK;
+    float best_ms = 0.0f;
+    rd_geometry bg{0, 0};
+    rd_status last = RD_E_NOMEM;
+    std::string last_msg = "no candidate geometry could allocate its workspaces";
+    const int tiles[4] = {ACC_T_SMALL, ACC_T_MID, ACC_T, ACC_T_LARGE};
+    const int slabs[4] = {8, 16, 24, 32};
+    for (int ti = 0; ti < 4 && res == RD_OK; ++ti)
+      for (int si = 0; si < 4 && res == RD_OK; ++si) {
+        const rd_geometry g{tiles[ti], slabs[si]};
+        rd_ctx* c = nullptr;
+        rd_status s = rd_create_ex(params, H, W, n, &g, &c);
+        if (s != RD_OK) {  // does not fit this radius range, or no memory: skip
+          last = s;
+          last_msg = g_create_error;
+          continue;
+        }
+        float ms = 0.0f;
+        s = rd_detect(c, frames_dev, n, H, W, dtype, stream, rings, ring_cap, counts, offs);
+        if (s == RD_OK && cudaEventRecord(e0, st) == cudaSuccess) {
+          for (int k = 0; k < 2 && s == RD_OK; ++k) s = rd_detect(c, frames_dev, n, H, W, dtype, stream, rings, ring_cap, counts, offs);
+          if (s == RD_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                             cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            s = RD_E_CUDA;
+        }
+        if (s != RD_OK) {
+          res = fail(nullptr, s, std::string("rd_autotune: ") + c->err);
+          rd_destroy(c);
+          break;
+        }
+        rd_destroy(c);
+        if (bg.tile == 0 || ms < best_ms) {
+          best_ms = ms;
+          bg = g;
+        }
+      }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(rings);
+    cudaFree(counts);
+    cudaFree(offs);
+    if (res != RD_OK) return res;
+    if (bg.tile == 0) return fail(nullptr, last, "rd_autotune: " + last_msg);
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mutex);
+      g_tuned[TuneKey{H, W, params->r_min, params->r_max, coarse_of(params)}] = bg;
+    }
+    *best = bg;
+    return RD_OK;
+  });
 }
 
 
@@ -961,81 +981,89 @@ static rd_status soft_prepare(rd_ctx* c, const void* frames, int n, int H, int W
 extern "C" rd_status rd_soft_score(rd_ctx* c, const void* frames_dev, int n, int H, int W, int dtype, void* stream,
                                    const rd_ring* rings_dev, const int* counts_dev, float* score_dev,
                                    float* dparams_dev) {
-  if (!c) return RD_E_INVAL;
-  if (!score_dev) return fail(c, RD_E_INVAL, "score_dev is NULL");
-  cudaStream_t st = (cudaStream_t)stream;
-  SoftArgs a;
-  rd_status s = soft_prepare(c, frames_dev, n, H, W, dtype, st, rings_dev, counts_dev, &a);
-  if (s != RD_OK) return s;
-  a.score = score_dev;
-  a.dparams = dparams_dev;
-  cudaError_t e = launch_soft_score(a, counts_dev, c->s_ring_off, st);
-  if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("soft score: ") + cudaGetErrorString(e));
-  return RD_OK;
+  return rd_abi::guard(c ? &c->err : &g_create_error, [&]() -> rd_status {
+    if (!c) return RD_E_INVAL;
+    if (!score_dev) return fail(c, RD_E_INVAL, "score_dev is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    SoftArgs a;
+    rd_status s = soft_prepare(c, frames_dev, n, H, W, dtype, st, rings_dev, counts_dev, &a);
+    if (s != RD_OK) return s;
+    a.score = score_dev;
+    a.dparams = dparams_dev;
+    cudaError_t e = launch_soft_score(a, counts_dev, c->s_ring_off, st);
+    if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("soft score: ") + cudaGetErrorString(e));
+    return RD_OK;
+  });
 }
 
 extern "C" rd_status rd_backward(rd_ctx* c, const float* frames_dev, int n, int H, int W, void* stream,
                                  const rd_ring* rings_dev, const int* counts_dev, const float* dscore_dev,
                                  float* dimage_dev, float* dparams_dev) {
-  if (!c) return RD_E_INVAL;
-  if (!dscore_dev || !dimage_dev) return fail(c, RD_E_INVAL, "dscore_dev and dimage_dev must not be NULL");
-  cudaStream_t st = (cudaStream_t)stream;
-  SoftArgs a;
-  rd_status s = soft_prepare(c, frames_dev, n, H, W, RD_F32, st, rings_dev, counts_dev, &a);
-  if (s != RD_OK) return s;
-  const size_t rec = sizeof(double) * (size_t)n * c->rl.cap;
-  cudaError_t e = cudaMemsetAsync(c->s_gk, 0, rec, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(c->s_gX, 0, rec, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(c->s_gY, 0, rec, st);
-  a.dscore = dscore_dev;
-  a.dparams = dparams_dev;
-  a.accumulate = 1;
-  a.dimage = dimage_dev;
-  if (e == cudaSuccess) e = launch_soft_score(a, counts_dev, c->s_ring_off, st);
-  if (e == cudaSuccess) e = launch_soft_backward_image(a, st);
-  if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("soft backward: ") + cudaGetErrorString(e));
-  return RD_OK;
+  return rd_abi::guard(c ? &c->err : &g_create_error, [&]() -> rd_status {
+    if (!c) return RD_E_INVAL;
+    if (!dscore_dev || !dimage_dev) return fail(c, RD_E_INVAL, "dscore_dev and dimage_dev must not be NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    SoftArgs a;
+    rd_status s = soft_prepare(c, frames_dev, n, H, W, RD_F32, st, rings_dev, counts_dev, &a);
+    if (s != RD_OK) return s;
+    const size_t rec = sizeof(double) * (size_t)n * c->rl.cap;
+    cudaError_t e = cudaMemsetAsync(c->s_gk, 0, rec, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->s_gX, 0, rec, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->s_gY, 0, rec, st);
+    a.dscore = dscore_dev;
+    a.dparams = dparams_dev;
+    a.accumulate = 1;
+    a.dimage = dimage_dev;
+    if (e == cudaSuccess) e = launch_soft_score(a, counts_dev, c->s_ring_off, st);
+    if (e == cudaSuccess) e = launch_soft_backward_image(a, st);
+    if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("soft backward: ") + cudaGetErrorString(e));
+    return RD_OK;
+  });
 }
 
 extern "C" rd_status rd_refine(rd_ctx* c, const void* frames_dev, int n, int H, int W, int dtype, void* stream,
                                rd_ring* rings_dev, const int* counts_dev, int iters, float step) {
-  if (!c) return RD_E_INVAL;
-  if (iters < 0 || !(step > 0.0f)) return fail(c, RD_E_INVAL, "iters must be >= 0 and step > 0");
-  cudaStream_t st = (cudaStream_t)stream;
-  SoftArgs a;
-  rd_status s = soft_prepare(c, frames_dev, n, H, W, dtype, st, rings_dev, counts_dev, &a);
-  if (s != RD_OK) return s;
-  a.rings_mut = rings_dev;
-  a.score = c->s_score;
-  a.dparams = c->s_dparams;
-  a.max_rings = c->max_batch * c->peak_cap;
-  a.step = step;
-  cudaError_t e = cudaSuccess;
-  for (int it = 0; it < iters && e == cudaSuccess; ++it) {
-    e = launch_soft_score(a, counts_dev, c->s_ring_off, st);
-    if (e == cudaSuccess) e = launch_soft_refine_step(a, st);
-  }
-  if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("refine: ") + cudaGetErrorString(e));
-  return RD_OK;
+  return rd_abi::guard(c ? &c->err : &g_create_error, [&]() -> rd_status {
+    if (!c) return RD_E_INVAL;
+    if (iters < 0 || !(step > 0.0f)) return fail(c, RD_E_INVAL, "iters must be >= 0 and step > 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    SoftArgs a;
+    rd_status s = soft_prepare(c, frames_dev, n, H, W, dtype, st, rings_dev, counts_dev, &a);
+    if (s != RD_OK) return s;
+    a.rings_mut = rings_dev;
+    a.score = c->s_score;
+    a.dparams = c->s_dparams;
+    a.max_rings = c->max_batch * c->peak_cap;
+    a.step = step;
+    cudaError_t e = cudaSuccess;
+    for (int it = 0; it < iters && e == cudaSuccess; ++it) {
+      e = launch_soft_score(a, counts_dev, c->s_ring_off, st);
+      if (e == cudaSuccess) e = launch_soft_refine_step(a, st);
+    }
+    if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("refine: ") + cudaGetErrorString(e));
+    return RD_OK;
+  });
 }
 
 
 // ---------------------------------------------------------------- feature stage
 extern "C" rd_status rd_set_features(rd_ctx* c, int features, float edge_thresh) {
-  if (!c) return RD_E_INVAL;
-  if (features != RD_FEATURES_RIDGE && features != RD_FEATURES_EDGE)
-    return fail(c, RD_E_INVAL, "features must be RD_FEATURES_RIDGE or RD_FEATURES_EDGE");
-  if (!(edge_thresh >= 0.0f) || !std::isfinite(edge_thresh)) return fail(c, RD_E_INVAL, "edge_thresh must be >= 0");
-  if (features == RD_FEATURES_EDGE && !c->e_x64) {
-    const size_t rec = (size_t)c->max_batch * c->rl.cap;
-    bool ok = dalloc(&c->e_x64, rec);
-    if (!ok) {
-      cudaGetLastError();
-      return fail(c, RD_E_NOMEM, "edge workspaces: device allocation failed");
+  return rd_abi::guard(c ? &c->err : &g_create_error, [&]() -> rd_status {
+    if (!c) return RD_E_INVAL;
+    if (features != RD_FEATURES_RIDGE && features != RD_FEATURES_EDGE)
+      return fail(c, RD_E_INVAL, "features must be RD_FEATURES_RIDGE or RD_FEATURES_EDGE");
+    if (!(edge_thresh >= 0.0f) || !std::isfinite(edge_thresh)) return fail(c, RD_E_INVAL, "edge_thresh must be >= 0");
+    if (features == RD_FEATURES_EDGE && !c->e_x64) {
+      const size_t rec = (size_t)c->max_batch * c->rl.cap;
+      bool ok = dalloc(&c->e_x64, rec);
+      if (!ok) {
+        cudaGetLastError();
+        return fail(c, RD_E_NOMEM, "edge workspaces: device allocation failed");
+      }
     }
-  }
-  c->features = features;
-  c->edge_thresh = (double)edge_thresh;
-  drop_graph(c);
-  return RD_OK;
+    c->features = features;
+    c->edge_thresh = (double)edge_thresh;
+    drop_graph(c);
+    return RD_OK;
+  });
 }

@@ -19,6 +19,7 @@
 // A frame's result does not depend on what it is batched with: rd_detect
 // processes the frames of a batch independently.
 #include "rd_internal.cuh"
+#include "rd_abi_guard.h"
 
 #include <algorithm>
 #include <chrono>
@@ -206,117 +207,120 @@ extern "C" const char* rd_serve_last_error(void) { return g_serve_error.c_str();
 
 extern "C" rd_status rd_serve_create(const rd_serve_class* classes, int n_classes, long long mem_budget,
                                      int queue_cap, rd_server** out) {
-  if (!out || !classes || n_classes < 1 || n_classes > 64 || queue_cap < 1)
-    return serve_fail(RD_E_INVAL, "NULL argument, n_classes outside [1, 64] or queue_cap < 1");
-  *out = nullptr;
-  for (int i = 0; i < n_classes; ++i) {
-    const rd_serve_class& c = classes[i];
-    if (c.slots < 1 || c.slots > 16 || c.max_batch < 1 || (c.dtype != RD_U8 && c.dtype != RD_U16))
-      return serve_fail(RD_E_INVAL, "class " + std::to_string(i) + ": slots in [1, 16], max_batch >= 1, dtype u8/u16");
-  }
-  rd_server* sv = new rd_server();
-  if (cudaGetDevice(&sv->device) != cudaSuccess) {
-    delete sv;
-    return serve_fail(RD_E_CUDA, "no CUDA device");
-  }
-  sv->queue_cap = queue_cap;
-  sv->classes.resize(n_classes);
-  rd_status st = RD_OK;
-  for (int ci = 0; ci < n_classes && st == RD_OK; ++ci) {
-    ServeClass& c = sv->classes[ci];
-    c.cfg = classes[ci];
-    c.frame_bytes = (size_t)c.cfg.H * c.cfg.W * (c.cfg.dtype == RD_U8 ? 1 : 2);
-    for (int k = 0; k < c.cfg.slots && st == RD_OK; ++k) {
-      size_t free0 = 0, free1 = 0, total = 0;
-      cudaMemGetInfo(&free0, &total);
-      rd_serve_slot* s = new rd_serve_slot();
-      s->server = sv;
-      s->cls = ci;
-      s->ring_cap = c.cfg.max_batch * 4096;
-      st = rd_create(&c.cfg.params, c.cfg.H, c.cfg.W, c.cfg.max_batch, &s->ctx);
-      if (st != RD_OK) {
-        g_serve_error = std::string("class ") + std::to_string(ci) + ": " + rd_last_error(nullptr);
-        free_slot(s);
-        break;
+  return rd_abi::guard(&g_serve_error, [&]() -> rd_status {
+    if (!out || !classes || n_classes < 1 || n_classes > 64 || queue_cap < 1)
+      return serve_fail(RD_E_INVAL, "NULL argument, n_classes outside [1, 64] or queue_cap < 1");
+    *out = nullptr;
+    for (int i = 0; i < n_classes; ++i) {
+      const rd_serve_class& c = classes[i];
+      if (c.slots < 1 || c.slots > 16 || c.max_batch < 1 || c.max_batch > 65535 ||
+          (c.dtype != RD_U8 && c.dtype != RD_U16))
+        return serve_fail(RD_E_INVAL,
+                          "class " + std::to_string(i) + ": slots in [1, 16], max_batch in [1, 65535], dtype u8/u16");
+    }
+    // Until the server is handed out, every exit (an error return or an
+    // exception) releases its slots and the server itself.
+    struct Owner {
+      rd_server* sv;
+      ~Owner() {
+        if (!sv) return;
+        for (rd_serve_slot* s : sv->all_slots) free_slot(s);
+        delete sv;
       }
-      bool ok = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) == cudaSuccess &&
-                cudaMallocHost((void**)&s->h_frames, (size_t)c.cfg.max_batch * c.frame_bytes) == cudaSuccess &&
-                cudaMallocHost((void**)&s->h_rings, sizeof(rd_ring) * s->ring_cap) == cudaSuccess &&
-                cudaMallocHost((void**)&s->h_counts, sizeof(int) * c.cfg.max_batch) == cudaSuccess &&
-                cudaMallocHost((void**)&s->h_offsets, sizeof(int) * c.cfg.max_batch) == cudaSuccess &&
-                cudaMalloc((void**)&s->d_frames, (size_t)c.cfg.max_batch * c.frame_bytes) == cudaSuccess &&
-                cudaMalloc((void**)&s->d_rings, sizeof(rd_ring) * s->ring_cap) == cudaSuccess &&
-                cudaMalloc((void**)&s->d_counts, sizeof(int) * c.cfg.max_batch) == cudaSuccess &&
-                cudaMalloc((void**)&s->d_offsets, sizeof(int) * c.cfg.max_batch) == cudaSuccess;
-      if (!ok) {
-        cudaGetLastError();
-        free_slot(s);
-        st = serve_fail(RD_E_NOMEM, "class " + std::to_string(ci) + ": slot buffers");
-        break;
-      }
-      cudaMemGetInfo(&free1, &total);
-      sv->mem_used += (long long)free0 - (long long)free1;
-      c.slots.push_back(s);
-      sv->all_slots.push_back(s);
-      if (mem_budget > 0 && sv->mem_used > mem_budget) {
-        st = serve_fail(RD_E_NOMEM, "the classes' slots need " + std::to_string(sv->mem_used) +
-                                        " bytes of device memory, above the budget of " + std::to_string(mem_budget));
-        break;
+    } own{new rd_server()};
+    rd_server* sv = own.sv;
+    if (cudaGetDevice(&sv->device) != cudaSuccess) return serve_fail(RD_E_CUDA, "no CUDA device");
+    sv->queue_cap = queue_cap;
+    sv->classes.resize(n_classes);
+    for (int ci = 0; ci < n_classes; ++ci) {
+      ServeClass& c = sv->classes[ci];
+      c.cfg = classes[ci];
+      c.frame_bytes = (size_t)c.cfg.H * c.cfg.W * (c.cfg.dtype == RD_U8 ? 1 : 2);
+      for (int k = 0; k < c.cfg.slots; ++k) {
+        size_t free0 = 0, free1 = 0, total = 0;
+        cudaMemGetInfo(&free0, &total);
+        sv->all_slots.reserve(sv->all_slots.size() + 1);  // so that the push below cannot fail
+        rd_serve_slot* s = new rd_serve_slot();
+        sv->all_slots.push_back(s);
+        s->server = sv;
+        s->cls = ci;
+        s->ring_cap = c.cfg.max_batch * 4096;
+        const rd_status st = rd_create(&c.cfg.params, c.cfg.H, c.cfg.W, c.cfg.max_batch, &s->ctx);
+        if (st != RD_OK) return serve_fail(st, "class " + std::to_string(ci) + ": " + rd_last_error(nullptr));
+        bool ok = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaMallocHost((void**)&s->h_frames, (size_t)c.cfg.max_batch * c.frame_bytes) == cudaSuccess &&
+                  cudaMallocHost((void**)&s->h_rings, sizeof(rd_ring) * s->ring_cap) == cudaSuccess &&
+                  cudaMallocHost((void**)&s->h_counts, sizeof(int) * c.cfg.max_batch) == cudaSuccess &&
+                  cudaMallocHost((void**)&s->h_offsets, sizeof(int) * c.cfg.max_batch) == cudaSuccess &&
+                  cudaMalloc((void**)&s->d_frames, (size_t)c.cfg.max_batch * c.frame_bytes) == cudaSuccess &&
+                  cudaMalloc((void**)&s->d_rings, sizeof(rd_ring) * s->ring_cap) == cudaSuccess &&
+                  cudaMalloc((void**)&s->d_counts, sizeof(int) * c.cfg.max_batch) == cudaSuccess &&
+                  cudaMalloc((void**)&s->d_offsets, sizeof(int) * c.cfg.max_batch) == cudaSuccess;
+        if (!ok) {
+          cudaGetLastError();
+          return serve_fail(RD_E_NOMEM, "class " + std::to_string(ci) + ": slot buffers");
+        }
+        cudaMemGetInfo(&free1, &total);
+        sv->mem_used += (long long)free0 - (long long)free1;
+        c.slots.push_back(s);
+        if (mem_budget > 0 && sv->mem_used > mem_budget)
+          return serve_fail(RD_E_NOMEM, "the classes' slots need " + std::to_string(sv->mem_used) +
+                                            " bytes of device memory, above the budget of " + std::to_string(mem_budget));
       }
     }
-  }
-  if (st != RD_OK) {
-    for (rd_serve_slot* s : sv->all_slots) free_slot(s);
-    delete sv;
-    return st;
-  }
-  sv->worker = std::thread(scheduler, sv);
-  *out = sv;
-  return RD_OK;
+    sv->worker = std::thread(scheduler, sv);
+    own.sv = nullptr;
+    *out = sv;
+    return RD_OK;
+  });
 }
 
 extern "C" rd_status rd_serve_submit(rd_server* sv, int cls, const void* frame_host, long long request_id) {
-  if (!sv || !frame_host) return serve_fail(RD_E_INVAL, "NULL argument");
-  if (cls < 0 || cls >= (int)sv->classes.size()) return serve_fail(RD_E_INVAL, "no such class");
-  ServeClass& c = sv->classes[cls];
-  Request r;
-  r.id = request_id;
-  r.frame.assign(static_cast<const unsigned char*>(frame_host), static_cast<const unsigned char*>(frame_host) + c.frame_bytes);
-  {
-    std::lock_guard<std::mutex> lock(sv->m);
-    if (sv->queued >= sv->queue_cap) return serve_fail(RD_E_BUSY, "request queue full");
-    r.t_submit = Clock::now();
-    c.queue.push_back(std::move(r));
-    ++sv->queued;
-    ++sv->submitted;
-  }
-  sv->cv_work.notify_one();
-  return RD_OK;
+  return rd_abi::guard(&g_serve_error, [&]() -> rd_status {
+    if (!sv || !frame_host) return serve_fail(RD_E_INVAL, "NULL argument");
+    if (cls < 0 || cls >= (int)sv->classes.size()) return serve_fail(RD_E_INVAL, "no such class");
+    ServeClass& c = sv->classes[cls];
+    Request r;
+    r.id = request_id;
+    r.frame.assign(static_cast<const unsigned char*>(frame_host), static_cast<const unsigned char*>(frame_host) + c.frame_bytes);
+    {
+      std::lock_guard<std::mutex> lock(sv->m);
+      if (sv->queued >= sv->queue_cap) return serve_fail(RD_E_BUSY, "request queue full");
+      r.t_submit = Clock::now();
+      c.queue.push_back(std::move(r));
+      ++sv->queued;
+      ++sv->submitted;
+    }
+    sv->cv_work.notify_one();
+    return RD_OK;
+  });
 }
 
 extern "C" int rd_serve_poll(rd_server* sv, long long* ids, int* classes, int* status, int* n_rings, rd_ring* rings,
                              int rings_cap, double* latency_us, int max_results, int wait_ms) {
-  if (!sv || !ids || max_results < 1 || rings_cap < 0 || (rings_cap > 0 && !rings)) return -1;
-  std::unique_lock<std::mutex> lock(sv->m);
-  if (sv->done.empty() && wait_ms > 0)
-    sv->cv_done.wait_for(lock, std::chrono::milliseconds(wait_ms), [&] { return !sv->done.empty(); });
-  int k = 0, used = 0;
-  while (k < max_results && !sv->done.empty()) {
-    Result& r = sv->done.front();
-    const int nr = (int)r.rings.size();
-    if (used + nr > rings_cap && k > 0) break;  // the next poll returns it
-    const int keep = std::min(nr, rings_cap - used);
-    ids[k] = r.id;
-    if (classes) classes[k] = r.cls;
-    if (status) status[k] = r.status;
-    if (n_rings) n_rings[k] = keep;
-    if (latency_us) latency_us[k] = r.latency_us;
-    if (keep > 0) std::memcpy(rings + used, r.rings.data(), sizeof(rd_ring) * keep);
-    used += keep;
-    sv->done.pop_front();
-    ++k;
-  }
-  return k;
+  return rd_abi::guard_count(&g_serve_error, [&]() -> int {
+    if (!sv || !ids || max_results < 1 || rings_cap < 0 || (rings_cap > 0 && !rings)) return -1;
+    std::unique_lock<std::mutex> lock(sv->m);
+    if (sv->done.empty() && wait_ms > 0)
+      sv->cv_done.wait_for(lock, std::chrono::milliseconds(wait_ms), [&] { return !sv->done.empty(); });
+    int k = 0, used = 0;
+    while (k < max_results && !sv->done.empty()) {
+      Result& r = sv->done.front();
+      const int nr = (int)r.rings.size();
+      if (used + nr > rings_cap && k > 0) break;  // the next poll returns it
+      const int keep = std::min(nr, rings_cap - used);
+      ids[k] = r.id;
+      if (classes) classes[k] = r.cls;
+      if (status) status[k] = r.status;
+      if (n_rings) n_rings[k] = keep;
+      if (latency_us) latency_us[k] = r.latency_us;
+      if (keep > 0) std::memcpy(rings + used, r.rings.data(), sizeof(rd_ring) * keep);
+      used += keep;
+      sv->done.pop_front();
+      ++k;
+    }
+    return k;
+  });
 }
 
 extern "C" rd_status rd_serve_stats(rd_server* sv, long long* out4) {

@@ -11,6 +11,7 @@
 // needs none: its scratch memory is one fixed array in this file, which
 // every GPU that loads the library holds until the process exits.
 #include "rd_internal.cuh"
+#include "rd_abi_guard.h"
 
 #include <cstddef>
 #include <mutex>
@@ -91,64 +92,66 @@ extern "C" const char* rd_static_last_error(void) { return g_static_error.c_str(
 extern "C" rd_status rd_ridges_static(const rd_params* p, const void* frame_dev, int H, int W, int dtype,
                                       void* stream, uint32_t* xy_dev, float* dir_dev, int cap,
                                       int* count_dev) {
-  if (!p || !frame_dev || !xy_dev || !dir_dev || !count_dev) return fail_static(RD_E_INVAL, "NULL argument");
-  if (!(p->sigma > 0.0f && p->sigma <= 4.0f)) return fail_static(RD_E_INVAL, "sigma must be in (0, 4]");
-  if (!(p->ridge_thresh <= 0.0f)) return fail_static(RD_E_INVAL, "ridge_thresh must be <= 0");
-  if (dtype != RD_U8 && dtype != RD_U16) return fail_static(RD_E_INVAL, "dtype must be RD_U8 or RD_U16");
-  GaussTaps taps;
-  taps.R = (rd_gaussian_taps(p->sigma, taps.q, 2 * MAX_RG + 1) - 1) / 2;
-  if (taps.R < 1) return fail_static(RD_E_INVAL, "sigma gives no Gaussian taps");
-  if (H < taps.R + 4 || W < taps.R + 4 || H < 12 || W < 12 || H > 65535 || W > 65535)
-    return fail_static(RD_E_INVAL, "frame size must be in [max(12, ceil(4 sigma) + 4), 65535]");
-  if ((long long)H * W > RD_STATIC_MAX_PIXELS)
-    return fail_static(RD_E_INVAL, "frame has more than RD_STATIC_MAX_PIXELS (1048576) pixels");
-  const int n_stx = (W + ST_TW - 1) / ST_TW, n_sty = (H + ST_TH - 1) / ST_TH;
-  if ((long long)n_stx * n_sty > STATIC_MAX_TILES)
-    return fail_static(RD_E_INVAL, "frame has more stencil tiles than the static scratch holds");
-  if (cap < 0 || cap > RD_STATIC_MAX_RIDGE)
-    return fail_static(RD_E_INVAL, "cap must be in [0, RD_STATIC_MAX_RIDGE] (262144)");
-  if (((uintptr_t)dir_dev & 15) != 0) return fail_static(RD_E_INVAL, "dir_dev must be 16-byte aligned");
+  return rd_abi::guard(&g_static_error, [&]() -> rd_status {
+    if (!p || !frame_dev || !xy_dev || !dir_dev || !count_dev) return fail_static(RD_E_INVAL, "NULL argument");
+    if (!(p->sigma > 0.0f && p->sigma <= 4.0f)) return fail_static(RD_E_INVAL, "sigma must be in (0, 4]");
+    if (!(p->ridge_thresh <= 0.0f)) return fail_static(RD_E_INVAL, "ridge_thresh must be <= 0");
+    if (dtype != RD_U8 && dtype != RD_U16) return fail_static(RD_E_INVAL, "dtype must be RD_U8 or RD_U16");
+    GaussTaps taps;
+    taps.R = (rd_gaussian_taps(p->sigma, taps.q, 2 * MAX_RG + 1) - 1) / 2;
+    if (taps.R < 1) return fail_static(RD_E_INVAL, "sigma gives no Gaussian taps");
+    if (H < taps.R + 4 || W < taps.R + 4 || H < 12 || W < 12 || H > 65535 || W > 65535)
+      return fail_static(RD_E_INVAL, "frame size must be in [max(12, ceil(4 sigma) + 4), 65535]");
+    if ((long long)H * W > RD_STATIC_MAX_PIXELS)
+      return fail_static(RD_E_INVAL, "frame has more than RD_STATIC_MAX_PIXELS (1048576) pixels");
+    const int n_stx = (W + ST_TW - 1) / ST_TW, n_sty = (H + ST_TH - 1) / ST_TH;
+    if ((long long)n_stx * n_sty > STATIC_MAX_TILES)
+      return fail_static(RD_E_INVAL, "frame has more stencil tiles than the static scratch holds");
+    if (cap < 0 || cap > RD_STATIC_MAX_RIDGE)
+      return fail_static(RD_E_INVAL, "cap must be in [0, RD_STATIC_MAX_RIDGE] (262144)");
+    if (((uintptr_t)dir_dev & 15) != 0) return fail_static(RD_E_INVAL, "dir_dev must be 16-byte aligned");
 
-  DeviceSetup dev;
-  rd_status s = setup_current_device(&dev);
-  if (s != RD_OK) return s;
-  StaticScratch* sc = dev.scratch;
-  cudaStream_t st = (cudaStream_t)stream;
+    DeviceSetup dev;
+    rd_status s = setup_current_device(&dev);
+    if (s != RD_OK) return s;
+    StaticScratch* sc = dev.scratch;
+    cudaStream_t st = (cudaStream_t)stream;
 
-  // The array keeps the previous call's contents.  The counters must start at
-  // zero; the tile index, Hessians and margins are written before they are
-  // read.
-  cudaError_t e = cudaMemsetAsync(count_dev, 0, sizeof(int), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(&sc->stats, 0, sizeof(DevStats), st);
-  if (e != cudaSuccess) return fail_cuda("cudaMemsetAsync", e);
+    // The array keeps the previous call's contents.  The counters must start at
+    // zero; the tile index, Hessians and margins are written before they are
+    // read.
+    cudaError_t e = cudaMemsetAsync(count_dev, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&sc->stats, 0, sizeof(DevStats), st);
+    if (e != cudaSuccess) return fail_cuda("cudaMemsetAsync", e);
 
-  long long S = 0;
-  for (int i = 0; i <= 2 * taps.R; ++i) S += taps.q[i];
-  StencilArgs a{};
-  a.edge = 0;
-  a.frames = frame_dev;
-  a.n = 1;
-  a.H = H;
-  a.W = W;
-  a.taps = taps;
-  a.tau = p->ridge_thresh;
-  a.tau64 = (double)p->ridge_thresh;
-  a.D64 = (double)(64LL * S * S);
-  a.invD = (float)(1.0 / a.D64);
-  a.rl.xy = xy_dev;
-  a.rl.dir = reinterpret_cast<float4*>(dir_dev);
-  a.rl.kvote = sc->kvote;
-  a.rl.hess = sc->hess;
-  a.rl.count = count_dev;
-  a.rl.tile_off = sc->tile_off;
-  a.rl.tile_cnt = sc->tile_cnt;
-  a.rl.cap = cap;
-  a.rl.n_stx = n_stx;
-  a.rl.n_sty = n_sty;
-  a.stats = &sc->stats;
-  e = launch_stencil(a, dtype, st);
-  if (e != cudaSuccess) return fail_cuda("stencil launch", e);
-  e = launch_refine(a.rl, 1, dev.n_sm, st);
-  if (e != cudaSuccess) return fail_cuda("refine launch", e);
-  return RD_OK;
+    long long S = 0;
+    for (int i = 0; i <= 2 * taps.R; ++i) S += taps.q[i];
+    StencilArgs a{};
+    a.edge = 0;
+    a.frames = frame_dev;
+    a.n = 1;
+    a.H = H;
+    a.W = W;
+    a.taps = taps;
+    a.tau = p->ridge_thresh;
+    a.tau64 = (double)p->ridge_thresh;
+    a.D64 = (double)(64LL * S * S);
+    a.invD = (float)(1.0 / a.D64);
+    a.rl.xy = xy_dev;
+    a.rl.dir = reinterpret_cast<float4*>(dir_dev);
+    a.rl.kvote = sc->kvote;
+    a.rl.hess = sc->hess;
+    a.rl.count = count_dev;
+    a.rl.tile_off = sc->tile_off;
+    a.rl.tile_cnt = sc->tile_cnt;
+    a.rl.cap = cap;
+    a.rl.n_stx = n_stx;
+    a.rl.n_sty = n_sty;
+    a.stats = &sc->stats;
+    e = launch_stencil(a, dtype, st);
+    if (e != cudaSuccess) return fail_cuda("stencil launch", e);
+    e = launch_refine(a.rl, 1, dev.n_sm, st);
+    if (e != cudaSuccess) return fail_cuda("refine launch", e);
+    return RD_OK;
+  });
 }

@@ -16,8 +16,9 @@ import numpy as np
 from . import _build
 
 RD_U8, RD_U16, RD_F32 = 0, 1, 2
-RD_OK, RD_E_INVAL, RD_E_NOMEM, RD_E_CUDA, RD_E_OVERFLOW, RD_E_TIMEOUT, RD_E_BUSY = range(7)
-STATUS_NAMES = ["RD_OK", "RD_E_INVAL", "RD_E_NOMEM", "RD_E_CUDA", "RD_E_OVERFLOW", "RD_E_TIMEOUT", "RD_E_BUSY"]
+RD_OK, RD_E_INVAL, RD_E_NOMEM, RD_E_CUDA, RD_E_OVERFLOW, RD_E_TIMEOUT, RD_E_BUSY, RD_E_HOST = range(8)
+STATUS_NAMES = ["RD_OK", "RD_E_INVAL", "RD_E_NOMEM", "RD_E_CUDA", "RD_E_OVERFLOW", "RD_E_TIMEOUT", "RD_E_BUSY",
+                "RD_E_HOST"]
 RD_RING_FIT_FAIL = 1
 PEAK_CAP = 4096   # per-frame peak capacity of a context
 

@@ -107,7 +107,8 @@ def test_serve_create_validates_classes(lib):
     """rd_serve_create rejects bad class descriptions before touching the GPU."""
     from paper_1310_1371_gb300 import rd, synth
     good = rd.rd_serve_class(rd.make_params(**synth.PLAIN_SMALL_PARAMS), 256, 256, rd.RD_U8, 4, 1)
-    for bad in (dict(slots=0), dict(slots=17), dict(max_batch=0), dict(dtype=7)):
+    for bad in (dict(slots=0), dict(slots=17), dict(max_batch=0), dict(max_batch=65536), dict(max_batch=1 << 30),
+                dict(dtype=7)):
         c = rd.rd_serve_class(good.params, good.H, good.W, bad.get("dtype", good.dtype),
                               bad.get("max_batch", good.max_batch), bad.get("slots", good.slots))
         arr = (rd.rd_serve_class * 1)(c)
@@ -117,6 +118,52 @@ def test_serve_create_validates_classes(lib):
     out = ctypes.c_void_p()
     assert lib.rd_serve_create(arr, 0, 0, 16, ctypes.byref(out)) == rd.RD_E_INVAL
     assert lib.rd_serve_create(arr, 1, 0, 0, ctypes.byref(out)) == rd.RD_E_INVAL
+
+
+def test_autotune_and_timing_reject_bad_sizes(lib):
+    """rd_autotune bounds its batch before allocating; rd_get_timing rejects a
+    negative capacity (both without GPU work)."""
+    from paper_1310_1371_gb300 import rd, synth
+    p = rd.make_params(**synth.PLAIN_SMALL_PARAMS)
+    g = rd.rd_geometry()
+    dummy = ctypes.c_void_p(16)                     # never dereferenced: the batch is checked first
+    for n in (0, -1, 65536, 1 << 30):
+        assert lib.rd_autotune(ctypes.byref(p), dummy, n, 256, 256, 0, None, ctypes.byref(g)) == rd.RD_E_INVAL
+        assert b"rd_autotune" in lib.rd_last_error(None)
+    ms = (ctypes.c_float * 8)()
+    assert lib.rd_get_timing(None, ms, 8) == -1
+
+
+def test_valid_create_without_a_device_releases_everything(lib):
+    """With valid arguments and no CUDA device, rd_create and rd_serve_create
+    stop at the device query: RD_E_CUDA, no handle, and the partly built
+    context or server is released by its scope guard (the process stays
+    usable for the next call)."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present: this checks the path without one")
+    from paper_1310_1371_gb300 import rd, synth
+    p = rd.make_params(**synth.PLAIN_SMALL_PARAMS)
+    for _ in range(3):
+        ctx = ctypes.c_void_p()
+        assert lib.rd_create(ctypes.byref(p), 256, 256, 2, ctypes.byref(ctx)) == rd.RD_E_CUDA
+        assert ctx.value is None and b"CUDA device" in lib.rd_last_error(None)
+        arr = (rd.rd_serve_class * 1)(rd.rd_serve_class(p, 256, 256, rd.RD_U8, 4, 2))
+        out = ctypes.c_void_p()
+        assert lib.rd_serve_create(arr, 1, 0, 16, ctypes.byref(out)) == rd.RD_E_CUDA
+        assert out.value is None and b"CUDA device" in lib.rd_serve_last_error()
+
+
+def test_status_codes_match_header():
+    """The binding's status names are the header's rd_status enumerators, in order."""
+    from paper_1310_1371_gb300 import rd
+    txt = open(os.path.join(ROOT, "include", "rd.h")).read()
+    body = re.search(r"typedef enum \{([^}]*)\} rd_status;", txt, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    pairs = re.findall(r"(RD_[A-Z_]+)\s*=\s*(\d+)", body)
+    assert [n for n, _ in pairs] == rd.STATUS_NAMES
+    assert [int(v) for _, v in pairs] == list(range(len(pairs)))
+    assert all(getattr(rd, n) == i for i, n in enumerate(rd.STATUS_NAMES))
 
 
 _STRUCTS = ("rd_params", "rd_ring", "rd_stats", "rd_geometry", "rd_serve_class")
