@@ -250,6 +250,68 @@ def check_window_and_threshold():
             and N[30, 30] == 0)
 
 
+def check_smooth_hot_brute_force(seed=11):
+    """N(v) = sum over the window of Q(d) A(v + d), zero outside the frame,
+    at every hotspot A(v) > T and 0 elsewhere: pure loops on a small random
+    accumulator whose hotspots touch every border."""
+    rng = np.random.default_rng(seed)
+    A = rng.integers(0, 7, size=(9, 11)).astype(np.int64)
+    Q = O.smoothing_weights(30, float(np.float32(0.05)), float(np.float32(0.25)))   # sigma 1.75, 13 x 13
+    Rs = (Q.shape[0] - 1) // 2
+    T = 3
+    H, W = A.shape
+    N = O.smooth_hot(A, Q, T)
+    for y in range(H):
+        for x in range(W):
+            want = 0
+            if A[y, x] > T:
+                for dy in range(-Rs, Rs + 1):
+                    for dx in range(-Rs, Rs + 1):
+                        if 0 <= y + dy < H and 0 <= x + dx < W:
+                            want += int(Q[dy + Rs, dx + Rs]) * int(A[y + dy, x + dx])
+            if int(N[y, x]) != want:
+                return False
+    return bool((A > T).any() and (A <= T).any())
+
+
+def check_peaks_brute_force(seed=12):
+    """The 3 x 3 x 3 maximum with exact S = N / r comparisons and ties given
+    to the first voxel in (r, y, x) order, by loops over Fractions on three
+    small levels with many equal values; out-of-frame neighbours score 0."""
+    from fractions import Fraction
+    rng = np.random.default_rng(seed)
+    r = 10
+    levels = {dr: rng.choice([0, 400000, 500000], size=(6, 7)).astype(np.int64) for dr in (-1, 1)}
+    levels[0] = rng.choice([0, 600000, 650000, 660000, 715000], size=(6, 7)).astype(np.int64)
+    # exactly equal S across levels: the level below precedes (strict), the level above follows
+    for (y, x), dr in (((2, 3), -1), ((4, 1), -1), ((1, 5), 1), ((3, 2), 1)):
+        levels[dr][y, x] = levels[0][y, x] * (r + dr) // r
+    p = small_params(peak_frac=0.15)
+    got = sorted(O.find_peaks_level(levels[-1], levels[0], levels[1], r, p))
+    thr = O.peak_threshold(p.peak_frac, r)
+    H, W = levels[0].shape
+    want = []
+    for y in range(H):
+        for x in range(W):
+            n = int(levels[0][y, x])
+            if not float(n) > thr:
+                continue
+            s = Fraction(n, r)
+            ok = True
+            for dr in (-1, 0, 1):
+                for dy in (-1, 0, 1):
+                    for dx in (-1, 0, 1):
+                        if (dr, dy, dx) == (0, 0, 0):
+                            continue
+                        yy, xx = y + dy, x + dx
+                        sn = Fraction(int(levels[dr][yy, xx]), r + dr) if 0 <= yy < H and 0 <= xx < W else 0
+                        first = (dr, dy, dx) < (0, 0, 0)
+                        ok = ok and (s > sn if first else s >= sn)
+            if ok:
+                want.append((x, y, r, n))
+    return got == sorted(want) and len(want) > 0
+
+
 def check_clean_ring_score():
     img = ring_image(120, 120, 60.2, 59.7, 25.0)
     p = small_params(r_min=15, r_max=35)
