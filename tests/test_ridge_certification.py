@@ -20,7 +20,8 @@ the workload's; the other is a quantile of k-, which puts many pixels near
 the k- < tau boundary.  The replay runs both without contraction and with
 the products contracted into fused multiply-adds, since the compiler may
 contract these plain-operation expressions.  Every pixel that FP32 decides
-must get the oracle's verdict.  On workload frames at the workload's
+must get the oracle's verdict; the directed-edge template (-|grad| in k-'s
+place) is replayed the same way.  On workload frames at the workload's
 threshold, the undecided pixels (re-tested in FP64 by the kernel) must be a
 small fraction.  Degenerate frames (a smoothed checkerboard is nearly flat)
 may leave every pixel undecided, which is the intended outcome.
@@ -219,6 +220,62 @@ def ridge_fast(k, sE, gy, gx, o, H, W, kc, ec, X, Y, eX, contract):
     return verdict
 
 
+# ---------------------------------------------------------------- the directed-edge variant
+def gradient32(Lf, invD):
+    """FP32 (gx, gy) of a padded rounded L (first-order Sobel), 2 px smaller on each side."""
+    W = Lf.shape[1]
+    l0, l1, l2, l3, l4 = (Lf[:, k:W - 4 + k] for k in range(5))
+    e = l0 + l4
+    rs = fma32(6.0, l2, fma32(4.0, l1 + l3, e))
+    rd1 = fma32(2.0, l3 - l1, l4 - l0)
+    H = Lf.shape[0]
+    x0, x1, x2, x3, x4 = (rd1[k:H - 4 + k] for k in range(5))
+    y0, y1, _, y3, y4 = (rs[k:H - 4 + k] for k in range(5))
+    Gx = fma32(6.0, x2, fma32(4.0, x1 + x3, x0 + x4))
+    Gy = fma32(2.0, y3 - y1, y4 - y0)
+    return Gx * invD, Gy * invD
+
+
+def replay_edges(img, sigma, edge_thresh, contract):
+    """Verdicts of the directed-edge test: -|grad| takes k-'s place, with
+    tau = -edge_thresh, delta = 576 u max L' / D and D = 128 S^2."""
+    H, W = img.shape
+    Lp, S = O.smooth_int(img, sigma)
+    invD = f32(1.0 / float(128 * S * S))
+    Lf = np.pad(Lp, PAD, mode="reflect").astype(F64).astype(np.float32)
+    gx, gy = gradient32(Lf, invD)
+    g = np.sqrt(gx * gx + gy * gy)                       # correctly rounded operations, no contraction
+    k = -g
+    tau = f32(-edge_thresh)
+    o = PAD - 2
+    verdict = np.zeros((H, W), np.int8)
+    for ty in range(0, H, TILE):
+        for tx in range(0, W, TILE):
+            region = Lf[PAD + ty - 3:PAD + ty + TILE + 3, PAD + tx - 3:PAD + tx + TILE + 3]
+            delta = mul_ru(mul_ru(region.max(), invD), f32(576 * 2.0 ** -24))
+            sE = fma32_ru(f32(1.5), delta, f32(4 * 2.0 ** -24) * g)
+            ys, xs = np.mgrid[ty:min(ty + TILE, H), tx:min(tx + TILE, W)]
+            ys, xs = ys.ravel(), xs.ravel()
+            c = (ys + o, xs + o)
+            kc, ec = k[c], sE[c]
+            dk = kc - tau
+            v = np.where(dk >= ec, 0, np.where(~(dk < -ec), 2, 1)).astype(np.int8)
+            cand = v == 1
+            gc = -kc
+            ok = (gc > f32(4.0) * delta) & (gc > 0)
+            with np.errstate(invalid="ignore", divide="ignore"):
+                X, Y = gx[c] / gc, gy[c] / gc
+                flip = (X < 0) | ((X == 0) & (Y < 0))
+                X, Y = np.where(flip, -X, X).astype(np.float32), np.where(flip, -Y, Y).astype(np.float32)
+                den = fma32(f32(-2.0), delta, gc) if contract else gc - f32(2.0) * delta
+                eX = ((f32(3.0) * delta) / den + f32(4 * 2.0 ** -24)).astype(np.float32)
+            v[cand & ~ok] = 2
+            sel = cand & ok
+            v[sel] = ridge_fast(k, sE, ys[sel], xs[sel], o, H, W, kc[sel], ec[sel], X[sel], Y[sel], eX[sel], contract)
+            verdict[ys, xs] = v
+    return verdict
+
+
 # ---------------------------------------------------------------- cases
 def cases():
     out = []
@@ -280,3 +337,25 @@ def test_adversarial_frames_are_mostly_decided():
         n_dec += int((v != 2).sum())
         n_ridge += int((v == 1).sum())
     assert n_dec > 0.5 * n_px and n_ridge > 100, (n_px, n_dec, n_ridge)
+
+
+EDGE_CASES = [("bound0", CASES[0][1]), ("bound4", CASES[4][1]),
+              ("discs_crop", np.ascontiguousarray(synth.disc_full(seed=3002).image[300:428, 200:360]))]
+
+
+@pytest.mark.parametrize("contract", [False, True])
+@pytest.mark.parametrize("idx", range(len(EDGE_CASES)))
+def test_certified_edge_verdicts(idx, contract):
+    """The directed-edge variant (Additional notes): the same certified
+    decision on -|grad|; every FP32-decided pixel gets the oracle's verdict."""
+    name, img = EDGE_CASES[idx]
+    gx, gy = O.gradient(img, 2.0)
+    g, X, Y, deg = O.edge_direction(gx, gy)
+    threshes = [float(np.float32(synth.DISC_FULL_PARAMS["edge_thresh"])), float(np.float32(np.quantile(g, 0.65)))]
+    for t in threshes:
+        want = O.edge_mask(g, X, Y, deg, t)
+        v = replay_edges(img, 2.0, t, contract)
+        decided = v != 2
+        bad = decided & ((v == 1) != want)
+        assert not bad.any(), (name, t, int(bad.sum()), np.argwhere(bad)[:5].tolist())
+        assert decided.mean() > 0.5 and ((v == 1).any() or not want.any()), (name, t, float(decided.mean()))
