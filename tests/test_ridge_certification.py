@@ -21,7 +21,8 @@ the k- < tau boundary.  The replay runs both without contraction and with
 the products contracted into fused multiply-adds, since the compiler may
 contract these plain-operation expressions.  Every pixel that FP32 decides
 must get the oracle's verdict; the directed-edge template (-|grad| in k-'s
-place) is replayed the same way.  On workload frames at the workload's
+place) and the soft path's mask on float frames are replayed the same way.
+On workload frames at the workload's
 threshold, the undecided pixels (re-tested in FP64 by the kernel) must be a
 small fraction.  Degenerate frames (a smoothed checkerboard is nearly flat)
 may leave every pixel undecided, which is the intended outcome.
@@ -276,6 +277,38 @@ def replay_edges(img, sigma, edge_thresh, contract):
     return verdict
 
 
+# ---------------------------------------------------------------- float frames (the soft score's ridge set)
+def replay_float(L, tau, contract):
+    """Verdicts of the soft path's mask on a float L (either sign): L rounded
+    to FP32, delta = 512 u max|L| / 64 = 2^-21 max|L| rounded up, the
+    Hessian scaled by exactly 1/64."""
+    H, W = L.shape
+    Lf = np.pad(L, PAD, mode="reflect").astype(np.float32)   # one rounding from float64
+    fa, fb, fc = hessian32(Lf, f32(1.0 / 64.0))
+    tau = f32(tau)
+    k, ek0, hdf, rad, M = eig_k(fa, fb, fc, contract)
+    o = PAD - 2
+    verdict = np.zeros((H, W), np.int8)
+    for ty in range(0, H, TILE):
+        for tx in range(0, W, TILE):
+            region = Lf[PAD + ty - 3:PAD + ty + TILE + 3, PAD + tx - 3:PAD + tx + TILE + 3]
+            delta = mul_ru(np.abs(region).max(), f32(2.0 ** -21))
+            sE = fma32_ru(f32(3.0), delta, ek0)
+            ys, xs = np.mgrid[ty:min(ty + TILE, H), tx:min(tx + TILE, W)]
+            ys, xs = ys.ravel(), xs.ravel()
+            c = (ys + o, xs + o)
+            kc, ec = k[c], sE[c]
+            dk = kc - tau
+            v = np.where(dk >= ec, 0, np.where(~(dk < -ec), 2, 1)).astype(np.int8)
+            cand = v == 1
+            ok, X, Y, eX = eig_dir(fb[c], hdf[c], rad[c], M[c], delta, contract)
+            v[cand & ~ok] = 2
+            sel = cand & ok
+            v[sel] = ridge_fast(k, sE, ys[sel], xs[sel], o, H, W, kc[sel], ec[sel], X[sel], Y[sel], eX[sel], contract)
+            verdict[ys, xs] = v
+    return verdict
+
+
 # ---------------------------------------------------------------- cases
 def cases():
     out = []
@@ -359,3 +392,34 @@ def test_certified_edge_verdicts(idx, contract):
         bad = decided & ((v == 1) != want)
         assert not bad.any(), (name, t, int(bad.sum()), np.argwhere(bad)[:5].tolist())
         assert decided.mean() > 0.5 and ((v == 1).any() or not want.any()), (name, t, float(decided.mean()))
+
+
+def _float_frames():
+    rng = np.random.default_rng(41)
+    yield "diff_crop", synth.diff_frame(0).image[100:228, 140:300].astype(np.float64)
+    yield "noise_offset", rng.normal(0.0, 1000.0, (96, 96)) - 3.0e4        # L of one sign, large offset
+    yield "noise_signed", rng.normal(0.0, 1000.0, (96, 96))                # L of both signs
+
+
+FLOAT_CASES = list(_float_frames())
+
+
+@pytest.mark.parametrize("contract", [False, True])
+@pytest.mark.parametrize("idx", range(len(FLOAT_CASES)))
+def test_certified_float_frame_verdicts(idx, contract):
+    """The soft score's ridge set on float frames: every FP32-decided pixel
+    gets the verdict of the FP64 definition (oracle.soft's Hessian)."""
+    from oracle import soft as S
+    name, img = FLOAT_CASES[idx]
+    g = S._taps_float(2.0)
+    L = S._correlate1d(S._correlate1d(img, g, 1), g, 0)
+    lxx, lyy, lxy = S.hessian_float(img, 2.0)
+    kdef, X, Y, deg = O.eigen(lxx, lyy, lxy)
+    for tau in (float(np.float32(synth.DIFF_PARAMS["ridge_thresh"])),
+                float(np.float32(min(-1e-6, np.quantile(kdef, 0.35))))):
+        want = O.ridge_mask(kdef, X, Y, deg, tau)
+        v = replay_float(L, tau, contract)
+        decided = v != 2
+        bad = decided & ((v == 1) != want)
+        assert not bad.any(), (name, tau, int(bad.sum()), np.argwhere(bad)[:5].tolist())
+        assert decided.mean() > 0.5 and ((v == 1).any() or not want.any()), (name, tau, float(decided.mean()))
