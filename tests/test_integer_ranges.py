@@ -49,3 +49,26 @@ def test_worst_case_frame_is_exact():
     assert np.all(Lp == 65535 * S * S)
     for h in O.hessian_int(Lp):
         assert not h.any()
+
+
+def _annulus_lattice_count(r, halfwidth):
+    """Integer offsets p with r - halfwidth <= |p| <= r + halfwidth."""
+    R = int(np.ceil(r + halfwidth)) + 1
+    ys, xs = np.mgrid[-R:R + 1, -R:R + 1]
+    d = np.hypot(xs, ys)
+    return int(((d >= r - halfwidth) & (d <= r + halfwidth)).sum())
+
+
+@pytest.mark.parametrize("c", [1, 2, 4])
+def test_vote_counts_fit_u16(c):
+    """The voting kernel keeps one level's counts as packed u16: no voxel may
+    reach 65536 votes, or the carry would spill into its neighbour.  A pixel
+    p votes into the voxel (cell) v at radius r only if p + s r X- rounds into
+    v's cell, i.e. |p - centre(v)| is within r +- c / sqrt 2 (the cell's
+    half-diagonal, plus 1/2 px rounding at c = 1), and it casts at most two
+    votes per level.  Even with every pixel of that annulus a ridge pixel,
+    at the largest voted radius (r_max + 1 = 251) the count stays far below
+    2^16."""
+    hw = c / np.sqrt(2.0) + 0.5
+    worst = max(_annulus_lattice_count(r, hw) for r in (2, 10, 50, 100, 200, 251))
+    assert 2 * worst < 65536, worst
