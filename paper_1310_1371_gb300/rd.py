@@ -19,6 +19,8 @@ RD_U8, RD_U16, RD_F32 = 0, 1, 2
 RD_OK, RD_E_INVAL, RD_E_NOMEM, RD_E_CUDA, RD_E_OVERFLOW, RD_E_TIMEOUT, RD_E_BUSY, RD_E_HOST = range(8)
 STATUS_NAMES = ["RD_OK", "RD_E_INVAL", "RD_E_NOMEM", "RD_E_CUDA", "RD_E_OVERFLOW", "RD_E_TIMEOUT", "RD_E_BUSY",
                 "RD_E_HOST"]
+# rd_stats.overflow bits (capacities that overflowed)
+RD_OVF_RIDGE, RD_OVF_BINS, RD_OVF_PEAKS, RD_OVF_RINGS, RD_OVF_SCORE = 1, 2, 4, 8, 16
 RD_RING_FIT_FAIL = 1
 PEAK_CAP = 4096   # per-frame peak capacity of a context
 

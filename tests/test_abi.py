@@ -164,6 +164,8 @@ def test_status_codes_match_header():
     assert [n for n, _ in pairs] == rd.STATUS_NAMES
     assert [int(v) for _, v in pairs] == list(range(len(pairs)))
     assert all(getattr(rd, n) == i for i, n in enumerate(rd.STATUS_NAMES))
+    ovf = dict((n, int(v)) for n, v in re.findall(r"#define (RD_OVF_[A-Z]+)\s+(\d+)", txt))
+    assert ovf and all(getattr(rd, n) == v for n, v in ovf.items()), ovf
 
 
 _STRUCTS = ("rd_params", "rd_ring", "rd_stats", "rd_geometry", "rd_serve_class")
