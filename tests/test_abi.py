@@ -154,6 +154,17 @@ def test_valid_create_without_a_device_releases_everything(lib):
         assert out.value is None and b"CUDA device" in lib.rd_serve_last_error()
 
 
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without librd.so the binding raises: there is no fallback path."""
+    from paper_1310_1371_gb300 import rd, _build
+    monkeypatch.setattr(rd, "_lib", None)
+    monkeypatch.setattr(_build, "LIB", str(tmp_path / "missing" / "librd.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        rd.load_library()
+    with pytest.raises(RuntimeError, match="not built"):
+        rd.Detector({"sigma": 2.0, "r_min": 5, "r_max": 20, "ridge_thresh": -1.0}, 64, 64)
+
+
 def test_status_codes_match_header():
     """The binding's status names are the header's rd_status enumerators, in order."""
     from paper_1310_1371_gb300 import rd
