@@ -312,6 +312,22 @@ def check_peaks_brute_force(seed=12):
     return got == sorted(want) and len(want) > 0
 
 
+def check_fringes_suppressed_at_ring_scale():
+    """Results: the thick outer ring admits scale selection; a Gaussian at
+    about its scale suppresses the thinner inner rings.  A ring of R = 40
+    with three inner fringes (period 4 px, amplitude halving) gives exactly
+    one ring at sigma = 2; at sigma = 0.7 the fringes come out as extra
+    concentric rings."""
+    img = synth._render(160, 160, np.array([[80.3, 79.6, 40.0]]), synth._fringed_ring(600.0, 1.5, 3), 400.0)
+    img = np.clip(np.rint(img), 0, 4095).astype(np.uint16)
+    base = dict(synth.PLAIN_FULL_PARAMS, r_min=8, r_max=60)
+    one = O.detect(img, O.Params.make(**base)).rings
+    many = O.detect(img, O.Params.make(**dict(base, sigma=0.7))).rings
+    return (len(one) == 1 and abs(float(one["r"][0]) - 40.0) < 0.1
+            and abs(float(one["cx"][0]) - 80.3) < 0.1 and abs(float(one["cy"][0]) - 79.6) < 0.1
+            and len(many) >= 2 and all(abs(float(a - b)) < 0.5 for a, b in zip(many["cx"], many["cx"][::-1])))
+
+
 def check_clean_ring_score():
     img = ring_image(120, 120, 60.2, 59.7, 25.0)
     p = small_params(r_min=15, r_max=35)
