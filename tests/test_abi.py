@@ -68,7 +68,12 @@ def test_create_rejects_bad_params(lib):
     good = dict(sigma=2.0, r_min=5, r_max=40, ridge_thresh=-1.0, peak_frac=0.35, vote_thresh=3)
     bad = [dict(good, sigma=0.0), dict(good, sigma=5.0), dict(good, r_min=1), dict(good, r_max=4),
            dict(good, ridge_thresh=0.5), dict(good, peak_frac=-1.0), dict(good, vote_thresh=-1),
-           dict(good, r_max=600), dict(good, coarse=3), dict(good, coarse=8), dict(good, coarse=-2)]
+           dict(good, r_max=600), dict(good, coarse=3), dict(good, coarse=8), dict(good, coarse=-2),
+           dict(good, sigma=float("nan")), dict(good, sigma=float("inf")), dict(good, ridge_thresh=float("nan")),
+           dict(good, peak_frac=float("inf")), dict(good, peak_frac=float("nan")), dict(good, annulus_w=float("nan")),
+           dict(good, annulus_w=65.0), dict(good, sig_a=float("nan")), dict(good, sig_b=float("inf")),
+           dict(good, sig_a=0.0, sig_b=-0.5), dict(good, sig_a=-0.01), dict(good, sig_a=2.0),
+           dict(good, vote_thresh=65535), dict(good, coarse=4, vote_thresh=4096)]
     for kw in bad:
         p = rd.make_params(**kw)
         ctx = ctypes.c_void_p()
