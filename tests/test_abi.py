@@ -170,6 +170,32 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         rd.Detector({"sigma": 2.0, "r_min": 5, "r_max": 20, "ridge_thresh": -1.0}, 64, 64)
 
 
+def test_static_entry_validates_before_device_work(lib):
+    """rd_ridges_static rejects bad arguments with RD_E_INVAL and a message,
+    before it touches a device (pointers below are never dereferenced)."""
+    from paper_1310_1371_gb300 import rd, synth
+    good = rd.make_params(**synth.PLAIN_SMALL_PARAMS)
+    p16 = ctypes.c_void_p(16)                       # 16-byte aligned, never read
+    cases = [
+        (good, None, 256, 256, rd.RD_U8, p16, p16, 1024, p16, b"NULL"),
+        (good, p16, 256, 256, rd.RD_U8, None, p16, 1024, p16, b"NULL"),
+        (good, p16, 256, 256, 7, p16, p16, 1024, p16, b"dtype"),
+        (good, p16, 8, 256, rd.RD_U8, p16, p16, 1024, p16, b"frame size"),
+        (good, p16, 2048, 2048, rd.RD_U8, p16, p16, 1024, p16, b"pixels"),
+        (good, p16, 256, 256, rd.RD_U8, p16, p16, -1, p16, b"cap"),
+        (good, p16, 256, 256, rd.RD_U8, p16, p16, 1 << 20, p16, b"cap"),
+        (good, p16, 256, 256, rd.RD_U8, p16, ctypes.c_void_p(20), 1024, p16, b"aligned"),
+        (rd.make_params(**dict(synth.PLAIN_SMALL_PARAMS, sigma=0.0)), p16, 256, 256, rd.RD_U8, p16, p16, 1024, p16,
+         b"sigma"),
+        (rd.make_params(**dict(synth.PLAIN_SMALL_PARAMS, ridge_thresh=1.0)), p16, 256, 256, rd.RD_U8, p16, p16, 1024,
+         p16, b"ridge_thresh"),
+    ]
+    for prm, frame, H, W, dt, xy, d, cap, cnt, msg in cases:
+        st = lib.rd_ridges_static(ctypes.byref(prm), frame, H, W, dt, None, xy, d, cap, cnt)
+        assert st == rd.RD_E_INVAL, msg
+        assert msg in lib.rd_static_last_error(), (msg, lib.rd_static_last_error())
+
+
 def test_status_codes_match_header():
     """The binding's status names are the header's rd_status enumerators, in order."""
     from paper_1310_1371_gb300 import rd
