@@ -94,6 +94,22 @@ def test_null_context_calls_fail_cleanly(lib):
     st = rd.rd_stats()
     assert lib.rd_get_stats(None, ctypes.byref(st)) == rd.RD_E_INVAL
     assert lib.rd_debug_ridges(None, 0, None, None, None, 0) == -1
+    assert lib.rd_detect_host(None, None, 1, 64, 64, 0, None, None, 0, None, None) == rd.RD_E_INVAL
+    assert lib.rd_set_graph(None, 1) == rd.RD_E_INVAL
+    assert lib.rd_set_timing(None, 1) == rd.RD_E_INVAL
+    assert lib.rd_set_features(None, 1, 1.0) == rd.RD_E_INVAL
+    assert lib.rd_debug_route(None, 1) == rd.RD_E_INVAL
+    assert lib.rd_debug_capture(None, None, None) == rd.RD_E_INVAL
+    g = rd.rd_geometry()
+    assert lib.rd_get_geometry(None, ctypes.byref(g)) == rd.RD_E_INVAL
+    assert lib.rd_soft_score(None, None, 1, 64, 64, 0, None, None, None, None, None) == rd.RD_E_INVAL
+    assert lib.rd_backward(None, None, 1, 64, 64, None, None, None, None, None, None) == rd.RD_E_INVAL
+    assert lib.rd_refine(None, None, 1, 64, 64, 0, None, None, None, 1, 0.1) == rd.RD_E_INVAL
+    ids = (ctypes.c_longlong * 4)()
+    assert lib.rd_serve_submit(None, 0, None, 1) == rd.RD_E_INVAL
+    assert lib.rd_serve_poll(None, ids, None, None, None, None, 0, None, 4, 0) == -1
+    assert lib.rd_serve_stats(None, ids) == rd.RD_E_INVAL
+    assert lib.rd_serve_destroy(None) == rd.RD_E_INVAL
 
 
 @pytest.mark.parametrize("geo", [(72, 12), (96, 3), (96, 65), (0, 8), (64, 0)])
