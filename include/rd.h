@@ -276,7 +276,7 @@ rd_status rd_autotune(const rd_params* params, const void* frames_dev, int n, in
 const char* rd_last_error(const rd_ctx* ctx);
 
 /* ---- host-only helpers (no GPU work): the exact weight tables -------------
- * rd_gaussian_taps writes the integer Gaussian taps Q_i = floor(2^14 g_i + 1/2),
+ * rd_gaussian_taps writes the integer Gaussian taps Q_i = floor(2^19 g_i + 1/2),
  * |i| <= ceil(4 sigma), of the smoothing step and returns their count (or -1
  * if cap is too small).  rd_level_weights writes the (2R+1)^2 integer level
  * smoothing weights floor(2^16 exp(-(dx^2+dy^2) / (2 sigma(r)^2)) + 1/2),

@@ -28,7 +28,7 @@ import dataclasses
 import math
 import numpy as np
 
-GAUSS_BITS = 14          # O1: Gaussian taps are integers summing to ~2^14
+GAUSS_BITS = 19          # O1: Gaussian taps are integers summing to ~2^19
 SMOOTH_BITS = 16         # O7: level-smoothing weights are integers, peak 2^16
 FIT_FAIL = 1             # ring flag: fewer than 5 annulus points or singular fit
 MIN_FIT_POINTS = 5
@@ -75,10 +75,13 @@ def gaussian_radius(sigma: float) -> int:
 
 
 def gaussian_taps(sigma: float) -> np.ndarray:
-    """Integer taps Q_i = floor(2^14 g_i + 1/2), g_i = e_i / sum(e),
+    """Integer taps Q_i = floor(2^19 g_i + 1/2), g_i = e_i / sum(e),
     e_i = exp(-i^2 / (2 sigma^2)), |i| <= R_g.  The smoothing operator is
     (1/S) sum_i Q_i f(x+i) with S = sum(Q): a normalised Gaussian quantised to
-    multiples of 2^-14, which makes smoothing of integer frames exact."""
+    multiples of 2^-19, which makes smoothing of integer frames exact.  The
+    quantisation is fine enough that the rings equal those of the
+    real-valued Gaussian (``detect_definition``), and coarse enough that the
+    exact Hessian of a 16-bit frame fits int64 (|H'| < 2^60)."""
     R = gaussian_radius(sigma)
     i = np.arange(-R, R + 1, dtype=np.float64)
     den = 2.0 * sigma * sigma
@@ -146,7 +149,9 @@ def hessian_scale(S: int) -> float:
 
 
 def hessian(image: np.ndarray, sigma: float):
-    """Lxx, Lyy, Lxy in float64 (one correctly rounded division each)."""
+    """Lxx, Lyy, Lxy in float64: each exact integer H' rounded to the
+    nearest float64 (exact below 2^53), then one correctly rounded
+    division by D."""
     Lp, S = smooth_int(image, sigma)
     hxx, hyy, hxy = hessian_int(Lp)
     D = hessian_scale(S)
@@ -578,3 +583,172 @@ def detect(image: np.ndarray, p: Params, keep: bool = False) -> Result:
         rings[i] = (cx, cy, rr, ix, iy, ir, nv / (float(1 << SMOOTH_BITS) * ir), nfit, flags)
     return Result(rings, ridge_xy, ridge_X, votes_in, 2 * len(xs) * len(levels), hotspots, smooth_macs,
                   As if keep else None, Ns if keep else None)
+
+
+# --------------------------------------------------------------------------
+# Definition mode: steps O1-O9 with the Gaussian taps of O1 and the level
+# weights of O7 as the paper defines them, real-valued, instead of quantised
+# to multiples of 2^-19 and 2^-16.  The exact path above quantises both so
+# that smoothing and scoring of integer frames become integer arithmetic; this
+# mode exists so that the tests can show that the quantisation changes no
+# ring.  Everything is float64, one IEEE operation per step; frames may be
+# integer or float.  With ``quantised=True`` the same float64 code takes the
+# quantised weights (Q_i / S and Q_r / 2^16), which ties this mode to the
+# exact path.
+# --------------------------------------------------------------------------
+def gaussian_taps_fp64(sigma: float) -> np.ndarray:
+    """g_i = e_i / sum(e), e_i = exp(-i^2 / (2 sigma^2)), |i| <= R_g: the
+    normalised, truncated Gaussian of O1 without quantisation."""
+    R = gaussian_radius(sigma)
+    i = np.arange(-R, R + 1, dtype=np.float64)
+    den = 2.0 * sigma * sigma
+    e = np.exp(-(i * i) / den)
+    tot = 0.0
+    for v in e:                      # left-to-right sum
+        tot = tot + v
+    return e / tot
+
+
+def _correlate1d_fp64(f: np.ndarray, taps: np.ndarray, axis: int) -> np.ndarray:
+    """Float64 correlation along one axis with reflect-101 borders.  The
+    taps of every stencil here are symmetric or antisymmetric, and the sum
+    is taken in paired form, t_0 f(x) + sum_{i>0} t_i (f(x+i) +/- f(x-i)), so
+    that the mirror identities of the exact sum hold exactly in float64 (at
+    a reflect-101 border an antisymmetric stencil gives exactly 0)."""
+    R = (len(taps) - 1) // 2
+    t = np.asarray(taps, dtype=np.float64)
+    if np.array_equal(t, t[::-1]):
+        sgn = 1.0
+    elif np.array_equal(t, -t[::-1]):
+        sgn = -1.0
+    else:
+        raise ValueError("taps must be symmetric or antisymmetric")
+    pad = [(0, 0), (0, 0)]
+    pad[axis] = (R, R)
+    fp = np.pad(f.astype(np.float64), pad, mode="reflect")
+    n = f.shape[axis]
+
+    def shifted(i):
+        sl = [slice(None), slice(None)]
+        sl[axis] = slice(R + i, R + i + n)
+        return fp[tuple(sl)]
+
+    out = t[R] * shifted(0)
+    for i in range(1, R + 1):
+        pair = shifted(i) + shifted(-i) if sgn > 0 else shifted(i) - shifted(-i)
+        out = out + t[R + i] * pair
+    return out
+
+
+def hessian_fp64(image: np.ndarray, sigma: float, quantised: bool = False):
+    """O1-O2 in float64: L = g_y * (g_x * I), then the 5x5 second-order
+    Sobel stencils of L divided by 64 (reflect-101 borders throughout).
+    g is the real Gaussian (``gaussian_taps_fp64``), or Q / S when
+    ``quantised``."""
+    if quantised:
+        Q = gaussian_taps(sigma)
+        g = Q.astype(np.float64) / float(Q.sum())
+    else:
+        g = gaussian_taps_fp64(sigma)
+    L = _correlate1d_fp64(_correlate1d_fp64(image, g, 1), g, 0)
+    s, d1, d2 = SOBEL_S, SOBEL_D1, SOBEL_D2
+    lxx = _correlate1d_fp64(_correlate1d_fp64(L, d2, 1), s, 0) / 64.0
+    lyy = _correlate1d_fp64(_correlate1d_fp64(L, s, 1), d2, 0) / 64.0
+    lxy = _correlate1d_fp64(_correlate1d_fp64(L, d1, 1), d1, 0) / 64.0
+    return lxx, lyy, lxy
+
+
+def smoothing_weights_fp64(r: int, sig_a: float, sig_b: float, c: int = 1,
+                           quantised: bool = False) -> np.ndarray:
+    """w_r(dy, dx) = exp(-(dx^2 + dy^2) / (2 sigma(r)^2)) on the window
+    |dx|, |dy| <= ceil(3 sigma(r)) (O7, peak 1, unnormalised), or
+    Q_r / 2^16 when ``quantised``; sigma(r) in cells of c px."""
+    if quantised:
+        return smoothing_weights(r, sig_a, sig_b, c).astype(np.float64) / float(1 << SMOOTH_BITS)
+    sg = level_sigma(r, sig_a, sig_b) / c
+    Rs = int(math.ceil(3.0 * sg))
+    d = np.arange(-Rs, Rs + 1, dtype=np.float64)
+    d2 = d[:, None] * d[:, None] + d[None, :] * d[None, :]
+    den = 2.0 * sg * sg
+    return np.exp(-d2 / den)
+
+
+def smooth_hot_fp64(A: np.ndarray, w: np.ndarray, hot: int, r: int) -> np.ndarray:
+    """S(v) = (1/r) sum_d w(d) A(v + d) at hotspots (A(v) > hot), 0
+    elsewhere; A = 0 outside the image (O6-O7 in float64)."""
+    H, W = A.shape
+    Rs = (w.shape[0] - 1) // 2
+    S = np.zeros((H, W), dtype=np.float64)
+    hy, hx = np.nonzero(A > hot)
+    if len(hy) == 0:
+        return S
+    Ap = np.pad(A, Rs, mode="constant").astype(np.float64)
+    acc = np.zeros(len(hy), dtype=np.float64)
+    for dy in range(-Rs, Rs + 1):
+        for dx in range(-Rs, Rs + 1):
+            acc += w[dy + Rs, dx + Rs] * Ap[hy + Rs + dy, hx + Rs + dx]
+    S[hy, hx] = acc / float(r)
+    return S
+
+
+def find_peaks_level_fp64(S_lo: np.ndarray, S_mid: np.ndarray, S_hi: np.ndarray, r: int,
+                          p: Params) -> list:
+    """O8 on float64 scores: S(v) > f 2 pi and, over the 26 neighbours,
+    S(v) > S(n) when n precedes v in (r, y, x) order and S(v) >= S(n)
+    otherwise; out-of-image neighbours score 0."""
+    H, W = S_mid.shape
+    thr = p.peak_frac * (2.0 * math.pi)
+    cy, cx = np.nonzero(S_mid > thr)
+    if len(cy) == 0:
+        return []
+    sv = S_mid[cy, cx]
+    ok = np.ones(len(cy), dtype=bool)
+    lvl = {-1: S_lo, 0: S_mid, 1: S_hi}
+    for dr, dy, dx in NEIGHBOURS:
+        yy, xx = cy + dy, cx + dx
+        inb = (yy >= 0) & (yy < H) & (xx >= 0) & (xx < W)
+        sn = np.where(inb, lvl[dr][np.clip(yy, 0, H - 1), np.clip(xx, 0, W - 1)], 0.0)
+        ok &= (sv > sn) if (dr, dy, dx) < (0, 0, 0) else (sv >= sn)
+    return [(int(x), int(y), int(r), float(s)) for x, y, s in zip(cx[ok], cy[ok], sv[ok])]
+
+
+def detect_definition(image: np.ndarray, p: Params, quantised: bool = False) -> Result:
+    """Frame -> rings with real-valued Gaussian taps and level weights
+    (``quantised=False``, the paper's definition) or their quantised
+    versions evaluated in float64 (``quantised=True``).  Steps O3-O6 and O9
+    are the functions of the exact path; ridges only (no edge variant).
+    ``rings['score']`` is S at the integer peak."""
+    if p.features != "ridge":
+        raise ValueError("definition mode covers the ridge method only")
+    H, W = image.shape
+    c = p.coarse
+    Hc, Wc = cell_grid(H, W, c)
+    Lxx, Lyy, Lxy = hessian_fp64(image, p.sigma, quantised)
+    k, X, Y, deg = eigen(Lxx, Lyy, Lxy)
+    mask = ridge_mask(k, X, Y, deg, p.ridge_thresh)
+    ys, xs = np.nonzero(mask)
+    ridge_xy = np.stack([xs, ys], axis=1).astype(np.int64)
+    ridge_X = np.stack([X[ys, xs], Y[ys, xs]], axis=1)
+    levels = radius_levels(p.r_min, p.r_max)
+    Ss = {}
+    votes_in = 0
+    peaks = []
+    for r in levels:
+        r = int(r)
+        bx, by = cast_votes(xs, ys, ridge_X[:, 0], ridge_X[:, 1], r, H, W, c)
+        votes_in += len(bx)
+        A = accumulate(bx, by, Hc, Wc)
+        Ss[r] = smooth_hot_fp64(A, smoothing_weights_fp64(r, p.sig_a, p.sig_b, c, quantised),
+                                hot_threshold(p), r)
+        if r - 1 >= p.r_min:
+            peaks += find_peaks_level_fp64(Ss[r - 2], Ss[r - 1], Ss[r], r - 1, p)
+            del Ss[r - 2]
+    peaks = [(c * x, c * y, r, s) for x, y, r, s in peaks]
+    peaks.sort(key=lambda t: (t[2], t[1], t[0]))
+    rings = np.zeros(len(peaks), dtype=RING_DTYPE)
+    w = annulus_width(p)
+    for i, (ix, iy, ir, s) in enumerate(peaks):
+        pts = annulus_members(ridge_xy, ix, iy, ir, w)
+        cx, cy, rr, nfit, flags = kasa_fit(pts, ix, iy, ir)
+        rings[i] = (cx, cy, rr, ix, iy, ir, s, nfit, flags)
+    return Result(rings, ridge_xy, ridge_X, votes_in, 2 * len(xs) * len(levels))

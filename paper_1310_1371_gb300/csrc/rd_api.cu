@@ -4,7 +4,7 @@
 //
 // The tables follow the definition operation by operation (compile with
 // -ffp-contract=off so that no multiply-add is fused):
-//   Gaussian taps  Q_i = floor(2^14 g_i + 1/2), g_i = e_i / sum(e),
+//   Gaussian taps  Q_i = floor(2^19 g_i + 1/2), g_i = e_i / sum(e),
 //                  e_i = exp(-(i^2) / (2 sigma sigma)), |i| <= ceil(4 sigma)
 //   level weights  floor(2^16 exp(-(dy^2 + dx^2) / (2 s s)) + 1/2),
 //                  s = (sig_a r + sig_b) / c, |dx|, |dy| <= ceil(3 s), with c

@@ -22,7 +22,7 @@
 
 namespace rd {
 
-constexpr int GAUSS_BITS = 14;     // Gaussian taps: integers summing to ~2^14
+constexpr int GAUSS_BITS = 19;     // Gaussian taps: integers summing to ~2^19
 constexpr int SMOOTH_BITS = 16;    // level-smoothing weights: peak 2^16
 constexpr int MAX_RG = 16;         // Gaussian half-width ceil(4 sigma), sigma <= 4
 constexpr int ST_TW = 32;          // stencil tile (output pixels)
@@ -87,6 +87,8 @@ struct StencilArgs {
   float invD;     // fl(1 / D)
   RidgeList rl;
   DevStats* stats;
+  uint32_t narrow_max;  // largest input value for which the exact Gaussian's pair sums fit u32
+                        // (set by launch_stencil from the taps: 2 S narrow_max < 2^32)
 };
 
 struct BinArgs {

@@ -42,12 +42,13 @@ def bilinear64(fx, fy, k00, k01, k10, k11):
 def hessians(rng, n):
     out = []
     for _ in range(n):
-        s = 10.0 ** rng.uniform(0, 15)
+        s = 10.0 ** rng.uniform(0, 17.5)                      # |H'| < 2^60 at 2^-19 taps
         out.append(tuple(int(v) for v in np.rint(rng.normal(0, s, 3))))
     for _ in range(n // 4):                                   # near-degenerate
-        base = int(10.0 ** rng.uniform(3, 14))
+        base = int(10.0 ** rng.uniform(3, 17.5))
         out.append((base + int(rng.integers(-2, 3)), base + int(rng.integers(-2, 3)), int(rng.integers(-2, 3))))
-    out += [(5, 5, 0), (0, 0, 0), (-7, 3, 0), (3, -7, 0), (4, 4, 1), (1 << 51, -(1 << 51), 1 << 50)]
+    out += [(5, 5, 0), (0, 0, 0), (-7, 3, 0), (3, -7, 0), (4, 4, 1), (1 << 51, -(1 << 51), 1 << 50),
+            ((1 << 59) + 1, -(1 << 59) - 3, (1 << 58) + 1)]
     return out
 
 

@@ -2,12 +2,18 @@
 detector accepts, the ranges its kernels rely on hold on the worst input,
 a frame of all 65535.
 
-* horizontal Gaussian sums P = sum Q_i I fit u32, and so does the pair
-  P_j + P_{2R-j} that the vertical pass forms before its multiply;
-* L' = sum Q_j P fits well inside u64, and is exact in float64 (< 2^53);
-* the second-order Sobel sums H' = (stencil) * L' stay below 2^52 in
-  magnitude (int64 with room, and the FP32 path's bound takes |L'| < 2^53);
-* the first-order Sobel of the edge variant likewise.
+* A stencil tile whose inputs are at most narrow_max = floor((2^32 - 1) /
+  (2 S)) keeps every horizontal Gaussian sum P = sum Q_i I below 2^31 and
+  the pair P_j + P_{2R-j} that the vertical pass forms before its multiply
+  below 2^32; narrow_max is at least 4095, so 8-bit and 12-bit frames are
+  always narrow.
+* A wider tile is smoothed once per byte of its inputs (high, then low):
+  each part's horizontal sums stay below 2^28 and L' = 2^8 L'(high) +
+  L'(low) below 2^54 (u64).
+* The second-order Sobel sums H' = (stencil) * L' stay below 2^60 in
+  magnitude (int64 with room); the first-order Sobel of the edge variant
+  below 2^61.  Above 2^53 the oracle's and the kernels' conversion of H' to
+  float64 rounds to nearest (ties to even) on both sides.
 The oracle's taps are the kernels' (checked in the ABI tests)."""
 import numpy as np
 import pytest
@@ -23,15 +29,20 @@ def test_worst_case_ranges(sigma):
     Q = O.gaussian_taps(s32).astype(object)
     S = int(sum(Q))
     assert all(q >= 0 for q in Q)
-    Imax = 65535
-    P = Imax * S                                   # every horizontal sum of the all-65535 frame
+    narrow_max = (2 ** 32 - 1) // (2 * S)
+    assert narrow_max >= 4095                      # 8- and 12-bit frames take the u32 path
+    P = narrow_max * S                             # largest horizontal sum of a narrow tile
     assert P < 2 ** 31 and 2 * P < 2 ** 32         # u32 sum, and the vertical pass's pair
-    L = P * S
-    assert L < 2 ** 53                             # exact in float64; u64 with 11 bits to spare
+    Pb = 255 * S                                   # one byte per part of a wide tile
+    assert 2 * Pb < 2 ** 28
+    Imax = 65535
+    L = Imax * S * S
+    assert (2 ** 8) * (255 * S * S) + 255 * S * S == L
+    assert L < 2 ** 54                             # u64 with 10 bits to spare
     # second-order Sobel: |d2| x |s| has coefficient mass 4 x 16 = 64 (and 6 x 6 = 36 for Lxy)
-    assert 64 * L < 2 ** 52
+    assert 64 * L < 2 ** 60
     # first-order Sobel of the edge variant: |d1| x |s| = 6 x 16 = 96
-    assert 96 * L < 2 ** 53
+    assert 96 * L < 2 ** 61
 
 
 def test_stencil_coefficients():

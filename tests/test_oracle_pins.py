@@ -45,15 +45,15 @@ def reflect101(i, n):
 
 # ---------------------------------------------------------------- O1
 def check_taps_are_gaussian(sigma):
-    """Taps sum to 2^14 within rounding, are symmetric and peaked at 0, and
+    """Taps sum to 2^19 within rounding, are symmetric and peaked at 0, and
     the normalised discrete variance is sigma^2 (a sampled Gaussian's second
-    moment; truncation at 4 sigma and 2^-14 quantisation change it by < 2e-3)."""
+    moment; truncation at 4 sigma and 2^-19 quantisation change it by < 2e-3)."""
     Q = O.gaussian_taps(sigma)
     R = (len(Q) - 1) // 2
     i = np.arange(-R, R + 1)
     S = Q.sum()
     var = float((Q * i * i).sum()) / float(S)
-    return (abs(int(S) - (1 << 14)) <= len(Q) and np.array_equal(Q, Q[::-1])
+    return (abs(int(S) - (1 << 19)) <= len(Q) and np.array_equal(Q, Q[::-1])
             and Q.argmax() == R and abs(var - sigma * sigma) < 2e-3 * max(1.0, sigma * sigma))
 
 

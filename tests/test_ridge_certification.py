@@ -152,7 +152,7 @@ def replay(img, sigma, tau, contract):
     Lp, S = O.smooth_int(img, sigma)
     invD = f32(1.0 / float(64 * S * S))
     Lpad = np.pad(Lp, PAD, mode="reflect")               # reflect-101 at every border
-    Lf = Lpad.astype(F64).astype(np.float32)             # L' < 2^53: one rounding
+    Lf = Lpad.astype(np.float32)                         # int64 to float32: one rounding
     fa, fb, fc = hessian32(Lf, invD)                     # pixel (y, x) at [y + PAD - 2, x + PAD - 2]
     tau = f32(tau)
     k, ek0, hdf, rad, M = eig_k(fa, fb, fc, contract)
@@ -243,7 +243,7 @@ def replay_edges(img, sigma, edge_thresh, contract):
     H, W = img.shape
     Lp, S = O.smooth_int(img, sigma)
     invD = f32(1.0 / float(128 * S * S))
-    Lf = np.pad(Lp, PAD, mode="reflect").astype(F64).astype(np.float32)
+    Lf = np.pad(Lp, PAD, mode="reflect").astype(np.float32)  # one rounding
     gx, gy = gradient32(Lf, invD)
     g = np.sqrt(gx * gx + gy * gy)                       # correctly rounded operations, no contraction
     k = -g

@@ -254,7 +254,7 @@ def hessian_D():
 def random_hessians(rng, n):
     out = []
     for _ in range(n):
-        scale = 10.0 ** rng.uniform(2, 15)
+        scale = 10.0 ** rng.uniform(2, 17.5)          # |H'| < 2^60 at 2^-19 taps
         A, C, B = (int(v) for v in np.rint(rng.normal(0, scale, 3)))
         out.append((A, C, B))
     return out
@@ -264,7 +264,7 @@ def near_degenerate(rng, n):
     """Eigenvalue gap a tiny fraction of the entries: large cond, ill records."""
     out = []
     for _ in range(n):
-        base = int(10.0 ** rng.uniform(8, 14))
+        base = int(10.0 ** rng.uniform(8, 17.5))
         A = base + int(rng.integers(-3, 4))
         C = base + int(rng.integers(-3, 4))
         B = int(rng.integers(-3, 4))
@@ -275,7 +275,7 @@ def near_degenerate(rng, n):
 def axes(rng, n):
     out = []
     for _ in range(n):
-        a, c = (int(v) for v in rng.integers(-10 ** 12, 10 ** 12, 2))
+        a, c = (int(v) for v in rng.integers(-10 ** 17, 10 ** 17, 2))
         if a != c:
             out.append((a, c, 0))
     return out
@@ -295,7 +295,7 @@ def near_boundary(rng, n, coarse):
         ys = math.sqrt(1 - xs * xs) * (1 if rng.random() < 0.5 else -1)
         if rng.random() < 0.5:
             xs, ys = ys, xs                        # the boundary in y instead
-        lam1 = -10.0 ** rng.uniform(9, 13)         # k-, the smaller eigenvalue
+        lam1 = -10.0 ** rng.uniform(9, 17)         # k-, the smaller eigenvalue
         lam2 = lam1 + abs(lam1) * 10.0 ** rng.uniform(-3, 0.5)
         v = np.array([xs, ys])
         w = np.array([-ys, xs])
