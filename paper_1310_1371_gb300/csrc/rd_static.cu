@@ -13,15 +13,29 @@
 #include "rd_internal.cuh"
 #include "rd_abi_guard.h"
 
+#include <cuda.h>
 #include <cstddef>
 #include <mutex>
 #include <string>
 
 namespace rd {
 
-// Frames of at most RD_STATIC_MAX_PIXELS pixels (each side >= 12) have at
-// most 3074 stencil tiles.
-constexpr int STATIC_MAX_TILES = 4096;
+// The most stencil tiles a frame within the limits can have (each side in
+// [12, 65535], at most RD_STATIC_MAX_PIXELS pixels): 2048, at 12 x 65535 (one
+// row of tiles).
+constexpr long long static_tiles_bound() {
+  long long best = 0;
+  for (long long h = 12; h <= 65535; ++h) {
+    long long w = RD_STATIC_MAX_PIXELS / h;
+    if (w > 65535) w = 65535;
+    if (w < 12) break;
+    const long long t = ((h + ST_TH - 1) / ST_TH) * ((w + ST_TW - 1) / ST_TW);
+    if (t > best) best = t;
+  }
+  return best;
+}
+constexpr int STATIC_MAX_TILES = 2048;
+static_assert(static_tiles_bound() <= STATIC_MAX_TILES, "stencil tile index too small for the frame limits");
 
 // Scratch of one call: K1's counters, its per-tile record index, the exact
 // Hessians it writes beside the caller's ridge list, and the vote-rounding
@@ -40,13 +54,21 @@ namespace {
 constexpr int MAX_DEVICES = 64;
 
 struct DeviceSetup {
-  StaticScratch* scratch;  // device address of g_rd_static_scratch
+  StaticScratch* scratch;      // device address of g_rd_static_scratch in the context below
+  unsigned long long ctx_id;   // unique id of the CUDA context the address was looked up in
   int n_sm;
 };
 
 std::mutex g_setup_mutex;
 DeviceSetup g_setup[MAX_DEVICES] = {};
 thread_local std::string g_static_error;
+
+// Driver entry points for the current context's identity, fetched through
+// the runtime so that the library does not link the driver library itself.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
 
 rd_status fail_static(rd_status s, const std::string& m) {
   g_static_error = m;
@@ -57,26 +79,62 @@ rd_status fail_cuda(const char* what, cudaError_t e) {
   return fail_static(RD_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-// Once per device, with that device current: the scratch array's device
+// Unique id of the calling thread's current CUDA context, 0 if none is
+// current yet.  Caller holds g_setup_mutex.
+rd_status current_context_id(unsigned long long* id) {
+  if (!g_ctx_get_current || !g_ctx_get_id) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+    if (e == cudaSuccess)
+      e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+    if (e != cudaSuccess) return fail_cuda("cudaGetDriverEntryPointByVersion", e);
+    if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+      return fail_static(RD_E_CUDA, "the driver has no cuCtxGetCurrent / cuCtxGetId");
+    g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+    g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f2);
+  }
+  CUcontext ctx = nullptr;
+  if (g_ctx_get_current(&ctx) != CUDA_SUCCESS) return fail_static(RD_E_CUDA, "cuCtxGetCurrent failed");
+  *id = 0;
+  if (ctx && g_ctx_get_id(ctx, id) != CUDA_SUCCESS) return fail_static(RD_E_CUDA, "cuCtxGetId failed");
+  return RD_OK;
+}
+
+// Set-up for the current device and context: the scratch array's device
 // address (its host-side name is only a stand-in for the symbol) and the SM
-// count that sizes the refinement grid.
+// count that sizes the refinement grid.  The address belongs to the context
+// it was looked up in, so it is cached per device together with that
+// context's unique id, and looked up again when another context is current
+// (a context rebuilt after cudaDeviceReset, or one the caller created with
+// the driver API).  A look-up loads the library's module into the context,
+// so the first call in each context must not be inside a stream capture.
 rd_status setup_current_device(DeviceSetup* out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail_cuda("cudaGetDevice", e);
   if (dev < 0 || dev >= MAX_DEVICES) return fail_static(RD_E_INVAL, "device index above 63");
   std::lock_guard<std::mutex> lock(g_setup_mutex);
+  unsigned long long id = 0;
+  rd_status st = current_context_id(&id);
+  if (st != RD_OK) return st;
   DeviceSetup& s = g_setup[dev];
-  if (!s.scratch) {
+  if (!s.scratch || id == 0 || s.ctx_id != id) {
     int n_sm = 0;
     e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return fail_cuda("cudaDeviceGetAttribute", e);
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_rd_static_scratch);
+    e = cudaGetSymbolAddress(&p, g_rd_static_scratch);  // makes the device's primary context current
     if (e != cudaSuccess) return fail_cuda("cudaGetSymbolAddress", e);
     if (!p) return fail_static(RD_E_CUDA, "cudaGetSymbolAddress returned NULL");
+    if (id == 0) {  // no context was current before the look-up: take the one it used
+      st = current_context_id(&id);
+      if (st != RD_OK) return st;
+    }
     s.n_sm = n_sm > 0 ? n_sm : 1;
     s.scratch = static_cast<StaticScratch*>(p);
+    s.ctx_id = id;
   }
   *out = s;
   return RD_OK;
@@ -110,6 +168,10 @@ extern "C" rd_status rd_ridges_static(const rd_params* p, const void* frame_dev,
     if (cap < 0 || cap > RD_STATIC_MAX_RIDGE)
       return fail_static(RD_E_INVAL, "cap must be in [0, RD_STATIC_MAX_RIDGE] (262144)");
     if (((uintptr_t)dir_dev & 15) != 0) return fail_static(RD_E_INVAL, "dir_dev must be 16-byte aligned");
+    if (((uintptr_t)xy_dev & 3) != 0) return fail_static(RD_E_INVAL, "xy_dev must be 4-byte aligned");
+    if (((uintptr_t)count_dev & 3) != 0) return fail_static(RD_E_INVAL, "count_dev must be 4-byte aligned");
+    if (dtype == RD_U16 && ((uintptr_t)frame_dev & 1) != 0)
+      return fail_static(RD_E_INVAL, "frame_dev must be 2-byte aligned for RD_U16");
 
     DeviceSetup dev;
     rd_status s = setup_current_device(&dev);

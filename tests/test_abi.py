@@ -200,7 +200,10 @@ def test_static_entry_validates_before_device_work(lib):
         (good, p16, 2048, 2048, rd.RD_U8, p16, p16, 1024, p16, b"pixels"),
         (good, p16, 256, 256, rd.RD_U8, p16, p16, -1, p16, b"cap"),
         (good, p16, 256, 256, rd.RD_U8, p16, p16, 1 << 20, p16, b"cap"),
-        (good, p16, 256, 256, rd.RD_U8, p16, ctypes.c_void_p(20), 1024, p16, b"aligned"),
+        (good, p16, 256, 256, rd.RD_U8, p16, ctypes.c_void_p(20), 1024, p16, b"dir_dev must be 16-byte aligned"),
+        (good, p16, 256, 256, rd.RD_U8, ctypes.c_void_p(18), p16, 1024, p16, b"xy_dev must be 4-byte aligned"),
+        (good, p16, 256, 256, rd.RD_U8, p16, p16, 1024, ctypes.c_void_p(17), b"count_dev must be 4-byte aligned"),
+        (good, ctypes.c_void_p(17), 256, 256, rd.RD_U16, p16, p16, 1024, p16, b"frame_dev must be 2-byte aligned"),
         (rd.make_params(**dict(synth.PLAIN_SMALL_PARAMS, sigma=0.0)), p16, 256, 256, rd.RD_U8, p16, p16, 1024, p16,
          b"sigma"),
         (rd.make_params(**dict(synth.PLAIN_SMALL_PARAMS, ridge_thresh=1.0)), p16, 256, 256, rd.RD_U8, p16, p16, 1024,

@@ -90,6 +90,37 @@ def test_two_calls_match_rd_detect(rd, torch):
 
 
 @pytest.mark.gpu
+def test_overflow_keeps_true_count_and_first_records(rd, torch):
+    """A capacity below the frame's ridge count: count_dev still holds the
+    true count, the first cap records are valid ridge pixels of rd_detect's
+    list (distinct, with its directions), and nothing is written past cap
+    (the buffers extend 64 records beyond the capacity the call is given)."""
+    cases = [(synth.plain_full(seed=1002).image, synth.PLAIN_FULL_PARAMS, 5000),
+             (synth.plain_small(seed=1001).image, synth.PLAIN_SMALL_PARAMS, 300)]
+    stream = torch.cuda.current_stream()
+    for img, params, cap in cases:
+        frame = torch.from_numpy(np.ascontiguousarray(img)).cuda()
+        xy_all = torch.full((cap + 64,), -1, dtype=torch.int32, device="cuda")
+        dirs_all = torch.full((cap + 64, 4), float("nan"), dtype=torch.float32, device="cuda")
+        count = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+        rd.rd_ridges_static(params, frame, xy_all[:cap], dirs_all[:cap], count, stream)
+        torch.cuda.synchronize()
+        ref_xy, ref_d = reference_ridges(rd, torch, img, params)
+        assert int(count.item()) == len(ref_xy) > cap
+        v = xy_all[:cap].cpu().numpy().view(np.uint32)
+        d = dirs_all[:cap].cpu().numpy()
+        gx, gy = (v & 0xFFFF).astype(np.int64), (v >> 16).astype(np.int64)
+        ref = {(int(x), int(y)): i for i, (x, y) in enumerate(ref_xy.tolist())}
+        keys = list(zip(gx.tolist(), gy.tolist()))
+        assert len(set(keys)) == cap, "records repeat"
+        assert all(k in ref for k in keys), "a record is not a ridge pixel of rd_detect"
+        idx = np.array([ref[k] for k in keys])
+        assert np.abs(d[:, :2] - ref_d[idx]).max() <= DIR_TOL
+        assert np.all(xy_all[cap:].cpu().numpy() == -1), "records written past cap"
+        assert np.all(np.isnan(dirs_all[cap:].cpu().numpy())), "directions written past cap"
+
+
+@pytest.mark.gpu
 def test_rejects_sizes_beyond_the_limits(rd, torch):
     p = synth.PLAIN_FULL_PARAMS
     count = torch.zeros(1, dtype=torch.int32, device="cuda")
