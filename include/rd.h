@@ -174,6 +174,11 @@ rd_status rd_set_graph(rd_ctx* ctx, int on);
  * counters to *out.  Returns RD_E_OVERFLOW when any RD_OVF_* bit is set. */
 rd_status rd_get_stats(rd_ctx* ctx, rd_stats* out);
 
+/* Device memory the context holds: the sum of its allocations (workspaces
+ * sized at rd_create, plus the soft path's and the edge variant's once
+ * allocated).  Host-side, no GPU work.  RD_E_INVAL on NULL arguments. */
+rd_status rd_get_device_bytes(const rd_ctx* ctx, long long* bytes);
+
 rd_status rd_destroy(rd_ctx* ctx);
 
 /* ---- differentiable soft score, its gradients and refinement --------------
@@ -321,6 +326,24 @@ int       rd_debug_ridges(rd_ctx* ctx, int f, int32_t* xy, float* dir, int64_t* 
 rd_status rd_debug_route(rd_ctx* ctx, int all_dense);
 rd_status rd_debug_capture(rd_ctx* ctx, int32_t* acc_dev, uint32_t* sm_dev);
 
+/* ---- measured peak of the voting unit --------------------------------------
+ * rd_probe_smem_atomics measures the rate of shared-memory atomic adds on the
+ * current device, the operation that accumulates votes (Results, "Directed
+ * ridge detection & votes collection"; Detailed algorithm step 4).  Every
+ * CTA (256 threads, ctas_per_sm per SM) adds 8 x iters times per thread into
+ * a 32 KB shared array with one address pattern: 0 conflict-free (a warp's
+ * lanes in 32 distinct banks), 1 packed u16 pairs (two lanes per word, as
+ * votes for horizontally adjacent voxels), 2 pseudo-random words (the
+ * address spread of a warp's votes).  One warm-up launch, then one launch
+ * timed with CUDA events on stream; the call waits for it.  Writes the adds
+ * per second to *atomics_per_s and the timed launch's milliseconds to *ms (may
+ * be NULL).  Allocates and frees 4 bytes of device memory.  Errors:
+ * RD_E_INVAL (pattern not 0-2, ctas_per_sm not 1-8, iters not 1-2^20, NULL
+ * atomics_per_s), RD_E_CUDA; message in rd_probe_last_error. */
+rd_status   rd_probe_smem_atomics(int pattern, int ctas_per_sm, int iters, void* stream, double* atomics_per_s,
+                                  float* ms);
+const char* rd_probe_last_error(void);
+
 /* ---- allocation-free directed-ridge stages --------------------------------
  * The paper has no counterpart to this entry point.  It serves callers that
  * cannot allocate device memory where they call the detector: acquisition
@@ -351,11 +374,18 @@ rd_status rd_debug_capture(rd_ctx* ctx, int32_t* acc_dev, uint32_t* sm_dev);
  * the same parameters (rd_debug_ridges), in an unspecified order.  Work is
  * enqueued on stream; outputs are valid once the stream has synchronised.
  * Errors: RD_E_INVAL (NULL pointer, bad parameter, frame or cap beyond the
- * limits, unaligned dir_dev: nothing is enqueued), RD_E_CUDA (set-up or a
- * launch failed).  The message is in rd_static_last_error (per host thread).
+ * limits, a pointer not aligned to its element -- dir_dev to 16 bytes, xy_dev
+ * and count_dev to 4, a RD_U16 frame_dev to 2: nothing is enqueued),
+ * RD_E_CUDA (set-up or a launch failed).  The message is in
+ * rd_static_last_error (per host thread).
  * Set-up: the first call on each device, with that device current, looks up
  * the array's device address (cudaGetSymbolAddress) and the SM count; make
- * that first call before any stream capture on that device.
+ * that first call before any stream capture on that device.  The address
+ * belongs to the CUDA context current at that call; a call made while
+ * another context is current on the device (a context created with the
+ * driver API, or the primary context rebuilt after cudaDeviceReset) repeats
+ * the look-up, so the first call in each such context must also come before
+ * any stream capture.
  * Sharing: every call on a device uses the same array, which keeps the last
  * call's contents (each call clears its counters on its stream before use).
  * Calls whose GPU work overlaps -- on streams with no ordering between them,
@@ -368,30 +398,55 @@ rd_status   rd_ridges_static(const rd_params* params, const void* frame_dev, int
 const char* rd_static_last_error(void);
 
 /* ---- continuous-batching request server ------------------------------------
- * Not in the paper (whose producer-consumer pool is its prior art, Methods).
  * One server serves single-frame requests of several size classes on the
- * current GPU.  Each class owns `slots` detector contexts with their own
- * streams and pinned staging, all created by rd_serve_create; their device
- * workspaces must fit mem_budget bytes (0: no limit), else RD_E_NOMEM and no
- * server.  A scheduler thread admits queued requests into free slots, up to
+ * current GPU (the paper's producer-consumer processing, Methods, made a
+ * device-resident request loop).  Each class runs its batches on up to
+ * `slots` detector contexts ("slots"), each with its own stream, pinned
+ * staging and mapped pinned outputs.  A scheduler thread admits queued
+ * requests, the class of the oldest request first, into a free slot, up to
  * max_batch frames per launch, so requests arriving while others are on the
- * GPU are admitted as slots free up and the slots' work overlaps.  A frame's
- * rings are the ones rd_detect gives for that frame alone.
+ * GPU are admitted as slots and memory free up, and the slots' work overlaps.
+ * A frame's rings are the ones rd_detect gives for that frame alone.
+ * Memory: a slot holds its context's workspaces (rd_get_device_bytes) and
+ * the device copy of its frames; the slots alive never hold more than
+ * mem_budget bytes together (0: no limit).  A new slot is made only when it
+ * fits beside the others; idle slots of other classes are destroyed, least
+ * recently used first, to make room; otherwise the class waits until
+ * batches in flight finish, and classes with newer requests take no new
+ * memory meanwhile.  rd_serve_create makes one slot per class (RD_E_NOMEM
+ * when one slot of some class exceeds the budget).  The detector writes
+ * rings, counts and offsets straight into mapped host memory, so only the
+ * rings found leave the device.
  *   rd_serve_submit copies the class's H x W frame (dtype of the class) from
- *     frame_host and queues it (RD_E_BUSY: queue_cap requests are waiting;
- *     RD_E_INVAL: bad class or pointer).  Thread-safe.
+ *     frame_host and queues it (RD_E_BUSY: queue_cap requests are waiting, or
+ *     completed results wait to be polled; RD_E_INVAL: bad class or
+ *     pointer).  Thread-safe.
  *   rd_serve_poll waits up to wait_ms for completed requests and returns up
  *     to max_results of them (-1 on bad arguments): ids, class, status
- *     (RD_OK or the error of its batch), ring count, latency from submission
- *     to results on the host (microseconds); their rings are concatenated in
- *     rings (a result whose rings do not fit stays for the next poll, unless
- *     it is the first, which is then truncated).  Thread-safe.
+ *     (RD_OK; the error of its batch; RD_E_NOMEM when a host allocation for
+ *     its result failed, or no slot could be made for its class), ring
+ *     count, latency from submission to results on the host (microseconds);
+ *     their rings are concatenated in rings (a result whose rings do not fit
+ *     stays for the next poll, unless it is the first, which is then
+ *     truncated).  Thread-safe.
  *   rd_serve_stats writes submitted, completed, batches launched and device
- *     bytes of the slots.
+ *     bytes of the slots alive; rd_serve_stats_ex writes up to cap of the
+ *     RD_SERVE_N_STATS values below and returns how many (-1: bad
+ *     arguments).
+ *   rd_serve_debug_inject makes the next `count` host allocations of one
+ *     kind fail as if the host were out of memory, for tests of the failure
+ *     path: RD_SERVE_FAIL_RESULT, a completed request's ring vector (that
+ *     request gets RD_E_NOMEM); RD_SERVE_FAIL_SLOT, the making of a new slot
+ *     (a class with no slot left fails its queued requests with RD_E_NOMEM).
  *   rd_serve_destroy stops admitting, waits for the batches in flight and
  *     frees everything; results not polled are dropped.
  * Errors of rd_serve_create / rd_serve_submit: rd_serve_last_error (per
  * host thread). */
+#define RD_SERVE_N_STATS 10  /* submitted, completed, batches, device bytes of the slots alive,
+                                their peak, slots made, slots destroyed to make room, scheduling
+                                rounds that waited for memory, failed requests, the budget      */
+#define RD_SERVE_FAIL_RESULT 1
+#define RD_SERVE_FAIL_SLOT   2
 typedef struct rd_serve_class {
   rd_params params;
   int H, W;       /* frame size of the class's requests                       */
@@ -408,6 +463,8 @@ rd_status   rd_serve_submit(rd_server* server, int cls, const void* frame_host, 
 int         rd_serve_poll(rd_server* server, long long* ids, int* classes, int* status, int* n_rings,
                           rd_ring* rings, int rings_cap, double* latency_us, int max_results, int wait_ms);
 rd_status   rd_serve_stats(rd_server* server, long long* out4);
+int         rd_serve_stats_ex(rd_server* server, long long* out, int cap);
+rd_status   rd_serve_debug_inject(rd_server* server, int kind, int count);
 rd_status   rd_serve_destroy(rd_server* server);
 const char* rd_serve_last_error(void);
 

@@ -107,6 +107,7 @@ struct rd_ctx {
   int g_shape[5] = {};
   cudaStream_t g_stream = nullptr;
   cudaEvent_t ev[RD_N_STAGES + 1] = {};
+  long long dev_bytes = 0;  // device memory the context holds (its cudaMalloc total)
   std::string err;
 };
 
@@ -200,6 +201,14 @@ static void free_all(rd_ctx* c) {
 template <typename T>
 static bool dalloc(T** p, size_t count) {
   return cudaMalloc((void**)p, sizeof(T) * (count ? count : 1)) == cudaSuccess;
+}
+
+// A context's allocation: counted in its device bytes.
+template <typename T>
+static bool dalloc(rd_ctx* c, T** p, size_t count) {
+  if (!dalloc(p, count)) return false;
+  c->dev_bytes += (long long)(sizeof(T) * (count ? count : 1));
+  return true;
 }
 
 static std::string validate(const rd_params* p) {
@@ -411,22 +420,22 @@ extern "C" rd_status rd_create_ex(const rd_params* params, int max_H, int max_W,
     if (c->n_bins_max > INT_MAX / 4) {
       return fail(nullptr, RD_E_INVAL, "too many accumulator bins (frames x tiles x slabs > 2^31): lower max_batch");
     }
-    bool ok = dalloc(&c->slabs, c->n_slabs) && dalloc(&c->q_rad, c->n_levels) &&
-              dalloc(&c->qq_off, h_qqoff.size()) && dalloc(&c->qq_tab, h_qqtab.size()) &&
-              dalloc(&c->qp_off, h_qpoff.size()) && dalloc(&c->qp_tab, h_qptab.size()) &&
-              dalloc(&c->fb_list, 4 * c->n_bins_max) && dalloc(&c->fb_count, 1) && dalloc(&c->queue, c->n_bins_max) &&
-              dalloc(&c->queue_ctr, 2) &&
-              dalloc(&c->nthr, c->n_levels) && dalloc(&c->rl.xy, nrec) &&
-              dalloc(&c->rl.dir, nrec) && dalloc(&c->rl.kvote, nrec) && dalloc(&c->rl.hess, 3 * nrec) &&
-              dalloc(&c->rl.count, max_batch) && dalloc(&c->rl.tile_off, (size_t)max_batch * n_stx * n_sty) &&
-              dalloc(&c->rl.tile_cnt, (size_t)max_batch * n_stx * n_sty) && dalloc(&c->bin_cnt, c->n_bins_max) &&
-              dalloc(&c->bin_off, c->n_bins_max) && dalloc(&c->bin_fill, c->n_bins_max) &&
-              dalloc(&c->block_sums, (c->n_bins_max + 1023) / 1024 + 1) && dalloc(&c->bin_total, 1) &&
-              dalloc(&c->pool, c->pool_cap) && dalloc(&c->peaks, (size_t)max_batch * c->peak_cap) &&
-              dalloc(&c->peak_count, max_batch) && dalloc(&c->stats, 1) &&
-              dalloc((unsigned char**)&c->stage_frames, (size_t)max_batch * max_H * max_W * 2) &&
-              dalloc(&c->stage_rings, (size_t)max_batch * c->peak_cap) && dalloc(&c->stage_counts, max_batch) &&
-              dalloc(&c->stage_offsets, max_batch);
+    bool ok = dalloc(c, &c->slabs, c->n_slabs) && dalloc(c, &c->q_rad, c->n_levels) &&
+              dalloc(c, &c->qq_off, h_qqoff.size()) && dalloc(c, &c->qq_tab, h_qqtab.size()) &&
+              dalloc(c, &c->qp_off, h_qpoff.size()) && dalloc(c, &c->qp_tab, h_qptab.size()) &&
+              dalloc(c, &c->fb_list, 4 * c->n_bins_max) && dalloc(c, &c->fb_count, 1) && dalloc(c, &c->queue, c->n_bins_max) &&
+              dalloc(c, &c->queue_ctr, 2) &&
+              dalloc(c, &c->nthr, c->n_levels) && dalloc(c, &c->rl.xy, nrec) &&
+              dalloc(c, &c->rl.dir, nrec) && dalloc(c, &c->rl.kvote, nrec) && dalloc(c, &c->rl.hess, 3 * nrec) &&
+              dalloc(c, &c->rl.count, max_batch) && dalloc(c, &c->rl.tile_off, (size_t)max_batch * n_stx * n_sty) &&
+              dalloc(c, &c->rl.tile_cnt, (size_t)max_batch * n_stx * n_sty) && dalloc(c, &c->bin_cnt, c->n_bins_max) &&
+              dalloc(c, &c->bin_off, c->n_bins_max) && dalloc(c, &c->bin_fill, c->n_bins_max) &&
+              dalloc(c, &c->block_sums, (c->n_bins_max + 1023) / 1024 + 1) && dalloc(c, &c->bin_total, 1) &&
+              dalloc(c, &c->pool, c->pool_cap) && dalloc(c, &c->peaks, (size_t)max_batch * c->peak_cap) &&
+              dalloc(c, &c->peak_count, max_batch) && dalloc(c, &c->stats, 1) &&
+              dalloc(c, (unsigned char**)&c->stage_frames, (size_t)max_batch * max_H * max_W * 2) &&
+              dalloc(c, &c->stage_rings, (size_t)max_batch * c->peak_cap) && dalloc(c, &c->stage_counts, max_batch) &&
+              dalloc(c, &c->stage_offsets, max_batch);
     if (!ok) {
       cudaGetLastError();
       return fail(nullptr, RD_E_NOMEM, "device allocation failed");
@@ -464,6 +473,7 @@ static rd_status detect_enqueue(rd_ctx* c, const void* frames_dev, int n, int H,
   if (H > c->max_H || W > c->max_W || H < c->taps.R + 4 || W < c->taps.R + 4 || H < 12 || W < 12)
     return fail(c, RD_E_INVAL, "frame size outside [max(12, ceil(4 sigma) + 4), rd_create maxima]");
   if (dtype != RD_U8 && dtype != RD_U16) return fail(c, RD_E_INVAL, "dtype must be RD_U8 or RD_U16");
+  NvtxScope trace("rd_detect");
   cudaStream_t st = (cudaStream_t)stream;
   c->last_stream = st;
   c->last_n = n;
@@ -518,10 +528,12 @@ static rd_status detect_enqueue(rd_ctx* c, const void* frames_dev, int n, int H,
     sa.invD = (float)(1.0 / sa.D64);
     rl.x64 = c->e_x64;  // the records keep their exact double direction
     sa.rl = rl;
+    NvtxScope stage("rd_detect:edges");
     chk(launch_stencil(sa, dtype, st));
     mark(1);
     mark(2);
   } else {
+    NvtxScope stage("rd_detect:ridges");
     chk(launch_stencil(sa, dtype, st));
     mark(1);
     chk(launch_refine(rl, n, c->n_sm, st));
@@ -547,7 +559,10 @@ static rd_status detect_enqueue(rd_ctx* c, const void* frames_dev, int n, int H,
   ba.pool = c->pool;
   ba.pool_cap = c->pool_cap;
   ba.stats = c->stats;
-  chk(launch_bins(ba, c->n_sm, st, n_bins, c->block_sums, c->bin_total));
+  {
+    NvtxScope stage("rd_detect:bins");
+    chk(launch_bins(ba, c->n_sm, st, n_bins, c->block_sums, c->bin_total));
+  }
   mark(3);
   if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("bins: ") + cudaGetErrorString(e));
 
@@ -597,7 +612,10 @@ static rd_status detect_enqueue(rd_ctx* c, const void* frames_dev, int n, int H,
   va.queue_head = c->queue_ctr + 1;
   va.vote_grid = c->n_sm;  // times the resident CTAs per SM (launch_vote)
   va.route_dense = c->route_dense;
-  chk(launch_vote(va, n_bins, st));
+  {
+    NvtxScope stage("rd_detect:vote");
+    chk(launch_vote(va, n_bins, st));
+  }
   mark(4);
   if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("vote: ") + cudaGetErrorString(e));
 
@@ -616,7 +634,10 @@ static rd_status detect_enqueue(rd_ctx* c, const void* frames_dev, int n, int H,
   fa.w = c->p.annulus_w + (float)((1 << c->lc) - 1);
   fa.w_int = (std::floor(fa.w) == fa.w) ? 1 : 0;
   fa.stats = c->stats;
-  chk(launch_fit(fa, c->peaks, counts_dev, offsets_dev, st));
+  {
+    NvtxScope stage("rd_detect:fit");
+    chk(launch_fit(fa, c->peaks, counts_dev, offsets_dev, st));
+  }
   mark(5);
   if (e != cudaSuccess) return fail(c, RD_E_CUDA, std::string("fit: ") + cudaGetErrorString(e));
   return RD_OK;
@@ -684,6 +705,7 @@ extern "C" rd_status rd_set_graph(rd_ctx* c, int on) {
 extern "C" rd_status rd_detect_host(rd_ctx* c, const void* frames_host, int n, int H, int W, int dtype, void* stream,
                                     rd_ring* rings_host, int ring_cap, int* counts_host, int* offsets_host) {
   return rd_abi::guard(c ? &c->err : &g_create_error, [&]() -> rd_status {
+    NvtxScope trace("rd_detect_host");
     if (!c) return RD_E_INVAL;
     if (!frames_host || !counts_host || !offsets_host || (ring_cap > 0 && !rings_host) || ring_cap < 0)
       return fail(c, RD_E_INVAL, "NULL buffer or negative ring_cap");
@@ -712,6 +734,12 @@ extern "C" rd_status rd_detect_host(rd_ctx* c, const void* frames_host, int n, i
     rd_stats stats;
     return rd_get_stats(c, &stats);
   });
+}
+
+extern "C" rd_status rd_get_device_bytes(const rd_ctx* c, long long* bytes) {
+  if (!c || !bytes) return RD_E_INVAL;
+  *bytes = c->dev_bytes;
+  return RD_OK;
 }
 
 extern "C" rd_status rd_get_stats(rd_ctx* c, rd_stats* out) {
@@ -825,6 +853,7 @@ extern "C" rd_status rd_get_geometry(const rd_ctx* c, rd_geometry* out) {
 extern "C" rd_status rd_autotune(const rd_params* params, const void* frames_dev, int n, int H, int W, int dtype,
                                  void* stream, rd_geometry* best) {
   return rd_abi::guard(&g_create_error, [&]() -> rd_status {
+    NvtxScope trace("rd_autotune");
     if (!params || !frames_dev || !best || n < 1 || n > 65535)
       return fail(nullptr, RD_E_INVAL, "rd_autotune: NULL argument or n outside [1, 65535]");
     std::string v = validate(params);
@@ -899,15 +928,15 @@ static rd_status ensure_soft(rd_ctx* c) {
   const size_t px = (size_t)c->max_batch * c->max_H * c->max_W;
   const size_t rec = (size_t)c->max_batch * c->rl.cap;
   const size_t rings = (size_t)c->max_batch * c->peak_cap;
-  bool ok = dalloc(&c->s_t0, px) && dalloc(&c->s_t1, px) && dalloc(&c->s_a, px) && dalloc(&c->s_b, px) &&
-            dalloc(&c->s_c, px) && dalloc(&c->s_k, px) && dalloc(&c->s_X, px) && dalloc(&c->s_Y, px) &&
-            dalloc(&c->s_count, c->max_batch) && dalloc(&c->s_xy, rec) && dalloc(&c->s_flags, rec) &&
-            dalloc(&c->s_rk, rec) && dalloc(&c->s_rX, rec) && dalloc(&c->s_rY, rec) && dalloc(&c->s_ra, rec) &&
-            dalloc(&c->s_rb, rec) && dalloc(&c->s_rc, rec) && dalloc(&c->s_rm, rec) && dalloc(&c->s_gk, rec) &&
-            dalloc(&c->s_gX, rec) && dalloc(&c->s_gY, rec) && dalloc(&c->s_ring_off, (size_t)c->max_batch + 1) &&
-            dalloc(&c->s_score, rings) && dalloc(&c->s_dparams, 3 * rings) &&
-            dalloc(&c->s_tile_off, (size_t)c->max_batch * ((c->max_W + 31) / 32) * ((c->max_H + 31) / 32)) &&
-            dalloc(&c->s_tile_cnt, (size_t)c->max_batch * ((c->max_W + 31) / 32) * ((c->max_H + 31) / 32));
+  bool ok = dalloc(c, &c->s_t0, px) && dalloc(c, &c->s_t1, px) && dalloc(c, &c->s_a, px) && dalloc(c, &c->s_b, px) &&
+            dalloc(c, &c->s_c, px) && dalloc(c, &c->s_k, px) && dalloc(c, &c->s_X, px) && dalloc(c, &c->s_Y, px) &&
+            dalloc(c, &c->s_count, c->max_batch) && dalloc(c, &c->s_xy, rec) && dalloc(c, &c->s_flags, rec) &&
+            dalloc(c, &c->s_rk, rec) && dalloc(c, &c->s_rX, rec) && dalloc(c, &c->s_rY, rec) && dalloc(c, &c->s_ra, rec) &&
+            dalloc(c, &c->s_rb, rec) && dalloc(c, &c->s_rc, rec) && dalloc(c, &c->s_rm, rec) && dalloc(c, &c->s_gk, rec) &&
+            dalloc(c, &c->s_gX, rec) && dalloc(c, &c->s_gY, rec) && dalloc(c, &c->s_ring_off, (size_t)c->max_batch + 1) &&
+            dalloc(c, &c->s_score, rings) && dalloc(c, &c->s_dparams, 3 * rings) &&
+            dalloc(c, &c->s_tile_off, (size_t)c->max_batch * ((c->max_W + 31) / 32) * ((c->max_H + 31) / 32)) &&
+            dalloc(c, &c->s_tile_cnt, (size_t)c->max_batch * ((c->max_W + 31) / 32) * ((c->max_H + 31) / 32));
   if (!ok) {
     cudaGetLastError();
     return fail(c, RD_E_NOMEM, "soft path: device allocation failed");
@@ -982,6 +1011,7 @@ extern "C" rd_status rd_soft_score(rd_ctx* c, const void* frames_dev, int n, int
                                    const rd_ring* rings_dev, const int* counts_dev, float* score_dev,
                                    float* dparams_dev) {
   return rd_abi::guard(c ? &c->err : &g_create_error, [&]() -> rd_status {
+    NvtxScope trace("rd_soft_score");
     if (!c) return RD_E_INVAL;
     if (!score_dev) return fail(c, RD_E_INVAL, "score_dev is NULL");
     cudaStream_t st = (cudaStream_t)stream;
@@ -1000,6 +1030,7 @@ extern "C" rd_status rd_backward(rd_ctx* c, const float* frames_dev, int n, int 
                                  const rd_ring* rings_dev, const int* counts_dev, const float* dscore_dev,
                                  float* dimage_dev, float* dparams_dev) {
   return rd_abi::guard(c ? &c->err : &g_create_error, [&]() -> rd_status {
+    NvtxScope trace("rd_backward");
     if (!c) return RD_E_INVAL;
     if (!dscore_dev || !dimage_dev) return fail(c, RD_E_INVAL, "dscore_dev and dimage_dev must not be NULL");
     cudaStream_t st = (cudaStream_t)stream;
@@ -1024,6 +1055,7 @@ extern "C" rd_status rd_backward(rd_ctx* c, const float* frames_dev, int n, int 
 extern "C" rd_status rd_refine(rd_ctx* c, const void* frames_dev, int n, int H, int W, int dtype, void* stream,
                                rd_ring* rings_dev, const int* counts_dev, int iters, float step) {
   return rd_abi::guard(c ? &c->err : &g_create_error, [&]() -> rd_status {
+    NvtxScope trace("rd_refine");
     if (!c) return RD_E_INVAL;
     if (iters < 0 || !(step > 0.0f)) return fail(c, RD_E_INVAL, "iters must be >= 0 and step > 0");
     cudaStream_t st = (cudaStream_t)stream;
@@ -1055,7 +1087,7 @@ extern "C" rd_status rd_set_features(rd_ctx* c, int features, float edge_thresh)
     if (!(edge_thresh >= 0.0f) || !std::isfinite(edge_thresh)) return fail(c, RD_E_INVAL, "edge_thresh must be >= 0");
     if (features == RD_FEATURES_EDGE && !c->e_x64) {
       const size_t rec = (size_t)c->max_batch * c->rl.cap;
-      bool ok = dalloc(&c->e_x64, rec);
+      bool ok = dalloc(c, &c->e_x64, rec);
       if (!ok) {
         cudaGetLastError();
         return fail(c, RD_E_NOMEM, "edge workspaces: device allocation failed");

@@ -17,10 +17,21 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 #include <climits>
+#include <nvtx3/nvToolsExt.h>
 
 #include "rd.h"
 
 namespace rd {
+
+// Host-side NVTX range over a scope: profilers (ncu --nvtx, nsys) attribute
+// the kernels enqueued inside it to the named stage.  Without an attached
+// tool the calls return at once.
+struct NvtxScope {
+  explicit NvtxScope(const char* name) { nvtxRangePushA(name); }
+  ~NvtxScope() { nvtxRangePop(); }
+  NvtxScope(const NvtxScope&) = delete;
+  NvtxScope& operator=(const NvtxScope&) = delete;
+};
 
 constexpr int GAUSS_BITS = 19;     // Gaussian taps: integers summing to ~2^19
 constexpr int SMOOTH_BITS = 16;    // level-smoothing weights: peak 2^16
@@ -89,6 +100,7 @@ struct StencilArgs {
   DevStats* stats;
   uint32_t narrow_max;  // largest input value for which the exact Gaussian's pair sums fit u32
                         // (set by launch_stencil from the taps: 2 S narrow_max < 2^32)
+  int vec_rows;         // frames and rows start on 16-byte boundaries (set by launch_stencil)
 };
 
 struct BinArgs {

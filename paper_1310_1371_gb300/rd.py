@@ -22,6 +22,7 @@ STATUS_NAMES = ["RD_OK", "RD_E_INVAL", "RD_E_NOMEM", "RD_E_CUDA", "RD_E_OVERFLOW
 # rd_stats.overflow bits (capacities that overflowed)
 RD_OVF_RIDGE, RD_OVF_BINS, RD_OVF_PEAKS, RD_OVF_RINGS, RD_OVF_SCORE = 1, 2, 4, 8, 16
 RD_RING_FIT_FAIL = 1
+RD_SERVE_FAIL_RESULT, RD_SERVE_FAIL_SLOT = 1, 2
 PEAK_CAP = 4096   # per-frame peak capacity of a context
 
 
@@ -73,6 +74,7 @@ def load_library(build: bool = False) -> ctypes.CDLL:
         "rd_detect_host": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_int,
                                    c_void_p, c_void_p]),
         "rd_get_stats": (c_int, [c_void_p, P(rd_stats)]),
+        "rd_get_device_bytes": (c_int, [c_void_p, P(ctypes.c_longlong)]),
         "rd_destroy": (c_int, [c_void_p]),
         "rd_last_error": (ctypes.c_char_p, [c_void_p]),
         "rd_gaussian_taps": (c_int, [c_float, P(c_int32), c_int]),
@@ -99,8 +101,12 @@ def load_library(build: bool = False) -> ctypes.CDLL:
         "rd_serve_poll": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p,
                                   c_int, c_int]),
         "rd_serve_stats": (c_int, [c_void_p, c_void_p]),
+        "rd_serve_stats_ex": (c_int, [c_void_p, c_void_p, c_int]),
+        "rd_serve_debug_inject": (c_int, [c_void_p, c_int, c_int]),
         "rd_serve_destroy": (c_int, [c_void_p]),
         "rd_serve_last_error": (ctypes.c_char_p, []),
+        "rd_probe_smem_atomics": (c_int, [c_int, c_int, c_int, c_void_p, P(ctypes.c_double), P(c_float)]),
+        "rd_probe_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -162,6 +168,24 @@ def rd_autotune(params: dict, frames, stream=None) -> tuple[int, int]:
     if st != RD_OK:
         raise RdError(st, lib.rd_last_error(None).decode())
     return g.tile, g.slab_levels
+
+
+PROBE_PATTERNS = {0: "conflict-free u32", 1: "packed u16 pairs", 2: "random (vote stream)"}
+
+
+def rd_probe_smem_atomics(pattern: int, ctas_per_sm: int = 4, iters: int = 4096, stream=None) -> tuple[float, float]:
+    """Measured shared-memory atomic adds per second of the current GPU for an
+    address pattern (0 conflict-free, 1 packed-u16 pairs, 2 random), and the
+    timed launch's milliseconds."""
+    import torch
+    lib = load_library()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rate, ms = ctypes.c_double(), c_float()
+    st = lib.rd_probe_smem_atomics(pattern, ctas_per_sm, iters, c_void_p(s.cuda_stream), ctypes.byref(rate),
+                                   ctypes.byref(ms))
+    if st != RD_OK:
+        raise RdError(st, lib.rd_probe_last_error().decode())
+    return rate.value, ms.value
 
 
 RD_STATIC_MAX_PIXELS = 1 << 20
@@ -509,10 +533,22 @@ class Server:
             o += int(nr[i])
         return out
 
+    STATS_EX = ("submitted", "completed", "batches", "device_bytes", "peak_device_bytes", "slots_made",
+                "slots_destroyed", "memory_waits", "failed", "budget")
+
     def stats(self):
-        buf = np.zeros(4, np.int64)
-        self.lib.rd_serve_stats(self.ptr, buf.ctypes.data)
-        return dict(submitted=int(buf[0]), completed=int(buf[1]), batches=int(buf[2]), device_bytes=int(buf[3]))
+        buf = np.zeros(len(self.STATS_EX), np.int64)
+        n = self.lib.rd_serve_stats_ex(self.ptr, buf.ctypes.data, len(buf))
+        if n != len(buf):
+            raise RdError(RD_E_INVAL, "rd_serve_stats_ex")
+        return {k: int(v) for k, v in zip(self.STATS_EX, buf)}
+
+    def inject(self, kind: str, count: int):
+        """Make the next `count` host allocations of a kind fail ('result' or 'slot')."""
+        code = {"result": RD_SERVE_FAIL_RESULT, "slot": RD_SERVE_FAIL_SLOT}[kind]
+        st = self.lib.rd_serve_debug_inject(self.ptr, code, int(count))
+        if st != RD_OK:
+            raise RdError(st, "rd_serve_debug_inject")
 
     def close(self):
         if getattr(self, "ptr", None) is not None and self.ptr.value:
