@@ -129,15 +129,14 @@ def oracle_pool_run(frames, params, n_jobs, workers):
 
 
 def oracle_rate(frames, params, budget_s):
-    """Frames/s and Mvotes/s of the FP64 oracle on a bounded sample: one
-    frame per worker process, as many rounds as fit in about budget_s (at
-    least one)."""
+    """Frames/s and Mvotes/s of the FP64 oracle on a bounded sample: whole
+    rounds of one frame per worker process (so that no worker idles), as
+    many as fit in about budget_s seconds of wall time, at least two."""
     workers = oracle_workers()
     one = time.perf_counter()
     _oracle_frame((frames[0], params))
     per_frame = time.perf_counter() - one
-    # about budget_s of CPU work in total: whole rounds of one frame per worker
-    rounds = max(1, min(4, round(budget_s / (max(per_frame, 1e-3) * workers))))
+    rounds = max(2, min(20, round(budget_s / max(per_frame, 1e-3))))
     fps, mv, dt = oracle_pool_run(frames, params, rounds * workers, workers)
     return fps, mv, rounds * workers, dt, workers
 
@@ -150,18 +149,20 @@ def run_reference(args):
     frames = [f.image for f in synth.plain_full_batch(4)]
     params = synth.PLAIN_FULL_PARAMS
     workers = oracle_workers()
-    # each step is one frame; the pool runs the steps frame-parallel
-    oracle_pool_run(frames, params, args.warmup, workers)
-    value, mv, dt = oracle_pool_run(frames, params, args.steps, workers)
+    # each step is one round: one frame per worker process, frame-parallel
+    # (so that no worker idles in the timed region)
+    oracle_pool_run(frames, params, args.warmup * workers, workers)
+    value, mv, dt = oracle_pool_run(frames, params, args.steps * workers, workers)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "step": "one frame through the FP64 CPU oracle",
+            "data": "synthetic", "config": {"workload": WORKLOAD,
+                                            "step": f"{workers} frames through the FP64 CPU oracle, one per worker",
                                             "workers": workers},
             "mvotes_per_s": mv,
             "cpu_baseline": {"value": value, "unit": "frames/s", "cores": workers, "kind": "oracle",
-                             "sample": f"{args.steps} frames of the workload (4 distinct, cycled), one per step, "
-                                       f"{workers} worker processes"},
+                             "sample": f"{args.steps * workers} frames of the workload (4 distinct, cycled), "
+                                       f"{workers} per step, one per worker process"},
             "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -180,6 +181,10 @@ def run_ours(args):
     B = args.batch
     params = synth.PLAIN_FULL_PARAMS
     imgs = np.stack(make_frames(B, rank))
+    video_imgs = serve_pool = None
+    if rank == 0 and args.extras:   # inputs of the extra legs, rendered in spawn pools
+        video_imgs = synth.video_images(args.extra_video_frames)
+        serve_pool = synth.serve_images(args.extra_serve_pool)
     frames = torch.from_numpy(imgs).cuda()
     geo = (args.tile, args.slab) if args.tile else None  # None: the automatic geometry
     det = rd.Detector(params, H, W, B, geometry=geo)
@@ -280,23 +285,51 @@ def run_ours(args):
         if os.path.exists(tfile):
             traffic_db = json.load(open(tfile))
 
-        def traffic_for(stage, src):
+        def counter_for(stage, src, key):
             t = traffic_db.get(stage)
-            if not t or t.get("source_sha1") != src_hash[src]:
+            if not t or t.get("source_sha1") != src_hash[src] or key not in t:
                 return None          # no capture of the current kernel
-            return t["bytes_per_frame"] * B
+            return t[key] * B
 
+        def traffic_for(stage, src):
+            return counter_for(stage, src, "bytes_per_frame")
+
+        # instruction issue peak: 152 SMs x 4 schedulers x 32 lanes per clock
+        issue_peak = 152 * 128 * sm_mhz * 1e6 / 1e9   # G thread-instructions/s
         k1 = {"kernel": "stencil_ridge", "bound": "hbm", "achieved": k1_bytes / (per_launch[0] / 1e3) / 1e9,
               "peak": hbm, "unit": "GB/s", "traffic": traffic_for("stencil_ridge", "k_stencil.cu"),
               "peak_source": hbm_src}
         k1["frac"] = k1["achieved"] / hbm
+        k1_instr = counter_for("stencil_ridge", "k_stencil.cu", "thread_instructions_per_frame")
+        k1["issue"] = None if k1_instr is None else {
+            "achieved": k1_instr / (per_launch[0] / 1e3) / 1e9, "peak": issue_peak, "unit": "G thread-instr/s",
+            "frac": k1_instr / (per_launch[0] / 1e3) / 1e9 / issue_peak,
+            "instructions_per_pixel": k1_instr / (B * H * W),
+            "source": "ncu smsp__thread_inst_executed.sum of the current kernel source (profiles/dram_traffic.json)",
+            "peak_source": f"152 SMs x 4 schedulers x 32 lanes x {sm_mhz:.0f} MHz"}
         k4 = {"kernel": "vote_accumulate_peaks", "bound": "alu", "achieved": k4_ops / (per_launch[3] / 1e3) / 1e9,
               "peak": int_peak, "unit": "Gop/s", "traffic": traffic_for("vote_accumulate_peaks", "k_vote.cu"),
               "ops_per_launch": int(k4_ops),
               "peak_source": f"152 SMs x 64 INT32 lanes x {sm_mhz:.0f} MHz (recipe unit counts and max clock)"}
         k4["frac"] = k4["achieved"] / int_peak
-        roofline = k4 if dom == 3 else (k1 if dom == 0 else k4)
-        other = k1 if roofline is k4 else k4
+        # shared-memory atomic adds: the unit that accumulates the votes, peak measured now on this GPU
+        probe = {}
+        for pat, name in rd.PROBE_PATTERNS.items():
+            rate, _ = rd.rd_probe_smem_atomics(pat, 4, 8192)
+            probe[name] = rate / 1e9
+        atom_peak = probe[rd.PROBE_PATTERNS[0]]
+        k4_atom = {"kernel": "vote_accumulate_peaks", "bound": "smem_atomic",
+                   "achieved": stats.votes / (per_launch[3] / 1e3) / 1e9, "peak": atom_peak,
+                   "unit": "G atomic adds/s", "traffic": traffic_for("vote_accumulate_peaks", "k_vote.cu"),
+                   "atomics_per_launch": int(stats.votes),
+                   "peak_source": "measured in this run: rd_probe_smem_atomics, conflict-free u32 adds",
+                   "measured_peaks": probe}
+        k4_atom["frac"] = k4_atom["achieved"] / atom_peak
+        k4_atom["frac_of_vote_stream_peak"] = k4_atom["achieved"] / probe[rd.PROBE_PATTERNS[2]]
+        if dom == 0:
+            roofline, other = k1, k4_atom
+        else:
+            roofline, other = k4_atom, k1
         # ---- CPU baseline (oracle, bounded sample)
         cpu_fps, cpu_mv, ndone, cpu_dt, cpu_cores = oracle_rate(imgs[: max(1, args.cpu_frames)], params,
                                                                args.cpu_budget)
@@ -315,6 +348,7 @@ def run_ours(args):
             "stage_ms_per_step": {s: round(float(v), 4) for s, v in zip(STAGES, per_launch)},
             "roofline": roofline,
             "roofline_other": other,
+            "roofline_alu": k4,
             "cpu_baseline": {"value": cpu_fps, "unit": "frames/s", "cores": cpu_cores, "kind": "oracle",
                              "sample": f"{ndone} frames of the workload in {cpu_dt:.1f} s, one per worker process",
                              "mvotes_per_s": cpu_mv},
@@ -324,8 +358,16 @@ def run_ours(args):
             "gpu_launches": KERNELS_PER_CALL * args.steps,
             "clocks": clocks,
         }
-        print(json.dumps(line), flush=True)
     det.close()
+    if rank == 0:
+        if args.extras:
+            # the metric's other parts, bounded: batched vs plain on a video
+            # subset, and a Poisson request stream through the server
+            line["batched_vs_plain"] = measure_video(args.extra_video_frames, args.extra_video_batch, 3,
+                                                     video_imgs)
+            line["serve"] = measure_serve(args.extra_serve_requests, args.serve_rate, serve_pool,
+                                          args.extra_serve_pool, args.serve_budget_gb)
+        print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 
@@ -334,19 +376,18 @@ def run_ours(args):
 VIDEO_METRIC = "frames/s, drifting-track video of 1024x1024 u8 frames (20-300 rings, r 5-40): batched graph path"
 
 
-def run_video(args):
+def measure_video(n, B, warmup, imgs=None):
     """The batched path (autotuned geometry, persistent voting, one CUDA-graph
-    replay per chunk of frames) against the plain per-frame path (one
-    rd_detect per frame) on the same resident video, with the results of both
-    compared frame by frame."""
+    replay per chunk of B frames) against the plain per-frame path (one
+    rd_detect per frame) on the same resident n-frame video, with the results
+    of both compared frame by frame (untimed).  Returns a dict."""
     from paper_1310_1371_gb300 import synth
-    n, B = args.video_frames, args.video_batch
     if n % B:
-        raise SystemExit("--video-frames must be a multiple of --video-batch")
-    imgs = synth.video_images(n)  # spawn pool, before any CUDA call
+        raise SystemExit("video frames must be a multiple of the video batch")
+    if imgs is None:
+        imgs = synth.video_images(n)  # spawn pool
     import torch
     from paper_1310_1371_gb300 import rd
-    torch.cuda.set_device(0)
     params = synth.VIDEO_PARAMS
     vid = torch.from_numpy(imgs).cuda()
     stream = torch.cuda.Stream()
@@ -380,12 +421,12 @@ def run_video(args):
                 plain.detect_async(vid[i:i + 1], stream)
         return out
 
-    for _ in range(args.warmup):  # the first pass captures the graph
+    for _ in range(warmup):  # the first pass captures the graph
         batched_pass()
-    for i in range(max(3, args.warmup)):
+    for i in range(max(3, warmup)):
         plain.detect_async(vid[i:i + 1], stream)
     torch.cuda.synchronize()
-    sampler = ClockSampler(0)
+    sampler = ClockSampler(torch.cuda.current_device())
     time.sleep(0.3)
     ev0.record(stream)
     batched_pass()
@@ -398,25 +439,39 @@ def run_video(args):
     torch.cuda.synchronize()
     ms_p = ev0.elapsed_time(ev1)
     clocks = sampler.stop()
-    # results of both paths, frame by frame (untimed)
     rb, votes = batched_pass(collect=True)
     rp = plain_pass(collect=True)
     fields = ("ix", "iy", "ir", "cx", "cy", "r", "score", "n_fit", "flags")
     identical = len(rb) == len(rp) == n and all(
         len(a) == len(b) and all(np.array_equal(a[k], b[k]) for k in fields) for a, b in zip(rb, rp))
-    line = {"metric": VIDEO_METRIC, "value": n / (ms_b / 1e3), "unit": "frames/s", "n_gpus": 1, "steps": 1,
-            "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "u8", "data": "synthetic",
-            "config": {"workload": f"video: {n} frames 1024x1024 u8, 20-300 drifting rings r 8-30, search r 5-40",
-                       "batch_frames": B, "geometry": list(geo), "graph": True,
-                       "l2": f"inputs ({imgs.nbytes / 2**20:.0f} MiB) larger than L2; no flush"},
-            "plain_per_frame": {"value": n / (ms_p / 1e3), "unit": "frames/s", "ms_total": ms_p},
-            "speedup_vs_plain": ms_p / ms_b, "identical_results": bool(identical),
-            "rings_total": int(sum(len(r) for r in rb)), "mvotes_per_s": votes / (ms_b / 1e3) / 1e6,
-            "gpu_launches": (n // B) * KERNELS_PER_CALL, "clocks": clocks}
-    print(json.dumps(line))
     batched.close()
     plain.close()
+    return {"batched_frames_per_s": n / (ms_b / 1e3), "plain_frames_per_s": n / (ms_p / 1e3),
+            "ms_batched": ms_b, "ms_plain": ms_p, "speedup_vs_plain": ms_p / ms_b,
+            "identical_results": bool(identical), "frames": n, "batch_frames": B, "geometry": list(geo),
+            "rings_total": int(sum(len(r) for r in rb)), "mvotes_per_s": votes / (ms_b / 1e3) / 1e6,
+            "bytes": int(imgs.nbytes), "clocks": clocks}
+
+
+def run_video(args):
+    """--workload video: the whole drifting-track video, batched vs plain."""
+    from paper_1310_1371_gb300 import synth
+    n, B = args.video_frames, args.video_batch
+    imgs = synth.video_images(n)  # spawn pool, before any CUDA call
+    import torch
+    torch.cuda.set_device(0)
+    v = measure_video(n, B, args.warmup, imgs)
+    line = {"metric": VIDEO_METRIC, "value": v["batched_frames_per_s"], "unit": "frames/s", "n_gpus": 1, "steps": 1,
+            "warmup": args.warmup, "ms_per_step": v["ms_batched"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": f"video: {n} frames 1024x1024 u8, 20-300 drifting rings r 8-30, search r 5-40",
+                       "batch_frames": B, "geometry": v["geometry"], "graph": True,
+                       "l2": f"inputs ({v['bytes'] / 2**20:.0f} MiB) larger than L2; no flush"},
+            "plain_per_frame": {"value": v["plain_frames_per_s"], "unit": "frames/s", "ms_total": v["ms_plain"]},
+            "speedup_vs_plain": v["speedup_vs_plain"], "identical_results": v["identical_results"],
+            "rings_total": v["rings_total"], "mvotes_per_s": v["mvotes_per_s"],
+            "gpu_launches": (n // B) * KERNELS_PER_CALL, "clocks": v["clocks"]}
+    print(json.dumps(line))
 
 
 # ------------------------------------------------------------------ differentiable soft score
@@ -530,30 +585,30 @@ def run_diff(args):
 SERVE_METRIC = "p50/p99 latency and frames/s, Poisson stream of single-frame requests (256^2-2048^2 u16)"
 
 
-def run_serve(args):
-    """A Poisson stream of single-frame requests (sizes uniform over
-    256^2 .. 2048^2, u16, 10-400 rings) through the continuous-batching
-    server; latency from submission to results on the host."""
+SERVE_SIZES = (256, 512, 1024, 2048)
+
+
+def measure_serve(n, rate, pool, pool_per_class, budget_gb):
+    """A Poisson stream of n single-frame requests at `rate`/s (sizes uniform
+    over 256^2 .. 2048^2, u16, 10-400 rings) through the continuous-batching
+    server; latency from submission to results on the host.  `pool` holds
+    the frames of each size class.  Returns a dict."""
     import threading
-    from paper_1310_1371_gb300 import synth
-    sizes = (256, 512, 1024, 2048)
-    pool = synth.serve_images(args.serve_pool)  # spawn pool, before any CUDA call
+    from paper_1310_1371_gb300 import rd, synth
     import torch
-    from paper_1310_1371_gb300 import rd
-    torch.cuda.set_device(0)
+    sizes = SERVE_SIZES
     batch = {256: 16, 512: 8, 1024: 4, 2048: 2}
     classes = [dict(params=synth.SERVE_CLASSES[s], H=s, W=s, dtype="u16", max_batch=batch[s], slots=2) for s in sizes]
-    server = rd.Server(classes, mem_budget=int(args.serve_budget_gb * 2**30), queue_cap=8192)
+    server = rd.Server(classes, mem_budget=int(budget_gb * 2**30), queue_cap=8192)
     for c, s in enumerate(sizes):  # warm-up: one request per class
         server.submit(c, pool[s][0], -1 - c)
     got = 0
     while got < len(sizes):
         got += len(server.poll(wait_ms=100))
-    n, rate = args.serve_requests, args.serve_rate
     rng = np.random.default_rng(1005)
     arrive = np.cumsum(rng.exponential(1.0 / rate, size=n))
     cls = rng.integers(0, len(sizes), size=n)
-    idx = rng.integers(0, args.serve_pool, size=n)
+    idx = rng.integers(0, pool_per_class, size=n)
     lat = np.zeros(n)
     status = np.zeros(n, dtype=np.int32)
     t_done = [0.0]
@@ -568,7 +623,7 @@ def run_serve(args):
             t_done[0] = time.perf_counter()
 
     th = threading.Thread(target=collect)
-    sampler = ClockSampler(0)
+    sampler = ClockSampler(torch.cuda.current_device())
     th.start()
     t0 = time.perf_counter()
     busy = 0
@@ -587,19 +642,34 @@ def run_serve(args):
     ms = lat / 1e3
     per = {f"{s}x{s}": {"requests": int((cls == c).sum()), "p50_ms": float(np.percentile(ms[cls == c], 50)),
                         "p99_ms": float(np.percentile(ms[cls == c], 99))} for c, s in enumerate(sizes)}
-    line = {"metric": SERVE_METRIC, "value": float(np.percentile(ms, 99)), "unit": "ms (p99 latency)",
-            "higher_is_better": False, "n_gpus": 1, "steps": n, "warmup": len(sizes),
-            "ms_per_step": wall * 1e3 / n, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
+    return {"requests": n, "offered_per_s": rate, "p50_ms": float(np.percentile(ms, 50)),
+            "p99_ms": float(np.percentile(ms, 99)), "frames_per_s": n / wall, "wall_s": wall, "per_class": per,
+            "batches": stats["batches"] - len(sizes), "device_bytes": stats["device_bytes"],
+            "errors": int((status != 0).sum()), "submit_retries_busy": busy, "max_batch": batch,
+            "slots_per_class": 2, "mem_budget_gb": budget_gb, "frames_per_class_pool": pool_per_class,
+            "clocks": clocks}
+
+
+def run_serve(args):
+    """--workload serve: the request stream, its latency percentiles."""
+    from paper_1310_1371_gb300 import synth
+    pool = synth.serve_images(args.serve_pool)  # spawn pool, before any CUDA call
+    import torch
+    torch.cuda.set_device(0)
+    n, rate = args.serve_requests, args.serve_rate
+    v = measure_serve(n, rate, pool, args.serve_pool, args.serve_budget_gb)
+    line = {"metric": SERVE_METRIC, "value": v["p99_ms"], "unit": "ms (p99 latency)",
+            "higher_is_better": False, "n_gpus": 1, "steps": n, "warmup": len(SERVE_SIZES),
+            "ms_per_step": v["wall_s"] * 1e3 / n, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
             "data": "synthetic",
             "config": {"workload": f"serve: {n} requests, Poisson {rate}/s, sizes uniform over 256..2048 squared, "
                                    f"10-400 rings, r ranges 5-20 / 5-40 / 8-96 / 8-160",
-                       "frames_per_class_pool": args.serve_pool, "max_batch": batch, "slots_per_class": 2,
+                       "frames_per_class_pool": args.serve_pool, "max_batch": v["max_batch"], "slots_per_class": 2,
                        "mem_budget_gb": args.serve_budget_gb},
-            "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
-            "frames_per_s": n / wall, "offered_per_s": rate, "per_class": per,
-            "batches": stats["batches"] - len(sizes), "device_bytes": stats["device_bytes"],
-            "errors": int((status != 0).sum()), "submit_retries_busy": busy,
-            "gpu_launches": KERNELS_PER_CALL * (stats["batches"] - len(sizes)), "clocks": clocks}
+            "p50_ms": v["p50_ms"], "p99_ms": v["p99_ms"], "frames_per_s": v["frames_per_s"], "offered_per_s": rate,
+            "per_class": v["per_class"], "batches": v["batches"], "device_bytes": v["device_bytes"],
+            "errors": v["errors"], "submit_retries_busy": v["submit_retries_busy"],
+            "gpu_launches": KERNELS_PER_CALL * v["batches"], "clocks": v["clocks"]}
     print(json.dumps(line))
 
 
@@ -773,6 +843,12 @@ def main():
     ap.add_argument("--diff-frames", type=int, default=256)
     ap.add_argument("--video-frames", type=int, default=2000)
     ap.add_argument("--video-batch", type=int, default=200)
+    ap.add_argument("--extras", type=int, default=1,
+                    help="default workload: add the batched-vs-plain and serving legs to the line (rank 0)")
+    ap.add_argument("--extra-video-frames", type=int, default=200)
+    ap.add_argument("--extra-video-batch", type=int, default=100)
+    ap.add_argument("--extra-serve-requests", type=int, default=1000)
+    ap.add_argument("--extra-serve-pool", type=int, default=4)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -18,7 +18,8 @@ CSRC = os.path.join(PKG, "csrc")
 OBJ = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "librd.so")
-SOURCES = ["rd_api.cu", "k_stencil.cu", "k_vote.cu", "k_fit.cu", "k_soft.cu", "rd_serve.cu", "rd_static.cu"]
+SOURCES = ["rd_api.cu", "k_stencil.cu", "k_vote.cu", "k_fit.cu", "k_soft.cu", "rd_serve.cu", "rd_static.cu",
+           "rd_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
                      "-Xcompiler", "-fPIC,-ffp-contract=off,-O2", "-I" + os.path.join(ROOT, "include")]

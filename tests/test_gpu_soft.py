@@ -63,6 +63,39 @@ def test_scores_and_gradients_match_oracle(torch):
     det.close()
 
 
+def test_full_size_frame_matches_oracle(torch):
+    """The differentiable workload at full size: one 512 x 512 f32 frame with
+    64 rings (jittered by up to 0.3 px).  All 64 rings go through the GPU
+    calls, so the tile-visit cut-off and the FP64 atomics of many
+    overlapping rings run at scale; the FP64 autograd oracle covers 16 of
+    them (every fourth).  Scores and ring gradients are compared for those
+    16, and the image gradient of a backward whose dscore is 0 for the other
+    48 rings is compared with the oracle's image gradient of the 16."""
+    from paper_1310_1371_gb300 import rd
+    fr = synth.diff_frame(0)
+    img = fr.image[None].astype(np.float32)
+    rng = np.random.default_rng(4004)
+    params = (fr.rings + rng.uniform(-0.3, 0.3, fr.rings.shape)).astype(np.float32)
+    n_r = len(params)
+    assert img.shape == (1, 512, 512) and n_r == 64
+    sel = np.arange(0, n_r, 4)
+    w = np.zeros(n_r, np.float32)
+    w[sel] = rng.uniform(0.5, 2.0, len(sel)).astype(np.float32)
+    det = rd.Detector(PARAMS, 512, 512, 1)
+    frames, counts, flat, rings = gpu_inputs(torch, rd, img, [params])
+    sc, dp = det.soft_score(frames, rings, counts, with_grad=True)
+    dimg, _ = det.backward(frames, rings, counts, torch.from_numpy(w).cuda())
+    sc, dp, dimg = (t.cpu().numpy() for t in (sc, dp, dimg))
+    pr = params[sel].astype(np.float64)
+    s1, _, g1, _ = S.soft_grads(img[0], pr, SP)
+    _, gimg, _, _ = S.soft_grads(img[0], pr, SP, dscore=w[sel].astype(np.float64))
+    assert np.allclose(sc[sel], s1, rtol=1e-5, atol=1e-6), np.abs(sc[sel] - s1).max()
+    assert np.abs(dp[sel] - g1).max() <= 1e-4 * np.abs(g1).max()
+    assert np.abs(dimg[0] - gimg).max() <= 1e-4 * np.abs(gimg).max()
+    assert np.abs(gimg).max() > 0 and np.all(s1 > 1.0)
+    det.close()
+
+
 def kink_free(rd_o, cx, cy, rho, h=1e-3, gmin=1e-8):
     """No vote with a non-negligible Gaussian factor lies within h of a grid line."""
     sig = SP.sig_a * rho + SP.sig_b
