@@ -113,25 +113,46 @@ __device__ __forceinline__ void grad32(const float* Rs, const float* Rd1, int st
 struct StencilSmem {
   unsigned l, x, f, k, scan, total;
 };
-// Row strides of the input tile and of the horizontal pass are odd, so that
-// the lanes of a warp, which take consecutive rows there, hit distinct banks.
-__host__ __device__ __forceinline__ int odd_stride(int w) { return w | 1; }
+// The input tile is stored as u16 from column x0 - ORG, ORG = HALO rounded
+// up to 16 pixels, so that interior tiles fill whole rows with aligned
+// 16-byte copies; its row stride is a multiple of 8 elements (16 bytes).
+// The horizontal pass's row stride is even, so that a thread's two outputs
+// go out as one 8-byte store.
+constexpr __host__ __device__ int in_org(int halo) { return (halo + 15) & ~15; }
+constexpr __host__ __device__ int in_stride(int halo) { return ST_TW + 2 * in_org(halo) + 8; }
+constexpr int P_STRIDE = ST_TW + 8;  // >= ST_TW + 6 outputs, even
 
 __host__ __device__ __forceinline__ StencilSmem stencil_smem_layout(int R) {
   const int HALO = R + 3;
-  const unsigned IW = odd_stride(ST_TW + 2 * HALO), IH = ST_TH + 2 * HALO;
-  const unsigned PW = ST_TW + 6, PWs = odd_stride(ST_TW + 6), LH = ST_TH + 6;
+  const unsigned IW = in_stride(HALO), IH = ST_TH + 2 * HALO;
+  const unsigned PW = ST_TW + 6, LH = ST_TH + 6;
   const unsigned HW2 = ST_TW + 2, HH2 = ST_TH + 2;
-  const unsigned in_bytes = (IH * IW + IH * PWs) * 4, rf_bytes = 3 * LH * HW2 * 4;
+  // the horizontal pass has two spare rows that the vertical pass's last
+  // window may read (their outputs are not stored)
+  const unsigned in_bytes = ((IH * IW * 2 + 15) & ~15u) + (IH + 2) * P_STRIDE * 4, rf_bytes = 3 * LH * HW2 * 4;
   const unsigned lf_bytes = LH * PW * 4, list_bytes = ST_TW * ST_TH * (1 + 2 + 2);
   StencilSmem L;
   L.l = 0;
   L.x = LH * PW * 8;
-  L.f = L.x + (((in_bytes > rf_bytes ? in_bytes : rf_bytes) + 7) & ~7u);
-  L.k = L.f + (((lf_bytes > list_bytes ? lf_bytes : list_bytes) + 7) & ~7u);
+  L.f = L.x + (((in_bytes > rf_bytes ? in_bytes : rf_bytes) + 15) & ~15u);
+  L.k = L.f + (((lf_bytes > list_bytes ? lf_bytes : list_bytes) + 15) & ~15u);
   L.scan = L.k + 2 * HH2 * HW2 * 4;
   L.total = L.scan + (ST_THREADS / 32 + 1) * 4;
   return L;
+}
+
+// Widen 16 bytes of u8 pixels to 16 u16 (two 16-byte halves).
+__device__ __forceinline__ void widen_u8(uint4 q, uint4& lo, uint4& hi) {
+  lo = make_uint4(__byte_perm(q.x, 0u, 0x4140), __byte_perm(q.x, 0u, 0x4342), __byte_perm(q.y, 0u, 0x4140),
+                  __byte_perm(q.y, 0u, 0x4342));
+  hi = make_uint4(__byte_perm(q.z, 0u, 0x4140), __byte_perm(q.z, 0u, 0x4342), __byte_perm(q.w, 0u, 0x4140),
+                  __byte_perm(q.w, 0u, 0x4342));
+}
+
+// Largest of the eight u16 in a 16-byte vector.
+__device__ __forceinline__ uint32_t max_u16x8(uint4 q) {
+  const uint32_t m = __vmaxu2(__vmaxu2(q.x, q.y), __vmaxu2(q.z, q.w));
+  return max(m & 0xffffu, m >> 16);
 }
 
 // RC > 0: the Gaussian half-width R is the compile-time RC (taps unrolled,
@@ -144,8 +165,8 @@ __global__ void __launch_bounds__(ST_THREADS, 1024 / ST_THREADS) k_stencil_ridge
   const int tid = threadIdx.x;
   const int R = RC > 0 ? RC : a.taps.R;
   const int HALO = R + 3;
-  const int IW = odd_stride(ST_TW + 2 * HALO), IH = ST_TH + 2 * HALO;
-  const int PW = ST_TW + 6, PWs = odd_stride(ST_TW + 6), LH = ST_TH + 6;
+  const int IW = in_stride(HALO), IH = ST_TH + 2 * HALO, ORG = in_org(HALO);
+  const int PW = ST_TW + 6, PWs = P_STRIDE, LH = ST_TH + 6;
   const int HW2 = ST_TW + 2, HH2 = ST_TH + 2;
   const int H = a.H, W = a.W;
 
@@ -156,8 +177,8 @@ __global__ void __launch_bounds__(ST_THREADS, 1024 / ST_THREADS) k_stencil_ridge
   // pixel lists.
   const StencilSmem Ls = stencil_smem_layout(R);
   unsigned long long* sL = reinterpret_cast<unsigned long long*>(smem + Ls.l);  // LH*PW
-  uint32_t* sI = reinterpret_cast<uint32_t*>(smem + Ls.x);                     // IH*IW
-  uint32_t* sP = sI + IH * IW;                                                 // IH*PWs
+  uint16_t* sI = reinterpret_cast<uint16_t*>(smem + Ls.x);                     // IH*IW, from column x0 - ORG
+  uint32_t* sP = reinterpret_cast<uint32_t*>(smem + Ls.x + ((IH * IW * 2 + 15) & ~15));  // IH*PWs
   float* sRs = reinterpret_cast<float*>(smem + Ls.x);                          // LH*HW2 each
   float* sRd2 = sRs + LH * HW2;
   float* sRd1 = sRd2 + LH * HW2;
@@ -171,24 +192,63 @@ __global__ void __launch_bounds__(ST_THREADS, 1024 / ST_THREADS) k_stencil_ridge
   __shared__ int32_t q[2 * MAX_RG + 1];
   __shared__ unsigned s_lmax;  // bits of the largest rounded L of the tile (all >= 0)
   __shared__ int s_nu;
+  __shared__ unsigned s_imax;  // largest input value of the tile and its halo
+  __shared__ int s_ncand;      // pixels listed for the direction test
 
   if (tid < 2 * R + 1) q[tid] = a.taps.q[tid];
   if (tid == 0) {
     s_lmax = 0u;
     s_nu = 0;
+    s_imax = 0u;
+    s_ncand = 0;
   }
 
   const int f = blockIdx.z;
   const int x0 = blockIdx.x * ST_TW, y0 = blockIdx.y * ST_TH;
   const Tin* img = reinterpret_cast<const Tin*>(a.frames) + (size_t)f * H * W;
 
-  // ---- A: input tile with reflect-101 halo, one row per warp step (only
-  //      tiles that reach past a border reflect)
+  // ---- A: input tile with reflect-101 halo.  Interior tiles of frames
+  //      whose rows are 16-byte aligned copy the aligned span [x0 - ORG,
+  //      x0 + ST_TW + ORG) of each row with 16-byte loads; other tiles load
+  //      pixel by pixel, reflecting at the borders, one row per warp step.
   {
     const int lane = tid & 31, warp = tid >> 5;
     const bool interior = x0 >= HALO && y0 >= HALO && x0 + ST_TW + HALO <= W && y0 + ST_TH + HALO <= H;
-    const int IWn = ST_TW + 2 * HALO;  // columns loaded (IW is the padded stride)
-    if constexpr (RC > 0) {
+    const bool vec = a.vec_rows && y0 >= HALO && y0 + ST_TH + HALO <= H && x0 >= ORG && x0 + ST_TW + ORG <= W;
+    const int IWn = ST_TW + 2 * HALO;  // columns used
+    const int coff = ORG - HALO;       // column of x0 - HALO in the tile
+    uint32_t vmax = 0u;
+    if (vec) {
+      constexpr int VEC = 16 / (int)sizeof(Tin);  // pixels per 16-byte load
+      const int NV = (ST_TW + 2 * ORG) / VEC;     // loads per row
+      constexpr int NIT = 3;                      // loads per thread in flight (>= 54 rows x 8 / 256)
+      for (int base = 0; base < IH * NV; base += NIT * ST_THREADS) {
+        uint4 q[NIT];
+#pragma unroll
+        for (int u = 0; u < NIT; ++u) {
+          const int it = min(base + u * ST_THREADS + tid, IH * NV - 1);
+          const int iy = it / NV, v = it - iy * NV;
+          const Tin* src = img + (size_t)(y0 - HALO + iy) * W + (x0 - ORG) + v * VEC;
+          q[u] = __ldg(reinterpret_cast<const uint4*>(src));
+        }
+#pragma unroll
+        for (int u = 0; u < NIT; ++u) {
+          const int it = base + u * ST_THREADS + tid;
+          if (it >= IH * NV) continue;
+          const int iy = it / NV, v = it - iy * NV;
+          uint16_t* dst = sI + iy * IW + v * VEC;
+          if constexpr (sizeof(Tin) == 1) {
+            uint4 lo, hi;
+            widen_u8(q[u], lo, hi);
+            reinterpret_cast<uint4*>(dst)[0] = lo;
+            reinterpret_cast<uint4*>(dst)[1] = hi;
+          } else {
+            reinterpret_cast<uint4*>(dst)[0] = q[u];
+            vmax = max(vmax, max_u16x8(q[u]));
+          }
+        }
+      }
+    } else if constexpr (RC > 0) {
       // all of a thread's loads are issued before its first store, so that
       // their latencies overlap
       constexpr int IHc = ST_TH + 2 * (RC + 3), IWc = ST_TW + 2 * (RC + 3);
@@ -214,49 +274,73 @@ __global__ void __launch_bounds__(ST_THREADS, 1024 / ST_THREADS) k_stencil_ridge
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           const int ix = lane + 32 * c;
-          if (iy < IHc && ix < IWc) sI[iy * IW + ix] = v[k][c];
+          if (iy < IHc && ix < IWc) sI[iy * IW + coff + ix] = (uint16_t)v[k][c];
+          vmax = max(vmax, v[k][c]);
         }
       }
     } else {
       for (int iy = warp; iy < IH; iy += ST_THREADS / 32) {
         const int gy = interior ? y0 - HALO + iy : reflect101(y0 - HALO + iy, H);
         const Tin* row = img + (size_t)gy * W;
-        uint32_t* dst = sI + iy * IW;
+        uint16_t* dst = sI + iy * IW + coff;
         for (int ix = lane; ix < IWn; ix += 32) {
           const int gx = interior ? x0 - HALO + ix : reflect101(x0 - HALO + ix, W);
-          dst[ix] = (uint32_t)row[gx];
+          dst[ix] = (uint16_t)row[gx];
+          vmax = max(vmax, (uint32_t)row[gx]);
         }
       }
+    }
+    if (sizeof(Tin) > 1) {
+      vmax = __reduce_max_sync(0xffffffffu, vmax);
+      if (lane == 0) atomicMax(&s_imax, vmax);
     }
   }
   __syncthreads();
 
+  // Exact smoothing, L' = sum_i sum_j Q_i Q_j I, in u32 / u64.  A tile whose
+  // inputs all lie in [0, narrow_max] keeps every horizontal sum below 2^31
+  // and every vertical pair of them below 2^32.  A wider tile (16-bit data
+  // above that) is smoothed twice, once for the high byte and once for the
+  // low byte of each input, and L' = 2^8 L'(high) + L'(low); each part's sums
+  // then stay below 2^28.
+  const bool wide = sizeof(Tin) > 1 && s_imax > a.narrow_max;
+  float lmax = 0.0f;
+  for (int part = wide ? 0 : 2; part < (wide ? 2 : 3); ++part) {
+  // part 0: high bytes, 1: low bytes, 2: the inputs themselves; the last
+  // part rounds L' to FP32
+  const uint32_t shift = part == 0 ? 8u : 0u, mask = part == 1 ? 0xffu : 0xffffffffu;
+  const bool last = part != 0;
+  if (part == 1) __syncthreads();  // the high part's vertical pass has read sP
+
   // ---- B: horizontal Gaussian, exact u32 (sum Q_i I < 2^31)
   if constexpr (RC > 0) {
-    // two adjacent outputs per thread from 2R + 2 inputs; lanes take rows
+    // two adjacent outputs per thread from 2R + 2 inputs; the lanes of a warp
+    // take neighbouring output pairs of a row (distinct banks)
     constexpr int NW = 2 * RC + 2;
-    const int NP = PW / 2;
+    constexpr int NP = (ST_TW + 6) / 2;
+    constexpr int CO = in_org(RC + 3) - (RC + 3);
     for (int i = tid; i < IH * NP; i += ST_THREADS) {
-      const int pp = i / IH, iy = i - pp * IH;
-      const uint32_t* row = sI + iy * IW + 2 * pp;
+      const int iy = i / NP, pp = i - iy * NP;
+      const uint16_t* row = sI + iy * IW + CO + 2 * pp;
       uint32_t w[NW];
 #pragma unroll
-      for (int k = 0; k < NW; ++k) w[k] = row[k];
+      for (int k = 0; k < NW; ++k) w[k] = ((uint32_t)row[k] >> shift) & mask;
       uint32_t acc0 = (uint32_t)a.taps.q[RC] * w[RC], acc1 = (uint32_t)a.taps.q[RC] * w[RC + 1];
 #pragma unroll
       for (int j = 0; j < RC; ++j) {
         acc0 += (uint32_t)a.taps.q[j] * (w[j] + w[2 * RC - j]);
         acc1 += (uint32_t)a.taps.q[j] * (w[j + 1] + w[2 * RC + 1 - j]);
       }
-      sP[iy * PWs + 2 * pp] = acc0;
-      sP[iy * PWs + 2 * pp + 1] = acc1;
+      *reinterpret_cast<uint2*>(sP + iy * PWs + 2 * pp) = make_uint2(acc0, acc1);
     }
   } else {
+    const int coff = ORG - HALO;
     for (int i = tid; i < IH * PW; i += ST_THREADS) {
       int iy = i / PW, px = i - iy * PW;
-      const uint32_t* row = sI + iy * IW + px;
-      uint32_t acc = (uint32_t)q[R] * row[R];
-      for (int j = 0; j < R; ++j) acc += (uint32_t)q[j] * (row[j] + row[2 * R - j]);
+      const uint16_t* row = sI + iy * IW + coff + px;
+      uint32_t acc = (uint32_t)q[R] * (((uint32_t)row[R] >> shift) & mask);
+      for (int j = 0; j < R; ++j)
+        acc += (uint32_t)q[j] * ((((uint32_t)row[j] >> shift) & mask) + (((uint32_t)row[2 * R - j] >> shift) & mask));
       sP[iy * PWs + px] = acc;
     }
   }
@@ -265,30 +349,37 @@ __global__ void __launch_bounds__(ST_THREADS, 1024 / ST_THREADS) k_stencil_ridge
   // ---- C: vertical Gaussian, exact u64: L' = sum_i sum_j Q_i Q_j I
   //      (a pair Q_j (P_j + P_2R-j) of horizontal sums stays below 2^32);
   //      also L' rounded to FP32 and the tile's largest value of it
-  float lmax = 0.0f;
   if constexpr (RC > 0) {
-    // two vertically adjacent outputs per thread; lanes take columns
-    constexpr int NW = 2 * RC + 2;
-    const int NL = LH / 2;
-    for (int i = tid; i < NL * PW; i += ST_THREADS) {
-      const int lp = i / PW, px = i - lp * PW;
-      const uint32_t* col = sP + (2 * lp) * PWs + px;
+    // three vertically adjacent outputs per thread from one window of 2R + 3
+    // horizontal sums; lanes take columns.  The last run's third row is past
+    // the tile: its window reads one row beyond the horizontal pass (the
+    // buffer has that row), and it is not stored.
+    constexpr int RUN = 3, NW = 2 * RC + RUN;
+    constexpr int NRUN = (ST_TH + 6 + RUN - 1) / RUN;
+    for (int i = tid; i < NRUN * PW; i += ST_THREADS) {
+      const int lr = i / PW, px = i - lr * PW;
+      const int ly0 = RUN * lr;
+      const uint32_t* col = sP + ly0 * PWs + px;
       uint32_t w[NW];
 #pragma unroll
       for (int k = 0; k < NW; ++k) w[k] = col[k * PWs];
-      unsigned long long acc0 = (unsigned long long)(uint32_t)a.taps.q[RC] * w[RC];
-      unsigned long long acc1 = (unsigned long long)(uint32_t)a.taps.q[RC] * w[RC + 1];
 #pragma unroll
-      for (int j = 0; j < RC; ++j) {
-        acc0 += (unsigned long long)(uint32_t)a.taps.q[j] * (unsigned long long)(w[j] + w[2 * RC - j]);
-        acc1 += (unsigned long long)(uint32_t)a.taps.q[j] * (unsigned long long)(w[j + 1] + w[2 * RC + 1 - j]);
+      for (int o = 0; o < RUN; ++o) {
+        unsigned long long acc = (unsigned long long)(uint32_t)a.taps.q[RC] * w[RC + o];
+#pragma unroll
+        for (int j = 0; j < RC; ++j)
+          acc += (unsigned long long)(uint32_t)a.taps.q[j] * (unsigned long long)(w[j + o] + w[2 * RC - j + o]);
+        if (ly0 + o < LH) {
+          const int idx = (ly0 + o) * PW + px;
+          if (part == 1) acc += sL[idx] << 8;
+          sL[idx] = acc;
+          if (last) {
+            const float fv = __ull2float_rn(acc);
+            sLf[idx] = fv;
+            lmax = fmaxf(lmax, fv);
+          }
+        }
       }
-      sL[(2 * lp) * PW + px] = acc0;
-      sL[(2 * lp + 1) * PW + px] = acc1;
-      const float f0 = __ull2float_rn(acc0), f1 = __ull2float_rn(acc1);
-      sLf[(2 * lp) * PW + px] = f0;
-      sLf[(2 * lp + 1) * PW + px] = f1;
-      lmax = fmaxf(lmax, fmaxf(f0, f1));
     }
   } else {
     for (int i = tid; i < LH * PW; i += ST_THREADS) {
@@ -297,12 +388,16 @@ __global__ void __launch_bounds__(ST_THREADS, 1024 / ST_THREADS) k_stencil_ridge
       unsigned long long acc = (unsigned long long)(uint32_t)q[R] * col[R * PWs];
       for (int j = 0; j < R; ++j)
         acc += (unsigned long long)(uint32_t)q[j] * (unsigned long long)(col[j * PWs] + col[(2 * R - j) * PWs]);
+      if (part == 1) acc += sL[i] << 8;
       sL[i] = acc;
-      const float fl = __ull2float_rn(acc);
-      sLf[i] = fl;
-      lmax = fmaxf(lmax, fl);
+      if (last) {
+        const float fl = __ull2float_rn(acc);
+        sLf[i] = fl;
+        lmax = fmaxf(lmax, fl);
+      }
     }
   }
+  }  // parts
   {
     const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(lmax));
     if ((tid & 31) == 0) atomicMax(&s_lmax, m);
@@ -358,60 +453,86 @@ __global__ void __launch_bounds__(ST_THREADS, 1024 / ST_THREADS) k_stencil_ridge
   }
   __syncthreads();
 
-  // ---- E: directed-ridge test of the tile's pixels, 4 per thread; pixels
-  //         that FP32 cannot decide go to a list for the exact test
-  int flags = 0;  // verdict of pixel j in bits 2j, 2j + 1
-  int nfb = 0;
+  // ---- E1: threshold test of the tile's pixels, 4 per thread: certainly no
+  //          ridge, undecided (listed for the exact test), or a candidate for
+  //          the direction test (listed, so that E2 runs it with full warps:
+  //          candidates cluster along the ridges)
+  uint16_t* sC = sR;  // the candidate list; the ridge list takes these bytes after the exact test
+  {
+    const int lane = tid & 31;
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    int pi = tid + j * ST_THREADS;
-    int ty = pi / ST_TW, tx = pi - ty * ST_TW;
-    int gx = x0 + tx, gy = y0 + ty;
-    int verdict = 0;
-    if (gx < W && gy < H) {
-      int hy = ty + 1, hx = tx + 1, c = hy * HW2 + hx;
-      float k = sK[c], ek = sE[c];
-      float dk = k - a.tau;  // exact near the boundary (Sterbenz)
-      if (dk >= ek) {
-        verdict = 0;
-      } else if (!(dk < -ek)) {
-        verdict = 2;
-      } else {
-        float X, Y, eX;
-        bool dir_ok;
-        if constexpr (EDGE) {
-          // unit gradient: (Gx, Gy) moves by <= sqrt 2 delta, so X by <=
-          // 2 sqrt 2 delta / |grad| plus the roundings
-          float gxf, gyf;
-          grad32(sRs, sRd1, HW2, c, a.invD, gxf, gyf);
-          const float g = -k;
-          dir_ok = g > 4.0f * delta && g > 0.0f;
-          X = __fdiv_rn(gxf, g);
-          Y = __fdiv_rn(gyf, g);
-          if (X < 0.0f || (X == 0.0f && Y < 0.0f)) {
-            X = -X;
-            Y = -Y;
-          }
-          eX = 3.0f * delta / (g - 2.0f * delta) + 4.0f * U32;
+    for (int j = 0; j < 4; ++j) {
+      const int pi = tid + j * ST_THREADS;
+      const int ty = pi / ST_TW, tx = pi - ty * ST_TW;
+      const int gx = x0 + tx, gy = y0 + ty;
+      uint8_t verdict = 0;
+      bool cand = false;
+      if (gx < W && gy < H) {
+        const int c = (ty + 1) * HW2 + tx + 1;
+        const float dk = sK[c] - a.tau;  // exact near the boundary (Sterbenz)
+        const float ek = sE[c];
+        if (dk >= ek) {
+          verdict = 0;
+        } else if (!(dk < -ek)) {
+          verdict = 2;
+          sU[atomicAdd(&s_nu, 1)] = (uint16_t)pi;
         } else {
-          float fa, fb, fc;
-          hess32(sRs, sRd2, sRd1, HW2, c, a.invD, fa, fb, fc);
-          float k2, ek2, hdf, rad;
-          eig32_k(fa, fb, fc, k2, ek2, hdf, rad);
-          float M = fabsf(fa) + fabsf(fb) + fabsf(fc);
-          dir_ok = eig32_dir(fb, hdf, rad, M, delta, X, Y, eX);
+          cand = true;
         }
-        verdict = dir_ok ? ridge_fast(sK, sE, HW2, hy, hx, gx, gy, H, W, k, ek, a.tau, X, Y, eX) : 2;
       }
-      if (verdict == 2) {
-        ++nfb;
-        sU[atomicAdd(&s_nu, 1)] = (uint16_t)pi;
+      sV[pi] = verdict;
+      const unsigned m = __ballot_sync(0xffffffffu, cand);
+      if (m) {
+        const int leader = __ffs(m) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(&s_ncand, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (cand) sC[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)pi;
       }
     }
-    flags |= verdict << (2 * j);
   }
-  if (nfb) atomicAdd(&a.stats->fallbacks, (unsigned long long)nfb);
   __syncthreads();
+  // ---- E2: direction test of the candidates (k- certainly below tau):
+  //          X- with its bound, then the certified local-minimum test
+  {
+    const int ncand = s_ncand;
+    for (int t = tid; t < ncand; t += ST_THREADS) {
+      const int pi = sC[t];
+      const int ty = pi / ST_TW, tx = pi - ty * ST_TW;
+      const int gx = x0 + tx, gy = y0 + ty;
+      const int hy = ty + 1, hx = tx + 1, c = hy * HW2 + hx;
+      const float k = sK[c], ek = sE[c];
+      float X, Y, eX;
+      bool dir_ok;
+      if constexpr (EDGE) {
+        // unit gradient: (Gx, Gy) moves by <= sqrt 2 delta, so X by <=
+        // 2 sqrt 2 delta / |grad| plus the roundings
+        float gxf, gyf;
+        grad32(sRs, sRd1, HW2, c, a.invD, gxf, gyf);
+        const float g = -k;
+        dir_ok = g > 4.0f * delta && g > 0.0f;
+        X = __fdiv_rn(gxf, g);
+        Y = __fdiv_rn(gyf, g);
+        if (X < 0.0f || (X == 0.0f && Y < 0.0f)) {
+          X = -X;
+          Y = -Y;
+        }
+        eX = 3.0f * delta / (g - 2.0f * delta) + 4.0f * U32;
+      } else {
+        float fa, fb, fc;
+        hess32(sRs, sRd2, sRd1, HW2, c, a.invD, fa, fb, fc);
+        float k2, ek2, hdf, rad;
+        eig32_k(fa, fb, fc, k2, ek2, hdf, rad);
+        float M = fabsf(fa) + fabsf(fb) + fabsf(fc);
+        dir_ok = eig32_dir(fb, hdf, rad, M, delta, X, Y, eX);
+      }
+      const int verdict = dir_ok ? ridge_fast(sK, sE, HW2, hy, hx, gx, gy, H, W, k, ek, a.tau, X, Y, eX) : 2;
+      sV[pi] = (uint8_t)verdict;
+      if (verdict == 2) sU[atomicAdd(&s_nu, 1)] = (uint16_t)pi;
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && s_nu) atomicAdd(&a.stats->fallbacks, (unsigned long long)s_nu);
   {
     // exact test of the listed pixels, FB_CHUNK at a time: first one thread
     // per (pixel, neighbour) for the exact k- of the 3x3 neighbourhood (the
@@ -461,9 +582,10 @@ __global__ void __launch_bounds__(ST_THREADS, 1024 / ST_THREADS) k_stencil_ridge
       __syncthreads();
     }
   }
+  // every verdict is now 0 or 1: flags holds pixel j's in bit 2j
+  int flags = 0;
 #pragma unroll
-  for (int j = 0; j < 4; ++j)
-    if (((flags >> (2 * j)) & 3) == 2) flags ^= (2 ^ (int)sV[tid + j * ST_THREADS]) << (2 * j);
+  for (int j = 0; j < 4; ++j) flags |= (int)sV[tid + j * ST_THREADS] << (2 * j);
 
   // ---- compaction: one block-wide exclusive scan of the per-thread counts
   //      into a list of the tile's ridge pixels (record order inside a tile
@@ -604,7 +726,13 @@ static void launch_stencil_r(const StencilArgs& a, dim3 grid, size_t sm, cudaStr
 }
 
 
-cudaError_t launch_stencil(const StencilArgs& a, int dtype, cudaStream_t st) {
+cudaError_t launch_stencil(const StencilArgs& args, int dtype, cudaStream_t st) {
+  StencilArgs a = args;
+  long long S = 0;
+  for (int i = 0; i <= 2 * a.taps.R; ++i) S += a.taps.q[i];
+  a.narrow_max = (uint32_t)((4294967295LL) / (2 * S));
+  const size_t px_bytes = dtype == 0 ? 1 : 2;
+  a.vec_rows = ((uintptr_t)a.frames % 16 == 0) && ((size_t)a.W * px_bytes % 16 == 0) ? 1 : 0;
   dim3 grid((a.W + ST_TW - 1) / ST_TW, (a.H + ST_TH - 1) / ST_TH, a.n);
   size_t sm = stencil_smem_bytes(a.taps.R);
   if (dtype == 0)
