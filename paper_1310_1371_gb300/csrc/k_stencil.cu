@@ -160,7 +160,7 @@ __device__ __forceinline__ uint32_t max_u16x8(uint4 q) {
 // EDGE: directed edges (Additional notes) -- the gradient replaces the
 // Hessian and -|grad| takes the place of k- in every test below.
 template <typename Tin, int RC, bool EDGE>
-__global__ void __launch_bounds__(ST_THREADS, 1024 / ST_THREADS) k_stencil_ridge(StencilArgs a) {
+__global__ void __launch_bounds__(ST_THREADS, 5) k_stencil_ridge(StencilArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x;
   const int R = RC > 0 ? RC : a.taps.R;
@@ -475,7 +475,8 @@ __global__ void __launch_bounds__(ST_THREADS, 1024 / ST_THREADS) k_stencil_ridge
           verdict = 0;
         } else if (!(dk < -ek)) {
           verdict = 2;
-          sU[atomicAdd(&s_nu, 1)] = (uint16_t)pi;
+          const int k = atomicAdd(&s_nu, 1);
+          if (RD_GUARD(k < ST_TW * ST_TH, a.stats)) sU[k] = (uint16_t)pi;
         } else {
           cand = true;
         }
@@ -487,7 +488,8 @@ __global__ void __launch_bounds__(ST_THREADS, 1024 / ST_THREADS) k_stencil_ridge
         int base = 0;
         if (lane == leader) base = atomicAdd(&s_ncand, __popc(m));
         base = __shfl_sync(0xffffffffu, base, leader);
-        if (cand) sC[base + __popc(m & ((1u << lane) - 1u))] = (uint16_t)pi;
+        const int k = base + __popc(m & ((1u << lane) - 1u));
+        if (cand && RD_GUARD(k < ST_TW * ST_TH, a.stats)) sC[k] = (uint16_t)pi;
       }
     }
   }
@@ -528,7 +530,10 @@ __global__ void __launch_bounds__(ST_THREADS, 1024 / ST_THREADS) k_stencil_ridge
       }
       const int verdict = dir_ok ? ridge_fast(sK, sE, HW2, hy, hx, gx, gy, H, W, k, ek, a.tau, X, Y, eX) : 2;
       sV[pi] = (uint8_t)verdict;
-      if (verdict == 2) sU[atomicAdd(&s_nu, 1)] = (uint16_t)pi;
+      if (verdict == 2) {
+        const int k = atomicAdd(&s_nu, 1);
+        if (RD_GUARD(k < ST_TW * ST_TH, a.stats)) sU[k] = (uint16_t)pi;
+      }
     }
   }
   __syncthreads();
