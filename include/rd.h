@@ -121,6 +121,8 @@ typedef struct rd_stats {
 #define RD_OVF_PEAKS 4      /* peak list of a frame full                          */
 #define RD_OVF_RINGS 8      /* caller's ring buffer too small                     */
 #define RD_OVF_SCORE 16     /* a smoothed vote sum exceeded 32 bits               */
+#define RD_OVF_CHECK 32     /* debug build only (compiled with RD_CHECK): a computed
+                               index fell outside its buffer; the access was skipped */
 
 typedef struct rd_ctx rd_ctx;
 

@@ -55,6 +55,16 @@ constexpr int FIT_WARPS = 8;
 // coefficient exceeds it always take the exact path.
 constexpr float KF_CONST = 1.72e-7f;
 
+// Debug build (compile with -DRD_CHECK): data-dependent indices into shared
+// and global buffers are checked before use.  A failed check sets
+// RD_OVF_CHECK in the call's statistics and the access is skipped; nothing
+// traps.  In the normal build the checks compile to nothing.
+#ifdef RD_CHECK
+#define RD_GUARD(cond, stats) ((cond) ? true : (atomicOr(&(stats)->overflow, RD_OVF_CHECK), false))
+#else
+#define RD_GUARD(cond, stats) true
+#endif
+
 struct DevStats {
   unsigned long long ridge, votes, peaks, fallbacks;
   int overflow;
