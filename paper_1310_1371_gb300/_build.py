@@ -39,17 +39,31 @@ def _stale(target: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, extra: list[str] | None = None, force: bool = False) -> str:
-    """Compile (only what changed) and return the path of librd.so."""
-    os.makedirs(OBJ, exist_ok=True)
+VARIANTS = {
+    None: (OBJ, LIB, []),
+    # debug build: data-dependent indices checked in the kernels (RD_OVF_CHECK)
+    "check": (os.path.join(PKG, "_build_check"), os.path.join(LIBDIR, "librd_check.so"), ["-DRD_CHECK"]),
+}
+
+
+def lib_path(variant: str | None = None) -> str:
+    return VARIANTS[variant][1]
+
+
+def build(verbose: bool = False, extra: list[str] | None = None, force: bool = False,
+          variant: str | None = None) -> str:
+    """Compile (only what changed) and return the path of librd.so (or of a
+    named variant: "check", the bounds-checked debug build librd_check.so)."""
+    obj_dir, lib, vflags = VARIANTS[variant]
+    os.makedirs(obj_dir, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(ROOT, "include", "rd.h"))
-    flags = NVCC_FLAGS + (extra or [])
+    flags = NVCC_FLAGS + vflags + (extra or [])
     procs, objs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(OBJ, src.replace(".cu", ".o"))
+        o = os.path.join(obj_dir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + headers):
             cmd = [nvcc(), "-c", s, "-o", o] + flags
@@ -65,12 +79,12 @@ def build(verbose: bool = False, extra: list[str] | None = None, force: bool = F
             failed.append(src)
     if failed:
         raise RuntimeError("nvcc failed for " + ", ".join(failed))
-    if force or procs or _stale(LIB, objs):
-        cmd = [nvcc(), "-shared", "-o", LIB] + objs + ARCH + ["-Xcompiler", "-fPIC", "-lpthread"]
+    if force or procs or _stale(lib, objs):
+        cmd = [nvcc(), "-shared", "-o", lib] + objs + ARCH + ["-Xcompiler", "-fPIC", "-lpthread"]
         if verbose:
             print(" ".join(cmd), flush=True)
         subprocess.run(cmd, check=True)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

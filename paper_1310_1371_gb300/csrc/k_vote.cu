@@ -111,9 +111,10 @@ __global__ void __launch_bounds__(256) k_bin(BinArgs a) {
           }
           tx = t.tx0 + kk;
           key = (unsigned)((ty * a.n_atx + tx) * a.n_slabs + s);
+          if (!RD_GUARD(tx >= 0 && tx < a.n_atx && ty >= 0 && ty < a.n_aty, a.stats)) key = 0xffffffffu;
         }
         const unsigned grp = __match_any_sync(0xffffffffu, key);
-        if (k >= nb) continue;
+        if (k >= nb || key == 0xffffffffu) continue;
         const int leader = __ffs(grp) - 1;
         const int n_grp = __popc(grp);
         const long long b = fbin + key;
@@ -455,7 +456,7 @@ __device__ __forceinline__ void dense_bin(const VoteArgs& a, int b, int sub, uns
       int la = q < n_cached ? cast_one(a, fbase, ec[q], rf, cc, nv, nfb) : -1;
       bool hot = false;
       int vyx = 0;
-      if (la >= 0) {
+      if (la >= 0 && RD_GUARD(la < RW * RW, a.stats)) {
         unsigned old = atomicAdd(&sA[la], 1u);
         if (old == vthr) {
           int ly = la / RW, lx = la - ly * RW;
@@ -475,7 +476,7 @@ __device__ __forceinline__ void dense_bin(const VoteArgs& a, int b, int sub, uns
       }
       bool hot = false;
       int vyx = 0;
-      if (la >= 0) {
+      if (la >= 0 && RD_GUARD(la < RW * RW, a.stats)) {
         unsigned old = atomicAdd(&sA[la], 1u);
         if (old == vthr) {
           int ly = la / RW, lx = la - ly * RW;
@@ -532,7 +533,10 @@ __device__ __forceinline__ void dense_bin(const VoteArgs& a, int b, int sub, uns
       }
       const uint32_t* ctr = sA + (vyr + h - 1) * RW + (vxr + h - 1);
       unsigned long long acc0 = 0, acc1 = 0;
-      for (int q = lane; q < nq2; q += 32) {
+      const bool win_ok = RD_GUARD(vyr - 1 + h - Rs >= 0 && vyr - 1 + h + Rs < RW && vxr - 1 + h - Rs >= 0 &&
+                                       vxr - 1 + h + Rs < RW,
+                                   a.stats);
+      for (int q = lane; q < nq2 && win_ok; q += 32) {
         int4 w = sQ4[q];  // two taps: (weight, offset), (weight, offset)
         acc0 += (unsigned long long)(uint32_t)w.x * ctr[w.y];
         acc1 += (unsigned long long)(uint32_t)w.z * ctr[w.w];
@@ -787,6 +791,7 @@ __device__ __forceinline__ void vote_bin_sparse(const VoteArgs& a, const int b, 
       if ((unsigned)(lx - lxlo) >= (unsigned)lxn || (unsigned)(ly - lylo) >= (unsigned)lyn) return;
       if (owned && (unsigned)(lx - h) < (unsigned)T && (unsigned)(ly - h) < (unsigned)T) ++nv;
       const int la = ly * RW + lx;
+      if (!RD_GUARD((unsigned)la < (unsigned)(RW * RW), a.stats)) return;
       const unsigned sh = (la & 1) << 4;
       const unsigned old = (atomicAdd(&sAw[la >> 1], 1u << sh) >> sh) & 0xffffu;
       if (old == vthr) {
@@ -893,8 +898,10 @@ __device__ __forceinline__ void vote_bin_sparse(const VoteArgs& a, const int b, 
         if (k < nhot) {
           const uint32_t key = sCoord[lst * SP_HOT + k];
           const uint16_t* ctr = sA16 + ((int)(key >> 8) + h - 1) * RW + ((int)(key & 0xffu) + h - 1);
-          if (sl == 0) acc = (unsigned long long)sG[0].z * ctr[0];
-          for (int q = 1 + sl; q <= ng; q += L) {
+          const int cy = (int)(key >> 8) + h - 1, cxk = (int)(key & 0xffu) + h - 1;
+          const bool win_ok = RD_GUARD(cy - Rs >= 0 && cy + Rs < RW && cxk - Rs >= 0 && cxk + Rs < RW, a.stats);
+          if (sl == 0 && win_ok) acc = (unsigned long long)sG[0].z * ctr[0];
+          for (int q = 1 + sl; q <= ng && win_ok; q += L) {
             const uint4 G = sG[q];
             const int o1 = (int)G.x, o2 = (int)G.y;
             const unsigned c4 = (unsigned)ctr[o1] + (unsigned)ctr[-o1] + (unsigned)ctr[o2] + (unsigned)ctr[-o2];

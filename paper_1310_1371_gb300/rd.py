@@ -20,7 +20,7 @@ RD_OK, RD_E_INVAL, RD_E_NOMEM, RD_E_CUDA, RD_E_OVERFLOW, RD_E_TIMEOUT, RD_E_BUSY
 STATUS_NAMES = ["RD_OK", "RD_E_INVAL", "RD_E_NOMEM", "RD_E_CUDA", "RD_E_OVERFLOW", "RD_E_TIMEOUT", "RD_E_BUSY",
                 "RD_E_HOST"]
 # rd_stats.overflow bits (capacities that overflowed)
-RD_OVF_RIDGE, RD_OVF_BINS, RD_OVF_PEAKS, RD_OVF_RINGS, RD_OVF_SCORE = 1, 2, 4, 8, 16
+RD_OVF_RIDGE, RD_OVF_BINS, RD_OVF_PEAKS, RD_OVF_RINGS, RD_OVF_SCORE, RD_OVF_CHECK = 1, 2, 4, 8, 16, 32
 RD_RING_FIT_FAIL = 1
 RD_SERVE_FAIL_RESULT, RD_SERVE_FAIL_SLOT = 1, 2
 PEAK_CAP = 4096   # per-frame peak capacity of a context
@@ -55,11 +55,14 @@ _lib = None
 
 
 def load_library(build: bool = False) -> ctypes.CDLL:
-    """Load librd.so from the package (building it first when asked)."""
+    """Load librd.so from the package (building it first when asked).  With
+    RD_LIB_VARIANT=check in the environment the bounds-checked debug build
+    librd_check.so is loaded instead."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.build() if build else _build.LIB
+    variant = os.environ.get("RD_LIB_VARIANT") or None
+    path = _build.build(variant=variant) if build else _build.lib_path(variant)
     if not os.path.exists(path):
         raise RuntimeError(f"librd.so not built ({path}); run __graft_entry__.build()")
     lib = ctypes.CDLL(path)
@@ -243,6 +246,14 @@ class Detector:
         self.rings = torch.empty(self.ring_cap * 10, dtype=torch.int32, device=dev)
         self.counts = torch.empty(max_batch, dtype=torch.int32, device=dev)
         self.offsets = torch.empty(max_batch, dtype=torch.int32, device=dev)
+
+    def device_bytes(self) -> int:
+        """rd_get_device_bytes: device memory the context holds."""
+        b = ctypes.c_longlong()
+        st = self.lib.rd_get_device_bytes(self.ctx, ctypes.byref(b))
+        if st != RD_OK:
+            raise RdError(st, "rd_get_device_bytes")
+        return int(b.value)
 
     def geometry(self) -> tuple[int, int]:
         g = rd_geometry()
