@@ -555,8 +555,10 @@ def run_diff(args):
         for i, j in enumerate(m):
             if j >= 0:
                 t = truth[f, i]
-                err_b.append((math.hypot(flat[o + j, 0] - t[0], flat[o + j, 1] - t[1]), abs(flat[o + j, 2] - t[2])))
-                err_a.append((math.hypot(ref[o + j, 0] - t[0], ref[o + j, 1] - t[1]), abs(ref[o + j, 2] - t[2])))
+                err_b.append((math.hypot(flat[o + j, 0] - t[0], flat[o + j, 1] - t[1]), abs(flat[o + j, 2] - t[2]),
+                              abs(flat[o + j, 0] - t[0]), abs(flat[o + j, 1] - t[1])))
+                err_a.append((math.hypot(ref[o + j, 0] - t[0], ref[o + j, 1] - t[1]), abs(ref[o + j, 2] - t[2]),
+                              abs(ref[o + j, 0] - t[0]), abs(ref[o + j, 1] - t[1])))
         o += k
     err_b, err_a = np.array(err_b), np.array(err_a)
     # the FP64 oracle's forward + backward on a bounded sample of frames
@@ -578,6 +580,8 @@ def run_diff(args):
                        "matched_rings": int(len(err_b)),
                        "median_centre_err_px": [float(np.median(err_b[:, 0])), float(np.median(err_a[:, 0]))],
                        "median_radius_err_px": [float(np.median(err_b[:, 1])), float(np.median(err_a[:, 1]))],
+                       "median_abs_cx_px": [float(np.median(err_b[:, 2])), float(np.median(err_a[:, 2]))],
+                       "median_abs_cy_px": [float(np.median(err_b[:, 3])), float(np.median(err_a[:, 3]))],
                        "note": "[before (hard detector, Kasa fit on u16-rounded frames), after rd_refine]"},
             "cpu_baseline": {"value": done / cpu_s, "unit": "frames/s", "cores": 1, "kind": "oracle",
                              "sample": f"{done} frames: FP64 soft score + autograd gradients in {cpu_s:.1f} s"},

@@ -188,13 +188,17 @@ rd_status rd_destroy(rd_ctx* ctx);
  * (Results, "Directed ridge detection & votes collection" and "Local maxima
  * detection in a noisy parameter space") used to refine rings by gradient
  * ascent and to differentiate a ring's score with respect to the image:
- *   Score(c, rho) = (1/rho) sum_{p in ridge} m(p) sum_{s = +-1} sum_{q in corners(v)}
+ *   Score(c, rho) = (1/rho) sum_{p in ridge} m(p) a(p) sum_{s = +-1} sum_{q in corners(v)}
  *                   bil(v, q) exp(-|q - c|^2 / (2 sigma(rho)^2)),
  *   v = p + s rho X-(p), m(p) = logistic((tau - k-(p)) / T), T = |tau| / 4,
+ *   a(p) = exp(-(|p - c| - rho)^2 / (2 (w/2)^2)),
  * where the directed-ridge set of the frame (the rd_detect rule, evaluated on
  * the frame in double precision) is held fixed, bil(v, q) are the bilinear
  * weights of the four grid points of v's cell (points outside the image get
- * nothing) and sigma(rho) = sig_a rho + sig_b.  c = (cx, cy) and rho = r
+ * nothing), sigma(rho) = sig_a rho + sig_b, and a(p) is the ring's soft
+ * annulus of half-width w = rd_params.annulus_w (the paper's ridge-point
+ * classification, Results: it keeps the pixels of neighbouring rings, which
+ * lie off the circle, out of the score).  c = (cx, cy) and rho = r
  * are read from the rings' float fields; frame i's rings are the counts_dev[i]
  * rings that follow frame i - 1's in rings_dev.  Computed in double
  * precision; outputs are float.  Frames may be RD_U8, RD_U16 or RD_F32
@@ -211,7 +215,8 @@ rd_status rd_destroy(rd_ctx* ctx);
  * rd_refine ascends the unnormalised vote mass r * Score of every ring (the
  * 1/r normalisation compares rings of different radii; for one ring it
  * would pull r inward by about sigma(r)^2 / r), iters steps of
- *   delta = step * sigma(r)^2 / Score * (dScore/dcx, dScore/dcy, dScore/dr + Score / r)
+ *   delta = step * se^2 / Score * (dScore/dcx, dScore/dcy, dScore/dr + Score / r),
+ *   1 / se^2 = 1 / sigma(r)^2 + 1 / (w/2)^2
  * (each component at most 0.5 px; r at least 1), updating cx, cy, r of
  * rings_dev in place; at most 4096 rings per frame. */
 rd_status rd_soft_score(rd_ctx* ctx, const void* frames_dev, int n, int H, int W, int dtype, void* stream,

@@ -9,9 +9,10 @@ ridge detection & votes collection" and "Local maxima detection in a noisy
 parameter space"), so that a ring's parameters can be refined by gradient
 ascent and the score differentiated with respect to the image:
 
-    Score(c, rho) = (1/rho) sum_{p in ridge} m(p) sum_{s = +1, -1}
+    Score(c, rho) = (1/rho) sum_{p in ridge} m(p) a(p) sum_{s = +1, -1}
                     sum_{q in corners(v)} bil(v, q) exp(-|q - c|^2 / (2 sigma(rho)^2)),
-    v = p + s rho X(p),   m(p) = logistic((tau - k(p)) / T),   sigma(rho) = sig_a rho + sig_b.
+    v = p + s rho X(p),   m(p) = logistic((tau - k(p)) / T),   sigma(rho) = sig_a rho + sig_b,
+    a(p) = exp(-(|p - c| - rho)^2 / (2 (w / 2)^2)).
 
 * The ridge set is the hard directed-ridge mask of the frame (steps O1-O4 of
   ``oracle.ringdet`` on the float frame) and is held fixed: the score is not
@@ -26,8 +27,17 @@ ascent and the score differentiated with respect to the image:
   restricted to the image domain, as in step O5).  Each grid point
   contributes the unnormalised Gaussian of step O7 centred at the continuous
   centre c, and the sum is normalised by 1/rho as in O7.
+* a(p) is the ring's soft annulus: the weight of a ridge pixel falls off as
+  a Gaussian of its distance from the circle (c, rho), with standard
+  deviation half the annulus half-width w of the classification step
+  (Results, "Ridge points classification & sub-pixel accuracy": the ridge
+  pixels within an annulus around each ring belong to it; w = 2 px).  It
+  keeps the votes of neighbouring rings' pixels, which lie off the circle,
+  out of a ring's score; without it a refined centre is worse than the
+  detector's circle fit on crowded frames.
 * Readings (the paper is silent): T = |tau| / 4 (with |tau| at least 1e-6);
-  the sum runs over all ridge pixels and both signs, with no window cut-off.
+  the annulus's standard deviation w / 2; the sum runs over all ridge pixels
+  and both signs, with no window cut-off.
 
 ``soft_score`` is the definition written out with NumPy.  ``soft_score_torch``
 is the same forward written with plain PyTorch CPU float64 ops; its autograd
@@ -47,16 +57,29 @@ class SoftParams:
     ridge_thresh: float
     sig_a: float
     sig_b: float
+    annulus_w: float = 2.0
 
     @property
     def temperature(self) -> float:
         return max(abs(self.ridge_thresh), 1e-6) / 4.0
 
+    @property
+    def annulus_sigma(self) -> float:
+        """Standard deviation of the soft annulus: half the half-width w."""
+        return self.annulus_w * 0.5
+
     @staticmethod
     def make(**kw) -> "SoftParams":
         f32 = lambda v: float(np.float32(v))  # parameters arrive as float32
         return SoftParams(f32(kw["sigma"]), f32(kw["ridge_thresh"]), f32(kw.get("sig_a", 0.05)),
-                          f32(kw.get("sig_b", 0.25)))
+                          f32(kw.get("sig_b", 0.25)), f32(kw.get("annulus_w", 2.0)))
+
+
+def annulus(xs, ys, cx, cy, rho, p: SoftParams):
+    """a(p) = exp(-(|p - c| - rho)^2 / (2 (w/2)^2)) for ridge pixels (xs, ys)."""
+    d = np.sqrt((xs - cx) * (xs - cx) + (ys - cy) * (ys - cy))
+    sa = p.annulus_sigma
+    return np.exp(-((d - rho) * (d - rho)) / (2.0 * sa * sa))
 
 
 def _taps_float(sigma: float) -> np.ndarray:
@@ -128,6 +151,7 @@ def soft_score(rd: Ridges, rings: np.ndarray, p: SoftParams, H: int, W: int) -> 
     for i, (cx, cy, rho) in enumerate(np.asarray(rings, dtype=np.float64)):
         sig = p.sig_a * rho + p.sig_b
         den = 2.0 * sig * sig
+        ma = m * annulus(fx0, fy0, cx, cy, rho, p)
         total = 0.0
         for s in (1.0, -1.0):
             vx = fx0 + s * rho * rd.X
@@ -142,7 +166,7 @@ def soft_score(rd: Ridges, rings: np.ndarray, p: SoftParams, H: int, W: int) -> 
                 qy = y0 + oy
                 inside = (qx >= 0) & (qx <= W - 1) & (qy >= 0) & (qy <= H - 1)
                 d2 = (qx - cx) ** 2 + (qy - cy) ** 2
-                total += float(np.sum(np.where(inside, m * w * np.exp(-d2 / den), 0.0)))
+                total += float(np.sum(np.where(inside, ma * w * np.exp(-d2 / den), 0.0)))
         out[i] = total / rho
     return out
 
@@ -192,10 +216,13 @@ def soft_score_torch(image, rings, rd: Ridges, p: SoftParams):
     fx0 = xs.to(torch.float64)
     fy0 = ys.to(torch.float64)
     out = []
+    sa = p.annulus_sigma
     for i in range(rings.shape[0]):
         cx, cy, rho = rings[i, 0], rings[i, 1], rings[i, 2]
         sig = p.sig_a * rho + p.sig_b
         den = 2.0 * sig * sig
+        dist = torch.sqrt((fx0 - cx) * (fx0 - cx) + (fy0 - cy) * (fy0 - cy))
+        ma = m * torch.exp(-((dist - rho) * (dist - rho)) / (2.0 * sa * sa))
         total = torch.zeros((), dtype=torch.float64)
         for sg in (1.0, -1.0):
             vx_ = fx0 + sg * rho * X
@@ -210,7 +237,7 @@ def soft_score_torch(image, rings, rd: Ridges, p: SoftParams):
                 qy = y0 + oy
                 inside = (qx >= 0) & (qx <= W - 1) & (qy >= 0) & (qy <= H - 1)
                 d2 = (qx - cx) ** 2 + (qy - cy) ** 2
-                total = total + torch.sum(torch.where(inside, m * w * torch.exp(-d2 / den), torch.zeros_like(w)))
+                total = total + torch.sum(torch.where(inside, ma * w * torch.exp(-d2 / den), torch.zeros_like(w)))
         out.append(total / rho)
     return torch.stack(out)
 

@@ -5,11 +5,16 @@
 // The paper has no differentiable form.  The score extends its voting and
 // scoring steps (Results, "Directed ridge detection & votes collection",
 // "Local maxima detection in a noisy parameter space") smoothly:
-//   Score(c, rho) = (1/rho) sum_{p in ridge} m(p) sum_{s=+-1} sum_{q in corners(v)}
+//   Score(c, rho) = (1/rho) sum_{p in ridge} m(p) a(p) sum_{s=+-1} sum_{q in corners(v)}
 //                   bil(v, q) exp(-|q - c|^2 / (2 sigma(rho)^2)),
 //   v = p + s rho X(p),  m(p) = logistic((tau - k(p)) / T),  T = |tau| / 4,
+//   a(p) = exp(-(|p - c| - rho)^2 / (2 sa^2)),  sa = w / 2,
 // with the hard directed-ridge set of the frame held fixed, grid points
 // outside the image receiving nothing, and sigma(rho) = sig_a rho + sig_b.
+// a(p) is the ring's soft annulus (Results, "Ridge points classification &
+// sub-pixel accuracy": the ridge pixels within an annulus of half-width w
+// around a ring are its own): it keeps pixels of neighbouring rings, which
+// lie off the circle, out of the score.
 // The image gradient flows through k and X to the exact-arithmetic chain
 // eigen <- 5x5 second-order Sobel / 64 <- Gaussian, each stencil with
 // reflect-101 borders; its adjoint is applied as gathers, recomputing the
@@ -412,7 +417,9 @@ __global__ void __launch_bounds__(256) k_soft_score(SoftArgs a) {
       __syncthreads();
       total = s_pre[nt];
     }
+    const double sa = a.sig_ann, sa2 = sa * sa;
     double T = 0.0, Tcx = 0.0, Tcy = 0.0, Tsig = 0.0, Trho = 0.0;
+    double TAcx = 0.0, TAcy = 0.0, TArho = 0.0;  // through the annulus weights' dependence on (c, rho)
     for (int q = threadIdx.x; q < total; q += blockDim.x) {
       int j = q;
       if (tiled) {  // the tile t with s_pre[t] <= q < s_pre[t + 1]
@@ -427,6 +434,14 @@ __global__ void __launch_bounds__(256) k_soft_score(SoftArgs a) {
       const uint32_t xy = a.xy[g];
       const double px = (double)(xy & 0xffffu), py = (double)(xy >> 16);
       const double X = a.rX[g], Y = a.rY[g], m = a.rm[g];
+      // the pixel's annulus weight; a pixel farther than 9 sa from the
+      // circle is left out (its weight is below e^-40.5 < 3e-18)
+      const double ddx = px - cx, ddy = py - cy;
+      const double dist = sqrt(ddx * ddx + ddy * ddy);
+      const double e = dist - rho;
+      if (!(fabs(e) <= 9.0 * sa)) continue;
+      const double A = exp(-(e * e) / (2.0 * sa2));
+      double tp = 0.0, tcx = 0.0, tcy = 0.0, tsig = 0.0, trho = 0.0;
       double gk = 0.0, gX = 0.0, gY = 0.0;
       for (int s = -1; s <= 1; s += 2) {
         const double vx = px + s * rho * X, vy = py + s * rho * Y;
@@ -443,14 +458,14 @@ __global__ void __launch_bounds__(256) k_soft_score(SoftArgs a) {
             const double d2 = dxq * dxq + dyq * dyq;
             const double G = exp(-d2 / den);
             const double mwG = m * wx * wy * G;
-            T += mwG;
-            Tcx += mwG * dxq;          // x 1/sig^2 below
-            Tcy += mwG * dyq;
-            Tsig += mwG * d2;          // x 1/sig^3 below
+            tp += mwG;
+            tcx += mwG * dxq;          // x 1/sig^2 below
+            tcy += mwG * dyq;
+            tsig += mwG * d2;          // x 1/sig^3 below
             // d w / d v: the cell corner is fixed, w = wx wy
             const double dwdvx = (ox ? 1.0 : -1.0) * wy, dwdvy = wx * (oy ? 1.0 : -1.0);
             const double mG = m * G;
-            Trho += mG * (dwdvx * s * X + dwdvy * s * Y);
+            trho += mG * (dwdvx * s * X + dwdvy * s * Y);
             if (a.accumulate) {
               gk += wx * wy * G;
               gX += mG * dwdvx * s * rho;
@@ -458,11 +473,23 @@ __global__ void __launch_bounds__(256) k_soft_score(SoftArgs a) {
             }
           }
       }
+      T += A * tp;
+      Tcx += A * tcx;
+      Tcy += A * tcy;
+      Tsig += A * tsig;
+      Trho += A * trho;
+      // dA/dc = A (-e / sa^2) (c - p) / |p - c|, dA/drho = A e / sa^2
+      if (dist > 0.0) {
+        const double fa = A * (-e / sa2) / dist;
+        TAcx += tp * fa * (cx - px);
+        TAcy += tp * fa * (cy - py);
+      }
+      TArho += tp * A * e / sa2;
       if (a.accumulate && (gk != 0.0 || gX != 0.0 || gY != 0.0)) {
         const double dm = -m * (1.0 - m) / a.temp;  // dm/dk
-        atomicAdd(&a.gk[g], ds * gk * dm / rho);
-        atomicAdd(&a.gX[g], ds * gX / rho);
-        atomicAdd(&a.gY[g], ds * gY / rho);
+        atomicAdd(&a.gk[g], ds * A * gk * dm / rho);
+        atomicAdd(&a.gX[g], ds * A * gX / rho);
+        atomicAdd(&a.gY[g], ds * A * gY / rho);
       }
     }
     T = block_sum(T, red);
@@ -470,15 +497,18 @@ __global__ void __launch_bounds__(256) k_soft_score(SoftArgs a) {
     Tcy = block_sum(Tcy, red);
     Tsig = block_sum(Tsig, red);
     Trho = block_sum(Trho, red);
+    TAcx = block_sum(TAcx, red);
+    TAcy = block_sum(TAcy, red);
+    TArho = block_sum(TArho, red);
     if (threadIdx.x == 0) {
       const double s2 = sig * sig;
       const double score = T / rho;
-      // dScore/drho: through the vote positions, sigma(rho) and the 1/rho
-      const double dT_drho = Trho + Tsig / (s2 * sig) * a.sig_a;
+      // dScore/drho: through the vote positions, sigma(rho), the annulus and the 1/rho
+      const double dT_drho = Trho + Tsig / (s2 * sig) * a.sig_a + TArho;
       if (a.score) a.score[i] = (float)score;
       if (a.dparams) {
-        a.dparams[3 * i + 0] = (float)(ds * Tcx / s2 / rho);
-        a.dparams[3 * i + 1] = (float)(ds * Tcy / s2 / rho);
+        a.dparams[3 * i + 0] = (float)(ds * (Tcx / s2 + TAcx) / rho);
+        a.dparams[3 * i + 1] = (float)(ds * (Tcy / s2 + TAcy) / rho);
         a.dparams[3 * i + 2] = (float)(ds * (dT_drho / rho - T / (rho * rho)));
       }
     }
@@ -625,8 +655,9 @@ cudaError_t launch_soft_backward_image(const SoftArgs& a, cudaStream_t st) {
 // score compares rings of different radii, but for one ring it pulls the
 // maximum in rho inward by about sigma^2 / rho.  Its gradient is
 // (rho dS/dc, rho dS/drho + S); with the Newton-like scaling by the
-// curvature -rho S / sigma^2 the step is
-//   delta = step * sigma(rho)^2 / S * (dS/dcx, dS/dcy, dS/drho + S / rho),
+// curvature -rho S / se^2, 1 / se^2 = 1 / sigma(rho)^2 + 1 / sa^2 (the vote
+// Gaussian and the annulus both narrow the maximum), the step is
+//   delta = step * se^2 / S * (dS/dcx, dS/dcy, dS/drho + S / rho),
 // each component at most 0.5 px.
 __global__ void k_soft_refine_step(SoftArgs a) {
   const int n_rings = min(a.ring_off[a.n], a.max_rings);
@@ -635,7 +666,9 @@ __global__ void k_soft_refine_step(SoftArgs a) {
     const float sc = a.score[i];
     if (!(sc > 0.0f)) continue;
     const float sig = a.sig_a * q.r + a.sig_b;
-    const float scale = a.step * sig * sig / sc;
+    const float sa = (float)a.sig_ann;
+    const float se2 = sig * sig * sa * sa / (sig * sig + sa * sa);
+    const float scale = a.step * se2 / sc;
     const float d0 = fminf(fmaxf(scale * a.dparams[3 * i + 0], -0.5f), 0.5f);
     const float d1 = fminf(fmaxf(scale * a.dparams[3 * i + 1], -0.5f), 0.5f);
     const float d2 = fminf(fmaxf(scale * (a.dparams[3 * i + 2] + sc / q.r), -0.5f), 0.5f);

@@ -971,6 +971,7 @@ static rd_status soft_prepare(rd_ctx* c, const void* frames, int n, int H, int W
   a->temp = std::max(std::fabs(a->tau), 1e-6) / 4.0;
   a->sig_a = (double)c->p.sig_a;
   a->sig_b = (double)c->p.sig_b;
+  a->sig_ann = 0.5 * (double)c->p.annulus_w;
   a->t0 = c->s_t0;
   a->t1 = c->s_t1;
   a->a = c->s_a;

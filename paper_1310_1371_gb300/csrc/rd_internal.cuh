@@ -189,6 +189,7 @@ struct SoftArgs {
   int R;                      // Gaussian half-width
   double g[2 * MAX_RG + 1];   // Gaussian taps Q_i / S
   double tau, temp, sig_a, sig_b;
+  double sig_ann;             // the soft annulus's standard deviation: half the annulus half-width w
   // dense FP64 images, n * H * W each
   double *t0, *t1, *a, *b, *c, *k, *X, *Y;
   // ridge records, frame f at [f * cap, f * cap + count[f]); those of 32 x 32

@@ -135,12 +135,31 @@ def test_maximum_near_truth():
 
 def test_closed_form_offset_centre():
     """All twelve votes land exactly on (20, 20): the score at c = (20 + d, 20)
-    is (12/5) exp(-d^2 / (2 sigma(5)^2)), sigma(5) = 0.05 * 5 + 0.25."""
+    is (1/5) exp(-d^2 / (2 sigma(5)^2)) times the sum of the twelve points'
+    annulus weights exp(-(|p - c| - 5)^2 / 2), sigma(5) = 0.05 * 5 + 0.25 and
+    the annulus's standard deviation w / 2 = 1 px; each point (5 cos t, 5 sin t)
+    from (20, 20) lies sqrt(25 - 10 d cos t + d^2) from c."""
     rd = twelve_points()
     sig = P.sig_a * 5.0 + P.sig_b
+    cosines = [1, -1, 0, 0, 0.6, 0.6, -0.6, -0.6, 0.8, 0.8, -0.8, -0.8]
     for d in (0.1, 0.3, 0.7):
         sc = S.soft_score(rd, np.array([[20.0 + d, 20.0, 5.0]]), P, 41, 41)[0]
-        assert abs(sc - 12.0 / 5.0 * math.exp(-d * d / (2 * sig * sig))) < 1e-12
+        ann = sum(math.exp(-((math.sqrt(25 - 10 * d * ct + d * d) - 5.0) ** 2) / 2.0) for ct in cosines)
+        assert ann < 12.0
+        assert abs(sc - ann / 5.0 * math.exp(-d * d / (2 * sig * sig))) < 1e-12
+
+
+def test_annulus_keeps_pixels_off_the_circle_out():
+    """A ridge pixel 2 px outside the circle whose vote lands on the centre
+    (a neighbouring ring's pixel pointing at c) counts with weight exp(-2)
+    (2 standard deviations of the annulus); a pixel on the circle counts fully."""
+    k = np.array([P.ridge_thresh - 60 * P.temperature] * 2)
+    # (27, 20): 7 px from c = (20, 20) with rho = 5, X = (1, 0): its vote lands at (22, 20);
+    # (25, 20): on the circle, its vote lands on c
+    for x, want in ((27, math.exp(-2.0) * math.exp(-4.0 / (2 * (P.sig_a * 5 + P.sig_b) ** 2))), (25, 1.0)):
+        rd = S.Ridges(np.array([x]), np.array([20]), k[:1], np.array([1.0]), np.array([0.0]), np.array([True]))
+        sc = S.soft_score(rd, np.array([[20.0, 20.0, 5.0]]), P, 41, 41)[0]
+        assert abs(sc * 5.0 - want) < 1e-12, (x, sc * 5.0, want)  # the other sign's vote is >= 10 px away
 
 
 def test_closed_form_bilinear_split():
@@ -177,9 +196,11 @@ def test_unnormalised_mass_is_stationary_at_the_true_radius():
 
 def test_votes_beyond_nine_sigma_are_negligible():
     """The GPU leaves out votes farther than 9 sigma(rho) + 1.5 px from the
-    centre.  On the synthetic soft-score frames their total contribution,
-    computed term by term from the oracle's ridge set, is below 1e-12 of the
-    score (the tolerances are 1e-5 for scores and 1e-4 for gradients)."""
+    centre, and ridge pixels farther than 9 annulus standard deviations from
+    the circle.  On the synthetic soft-score frames their total contribution,
+    computed term by term from the oracle's ridge set (without the annulus
+    factor, an upper bound, for the first kind), is below 1e-12 of the score
+    (the tolerances are 1e-5 for scores and 1e-4 for gradients)."""
     fr = synth.diff_frames(2, seed=2011, H=128, W=128, n_rings=4)
     sp = S.SoftParams.make(**synth.DIFF_PARAMS)
     for f in fr:
@@ -200,4 +221,10 @@ def test_votes_beyond_nine_sigma_are_negligible():
                     for oy in (0, 1):
                         d2 = (x0 + ox - cx) ** 2 + (y0 + oy - cy) ** 2
                         left_out += float(np.sum(m[far] * np.exp(-d2 / (2 * sig * sig))))
+            # pixels off the circle by more than 9 annulus standard deviations
+            sa = sp.annulus_sigma
+            dist = np.hypot(rd.xs - cx, rd.ys - cy)
+            off = np.abs(dist - rho) > 9.0 * sa
+            a_off = np.exp(-((dist[off] - rho) ** 2) / (2 * sa * sa))
+            left_out += float(np.sum(2.0 * m[off] * a_off))   # every vote's weights sum to at most 1 per sign
             assert score > 0 and left_out / rho <= 1e-12 * score, (left_out, score)
