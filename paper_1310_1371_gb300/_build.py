@@ -47,14 +47,14 @@ VARIANTS = {
 
 
 def lib_path(variant: str | None = None) -> str:
-    return VARIANTS[variant][1]
+    return LIB if variant is None else VARIANTS[variant][1]
 
 
 def build(verbose: bool = False, extra: list[str] | None = None, force: bool = False,
           variant: str | None = None) -> str:
     """Compile (only what changed) and return the path of librd.so (or of a
     named variant: "check", the bounds-checked debug build librd_check.so)."""
-    obj_dir, lib, vflags = VARIANTS[variant]
+    obj_dir, lib, vflags = (OBJ, LIB, []) if variant is None else VARIANTS[variant]
     os.makedirs(obj_dir, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
