@@ -566,12 +566,14 @@ __global__ void __launch_bounds__(ST_THREADS, 5) k_stencil_ridge(StencilArgs a) 
         } else {
           long long ha, hc, hb;
           hess_exact(sL, PW, ty + n / 3, tx + n % 3, ha, hc, hb);
-          const Eig64 e = eigen64(ha, hc, hb, a.D64);
-          sKn[t] = e.k;
-          if (n == 4) {
+          if (n == 4) {  // the centre's X- too; its neighbours need only k-
+            const Eig64 e = eigen64(ha, hc, hb, a.D64);
+            sKn[t] = e.k;
             sXc[2 * p] = e.X;
             sXc[2 * p + 1] = e.Y;
             sDg[p] = e.degenerate ? 1 : 0;
+          } else {
+            sKn[t] = eigen64_k(ha, hc, hb, a.D64);
           }
         }
       }

@@ -81,7 +81,19 @@ static __device__ __noinline__ bool ridge_exact_nb(const double* kn, double X, d
   return true;
 }
 
-// 0 = certainly not a ridge, 1 = certainly a ridge, 2 = undecided in FP32
+// 0 = certainly not a ridge, 1 = certainly a ridge, 2 = undecided in FP32.
+// Each sample p +/- X- is interpolated on the cell that holds the FP32
+// sample.  The exact sample lies in the box of half-width eX around it and
+// within one pixel of p (|X-| <= 1 component-wise).  Where the box crosses a
+// cell edge (the FP32 sample is within eX of an integer, a test exact by
+// Sterbenz), the corner set grows along that axis to all three columns (or
+// rows) within one pixel of p, clipped to the image.  The bilinear
+// interpolant is continuous, and along an axis-parallel path its slope never
+// exceeds the spread (max - min) of the corners of the cells it crosses, so
+// between the two samples it moves by at most 2 eX times the spread of the
+// corner set; the corner errors and the interpolation's rounding are bounded
+// over the same set.  A box that reaches an image border stays undecided (the
+// definition clamps corners there).
 __device__ __forceinline__ int ridge_fast(const float* sK, const float* sE, int stride, int hy, int hx, int gx, int gy,
                                           int H, int W, float k, float ek, float tau, float X, float Y, float eX) {
   int verdict = 1;
@@ -90,24 +102,32 @@ __device__ __forceinline__ int ridge_fast(const float* sK, const float* sE, int 
     float lowx = (float)(-gx), highx = (float)(W - 1 - gx);
     float lowy = (float)(-gy), highy = (float)(H - 1 - gy);
     if (ox < lowx - eX || ox > highx + eX || oy < lowy - eX || oy > highy + eX) return 0;
-    if (eX > 0.0f) {
-      if (ox <= lowx + eX || ox >= highx - eX || oy <= lowy + eX || oy >= highy - eX) return 2;
-      // a sample within eX of a cell edge may lie in the neighbouring cell
-      if (fabsf(ox - rintf(ox)) <= eX || fabsf(oy - rintf(oy)) <= eX) return 2;
-    }
+    if (eX > 0.0f && (ox <= lowx + eX || ox >= highx - eX || oy <= lowy + eX || oy >= highy - eX)) return 2;
     float flx = floorf(ox), fly = floorf(oy);
     float fx = ox - flx, fy = oy - fly;
     int cx0 = gx + (int)flx, cy0 = gy + (int)fly;
     int cx1 = fx == 0.0f ? cx0 : min(cx0 + 1, W - 1);
     int cy1 = fy == 0.0f ? cy0 : min(cy0 + 1, H - 1);
     int lx0 = hx + (cx0 - gx), lx1 = hx + (cx1 - gx), ly0 = hy + (cy0 - gy), ly1 = hy + (cy1 - gy);
-    int i00 = ly0 * stride + lx0, i01 = ly0 * stride + lx1, i10 = ly1 * stride + lx0, i11 = ly1 * stride + lx1;
-    float k00 = sK[i00], k01 = sK[i01], k10 = sK[i10], k11 = sK[i11];
+    float k00 = sK[ly0 * stride + lx0], k01 = sK[ly0 * stride + lx1], k10 = sK[ly1 * stride + lx0],
+          k11 = sK[ly1 * stride + lx1];
     float gxw = 1.0f - fx, gyw = 1.0f - fy;
     float kt = gyw * (gxw * k00 + fx * k01) + fy * (gxw * k10 + fx * k11);
-    float kmax = fmaxf(fmaxf(k00, k01), fmaxf(k10, k11));
-    float kmin = fminf(fminf(k00, k01), fminf(k10, k11));
-    float ekc = fmaxf(fmaxf(sE[i00], sE[i01]), fmaxf(sE[i10], sE[i11]));
+    // the corner set, as offsets from p
+    const bool ex = eX > 0.0f && fabsf(ox - rintf(ox)) <= eX;
+    const bool ey = eX > 0.0f && fabsf(oy - rintf(oy)) <= eX;
+    const int xa = ex ? max(-1, -gx) : cx0 - gx, xb = ex ? min(1, W - 1 - gx) : cx1 - gx;
+    const int ya = ey ? max(-1, -gy) : cy0 - gy, yb = ey ? min(1, H - 1 - gy) : cy1 - gy;
+    float kmax = k00, kmin = k00, ekc = 0.0f;
+    for (int dy = ya; dy <= yb; ++dy) {
+      const int row = (hy + dy) * stride + hx;
+      for (int dx = xa; dx <= xb; ++dx) {
+        const float kc = sK[row + dx];
+        kmax = fmaxf(kmax, kc);
+        kmin = fminf(kmin, kc);
+        ekc = fmaxf(ekc, sE[row + dx]);
+      }
+    }
     float kabs = fmaxf(fabsf(kmax), fabsf(kmin));
     float m = ek + ekc + 2.0f * eX * (kmax - kmin) + 8.0f * U32 * kabs + 1e-30f;
     float diff = kt - k;  // need k < kt (s = +) or k <= kt (s = -)

@@ -250,6 +250,17 @@ struct Eig64 {
 // v2 = (k - c, b), the larger squared norm wins (v1 on a tie); normalised;
 // sign X > 0 or (X == 0 and Y > 0).  Degenerate (both candidates zero): never
 // a ridge.
+// k- alone (the same operations as eigen64's k)
+__device__ inline double eigen64_k(long long hxx, long long hyy, long long hxy, double D) {
+  double a = d_div(__ll2double_rn(hxx), D);
+  double c = d_div(__ll2double_rn(hyy), D);
+  double b = d_div(__ll2double_rn(hxy), D);
+  double half_tr = d_mul(d_add(a, c), 0.5);
+  double half_df = d_mul(d_sub(a, c), 0.5);
+  double rad = d_sqrt(d_add(d_mul(half_df, half_df), d_mul(b, b)));
+  return d_sub(half_tr, rad);
+}
+
 __device__ inline Eig64 eigen64(long long hxx, long long hyy, long long hxy, double D) {
   double a = d_div(__ll2double_rn(hxx), D);
   double c = d_div(__ll2double_rn(hyy), D);
