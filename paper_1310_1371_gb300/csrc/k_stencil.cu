@@ -12,6 +12,7 @@
 #include "rd_internal.cuh"
 #include "rd_cert.cuh"
 #include <climits>
+#include <type_traits>
 
 namespace rd {
 
@@ -305,12 +306,13 @@ __global__ void __launch_bounds__(ST_THREADS, 5) k_stencil_ridge(StencilArgs a) 
   // then stay below 2^28.
   const bool wide = sizeof(Tin) > 1 && s_imax > a.narrow_max;
   float lmax = 0.0f;
-  for (int part = wide ? 0 : 2; part < (wide ? 2 : 3); ++part) {
   // part 0: high bytes, 1: low bytes, 2: the inputs themselves; the last
-  // part rounds L' to FP32
-  const uint32_t shift = part == 0 ? 8u : 0u, mask = part == 1 ? 0xffu : 0xffffffffu;
-  const bool last = part != 0;
-  if (part == 1) __syncthreads();  // the high part's vertical pass has read sP
+  // part rounds L' to FP32.  The part is a compile-time constant of each
+  // instance, so the narrow case extracts nothing.
+  auto smooth = [&](auto part_c) {
+  constexpr int part = decltype(part_c)::value;
+  constexpr uint32_t shift = part == 0 ? 8u : 0u, mask = part == 1 ? 0xffu : 0xffffffffu;
+  constexpr bool last = part != 0;
 
   // ---- B: horizontal Gaussian, exact u32 (sum Q_i I < 2^31)
   if constexpr (RC > 0) {
@@ -371,9 +373,9 @@ __global__ void __launch_bounds__(ST_THREADS, 5) k_stencil_ridge(StencilArgs a) 
           acc += (unsigned long long)(uint32_t)a.taps.q[j] * (unsigned long long)(w[j + o] + w[2 * RC - j + o]);
         if (ly0 + o < LH) {
           const int idx = (ly0 + o) * PW + px;
-          if (part == 1) acc += sL[idx] << 8;
+          if constexpr (part == 1) acc += sL[idx] << 8;
           sL[idx] = acc;
-          if (last) {
+          if constexpr (last) {
             const float fv = __ull2float_rn(acc);
             sLf[idx] = fv;
             lmax = fmaxf(lmax, fv);
@@ -388,16 +390,23 @@ __global__ void __launch_bounds__(ST_THREADS, 5) k_stencil_ridge(StencilArgs a) 
       unsigned long long acc = (unsigned long long)(uint32_t)q[R] * col[R * PWs];
       for (int j = 0; j < R; ++j)
         acc += (unsigned long long)(uint32_t)q[j] * (unsigned long long)(col[j * PWs] + col[(2 * R - j) * PWs]);
-      if (part == 1) acc += sL[i] << 8;
+      if constexpr (part == 1) acc += sL[i] << 8;
       sL[i] = acc;
-      if (last) {
+      if constexpr (last) {
         const float fl = __ull2float_rn(acc);
         sLf[i] = fl;
         lmax = fmaxf(lmax, fl);
       }
     }
   }
-  }  // parts
+  };
+  if (wide) {
+    smooth(std::integral_constant<int, 0>{});
+    __syncthreads();  // the high part's vertical pass has read sP
+    smooth(std::integral_constant<int, 1>{});
+  } else {
+    smooth(std::integral_constant<int, 2>{});
+  }
   {
     const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(lmax));
     if ((tid & 31) == 0) atomicMax(&s_lmax, m);

@@ -109,23 +109,28 @@ __device__ __forceinline__ int ridge_fast(const float* sK, const float* sE, int 
     int cx1 = fx == 0.0f ? cx0 : min(cx0 + 1, W - 1);
     int cy1 = fy == 0.0f ? cy0 : min(cy0 + 1, H - 1);
     int lx0 = hx + (cx0 - gx), lx1 = hx + (cx1 - gx), ly0 = hy + (cy0 - gy), ly1 = hy + (cy1 - gy);
-    float k00 = sK[ly0 * stride + lx0], k01 = sK[ly0 * stride + lx1], k10 = sK[ly1 * stride + lx0],
-          k11 = sK[ly1 * stride + lx1];
+    int i00 = ly0 * stride + lx0, i01 = ly0 * stride + lx1, i10 = ly1 * stride + lx0, i11 = ly1 * stride + lx1;
+    float k00 = sK[i00], k01 = sK[i01], k10 = sK[i10], k11 = sK[i11];
     float gxw = 1.0f - fx, gyw = 1.0f - fy;
     float kt = gyw * (gxw * k00 + fx * k01) + fy * (gxw * k10 + fx * k11);
-    // the corner set, as offsets from p
+    float kmax = fmaxf(fmaxf(k00, k01), fmaxf(k10, k11));
+    float kmin = fminf(fminf(k00, k01), fminf(k10, k11));
+    float ekc = fmaxf(fmaxf(sE[i00], sE[i01]), fmaxf(sE[i10], sE[i11]));
+    // the corner set grows where the box crosses a cell edge (rare): all
+    // columns (rows) within one pixel of p along that axis, in the image
     const bool ex = eX > 0.0f && fabsf(ox - rintf(ox)) <= eX;
     const bool ey = eX > 0.0f && fabsf(oy - rintf(oy)) <= eX;
-    const int xa = ex ? max(-1, -gx) : cx0 - gx, xb = ex ? min(1, W - 1 - gx) : cx1 - gx;
-    const int ya = ey ? max(-1, -gy) : cy0 - gy, yb = ey ? min(1, H - 1 - gy) : cy1 - gy;
-    float kmax = k00, kmin = k00, ekc = 0.0f;
-    for (int dy = ya; dy <= yb; ++dy) {
-      const int row = (hy + dy) * stride + hx;
-      for (int dx = xa; dx <= xb; ++dx) {
-        const float kc = sK[row + dx];
-        kmax = fmaxf(kmax, kc);
-        kmin = fminf(kmin, kc);
-        ekc = fmaxf(ekc, sE[row + dx]);
+    if (ex || ey) {
+      const int xa = ex ? max(-1, -gx) : cx0 - gx, xb = ex ? min(1, W - 1 - gx) : cx1 - gx;
+      const int ya = ey ? max(-1, -gy) : cy0 - gy, yb = ey ? min(1, H - 1 - gy) : cy1 - gy;
+      for (int dy = ya; dy <= yb; ++dy) {
+        const int row = (hy + dy) * stride + hx;
+        for (int dx = xa; dx <= xb; ++dx) {
+          const float kc = sK[row + dx];
+          kmax = fmaxf(kmax, kc);
+          kmin = fminf(kmin, kc);
+          ekc = fmaxf(ekc, sE[row + dx]);
+        }
       }
     }
     float kabs = fmaxf(fabsf(kmax), fabsf(kmin));
