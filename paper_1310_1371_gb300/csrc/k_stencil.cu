@@ -535,7 +535,20 @@ __global__ void __launch_bounds__(ST_THREADS, 5) k_stencil_ridge(StencilArgs a) 
         float k2, ek2, hdf, rad;
         eig32_k(fa, fb, fc, k2, ek2, hdf, rad);
         float M = fabsf(fa) + fabsf(fb) + fabsf(fc);
-        dir_ok = eig32_dir(fb, hdf, rad, M, delta, X, Y, eX);
+        if (gx == 0 || gx == W - 1 || gy == 0 || gy == H - 1) {
+          // On a border row or column the reflect-101 extension of L' is
+          // symmetric about that line, so the exact Hxy' is 0 and X- is an
+          // exact axis: (1, 0) where Lxx < Lyy, (0, 1) where Lxx > Lyy (the
+          // other candidate vector is only rounding).  hdf is within delta
+          // (plus a relative 2^-24) of (Lxx - Lyy) / 2, so |hdf| > 2 delta
+          // fixes the sign, and the sample offsets are exact integers.
+          dir_ok = fabsf(hdf) > 2.0f * delta;
+          X = hdf < 0.0f ? 1.0f : 0.0f;
+          Y = 1.0f - X;
+          eX = 0.0f;
+        } else {
+          dir_ok = eig32_dir(fb, hdf, rad, M, delta, X, Y, eX);
+        }
       }
       const int verdict = dir_ok ? ridge_fast(sK, sE, HW2, hy, hx, gx, gy, H, W, k, ek, a.tau, X, Y, eX) : 2;
       sV[pi] = (uint8_t)verdict;

@@ -171,6 +171,13 @@ def replay(img, sigma, tau, contract):
             v = np.where(dk >= ec, 0, np.where(~(dk < -ec), 2, 1)).astype(np.int8)
             cand = v == 1
             ok, X, Y, eX = eig_dir(fb[c], hdf[c], rad[c], M[c], delta, contract)
+            # border rows and columns: the exact Hxy is 0, X- an exact axis
+            border = (xs == 0) | (xs == W - 1) | (ys == 0) | (ys == H - 1)
+            hd = hdf[c]
+            ok = np.where(border, np.abs(hd) > f32(2.0) * delta, ok)
+            X = np.where(border, np.where(hd < 0, f32(1.0), f32(0.0)), X).astype(np.float32)
+            Y = np.where(border, f32(1.0) - X, Y).astype(np.float32)
+            eX = np.where(border, f32(0.0), eX).astype(np.float32)
             v[cand & ~ok] = 2
             sel = cand & ok
             v[sel] = ridge_fast(k, sE, ys[sel], xs[sel], o, H, W, kc[sel], ec[sel], X[sel], Y[sel], eX[sel], contract)
@@ -401,6 +408,30 @@ def test_widened_corner_sets_decide_near_axis_directions():
             assert (~decided).mean() < 0.0025, float((~decided).mean())
         else:
             assert WIDENED["decided"] > 0, WIDENED
+
+
+def test_border_pixels_take_the_exact_axis_direction():
+    """On the image's border rows and columns the reflect-101 extension makes
+    the exact Hxy 0, so X- is an exact axis and the FP32 test decides border
+    pixels with exact sample offsets: on a workload crop and the bound test's
+    frames every border pixel whose k- is below tau is decided, ridges among
+    them, each with the definition's verdict."""
+    full = synth.plain_full(seed=[1002, 5]).image
+    frames = [np.ascontiguousarray(full[300:556, 200:456]), CASES[0][1], CASES[4][1]]
+    n_ridge = 0
+    for img in frames:
+        a, c, b = O.hessian(img, 2.0)
+        assert not b[0].any() and not b[-1].any() and not b[:, 0].any() and not b[:, -1].any()
+        kdef, X, Y, deg = O.eigen(a, c, b)
+        want = O.ridge_mask(kdef, X, Y, deg, float(np.float32(-2.0)))
+        v = replay(img, 2.0, -2.0, True)
+        border = np.zeros(img.shape, bool)
+        border[0, :] = border[-1, :] = border[:, 0] = border[:, -1] = True
+        cand = border & (kdef < -2.0)
+        assert cand.sum() > 50 and (v[cand] != 2).all()
+        assert not ((v != 2) & ((v == 1) != want)).any()
+        n_ridge += int((border & (v == 1)).sum())
+    assert n_ridge > 20, n_ridge
 
 
 def test_adversarial_frames_are_mostly_decided():
