@@ -91,16 +91,11 @@ __device__ __forceinline__ Grad64 grad64(long long gx, long long gy, double D, d
 // Pixels per step of the exact test (9 threads each).
 constexpr int FB_CHUNK = ST_THREADS / 9;
 
-
-
-
-// FP32 gradient (Gx, Gy) = fl(G') x fl(1/D) at Hessian-tile index c0 from
-// the row filters: the column filter s of d1 rows, and d1 of s rows.
-__device__ __forceinline__ void grad32(const float* Rs, const float* Rd1, int st, int c0, float invD, float& gx,
-                                       float& gy) {
-  const float x0 = Rd1[c0], x1 = Rd1[c0 + st], x2 = Rd1[c0 + 2 * st], x3 = Rd1[c0 + 3 * st], x4 = Rd1[c0 + 4 * st];
+// FP32 gradient (Gx, Gy) = fl(G') x fl(1/D) from the row filters of five
+// consecutive rows: the column filter s of the d1 rows, and d1 of the s rows.
+__device__ __forceinline__ void grad32_v(float x0, float x1, float x2, float x3, float x4, float y0, float y1, float y3,
+                                         float y4, float invD, float& gx, float& gy) {
   const float Gx = __fmaf_rn(6.0f, x2, __fmaf_rn(4.0f, __fadd_rn(x1, x3), __fadd_rn(x0, x4)));
-  const float y0 = Rs[c0], y1 = Rs[c0 + st], y3 = Rs[c0 + 3 * st], y4 = Rs[c0 + 4 * st];
   const float Gy = __fmaf_rn(2.0f, __fsub_rn(y3, y1), __fsub_rn(y4, y0));
   gx = __fmul_rn(Gx, invD);
   gy = __fmul_rn(Gy, invD);
@@ -108,9 +103,9 @@ __device__ __forceinline__ void grad32(const float* Rs, const float* Rd1, int st
 
 // Shared-memory layout of K1 (byte offsets, all 8-byte aligned): the exact
 // smoothed tile L' (u64, alive to the end), one region holding first the
-// input tile and the horizontal pass (u32) and then the FP32 row filters of
-// L, the rounded L (f32) whose bytes later hold the pixel lists, k- and its
-// error bound (f32), and the compaction scratch.
+// input tile and the horizontal pass (u32) and then the FP32 Hessian
+// entries (or gradient) of L, the rounded L (f32) whose bytes later hold the
+// pixel lists, k- and its error bound (f32), and the compaction scratch.
 struct StencilSmem {
   unsigned l, x, f, k, scan, total;
 };
@@ -130,12 +125,12 @@ __host__ __device__ __forceinline__ StencilSmem stencil_smem_layout(int R) {
   const unsigned HW2 = ST_TW + 2, HH2 = ST_TH + 2;
   // the horizontal pass has two spare rows that the vertical pass's last
   // window may read (their outputs are not stored)
-  const unsigned in_bytes = ((IH * IW * 2 + 15) & ~15u) + (IH + 2) * P_STRIDE * 4, rf_bytes = 3 * LH * HW2 * 4;
+  const unsigned in_bytes = ((IH * IW * 2 + 15) & ~15u) + (IH + 2) * P_STRIDE * 4, hf_bytes = 3 * HH2 * HW2 * 4;
   const unsigned lf_bytes = LH * PW * 4, list_bytes = ST_TW * ST_TH * (1 + 2 + 2);
   StencilSmem L;
   L.l = 0;
   L.x = LH * PW * 8;
-  L.f = L.x + (((in_bytes > rf_bytes ? in_bytes : rf_bytes) + 15) & ~15u);
+  L.f = L.x + (((in_bytes > hf_bytes ? in_bytes : hf_bytes) + 15) & ~15u);
   L.k = L.f + (((lf_bytes > list_bytes ? lf_bytes : list_bytes) + 15) & ~15u);
   L.scan = L.k + 2 * HH2 * HW2 * 4;
   L.total = L.scan + (ST_THREADS / 32 + 1) * 4;
@@ -173,16 +168,16 @@ __global__ void __launch_bounds__(ST_THREADS, 5) k_stencil_ridge(StencilArgs a) 
 
   // shared memory carve-up (8-byte aligned pieces first).  The input tile
   // and the horizontal pass (sI, sP) are dead once the vertical pass is
-  // done, and the row filters are written after it, so they share bytes;
-  // the rounded L is dead after the row filters and its bytes take the
-  // pixel lists.
+  // done, and the FP32 Hessian entries are written after it, so they share
+  // bytes; the rounded L is dead after the Hessian pass and its bytes take
+  // the pixel lists.
   const StencilSmem Ls = stencil_smem_layout(R);
   unsigned long long* sL = reinterpret_cast<unsigned long long*>(smem + Ls.l);  // LH*PW
   uint16_t* sI = reinterpret_cast<uint16_t*>(smem + Ls.x);                     // IH*IW, from column x0 - ORG
   uint32_t* sP = reinterpret_cast<uint32_t*>(smem + Ls.x + ((IH * IW * 2 + 15) & ~15));  // IH*PWs
-  float* sRs = reinterpret_cast<float*>(smem + Ls.x);                          // LH*HW2 each
-  float* sRd2 = sRs + LH * HW2;
-  float* sRd1 = sRd2 + LH * HW2;
+  float* sHa = reinterpret_cast<float*>(smem + Ls.x);                          // HH2*HW2 each
+  float* sHb = sHa + HH2 * HW2;
+  float* sHc = sHb + HH2 * HW2;
   float* sLf = reinterpret_cast<float*>(smem + Ls.f);                          // LH*PW
   uint16_t* sU = reinterpret_cast<uint16_t*>(smem + Ls.f);                     // undecided pixels
   uint16_t* sR = sU + ST_TW * ST_TH;                                           // ridge pixels
@@ -413,18 +408,12 @@ __global__ void __launch_bounds__(ST_THREADS, 5) k_stencil_ridge(StencilArgs a) 
   }
   __syncthreads();
 
-  // ---- D: FP32 Hessian of the rounded L and FP32 k- with its error bound,
-  //         on the tile plus a one-pixel ring.  D1: the row filters s, d2
-  //         and d1 of each row; D2: the column filters (hess32).
-  for (int i = tid; i < LH * HW2; i += ST_THREADS) {
-    const int ly = i / HW2, hx = i - ly * HW2;
-    const float* row = sLf + ly * PW + hx;
-    const float l0 = row[0], l1 = row[1], l2 = row[2], l3 = row[3], l4 = row[4];
-    const float e = __fadd_rn(l0, l4);
-    sRs[i] = __fmaf_rn(6.0f, l2, __fmaf_rn(4.0f, __fadd_rn(l1, l3), e));
-    sRd2[i] = __fmaf_rn(-2.0f, l2, e);
-    sRd1[i] = __fmaf_rn(2.0f, __fsub_rn(l3, l1), __fsub_rn(l4, l0));
-  }
+  // ---- D: FP32 Hessian (gradient) of the rounded L and FP32 k- with its
+  //         error bound on the tile plus a one-pixel ring.  A thread takes a
+  //         column strip of DRUN points: it forms the row filters s, d2 and
+  //         d1 of the strip's DRUN + 4 rows (row_filters32) in registers and
+  //         the column filters from them (hess32_v, grad32_v), and stores k-,
+  //         its bound and the entries, which the direction test reads.
   // Bound on |fl(H) x fl(1/D) - H'/D| for each entry (hess32), u = 2^-24,
   // with 0 <= L' <= Lm (Lm: the tile's largest rounded L, >= L'(1 - u)).
   // Each rounding adds at most u |its result|, times the coefficient that
@@ -439,25 +428,48 @@ __global__ void __launch_bounds__(ST_THREADS, 5) k_stencil_ridge(StencilArgs a) 
   // filter) + 96 (scaling) = 396 u Lm / D, Gy 96 + 6 x 36 + 96 + 96 = 504;
   // delta = 576 u Lm / D.
   const float delta = __fmul_ru(__fmul_ru(__uint_as_float(s_lmax), a.invD), EDGE ? 0x1.2p-15f : 0x1.cp-16f);
-  __syncthreads();
-  for (int i = tid; i < HH2 * HW2; i += ST_THREADS) {
-    if constexpr (EDGE) {
-      float gx, gy;
-      grad32(sRs, sRd1, HW2, i, a.invD, gx, gy);
-      const float g = __fsqrt_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)));
-      sK[i] = -g;
-      // |grad| is 1-Lipschitz: the inputs move it by <= sqrt 2 delta; four
-      // roundings by <= 4 u |grad|
-      sE[i] = __fmaf_ru(1.5f, delta, 4.0f * U32 * g);
-    } else {
-      float fa, fb, fc;
-      hess32(sRs, sRd2, sRd1, HW2, i, a.invD, fa, fb, fc);
-      float k, ek, hdf, rad;
-      eig32_k(fa, fb, fc, k, ek, hdf, rad);
-      sK[i] = k;
-      // an eigenvalue moves by at most the spectral norm of the perturbation,
-      // which is at most its Frobenius norm, <= 2 delta
-      sE[i] = __fmaf_ru(3.0f, delta, ek);
+  {
+    constexpr int DRUN = 5;
+    constexpr int NSTRIP = (ST_TH + 2 + DRUN - 1) / DRUN;
+    for (int t = tid; t < NSTRIP * HW2; t += ST_THREADS) {
+      const int strip = t / HW2, hx = t - strip * HW2;
+      const int hy0 = strip * DRUN;
+      float rs[DRUN + 4], rd2[DRUN + 4], rd1[DRUN + 4];
+#pragma unroll
+      for (int r = 0; r < DRUN + 4; ++r) {
+        // rows past the tile's last point repeat its last row (not used)
+        const int ly = min(hy0 + r, LH - 1);
+        row_filters32(sLf + ly * PW + hx, rs[r], rd2[r], rd1[r]);
+        if (r < 4) continue;
+        const int o = r - 4;
+        if (hy0 + o >= HH2) continue;
+        const int i = (hy0 + o) * HW2 + hx;
+        if constexpr (EDGE) {
+          float gx, gy;
+          grad32_v(rd1[o], rd1[o + 1], rd1[o + 2], rd1[o + 3], rd1[o + 4], rs[o], rs[o + 1], rs[o + 3], rs[o + 4],
+                   a.invD, gx, gy);
+          const float g = __fsqrt_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)));
+          sK[i] = -g;
+          // |grad| is 1-Lipschitz: the inputs move it by <= sqrt 2 delta; four
+          // roundings by <= 4 u |grad|
+          sE[i] = __fmaf_ru(1.5f, delta, 4.0f * U32 * g);
+          sHa[i] = gx;
+          sHb[i] = gy;
+        } else {
+          float fa, fb, fc;
+          hess32_v(rd2[o], rd2[o + 1], rd2[o + 2], rd2[o + 3], rd2[o + 4], rs[o], rs[o + 2], rs[o + 4], rd1[o],
+                   rd1[o + 1], rd1[o + 3], rd1[o + 4], a.invD, fa, fb, fc);
+          float k, ek, hdf, rad;
+          eig32_k(fa, fb, fc, k, ek, hdf, rad);
+          sK[i] = k;
+          // an eigenvalue moves by at most the spectral norm of the
+          // perturbation, which is at most its Frobenius norm, <= 2 delta
+          sE[i] = __fmaf_ru(3.0f, delta, ek);
+          sHa[i] = fa;
+          sHb[i] = fb;
+          sHc[i] = fc;
+        }
+      }
     }
   }
   __syncthreads();
@@ -518,8 +530,7 @@ __global__ void __launch_bounds__(ST_THREADS, 5) k_stencil_ridge(StencilArgs a) 
       if constexpr (EDGE) {
         // unit gradient: (Gx, Gy) moves by <= sqrt 2 delta, so X by <=
         // 2 sqrt 2 delta / |grad| plus the roundings
-        float gxf, gyf;
-        grad32(sRs, sRd1, HW2, c, a.invD, gxf, gyf);
+        const float gxf = sHa[c], gyf = sHb[c];
         const float g = -k;
         dir_ok = g > 4.0f * delta && g > 0.0f;
         X = __fdiv_rn(gxf, g);
@@ -530,8 +541,7 @@ __global__ void __launch_bounds__(ST_THREADS, 5) k_stencil_ridge(StencilArgs a) 
         }
         eX = 3.0f * delta / (g - 2.0f * delta) + 4.0f * U32;
       } else {
-        float fa, fb, fc;
-        hess32(sRs, sRd2, sRd1, HW2, c, a.invD, fa, fb, fc);
+        const float fa = sHa[c], fb = sHb[c], fc = sHc[c];
         float k2, ek2, hdf, rad;
         eig32_k(fa, fb, fc, k2, ek2, hdf, rad);
         float M = fabsf(fa) + fabsf(fb) + fabsf(fc);
@@ -564,7 +574,7 @@ __global__ void __launch_bounds__(ST_THREADS, 5) k_stencil_ridge(StencilArgs a) 
     // exact test of the listed pixels, FB_CHUNK at a time: first one thread
     // per (pixel, neighbour) for the exact k- of the 3x3 neighbourhood (the
     // bilinear corners of both samples lie in it) and the centre's X-, then
-    // one thread per pixel for the decision.  The row filters are dead now.
+    // one thread per pixel for the decision.  The FP32 entries are dead now.
     double* sKn = reinterpret_cast<double*>(smem + Ls.x);  // FB_CHUNK x 9
     double* sXc = sKn + FB_CHUNK * 9;                      // FB_CHUNK x 2
     uint8_t* sDg = reinterpret_cast<uint8_t*>(sXc + FB_CHUNK * 2);

@@ -142,21 +142,39 @@ __device__ __forceinline__ int ridge_fast(const float* sK, const float* sE, int 
   return verdict;
 }
 
-// FP32 Hessian entries (a, b, c) = fl(H) x fl(1/D) at Hessian-tile index c0
-// from the row filters (row stride st): the column filters s, d2 and d1
-// over rows c0, c0 + st, ..., c0 + 4 st, each operation correctly rounded in
-// the written order (no contraction).
-__device__ __forceinline__ void hess32(const float* Rs, const float* Rd2, const float* Rd1, int st, int c0, float invD,
-                                       float& fa, float& fb, float& fc) {
-  const float x0 = Rd2[c0], x1 = Rd2[c0 + st], x2 = Rd2[c0 + 2 * st], x3 = Rd2[c0 + 3 * st], x4 = Rd2[c0 + 4 * st];
+// FP32 row filters of one Hessian-tile row point from five consecutive
+// rounded L values: s = l0 + 4 (l1 + l3) + 6 l2 + l4, d2 = l0 - 2 l2 + l4,
+// d1 = (l4 - l0) + 2 (l3 - l1), each operation correctly rounded in the
+// written order.
+__device__ __forceinline__ void row_filters32(const float* row, float& rs, float& rd2, float& rd1) {
+  const float l0 = row[0], l1 = row[1], l2 = row[2], l3 = row[3], l4 = row[4];
+  const float e = __fadd_rn(l0, l4);
+  rs = __fmaf_rn(6.0f, l2, __fmaf_rn(4.0f, __fadd_rn(l1, l3), e));
+  rd2 = __fmaf_rn(-2.0f, l2, e);
+  rd1 = __fmaf_rn(2.0f, __fsub_rn(l3, l1), __fsub_rn(l4, l0));
+}
+
+// FP32 Hessian entries (a, b, c) = fl(H) x fl(1/D) from the row filters of
+// five consecutive rows: the column filters s over d2 (Lxx), d2 over s (Lyy)
+// and d1 over d1 (Lxy), each operation correctly rounded in the written
+// order (no contraction).
+__device__ __forceinline__ void hess32_v(float x0, float x1, float x2, float x3, float x4, float y0, float y2, float y4,
+                                         float z0, float z1, float z3, float z4, float invD, float& fa, float& fb,
+                                         float& fc) {
   const float hxx = __fmaf_rn(6.0f, x2, __fmaf_rn(4.0f, __fadd_rn(x1, x3), __fadd_rn(x0, x4)));
-  const float y0 = Rs[c0], y2 = Rs[c0 + 2 * st], y4 = Rs[c0 + 4 * st];
   const float hyy = __fmaf_rn(-2.0f, y2, __fadd_rn(y0, y4));
-  const float z0 = Rd1[c0], z1 = Rd1[c0 + st], z3 = Rd1[c0 + 3 * st], z4 = Rd1[c0 + 4 * st];
   const float hxy = __fmaf_rn(2.0f, __fsub_rn(z3, z1), __fsub_rn(z4, z0));
   fa = __fmul_rn(hxx, invD);
   fb = __fmul_rn(hxy, invD);
   fc = __fmul_rn(hyy, invD);
+}
+
+// The same at Hessian-tile index c0 from row-filter arrays (row stride st),
+// over rows c0, c0 + st, ..., c0 + 4 st.
+__device__ __forceinline__ void hess32(const float* Rs, const float* Rd2, const float* Rd1, int st, int c0, float invD,
+                                       float& fa, float& fb, float& fc) {
+  hess32_v(Rd2[c0], Rd2[c0 + st], Rd2[c0 + 2 * st], Rd2[c0 + 3 * st], Rd2[c0 + 4 * st], Rs[c0], Rs[c0 + 2 * st],
+           Rs[c0 + 4 * st], Rd1[c0], Rd1[c0 + st], Rd1[c0 + 3 * st], Rd1[c0 + 4 * st], invD, fa, fb, fc);
 }
 
 }  // namespace rd
