@@ -112,20 +112,25 @@ struct StencilSmem {
 // The input tile is stored as u16 from column x0 - ORG, ORG = HALO rounded
 // up to 16 pixels, so that interior tiles fill whole rows with aligned
 // 16-byte copies; its row stride is a multiple of 8 elements (16 bytes).
-// The horizontal pass's row stride is even, so that a thread's two outputs
-// go out as one 8-byte store.
+// The horizontal pass's row stride is a multiple of 4, so that a thread's
+// four outputs go out as one 16-byte store.
 constexpr __host__ __device__ int in_org(int halo) { return (halo + 15) & ~15; }
 constexpr __host__ __device__ int in_stride(int halo) { return ST_TW + 2 * in_org(halo) + 8; }
-constexpr int P_STRIDE = ST_TW + 8;  // >= ST_TW + 6 outputs, even
+constexpr int P_STRIDE = ST_TW + 8;  // >= ST_TW + 6 outputs, a multiple of 4
+// Rows per thread of the vertical pass, and the horizontal pass's spare rows
+// that its last window reads past the tile (outputs not stored).
+constexpr int C_RUN = 7;
+constexpr int C_SPARE = (ST_TH + 6 + C_RUN - 1) / C_RUN * C_RUN - (ST_TH + 6);
 
 __host__ __device__ __forceinline__ StencilSmem stencil_smem_layout(int R) {
   const int HALO = R + 3;
   const unsigned IW = in_stride(HALO), IH = ST_TH + 2 * HALO;
   const unsigned PW = ST_TW + 6, LH = ST_TH + 6;
   const unsigned HW2 = ST_TW + 2, HH2 = ST_TH + 2;
-  // the horizontal pass has two spare rows that the vertical pass's last
+  // the horizontal pass has C_SPARE spare rows that the vertical pass's last
   // window may read (their outputs are not stored)
-  const unsigned in_bytes = ((IH * IW * 2 + 15) & ~15u) + (IH + 2) * P_STRIDE * 4, hf_bytes = 3 * HH2 * HW2 * 4;
+  const unsigned in_bytes = ((IH * IW * 2 + 15) & ~15u) + (IH + C_SPARE) * P_STRIDE * 4,
+                 hf_bytes = 3 * HH2 * HW2 * 4;
   const unsigned lf_bytes = LH * PW * 4, list_bytes = ST_TW * ST_TH * (1 + 2 + 2);
   StencilSmem L;
   L.l = 0;
@@ -311,24 +316,27 @@ __global__ void __launch_bounds__(ST_THREADS, 5) k_stencil_ridge(StencilArgs a) 
 
   // ---- B: horizontal Gaussian, exact u32 (sum Q_i I < 2^31)
   if constexpr (RC > 0) {
-    // two adjacent outputs per thread from 2R + 2 inputs; the lanes of a warp
-    // take neighbouring output pairs of a row (distinct banks)
-    constexpr int NW = 2 * RC + 2;
-    constexpr int NP = (ST_TW + 6) / 2;
+    // four adjacent outputs per thread from 2R + 4 inputs, stored as one
+    // 16-byte vector; the lanes of a warp take neighbouring output quads of a
+    // row.  The last quad's two outputs past ST_TW + 6 are not read later.
+    constexpr int NW = 2 * RC + 4;
+    constexpr int NQ = (ST_TW + 6 + 3) / 4;
     constexpr int CO = in_org(RC + 3) - (RC + 3);
-    for (int i = tid; i < IH * NP; i += ST_THREADS) {
-      const int iy = i / NP, pp = i - iy * NP;
-      const uint16_t* row = sI + iy * IW + CO + 2 * pp;
+    static_assert(4 * NQ <= P_STRIDE, "the horizontal pass's row holds every quad");
+    for (int i = tid; i < IH * NQ; i += ST_THREADS) {
+      const int iy = i / NQ, qq = i - iy * NQ;
+      const uint16_t* row = sI + iy * IW + CO + 4 * qq;
       uint32_t w[NW];
 #pragma unroll
       for (int k = 0; k < NW; ++k) w[k] = ((uint32_t)row[k] >> shift) & mask;
-      uint32_t acc0 = (uint32_t)a.taps.q[RC] * w[RC], acc1 = (uint32_t)a.taps.q[RC] * w[RC + 1];
+      uint32_t acc[4];
 #pragma unroll
-      for (int j = 0; j < RC; ++j) {
-        acc0 += (uint32_t)a.taps.q[j] * (w[j] + w[2 * RC - j]);
-        acc1 += (uint32_t)a.taps.q[j] * (w[j + 1] + w[2 * RC + 1 - j]);
+      for (int o = 0; o < 4; ++o) {
+        acc[o] = (uint32_t)a.taps.q[RC] * w[RC + o];
+#pragma unroll
+        for (int j = 0; j < RC; ++j) acc[o] += (uint32_t)a.taps.q[j] * (w[j + o] + w[2 * RC - j + o]);
       }
-      *reinterpret_cast<uint2*>(sP + iy * PWs + 2 * pp) = make_uint2(acc0, acc1);
+      *reinterpret_cast<uint4*>(sP + iy * PWs + 4 * qq) = make_uint4(acc[0], acc[1], acc[2], acc[3]);
     }
   } else {
     const int coff = ORG - HALO;
@@ -347,11 +355,11 @@ __global__ void __launch_bounds__(ST_THREADS, 5) k_stencil_ridge(StencilArgs a) 
   //      (a pair Q_j (P_j + P_2R-j) of horizontal sums stays below 2^32);
   //      also L' rounded to FP32 and the tile's largest value of it
   if constexpr (RC > 0) {
-    // three vertically adjacent outputs per thread from one window of 2R + 3
-    // horizontal sums; lanes take columns.  The last run's third row is past
-    // the tile: its window reads one row beyond the horizontal pass (the
-    // buffer has that row), and it is not stored.
-    constexpr int RUN = 3, NW = 2 * RC + RUN;
+    // C_RUN vertically adjacent outputs per thread from one window of
+    // 2R + C_RUN horizontal sums; lanes take columns, and one pass covers the
+    // tile.  The last run's rows past the tile read the horizontal pass's
+    // spare rows (never written) and are not stored.
+    constexpr int RUN = C_RUN, NW = 2 * RC + RUN;
     constexpr int NRUN = (ST_TH + 6 + RUN - 1) / RUN;
     for (int i = tid; i < NRUN * PW; i += ST_THREADS) {
       const int lr = i / PW, px = i - lr * PW;
