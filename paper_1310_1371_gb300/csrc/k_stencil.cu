@@ -489,6 +489,7 @@ __global__ void __launch_bounds__(ST_THREADS, 5) k_stencil_ridge(StencilArgs a) 
   uint16_t* sC = sR;  // the candidate list; the ridge list takes these bytes after the exact test
   {
     const int lane = tid & 31;
+    unsigned m[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int pi = tid + j * ST_THREADS;
@@ -511,14 +512,21 @@ __global__ void __launch_bounds__(ST_THREADS, 5) k_stencil_ridge(StencilArgs a) 
         }
       }
       sV[pi] = verdict;
-      const unsigned m = __ballot_sync(0xffffffffu, cand);
-      if (m) {
-        const int leader = __ffs(m) - 1;
-        int base = 0;
-        if (lane == leader) base = atomicAdd(&s_ncand, __popc(m));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        const int k = base + __popc(m & ((1u << lane) - 1u));
-        if (cand && RD_GUARD(k < ST_TW * ST_TH, a.stats)) sC[k] = (uint16_t)pi;
+      m[j] = __ballot_sync(0xffffffffu, cand);
+    }
+    // one list reservation per warp for its four rows of candidates
+    const int n = __popc(m[0]) + __popc(m[1]) + __popc(m[2]) + __popc(m[3]);
+    if (n) {
+      int base = 0;
+      if (lane == 0) base = atomicAdd(&s_ncand, n);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int k = base + __popc(m[j] & below);
+        if (((m[j] >> lane) & 1u) && RD_GUARD(k < ST_TW * ST_TH, a.stats))
+          sC[k] = (uint16_t)(tid + j * ST_THREADS);
+        base += __popc(m[j]);
       }
     }
   }
