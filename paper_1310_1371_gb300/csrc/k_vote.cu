@@ -69,14 +69,38 @@ __device__ __forceinline__ SegTiles seg_tiles(const BinArgs& a, float px, float 
 // and the group leader makes one atomic for the group.  The entry order
 // inside a bin is immaterial downstream (votes commute; peaks are sorted
 // before the fit).
+//
+// With a.cta_cnt set (frames of at most BIN_SMEM_MAX bins) the atomics stay
+// in shared memory: the count pass counts the CTA's entries per bin of its
+// frame and stores them per (bin, CTA), adding them to the bin totals; the
+// fill pass starts each bin at its offset plus the counts of the frame's
+// earlier CTAs, so that every CTA fills a range of its own in each bin.
 template <bool FILL, int T>
 __global__ void __launch_bounds__(256) k_bin(BinArgs a) {
+  extern __shared__ int s_bin[];  // per bin of the frame: count (count pass) or next position (fill pass)
   const int lane = threadIdx.x & 31;
   const int gstride = gridDim.x * blockDim.x;
   const int wbase = blockIdx.x * blockDim.x + (threadIdx.x & ~31);
   const int f = blockIdx.y;
   const int cnt = min(a.rl.count[f], a.rl.cap);
-  const long long fbin = (long long)f * a.n_aty * a.n_atx * a.n_slabs;
+  const int nbf = a.n_aty * a.n_atx * a.n_slabs;
+  const long long fbin = (long long)f * nbf;
+  const bool local = a.cta_cnt != nullptr;
+  if (local) {
+    if (!FILL) {
+      for (int b = threadIdx.x; b < nbf; b += blockDim.x) s_bin[b] = 0;
+    } else {
+      // one warp per bin: the bin's offset plus the frame's earlier CTAs' counts
+      for (int b = threadIdx.x >> 5; b < nbf; b += blockDim.x >> 5) {
+        const int* cc = a.cta_cnt + (size_t)(fbin + b) * gridDim.x;
+        int sum = 0;
+        for (int c = lane; c < (int)blockIdx.x; c += 32) sum += cc[c];
+        sum = __reduce_add_sync(0xffffffffu, sum);
+        if (lane == 0) s_bin[b] = a.bin_off[fbin + b] + sum;
+      }
+    }
+    __syncthreads();
+  }
   for (int s = 0; s < a.n_slabs; ++s) {
     const int4 sl = a.slabs[s];
     const float r0 = (float)(sl.x - 1), r1 = (float)(sl.y + 1);
@@ -119,12 +143,19 @@ __global__ void __launch_bounds__(256) k_bin(BinArgs a) {
         const int n_grp = __popc(grp);
         const long long b = fbin + key;
         if (!FILL) {
-          if (lane == leader) atomicAdd(&a.bin_cnt[b], n_grp);
+          if (lane == leader) {
+            if (local)
+              atomicAdd(&s_bin[key], n_grp);
+            else
+              atomicAdd(&a.bin_cnt[b], n_grp);
+          }
         } else {
-          int first = 0;
-          if (lane == leader) first = atomicAdd(&a.bin_fill[b], n_grp);
+          long long first = 0;
+          if (lane == leader)
+            first = local ? (long long)atomicAdd(&s_bin[key], n_grp)
+                          : (long long)a.bin_off[b] + atomicAdd(&a.bin_fill[b], n_grp);
           first = __shfl_sync(grp, first, leader);
-          const long long pos = (long long)a.bin_off[b] + first + __popc(grp & ((1u << lane) - 1u));
+          const long long pos = first + __popc(grp & ((1u << lane) - 1u));
           if (pos < a.pool_cap) {
             const float sgn = sg == 0 ? 1.0f : -1.0f;
             // A direction with a component exactly 0 (both parts) is an exact
@@ -144,6 +175,14 @@ __global__ void __launch_bounds__(256) k_bin(BinArgs a) {
           }
         }
       }
+    }
+  }
+  if (!FILL && local) {
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
+      const int v = s_bin[b];
+      a.cta_cnt[(size_t)(fbin + b) * gridDim.x + blockIdx.x] = v;
+      if (v) atomicAdd(&a.bin_cnt[fbin + b], v);
     }
   }
 }
@@ -1044,16 +1083,21 @@ __device__ __forceinline__ void vote_bin_sparse(const VoteArgs& a, const int b, 
 cudaError_t launch_bins(const BinArgs& a, int n_sm, cudaStream_t st, long long n_bins, int* block_sums,
                         long long* total_dev) {
   cudaError_t e;
-  // about 8 CTAs per SM in total, split over the frames (grid rows)
-  const dim3 grid((unsigned)std::max(1, (n_sm * 8 + a.n_frames - 1) / a.n_frames), (unsigned)a.n_frames);
+  // about 8 CTAs per SM in total, split over the frames (grid rows); with
+  // per-CTA counts (a.cta_cnt) at most BIN_GRID_MAX CTAs per frame
+  int gx = std::max(1, (n_sm * 8 + a.n_frames - 1) / a.n_frames);
+  const int nbf = a.n_aty * a.n_atx * a.n_slabs;
+  if (a.cta_cnt) gx = std::min(gx, BIN_GRID_MAX);
+  const size_t smem = a.cta_cnt ? sizeof(int) * (size_t)nbf : 0;
+  const dim3 grid((unsigned)gx, (unsigned)a.n_frames);
   if (a.T == ACC_T)
-    k_bin<false, ACC_T><<<grid, 256, 0, st>>>(a);
+    k_bin<false, ACC_T><<<grid, 256, smem, st>>>(a);
   else if (a.T == ACC_T_MID)
-    k_bin<false, ACC_T_MID><<<grid, 256, 0, st>>>(a);
+    k_bin<false, ACC_T_MID><<<grid, 256, smem, st>>>(a);
   else if (a.T == ACC_T_LARGE)
-    k_bin<false, ACC_T_LARGE><<<grid, 256, 0, st>>>(a);
+    k_bin<false, ACC_T_LARGE><<<grid, 256, smem, st>>>(a);
   else
-    k_bin<false, ACC_T_SMALL><<<grid, 256, 0, st>>>(a);
+    k_bin<false, ACC_T_SMALL><<<grid, 256, smem, st>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   int nb = (int)((n_bins + 1023) / 1024);
   k_scan_blocks<<<nb, 1024, 0, st>>>(a.bin_cnt, const_cast<int*>(a.bin_off), block_sums, n_bins);
@@ -1061,13 +1105,13 @@ cudaError_t launch_bins(const BinArgs& a, int n_sm, cudaStream_t st, long long n
   k_scan_add<<<nb, 1024, 0, st>>>(const_cast<int*>(a.bin_off), block_sums, n_bins);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (a.T == ACC_T)
-    k_bin<true, ACC_T><<<grid, 256, 0, st>>>(a);
+    k_bin<true, ACC_T><<<grid, 256, smem, st>>>(a);
   else if (a.T == ACC_T_MID)
-    k_bin<true, ACC_T_MID><<<grid, 256, 0, st>>>(a);
+    k_bin<true, ACC_T_MID><<<grid, 256, smem, st>>>(a);
   else if (a.T == ACC_T_LARGE)
-    k_bin<true, ACC_T_LARGE><<<grid, 256, 0, st>>>(a);
+    k_bin<true, ACC_T_LARGE><<<grid, 256, smem, st>>>(a);
   else
-    k_bin<true, ACC_T_SMALL><<<grid, 256, 0, st>>>(a);
+    k_bin<true, ACC_T_SMALL><<<grid, 256, smem, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -62,6 +62,7 @@ struct rd_ctx {
   int* bin_cnt = nullptr;
   int* bin_off = nullptr;
   int* bin_fill = nullptr;
+  int* cta_cnt = nullptr;  // per (frame, bin, binning CTA) entry counts; null: frames over BIN_SMEM_MAX bins
   int* block_sums = nullptr;
   long long* bin_total = nullptr;
   uint4* pool = nullptr;
@@ -183,8 +184,8 @@ static rd_status fail(rd_ctx* c, rd_status s, const std::string& m) {
 
 static void free_all(rd_ctx* c) {
   void* ptrs[] = {c->slabs, c->q_rad, c->qq_off, c->qq_tab, c->qp_off, c->qp_tab, c->fb_list, c->fb_count, c->queue, c->queue_ctr, c->nthr, c->rl.xy, c->rl.dir, c->rl.kvote, c->rl.hess,
-                  c->rl.count, c->rl.tile_off, c->rl.tile_cnt, c->bin_cnt, c->bin_off, c->bin_fill, c->block_sums,
-                  c->bin_total, c->pool, c->peaks, c->peak_count, c->stats, c->stage_frames, c->stage_rings,
+                  c->rl.count, c->rl.tile_off, c->rl.tile_cnt, c->bin_cnt, c->bin_off, c->bin_fill, c->cta_cnt,
+                  c->block_sums, c->bin_total, c->pool, c->peaks, c->peak_count, c->stats, c->stage_frames, c->stage_rings,
                   c->stage_counts, c->stage_offsets};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -420,7 +421,13 @@ extern "C" rd_status rd_create_ex(const rd_params* params, int max_H, int max_W,
     if (c->n_bins_max > INT_MAX / 4) {
       return fail(nullptr, RD_E_INVAL, "too many accumulator bins (frames x tiles x slabs > 2^31): lower max_batch");
     }
-    bool ok = dalloc(c, &c->slabs, c->n_slabs) && dalloc(c, &c->q_rad, c->n_levels) &&
+    // per-CTA bin counts of shared-memory binning: frames x bins x CTAs per
+    // frame, at most min(BIN_GRID_MAX, ceil(8 SMs / frames)) CTAs per frame
+    const long long nbf_max = (long long)n_atx * n_aty * c->n_slabs;
+    const long long cta_cols = std::min<long long>((long long)BIN_GRID_MAX * max_batch, 8LL * c->n_sm + max_batch);
+    const bool bin_local = nbf_max <= BIN_SMEM_MAX;
+    bool ok = (!bin_local || dalloc(c, &c->cta_cnt, (size_t)(nbf_max * cta_cols))) &&
+              dalloc(c, &c->slabs, c->n_slabs) && dalloc(c, &c->q_rad, c->n_levels) &&
               dalloc(c, &c->qq_off, h_qqoff.size()) && dalloc(c, &c->qq_tab, h_qqtab.size()) &&
               dalloc(c, &c->qp_off, h_qpoff.size()) && dalloc(c, &c->qp_tab, h_qptab.size()) &&
               dalloc(c, &c->fb_list, 4 * c->n_bins_max) && dalloc(c, &c->fb_count, 1) && dalloc(c, &c->queue, c->n_bins_max) &&
@@ -556,6 +563,7 @@ static rd_status detect_enqueue(rd_ctx* c, const void* frames_dev, int n, int H,
   ba.bin_cnt = c->bin_cnt;
   ba.bin_off = c->bin_off;
   ba.bin_fill = c->bin_fill;
+  ba.cta_cnt = c->cta_cnt;  // null for frames over BIN_SMEM_MAX bins (allocated for the largest frame)
   ba.pool = c->pool;
   ba.pool_cap = c->pool_cap;
   ba.stats = c->stats;

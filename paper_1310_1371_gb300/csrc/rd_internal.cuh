@@ -49,6 +49,8 @@ constexpr int SLAB_LEVELS = 12;    // peak levels per r-slab of the smaller-tile
 constexpr int MAX_SLAB_LEVELS = 64;
 constexpr int DEFAULT_SLAB_LEVELS = 32;  // the automatic geometry's slab depth
 constexpr int FIT_WARPS = 8;
+constexpr int BIN_SMEM_MAX = 8192;  // bins per frame up to which binning counts in shared memory
+constexpr int BIN_GRID_MAX = 64;    // binning CTAs per frame in that mode
 // Vote-rounding margin coefficient shared by every well-conditioned ridge
 // pixel: 1.25 (|X_lo| + e_X + 2^-24) + 2^-24 with |X_lo| <= 2^-25 and the
 // direction error e_X <= 5e-12 (condition number <= 1e3).  Pixels whose own
@@ -123,6 +125,7 @@ struct BinArgs {
   int* bin_cnt;
   const int* bin_off;
   int* bin_fill;
+  int* cta_cnt;              // per (frame, bin, CTA of the frame's grid row): entries (null: global counters)
   uint4* pool;               // per entry: int16 x | int16 y << 16 in px relative to the tile region
                              // (origin 2^lc (tx T - h, ty T - h)), s X, s Y,
                              // index << 3 | exact axis << 2 | ill << 1 | (s < 0)
