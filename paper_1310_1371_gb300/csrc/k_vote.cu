@@ -828,7 +828,7 @@ __device__ __forceinline__ void vote_bin_sparse(const VoteArgs& a, const int b, 
     // hotspot registration on the increment that crosses the threshold.
     auto cast = [&](int lx, int ly) {
       if ((unsigned)(lx - lxlo) >= (unsigned)lxn || (unsigned)(ly - lylo) >= (unsigned)lyn) return;
-      if (owned && (unsigned)(lx - h) < (unsigned)T && (unsigned)(ly - h) < (unsigned)T) ++nv;
+      nv += (owned && max((unsigned)(lx - h), (unsigned)(ly - h)) < (unsigned)T) ? 1u : 0u;  // inside the tile
       const int la = ly * RW + lx;
       if (!RD_GUARD((unsigned)la < (unsigned)(RW * RW), a.stats)) return;
       const unsigned sh = (la & 1) << 4;
