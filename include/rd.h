@@ -326,11 +326,14 @@ int       rd_get_timing(rd_ctx* ctx, float* ms, int cap);
  * capture off).  The smoothed accumulator is written at hotspots only; the
  * caller zero-fills the arrays. */
 int       rd_debug_ridges(rd_ctx* ctx, int f, int32_t* xy, float* dir, int64_t* hess, int cap);
-/* rd_debug_route(ctx, 1) makes the following rd_detect calls process every
- * accumulator tile with the dense-storage voting kernel (normally used only
- * for tiles whose hotspots exceed the sparse kernel's capacities); the
- * results are identical.  0 restores the normal routing. */
-rd_status rd_debug_route(rd_ctx* ctx, int all_dense);
+/* rd_debug_route(ctx, flags) changes the routing of the following rd_detect
+ * calls; the results are identical.  Bit 0 processes every accumulator tile
+ * with the dense-storage voting kernel (normally used only for tiles whose
+ * hotspots exceed the sparse kernel's capacities).  Bit 1 bins with global
+ * atomic counters (normally used only for frames of more than 8192
+ * accumulator bins) instead of per-CTA counters in shared memory.  0
+ * restores the normal routing; other bits: RD_E_INVAL. */
+rd_status rd_debug_route(rd_ctx* ctx, int flags);
 rd_status rd_debug_capture(rd_ctx* ctx, int32_t* acc_dev, uint32_t* sm_dev);
 
 /* ---- measured peak of the voting unit --------------------------------------

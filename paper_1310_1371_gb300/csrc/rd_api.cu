@@ -77,6 +77,7 @@ struct rd_ctx {
   int32_t* dbg_acc = nullptr;
   uint32_t* dbg_sm = nullptr;
   int route_dense = 0;
+  int bin_global = 0;  // rd_debug_route bit 1: binning with global counters
   // staging for rd_detect_host
   void* stage_frames = nullptr;
   rd_ring* stage_rings = nullptr;
@@ -563,7 +564,7 @@ static rd_status detect_enqueue(rd_ctx* c, const void* frames_dev, int n, int H,
   ba.bin_cnt = c->bin_cnt;
   ba.bin_off = c->bin_off;
   ba.bin_fill = c->bin_fill;
-  ba.cta_cnt = c->cta_cnt;  // null for frames over BIN_SMEM_MAX bins (allocated for the largest frame)
+  ba.cta_cnt = c->bin_global ? nullptr : c->cta_cnt;  // null: global counters (large frames, or rd_debug_route)
   ba.pool = c->pool;
   ba.pool_cap = c->pool_cap;
   ba.stats = c->stats;
@@ -833,9 +834,10 @@ extern "C" int rd_debug_ridges(rd_ctx* c, int f, int32_t* xy, float* dir, int64_
   });
 }
 
-extern "C" rd_status rd_debug_route(rd_ctx* c, int all_dense) {
-  if (!c) return RD_E_INVAL;
-  c->route_dense = all_dense ? 1 : 0;
+extern "C" rd_status rd_debug_route(rd_ctx* c, int flags) {
+  if (!c || (flags & ~3)) return RD_E_INVAL;
+  c->route_dense = flags & 1;
+  c->bin_global = (flags >> 1) & 1;
   drop_graph(c);
   return RD_OK;
 }

@@ -430,8 +430,8 @@ class Detector:
                                      d.ctypes.data_as(POINTER(c_float)), h.ctypes.data_as(POINTER(c_int64)), n)
         return xy, d, h
 
-    def debug_route(self, all_dense: bool):
-        st = self.lib.rd_debug_route(self.ctx, 1 if all_dense else 0)
+    def debug_route(self, all_dense: bool, bin_global: bool = False):
+        st = self.lib.rd_debug_route(self.ctx, (1 if all_dense else 0) | (2 if bin_global else 0))
         if st != RD_OK:
             raise self._err(st)
 

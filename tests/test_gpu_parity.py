@@ -25,14 +25,14 @@ def torch():
     return t
 
 
-def run(torch, frames, params, capture=False, max_hw=None, dense=False):
+def run(torch, frames, params, capture=False, max_hw=None, dense=False, bin_global=False):
     from paper_1310_1371_gb300 import rd
     frames = [np.ascontiguousarray(f) for f in frames]
     H, W = frames[0].shape
     mh, mw = max_hw or (H, W)
     det = rd.Detector(params, mh, mw, len(frames))
-    if dense:
-        det.debug_route(True)
+    if dense or bin_global:
+        det.debug_route(dense, bin_global)
     t = torch.from_numpy(np.stack(frames)).cuda()
     acc = sm = None
     if capture:
@@ -233,6 +233,24 @@ def test_plain_full_batch_sampled(torch):
         ref = O.detect(frames[i], p)
         assert_rings_match(out["rings"][i], ref.rings)
         assert_ridges_match(out["ridges"][i], frames[i], p)
+
+
+def test_global_bin_counters_equal_shared_ones(torch):
+    """Binning with global atomic counters (the route of frames with more than
+    8192 accumulator bins) gives the same rings and the same vote, hotspot and
+    smoothing counts as the per-CTA shared-memory counters, on a batch of the
+    benchmark workload and on small frames with many CTAs per frame."""
+    cases = [([fr.image for fr in synth.plain_full_batch(4)], synth.PLAIN_FULL_PARAMS),
+             ([synth.plain_small(seed=s).image for s in (41, 42)], synth.PLAIN_SMALL_PARAMS)]
+    for frames, params in cases:
+        a = run(torch, frames, params)
+        b = run(torch, frames, params, bin_global=True)
+        for i in range(len(frames)):
+            for k in ("ix", "iy", "ir", "cx", "cy", "r", "score", "n_fit", "flags"):
+                assert np.array_equal(a["rings"][i][k], b["rings"][i][k]), (i, k)
+        for k in ("ridge_pixels", "votes", "peaks", "hotspots", "smooth_macs", "overflow"):
+            assert getattr(a["stats"], k) == getattr(b["stats"], k), k
+        assert a["stats"].votes > 0
 
 
 def test_crowded_bins_hand_off_to_dense(torch):
