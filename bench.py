@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 METRIC = "frames/s at 1024x1024 u16, r 8-96 (ridge-directed ring detection)"
 WORKLOAD = "plain_full: 1024x1024 u16 frames, 150 rings r 10-80 with fringes, search r 8-96, sigma 2"
 H = W = 1024
-KERNELS_PER_CALL = 13   # stencil, refine, bin count, 3 scan, bin fill, queue, vote, vote (dense fallback), sort, offsets, fit
+KERNELS_PER_CALL = 14   # stencil, refine, bin count, per-CTA bin scan, 3 scan, bin fill, queue, vote, vote (dense fallback), sort, offsets, fit
 STAGES = ["stencil_ridge", "ridge_refine", "vote_bin", "vote_accumulate_peaks", "sort_fit"]
 
 

@@ -72,9 +72,10 @@ __device__ __forceinline__ SegTiles seg_tiles(const BinArgs& a, float px, float 
 //
 // With a.cta_cnt set (frames of at most BIN_SMEM_MAX bins) the atomics stay
 // in shared memory: the count pass counts the CTA's entries per bin of its
-// frame and stores them per (bin, CTA), adding them to the bin totals; the
-// fill pass starts each bin at its offset plus the counts of the frame's
-// earlier CTAs, so that every CTA fills a range of its own in each bin.
+// frame and stores them per (bin, CTA); k_bin_cta_scan turns those into each
+// CTA's start within the bin and the bin totals; the fill pass starts each
+// bin at its offset plus that start, so that every CTA fills a range of its
+// own in each bin.
 template <bool FILL, int T>
 __global__ void __launch_bounds__(256) k_bin(BinArgs a) {
   extern __shared__ int s_bin[];  // per bin of the frame: count (count pass) or next position (fill pass)
@@ -90,14 +91,9 @@ __global__ void __launch_bounds__(256) k_bin(BinArgs a) {
     if (!FILL) {
       for (int b = threadIdx.x; b < nbf; b += blockDim.x) s_bin[b] = 0;
     } else {
-      // one warp per bin: the bin's offset plus the frame's earlier CTAs' counts
-      for (int b = threadIdx.x >> 5; b < nbf; b += blockDim.x >> 5) {
-        const int* cc = a.cta_cnt + (size_t)(fbin + b) * gridDim.x;
-        int sum = 0;
-        for (int c = lane; c < (int)blockIdx.x; c += 32) sum += cc[c];
-        sum = __reduce_add_sync(0xffffffffu, sum);
-        if (lane == 0) s_bin[b] = a.bin_off[fbin + b] + sum;
-      }
+      // the bin's offset plus the frame's earlier CTAs' counts (k_bin_cta_scan)
+      for (int b = threadIdx.x; b < nbf; b += blockDim.x)
+        s_bin[b] = a.bin_off[fbin + b] + a.cta_cnt[(size_t)(fbin + b) * gridDim.x + blockIdx.x];
     }
     __syncthreads();
   }
@@ -179,12 +175,33 @@ __global__ void __launch_bounds__(256) k_bin(BinArgs a) {
   }
   if (!FILL && local) {
     __syncthreads();
-    for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
-      const int v = s_bin[b];
-      a.cta_cnt[(size_t)(fbin + b) * gridDim.x + blockIdx.x] = v;
-      if (v) atomicAdd(&a.bin_cnt[fbin + b], v);
-    }
+    for (int b = threadIdx.x; b < nbf; b += blockDim.x)
+      a.cta_cnt[(size_t)(fbin + b) * gridDim.x + blockIdx.x] = s_bin[b];
   }
+}
+
+// Between the two binning passes with per-CTA counts: one warp per bin turns
+// the counts of the frame's gx CTAs (gx <= 64) into exclusive prefixes, in
+// place, and writes the bin's total.
+__global__ void __launch_bounds__(256) k_bin_cta_scan(int* cta_cnt, int* bin_cnt, long long n_bins, int gx) {
+  const long long b = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (b >= n_bins) return;
+  int* cc = cta_cnt + (size_t)b * gx;
+  int carry = 0;
+  for (int c0 = 0; c0 < gx; c0 += 32) {
+    const int c = c0 + lane;
+    const int v = c < gx ? cc[c] : 0;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (c < gx) cc[c] = carry + incl - v;
+    carry += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  if (lane == 0) bin_cnt[b] = carry;
 }
 
 // ---- exclusive scan of int counts (three phases, 1024 per block) ----------
@@ -1099,6 +1116,10 @@ cudaError_t launch_bins(const BinArgs& a, int n_sm, cudaStream_t st, long long n
   else
     k_bin<false, ACC_T_SMALL><<<grid, 256, smem, st>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (a.cta_cnt) {
+    k_bin_cta_scan<<<(unsigned)((n_bins + 7) / 8), 256, 0, st>>>(a.cta_cnt, a.bin_cnt, n_bins, gx);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   int nb = (int)((n_bins + 1023) / 1024);
   k_scan_blocks<<<nb, 1024, 0, st>>>(a.bin_cnt, const_cast<int*>(a.bin_off), block_sums, n_bins);
   k_scan_sums<<<1, 1024, 0, st>>>(block_sums, nb, total_dev);
