@@ -157,7 +157,7 @@ __device__ __forceinline__ uint32_t max_u16x8(uint4 q) {
 }
 
 // RC > 0: the Gaussian half-width R is the compile-time RC (taps unrolled,
-// two outputs per thread from a register window); RC = 0: R from the taps.
+// several outputs per thread from register windows); RC = 0: R from the taps.
 // EDGE: directed edges (Additional notes) -- the gradient replaces the
 // Hessian and -|grad| takes the place of k- in every test below.
 template <typename Tin, int RC, bool EDGE>
@@ -614,14 +614,15 @@ __global__ void __launch_bounds__(ST_THREADS, 5) k_stencil_ridge(StencilArgs a) 
         } else {
           long long ha, hc, hb;
           hess_exact(sL, PW, ty + n / 3, tx + n % 3, ha, hc, hb);
-          if (n == 4) {  // the centre's X- too; its neighbours need only k-
-            const Eig64 e = eigen64(ha, hc, hb, a.D64);
-            sKn[t] = e.k;
+          double ea, ec, eb;
+          const double k = eigen64_k(ha, hc, hb, a.D64, ea, ec, eb);  // all nine lanes together
+          sKn[t] = k;
+          if (n == 4) {  // the centre's X- too
+            Eig64 e;
+            eigen64_dir(ea, ec, eb, k, e);
             sXc[2 * p] = e.X;
             sXc[2 * p + 1] = e.Y;
             sDg[p] = e.degenerate ? 1 : 0;
-          } else {
-            sKn[t] = eigen64_k(ha, hc, hb, a.D64);
           }
         }
       }

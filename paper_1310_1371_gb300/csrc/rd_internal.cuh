@@ -248,43 +248,36 @@ struct Eig64 {
   bool degenerate;
 };
 
-// k- and X- of H = [[a, b], [b, c]] with a = Hxx'/D, c = Hyy'/D, b = Hxy'/D:
-// k = (a + c)/2 - sqrt(((a - c)/2)^2 + b^2); candidates v1 = (b, k - a),
-// v2 = (k - c, b), the larger squared norm wins (v1 on a tie); normalised;
-// sign X > 0 or (X == 0 and Y > 0).  Degenerate (both candidates zero): never
-// a ridge.
-// k- alone (the same operations as eigen64's k)
-__device__ inline double eigen64_k(long long hxx, long long hyy, long long hxy, double D) {
-  double a = d_div(__ll2double_rn(hxx), D);
-  double c = d_div(__ll2double_rn(hyy), D);
-  double b = d_div(__ll2double_rn(hxy), D);
+// The definition's entries a = Hxx'/D, c = Hyy'/D, b = Hxy'/D and
+// k = (a + c)/2 - sqrt(((a - c)/2)^2 + b^2), one correctly rounded
+// operation per step.
+__device__ inline double eigen64_k(long long hxx, long long hyy, long long hxy, double D, double& a, double& c,
+                                   double& b) {
+  a = d_div(__ll2double_rn(hxx), D);
+  c = d_div(__ll2double_rn(hyy), D);
+  b = d_div(__ll2double_rn(hxy), D);
   double half_tr = d_mul(d_add(a, c), 0.5);
   double half_df = d_mul(d_sub(a, c), 0.5);
   double rad = d_sqrt(d_add(d_mul(half_df, half_df), d_mul(b, b)));
   return d_sub(half_tr, rad);
 }
 
-__device__ inline Eig64 eigen64(long long hxx, long long hyy, long long hxy, double D) {
-  double a = d_div(__ll2double_rn(hxx), D);
-  double c = d_div(__ll2double_rn(hyy), D);
-  double b = d_div(__ll2double_rn(hxy), D);
-  double half_tr = d_mul(d_add(a, c), 0.5);
-  double half_df = d_mul(d_sub(a, c), 0.5);
-  double rad = d_sqrt(d_add(d_mul(half_df, half_df), d_mul(b, b)));
-  double k = d_sub(half_tr, rad);
+// X- from the entries and k: candidates v1 = (b, k - a), v2 = (k - c, b),
+// the larger squared norm wins (v1 on a tie); normalised; sign X > 0 or
+// (X == 0 and Y > 0).  Degenerate (both candidates zero): never a ridge.
+__device__ inline void eigen64_dir(double a, double c, double b, double k, Eig64& e) {
   double v1x = b, v1y = d_sub(k, a);
   double v2x = d_sub(k, c), v2y = b;
   double n1 = d_add(d_mul(v1x, v1x), d_mul(v1y, v1y));
   double n2 = d_add(d_mul(v2x, v2x), d_mul(v2y, v2y));
   bool use1 = n1 >= n2;
   double vx = use1 ? v1x : v2x, vy = use1 ? v1y : v2y, n = use1 ? n1 : n2;
-  Eig64 e;
   e.k = k;
   e.degenerate = (n == 0.0);
   if (e.degenerate) {
     e.X = 0.0;
     e.Y = 0.0;
-    return e;
+    return;
   }
   double nrm = d_sqrt(n);
   double X = d_div(vx, nrm), Y = d_div(vy, nrm);
@@ -294,6 +287,14 @@ __device__ inline Eig64 eigen64(long long hxx, long long hyy, long long hxy, dou
   }
   e.X = X;
   e.Y = Y;
+}
+
+// k- and X- of H = [[a, b], [b, c]] (the two steps above).
+__device__ inline Eig64 eigen64(long long hxx, long long hyy, long long hxy, double D) {
+  double a, c, b;
+  const double k = eigen64_k(hxx, hyy, hxy, D, a, c, b);
+  Eig64 e;
+  eigen64_dir(a, c, b, k, e);
   return e;
 }
 
