@@ -920,13 +920,15 @@ __device__ __forceinline__ void vote_bin_sparse(const VoteArgs& a, const int b, 
     __syncthreads();
     if (s_abort) break;  // uniform: read after the barrier
 
-    // ---- phase 2: hash this level's hotspots (thread per hotspot; the peak
-    //      tests of levels r - 1 .. r + 1 look them up after the next barrier)
-    //      and smooth at them (warp per hotspot)
+    // ---- phase 2: hash this level's hotspots (thread per hotspot, starting
+    //      with the last warp, which smooths the fewest; the peak tests of
+    //      levels r - 1 .. r + 1 look them up after the next barrier) and
+    //      smooth at them (warp per hotspot)
     const int nhot = s_nhot[lst];
     {
       unsigned own = 0;
-      for (int k = tid; k < nhot; k += SP_THREADS) {
+      const int ht = (tid + 32) % SP_THREADS;  // the last warp's lanes take hotspots 0 .. 31
+      for (int k = ht; k < nhot; k += SP_THREADS) {
         const uint32_t key = sCoord[lst * SP_HOT + k];
         uint32_t hh = sp_hash(key);
         for (int p = 0; p < SP_HASH; ++p) {
