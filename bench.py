@@ -277,9 +277,13 @@ def run_ours(args):
         # K4: one increment per vote plus one multiply-add per smoothing-window tap at each hotspot
         k4_ops = stats.votes + stats.smooth_macs
         int_peak = 152 * 64 * sm_mhz * 1e6 / 1e9  # Gop/s: INT32 multiply-add issue rate, 64 lanes/SM/clk
+        # a capture belongs to the kernel's source file and the shared headers it includes
         src_hash = {}
         for f in ("k_stencil.cu", "k_vote.cu"):
-            src_hash[f] = hashlib.sha1(open(os.path.join(ROOT, "paper_1310_1371_gb300", "csrc", f), "rb").read()).hexdigest()[:12]
+            h = hashlib.sha1()
+            for part in (f, "rd_internal.cuh", "rd_cert.cuh"):
+                h.update(open(os.path.join(ROOT, "paper_1310_1371_gb300", "csrc", part), "rb").read())
+            src_hash[f] = h.hexdigest()[:12]
         traffic_db = {}
         tfile = os.path.join(ROOT, "profiles", "dram_traffic.json")
         if os.path.exists(tfile):

@@ -92,8 +92,8 @@ static __device__ __noinline__ bool ridge_exact_nb(const double* kn, double X, d
 // exceeds the spread (max - min) of the corners of the cells it crosses, so
 // between the two samples it moves by at most 2 eX times the spread of the
 // corner set; the corner errors and the interpolation's rounding are bounded
-// over the same set.  A box that reaches an image border stays undecided (the
-// definition clamps corners there).
+// over the same set.  On the image's border rows and columns a box that
+// reaches the border stays undecided (the exact sample may lie outside).
 __device__ __forceinline__ int ridge_fast(const float* sK, const float* sE, int stride, int hy, int hx, int gx, int gy,
                                           int H, int W, float k, float ek, float tau, float X, float Y, float eX) {
   int verdict = 1;
@@ -102,7 +102,12 @@ __device__ __forceinline__ int ridge_fast(const float* sK, const float* sE, int 
     float lowx = (float)(-gx), highx = (float)(W - 1 - gx);
     float lowy = (float)(-gy), highy = (float)(H - 1 - gy);
     if (ox < lowx - eX || ox > highx + eX || oy < lowy - eX || oy > highy + eX) return 0;
-    if (eX > 0.0f && (ox <= lowx + eX || ox >= highx - eX || oy <= lowy + eX || oy >= highy - eX)) return 2;
+    // Off the border rows and columns the exact sample is inside the image
+    // (|X-| <= 1 component-wise), so only there can a box near a border hide
+    // a sample outside it.
+    const bool bx = gx == 0 || gx == W - 1, by = gy == 0 || gy == H - 1;
+    if (eX > 0.0f && ((bx && (ox <= lowx + eX || ox >= highx - eX)) || (by && (oy <= lowy + eX || oy >= highy - eX))))
+      return 2;
     float flx = floorf(ox), fly = floorf(oy);
     float fx = ox - flx, fy = oy - fly;
     int cx0 = gx + (int)flx, cy0 = gy + (int)fly;

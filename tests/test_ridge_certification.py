@@ -198,7 +198,9 @@ def ridge_fast(k, sE, gy, gx, o, H, W, kc, ec, X, Y, eX, contract):
         lowx, highx = (-gx).astype(np.float32), (W - 1 - gx).astype(np.float32)
         lowy, highy = (-gy).astype(np.float32), (H - 1 - gy).astype(np.float32)
         out = (ox < lowx - eX) | (ox > highx + eX) | (oy < lowy - eX) | (oy > highy + eX)
-        near = (eX > 0) & ((ox <= lowx + eX) | (ox >= highx - eX) | (oy <= lowy + eX) | (oy >= highy - eX))
+        bx = (gx == 0) | (gx == W - 1)
+        by = (gy == 0) | (gy == H - 1)
+        near = (eX > 0) & ((bx & ((ox <= lowx + eX) | (ox >= highx - eX))) | (by & ((oy <= lowy + eX) | (oy >= highy - eX))))
         go = ~out & ~near & ~final0 & ~undecided          # the kernel returns at the first 0 or border 2
         final0 |= out & ~undecided
         undecided |= ~out & near & ~final0
