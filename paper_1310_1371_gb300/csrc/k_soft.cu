@@ -368,6 +368,15 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 
 constexpr int SOFT_MAX_TILES = 256;  // tiles a ring visits through the tile index
 
+// exp(x) for the score's Gaussian factors (x <= 0) in FP32: expf is within
+// 2 ulp (relative 2.4e-7) and rounding x to FP32 moves it by at most
+// 2^-24 |x|, so a factor with |x| <= 40.5 errs by under 3e-6 of itself;
+// smaller factors (below e^-40.5) change a score by less than 1e-12 of its
+// value whatever their error.  A score, a sum of positive factors, thus errs
+// by under 3e-6 of its value.  The GB300's FP32 exponential runs at many
+// times the rate of its FP64 one.
+__device__ __forceinline__ double score_exp(double x) { return (double)expf((float)x); }
+
 __global__ void __launch_bounds__(256) k_soft_score(SoftArgs a) {
   __shared__ double red[8];
   __shared__ int s_off[SOFT_MAX_TILES], s_pre[SOFT_MAX_TILES + 1];
@@ -440,7 +449,7 @@ __global__ void __launch_bounds__(256) k_soft_score(SoftArgs a) {
       const double dist = sqrt(ddx * ddx + ddy * ddy);
       const double e = dist - rho;
       if (!(fabs(e) <= 9.0 * sa)) continue;
-      const double A = exp(-(e * e) / (2.0 * sa2));
+      const double A = score_exp(-(e * e) / (2.0 * sa2));
       double tp = 0.0, tcx = 0.0, tcy = 0.0, tsig = 0.0, trho = 0.0;
       double gk = 0.0, gX = 0.0, gY = 0.0;
       for (int s = -1; s <= 1; s += 2) {
@@ -456,7 +465,7 @@ __global__ void __launch_bounds__(256) k_soft_score(SoftArgs a) {
             const double wx = ox ? fx : 1.0 - fx, wy = oy ? fy : 1.0 - fy;
             const double dxq = qx - cx, dyq = qy - cy;
             const double d2 = dxq * dxq + dyq * dyq;
-            const double G = exp(-d2 / den);
+            const double G = score_exp(-d2 / den);
             const double mwG = m * wx * wy * G;
             tp += mwG;
             tcx += mwG * dxq;          // x 1/sig^2 below
