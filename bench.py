@@ -601,7 +601,7 @@ SERVE_METRIC = "p50/p99 latency and frames/s, Poisson stream of single-frame req
 SERVE_SIZES = (256, 512, 1024, 2048)
 
 
-def measure_serve(n, rate, pool, pool_per_class, budget_gb):
+def measure_serve(n, rate, pool, pool_per_class, budget_gb, slots=2):
     """A Poisson stream of n single-frame requests at `rate`/s (sizes uniform
     over 256^2 .. 2048^2, u16, 10-400 rings) through the continuous-batching
     server; latency from submission to results on the host.  `pool` holds
@@ -611,7 +611,7 @@ def measure_serve(n, rate, pool, pool_per_class, budget_gb):
     import torch
     sizes = SERVE_SIZES
     batch = {256: 16, 512: 8, 1024: 4, 2048: 2}
-    classes = [dict(params=synth.SERVE_CLASSES[s], H=s, W=s, dtype="u16", max_batch=batch[s], slots=2) for s in sizes]
+    classes = [dict(params=synth.SERVE_CLASSES[s], H=s, W=s, dtype="u16", max_batch=batch[s], slots=slots) for s in sizes]
     server = rd.Server(classes, mem_budget=int(budget_gb * 2**30), queue_cap=8192)
     for c, s in enumerate(sizes):  # warm-up: one request per class
         server.submit(c, pool[s][0], -1 - c)
@@ -659,7 +659,7 @@ def measure_serve(n, rate, pool, pool_per_class, budget_gb):
             "p99_ms": float(np.percentile(ms, 99)), "frames_per_s": n / wall, "wall_s": wall, "per_class": per,
             "batches": stats["batches"] - len(sizes), "device_bytes": stats["device_bytes"],
             "errors": int((status != 0).sum()), "submit_retries_busy": busy, "max_batch": batch,
-            "slots_per_class": 2, "mem_budget_gb": budget_gb, "frames_per_class_pool": pool_per_class,
+            "slots_per_class": slots, "mem_budget_gb": budget_gb, "frames_per_class_pool": pool_per_class,
             "clocks": clocks}
 
 
@@ -670,14 +670,15 @@ def run_serve(args):
     import torch
     torch.cuda.set_device(0)
     n, rate = args.serve_requests, args.serve_rate
-    v = measure_serve(n, rate, pool, args.serve_pool, args.serve_budget_gb)
+    v = measure_serve(n, rate, pool, args.serve_pool, args.serve_budget_gb, args.serve_slots)
     line = {"metric": SERVE_METRIC, "value": v["p99_ms"], "unit": "ms (p99 latency)",
             "higher_is_better": False, "n_gpus": 1, "steps": n, "warmup": len(SERVE_SIZES),
             "ms_per_step": v["wall_s"] * 1e3 / n, "scaling": "weak", "vs_baseline": None, "dtype": "u16",
             "data": "synthetic",
             "config": {"workload": f"serve: {n} requests, Poisson {rate}/s, sizes uniform over 256..2048 squared, "
                                    f"10-400 rings, r ranges 5-20 / 5-40 / 8-96 / 8-160",
-                       "frames_per_class_pool": args.serve_pool, "max_batch": v["max_batch"], "slots_per_class": 2,
+                       "frames_per_class_pool": args.serve_pool, "max_batch": v["max_batch"],
+                       "slots_per_class": args.serve_slots,
                        "mem_budget_gb": args.serve_budget_gb},
             "p50_ms": v["p50_ms"], "p99_ms": v["p99_ms"], "frames_per_s": v["frames_per_s"], "offered_per_s": rate,
             "per_class": v["per_class"], "batches": v["batches"], "device_bytes": v["device_bytes"],
@@ -853,6 +854,7 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=500.0)
     ap.add_argument("--serve-pool", type=int, default=8)
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
+    ap.add_argument("--serve-slots", type=int, default=2, help="server slots (context, stream, staging) per size class")
     ap.add_argument("--diff-frames", type=int, default=256)
     ap.add_argument("--video-frames", type=int, default=2000)
     ap.add_argument("--video-batch", type=int, default=2000,
