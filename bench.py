@@ -330,6 +330,13 @@ def run_ours(args):
                    "measured_peaks": probe}
         k4_atom["frac"] = k4_atom["achieved"] / atom_peak
         k4_atom["frac_of_vote_stream_peak"] = k4_atom["achieved"] / probe[rd.PROBE_PATTERNS[2]]
+        k4_instr = counter_for("vote_accumulate_peaks", "k_vote.cu", "thread_instructions_per_frame")
+        k4_atom["issue"] = None if k4_instr is None else {
+            "achieved": k4_instr / (per_launch[3] / 1e3) / 1e9, "peak": issue_peak, "unit": "G thread-instr/s",
+            "frac": k4_instr / (per_launch[3] / 1e3) / 1e9 / issue_peak,
+            "instructions_per_vote": k4_instr / max(1.0, float(stats.votes)),
+            "source": "ncu smsp__thread_inst_executed.sum of the current kernel source (profiles/dram_traffic.json)",
+            "peak_source": f"152 SMs x 4 schedulers x 32 lanes x {sm_mhz:.0f} MHz"}
         if dom == 0:
             roofline, other = k1, k4_atom
         else:
